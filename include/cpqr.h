@@ -1,0 +1,182 @@
+/*
+ * cpqr.h - C ABI of the GB300 (sm_103a) CP-ALS-QR library.
+ *
+ * Method: CP-ALS-QR (Alg. 2) with the restructured dimension tree (Section
+ * 3.1) and the customised extrapolation on Q0 (eq. 19, Alg. 3), i.e. the
+ * ALS-QR-BRE algorithm.  A dense N-way tensor X (C order: last index fastest)
+ * is approximated by [[lambda; A^(1), ..., A^(N)]] of rank R.
+ *
+ * Conventions for every entry point below:
+ *  - Matrices are row-major.  A factor A^(n) is I_n x R with element (i, r)
+ *    at [i * R + r]; an R x R triangle likewise.
+ *  - "device" pointers must come from cudaMalloc / a CUDA caching allocator on
+ *    the current device; "host" pointers are ordinary host memory.
+ *  - All GPU work is issued on the cudaStream_t given at init (passed as
+ *    void*; NULL = legacy default stream).  Calls that return host results
+ *    synchronise that stream before returning.
+ *  - No entry point aborts or exits.  Errors are returned as cpqr_status and
+ *    are sticky in a context: after the first failure every later call on the
+ *    same context returns the same status.  cp_als_qr_strerror() names them.
+ *  - The library owns all of its workspaces; the caller owns X and every
+ *    buffer it passes.  X is borrowed read-only and must outlive the context.
+ *  - Limits: 3 <= N <= 5, 1 <= R <= 32, R <= I_n for every n (compact QR of
+ *    each factor), prod(I_n) < 2^40.
+ */
+#ifndef CPQR_H
+#define CPQR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cpqr_ctx cpqr_ctx; /* opaque, owned by the library */
+
+typedef enum {
+  CPQR_OK = 0,
+  CPQR_EINVAL = 1,      /* bad argument (sizes, pointers, enum values) */
+  CPQR_ENOMEM = 2,      /* device allocation failed */
+  CPQR_ECUDA = 3,       /* a CUDA call failed (launch, copy, device fault) */
+  CPQR_ESINGULAR = 4,   /* a column norm lambda_r or a diagonal of R0 became 0 */
+  CPQR_ENONFINITE = 5,  /* NaN or Inf in the fit */
+  CPQR_ETIMEOUT = 6,    /* a bounded device wait gave up */
+  CPQR_ENOTCONV = 7,    /* cp_als_qr_fit hit max_sweeps before tol */
+  CPQR_EUNSUPPORTED = 8 /* valid request this build does not implement */
+} cpqr_status;
+
+/* TTM schedule of line 6 of Alg. 3 (Section 3.1; costs in Tables 1-6). */
+typedef enum {
+  CPQR_TREE_NONE = 0,        /* every mode update contracts X directly */
+  CPQR_TREE_STANDARD = 1,    /* dimension tree, 2 full-tensor TTMs per sweep */
+  CPQR_TREE_RESTRUCTURED = 2 /* restructured tree, 1 full TTM per sweep after the first */
+} cpqr_tree;
+
+/* Arithmetic of the TTM chains.  Z_n = Q0 R0, the R0^{-T} solve and the
+ * factor QRs are FP64 in both modes. */
+typedef enum {
+  CPQR_PREC_FP64 = 0,      /* every TTM in FP64 (X promoted exactly) */
+  CPQR_PREC_SPLIT_BF16 = 1 /* full-tensor TTMs on tcgen05 tensor cores with X and Q split
+                              into bf16 hi + lo (hi*hi + hi*lo + lo*hi, FP32 accumulate);
+                              deeper TTMs in FP32; V = Y_(n) Q0 with FP64 accumulation */
+} cpqr_prec;
+
+/* Extrapolation on Q0 (eq. 19). */
+typedef enum {
+  CPQR_EXTRAP_NONE = 0,   /* beta = 0: ALS-QR-BR */
+  CPQR_EXTRAP_PAPER = 1,  /* Section 4.2 rule: alpha = 1/10, beta chosen by fit level once
+                             |fit_k - fit_{k-1}| < 0.03, then fixed */
+  CPQR_EXTRAP_FIXED = 2,  /* beta = beta_fixed from the second sweep on */
+  CPQR_EXTRAP_LEARNED = 3 /* beta proposed by the learned model; the Section 4.2 rule is the
+                             fallback and judges every proposal by the fit it reaches */
+} cpqr_extrap;
+
+typedef struct {
+  int32_t tree;       /* cpqr_tree */
+  int32_t prec;       /* cpqr_prec */
+  int32_t extrap;     /* cpqr_extrap */
+  int32_t reserved0;
+  double alpha;       /* eq. 19 alpha; <= 0 selects 1/10 */
+  double beta_fixed;  /* beta for CPQR_EXTRAP_FIXED */
+  uint64_t seed;      /* seed of the N(0,1) starting factors when A0 is NULL */
+  const float* mlp_weights; /* host, CPQR_MLP_NPARAMS floats, for CPQR_EXTRAP_LEARNED (NULL =
+                               the rule alone) */
+} cpqr_options;
+
+/* Per-context counters. */
+typedef struct {
+  int64_t sweeps;          /* sweeps done */
+  int64_t ttm_flops;       /* 2 * R * prod(source dims) summed over every TTM issued */
+  int64_t full_ttms;       /* TTMs that read all of X */
+  double last_fit;         /* fit after the last sweep */
+  double beta;             /* beta used by the last sweep */
+  int64_t proposals;       /* learned proposals evaluated */
+  int64_t accepted;        /* learned proposals accepted by the judge */
+} cpqr_stats;
+
+/* Fill *opt with the defaults: restructured tree, FP64, paper extrapolation,
+ * alpha = 0.1, beta_fixed = 0, seed = 0, no learned model. */
+void cp_als_qr_default_options(cpqr_options* opt);
+
+/* Create a context for X (device, C order, dims[0..N-1], float32 if x_is_fp64 = 0 else
+ * float64) and rank R, and run Alg. 2's "Initialize": starting factors A0 (host array of
+ * N host pointers to I_n x R FP64 row-major; NULL draws N(0,1) from opt->seed), their QRs
+ * with positive diagonal, ||X||^2, and, for CPQR_PREC_SPLIT_BF16, the bf16 hi/lo split of X
+ * (one pass over X).  opt NULL = defaults.  stream: cudaStream_t or NULL.
+ * On failure *out is NULL and nothing is leaked. */
+cpqr_status cp_als_qr_init(cpqr_ctx** out, int32_t N, const int64_t* dims, int32_t R,
+                           const void* X_dev, int32_t x_is_fp64, const double* const* A0_host,
+                           const cpqr_options* opt, void* stream);
+
+/* Run nsweeps sweeps (outer iterations of Alg. 3: every mode updated once, TTMs per the
+ * schedule, customised extrapolation per the options).  fits_host (nsweeps doubles, may be
+ * NULL) receives the fit after each sweep, computed as in Section 4.1 from the last mode of
+ * the sweep: 1 - sqrt(max(||X||^2 - 2<V0, V^> + ||V^||^2, 0)) / ||X||. */
+cpqr_status cp_als_qr_sweep(cpqr_ctx* ctx, int32_t nsweeps, double* fits_host);
+
+/* Sweep until |fit_k - fit_{k-1}| < tol (the stopping test of Alg. 2/3, read as a change in
+ * fit) or max_sweeps; returns CPQR_ENOTCONV (not sticky) if max_sweeps was reached first.
+ * final_fit / sweeps_done may be NULL. */
+cpqr_status cp_als_qr_fit(cpqr_ctx* ctx, double tol, int32_t max_sweeps, double* final_fit,
+                          int32_t* sweeps_done);
+
+/* Copy factor n (I_n x R, unit columns) and, if lambda_host != NULL, the weights (R) to the
+ * host.  Q_host / R_host (may be NULL) receive Q_n (I_n x R) and R_n (R x R, upper, positive
+ * diagonal) of the current factor. */
+cpqr_status cp_als_qr_get(cpqr_ctx* ctx, int32_t n, double* A_host, double* lambda_host,
+                          double* Q_host, double* R_host);
+
+/* Counters since init. */
+cpqr_status cp_als_qr_stats(cpqr_ctx* ctx, cpqr_stats* out);
+
+/* Exact fit of the current model by one pass over X: 1 - ||X - [[lambda; A]]|| / ||X|| with
+ * every model entry and the residual sum in FP64.  Costs N*R flops per element of X. */
+cpqr_status cp_als_qr_fit_exact(cpqr_ctx* ctx, double* fit);
+
+/* Release every device allocation of ctx (NULL is ignored). */
+void cp_als_qr_destroy(cpqr_ctx* ctx);
+
+/* Static string for a status code. */
+const char* cp_als_qr_strerror(int32_t status);
+
+/* The TTM schedule the library runs (Section 3.1), host only, no GPU needed.  Writes up to
+ * cap operations of nsweeps sweeps as 4 int32 each into ops (may be NULL to count):
+ *   {0, dst, src, k}  TTM: node dst = node src x_k Q_k^T (node 0 is X, modes 0-based)
+ *   {1, n, leaf, 0}   mode-n update from node leaf
+ *   {2, id, 0, 0}     node id released
+ * *count = number of operations, *flops = sum of 2 * R * prod(source dims). */
+cpqr_status cp_als_qr_schedule(int32_t N, const int64_t* dims, int32_t R, int32_t tree,
+                               int32_t nsweeps, int32_t* ops, int64_t cap, int64_t* count,
+                               int64_t* flops);
+
+/* ---- Operation-level entry points (the steps of one mode update, on device buffers) ---- */
+
+/* Mode-k product out = T x_k Q^T (Section 2.1) of a dense C-order tensor T with dims
+ * tdims[0..nd-1] and Q (I_k x R, row-major, I_k = tdims[k]).  out has dims tdims with
+ * tdims[k] replaced by R.  dtype: 0 = FP64 T, Q, out; 1 = FP32 T, Q, out (FFMA, FP32
+ * accumulate); 2 = FP32 T, FP64 Q, FP64 out; 3 = split-bf16 tensor-core path: T FP32, Q FP64,
+ * out FP32 (tcgen05; T and Q are split into bf16 hi + lo internally).  stream: cudaStream_t. */
+cpqr_status cpqr_ttm(const void* T_dev, int32_t nd, const int64_t* tdims, int32_t k,
+                     const void* Q_dev, int32_t R, void* out_dev, int32_t dtype, void* stream);
+
+/* Compact QR of an M x R FP64 matrix (row-major, device) by Householder reflections with
+ * diag(R) > 0 (Alg. 2 line 10): Q_dev (M x R) and R_dev (R x R) receive the factors. */
+cpqr_status cpqr_house_qr(const double* A_dev, int64_t M, int32_t R, double* Q_dev,
+                          double* R_dev, void* stream);
+
+/* QR of Z = R_1 (.) ... (.) R_m, the Khatri-Rao product of m upper-triangular R x R
+ * matrices (Alg. 2 lines 3-4), rows (r_1, ..., r_m) with r_m fastest: Rs_dev holds the m
+ * triangles back to back (device, FP64).  Q0_dev (R^m x R) and R0_dev (R x R) receive the
+ * factors, diag(R0) > 0. */
+cpqr_status cpqr_krp_qr(const double* Rs_dev, int32_t m, int32_t R, double* Q0_dev,
+                        double* R0_dev, void* stream);
+
+/* Number of float parameters of the learned beta model (3 hidden layers of 128). */
+#define CPQR_MLP_FEATURES 40
+#define CPQR_MLP_HIDDEN 128
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CPQR_H */

@@ -581,11 +581,11 @@ def qr_update_direct(X: np.ndarray, A: Sequence[np.ndarray], n: int) -> np.ndarr
 
 
 def subspace_sine(A: np.ndarray, B: np.ndarray) -> float:
-    """Largest principal-angle sine between the column spaces of A and B."""
+    """Largest principal-angle sine between the column spaces of A and B,
+    ||(I - Qa Qa^T) Qb||_2, which (unlike sqrt(1 - cos^2)) resolves angles down to rounding."""
     qa, _ = np.linalg.qr(A)
     qb, _ = np.linalg.qr(B)
-    s = np.linalg.svd(qa.T @ qb, compute_uv=False)
-    return float(math.sqrt(max(0.0, 1.0 - float(np.min(s)) ** 2)))
+    return float(np.linalg.norm(qb - qa @ (qa.T @ qb), 2))
 
 
 def factor_match_score(A_true: Sequence[np.ndarray], A_est: Sequence[np.ndarray], lam_true=None, lam_est=None) -> float:

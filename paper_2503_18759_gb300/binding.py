@@ -1,0 +1,243 @@
+"""ctypes binding of libcpqr.so: the C ABI of include/cpqr.h with the same names.
+
+Argument marshalling only: every step of the decomposition runs in the CUDA
+library.  Device buffers are passed as integer addresses (e.g. a torch
+tensor's ``data_ptr()``), host buffers as numpy arrays.  A missing library or
+a non-OK status raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcpqr.so")
+
+TREE_NONE, TREE_STANDARD, TREE_RESTRUCTURED = 0, 1, 2
+PREC_FP64, PREC_SPLIT_BF16 = 0, 1
+EXTRAP_NONE, EXTRAP_PAPER, EXTRAP_FIXED, EXTRAP_LEARNED = 0, 1, 2, 3
+TTM_F64, TTM_F32, TTM_F32_IN_F64, TTM_SPLIT_BF16 = 0, 1, 2, 3
+
+OK, ENOTCONV = 0, 7
+
+
+class CpqrError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {cp_als_qr_strerror(status)} (status {status})")
+        self.status = status
+
+
+class Options(C.Structure):
+    _fields_ = [("tree", C.c_int32), ("prec", C.c_int32), ("extrap", C.c_int32), ("reserved0", C.c_int32),
+                ("alpha", C.c_double), ("beta_fixed", C.c_double), ("seed", C.c_uint64),
+                ("mlp_weights", C.POINTER(C.c_float))]
+
+
+class Stats(C.Structure):
+    _fields_ = [("sweeps", C.c_int64), ("ttm_flops", C.c_int64), ("full_ttms", C.c_int64),
+                ("last_fit", C.c_double), ("beta", C.c_double), ("proposals", C.c_int64),
+                ("accepted", C.c_int64)]
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libcpqr.so (built in-tree); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_2503_18759_gb300.build`")
+    L = C.CDLL(LIB_PATH)
+    vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    P = C.POINTER
+    L.cp_als_qr_default_options.argtypes = [P(Options)]
+    L.cp_als_qr_default_options.restype = None
+    L.cp_als_qr_init.argtypes = [P(vp), i32, P(i64), i32, vp, i32, P(P(dbl)), P(Options), vp]
+    L.cp_als_qr_sweep.argtypes = [vp, i32, P(dbl)]
+    L.cp_als_qr_fit.argtypes = [vp, dbl, i32, P(dbl), P(i32)]
+    L.cp_als_qr_get.argtypes = [vp, i32, P(dbl), P(dbl), P(dbl), P(dbl)]
+    L.cp_als_qr_stats.argtypes = [vp, P(Stats)]
+    L.cp_als_qr_fit_exact.argtypes = [vp, P(dbl)]
+    L.cp_als_qr_destroy.argtypes = [vp]
+    L.cp_als_qr_destroy.restype = None
+    L.cp_als_qr_strerror.argtypes = [i32]
+    L.cp_als_qr_strerror.restype = C.c_char_p
+    L.cp_als_qr_schedule.argtypes = [i32, P(i64), i32, i32, i32, P(i32), i64, P(i64), P(i64)]
+    L.cpqr_ttm.argtypes = [vp, i32, P(i64), i32, vp, i32, vp, i32, vp]
+    L.cpqr_house_qr.argtypes = [vp, i64, i32, vp, vp, vp]
+    L.cpqr_krp_qr.argtypes = [vp, i32, i32, vp, vp, vp]
+    for name in ("cp_als_qr_init", "cp_als_qr_sweep", "cp_als_qr_fit", "cp_als_qr_get", "cp_als_qr_stats",
+                 "cp_als_qr_fit_exact", "cp_als_qr_schedule", "cpqr_ttm", "cpqr_house_qr", "cpqr_krp_qr"):
+        getattr(L, name).restype = i32
+    _lib = L
+    return L
+
+
+def _check(status: int, where: str, allow=(OK,)) -> int:
+    if status not in allow:
+        raise CpqrError(status, where)
+    return status
+
+
+def _i64(seq) -> C.Array:
+    return (C.c_int64 * len(seq))(*[int(v) for v in seq])
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def cp_als_qr_strerror(status: int) -> str:
+    return lib().cp_als_qr_strerror(int(status)).decode()
+
+
+def cp_als_qr_default_options() -> Options:
+    o = Options()
+    lib().cp_als_qr_default_options(C.byref(o))
+    return o
+
+
+def make_options(tree=TREE_RESTRUCTURED, prec=PREC_FP64, extrap=EXTRAP_PAPER, alpha=0.1, beta_fixed=0.0,
+                 seed=0, mlp_weights: Optional[np.ndarray] = None) -> Options:
+    o = cp_als_qr_default_options()
+    o.tree, o.prec, o.extrap = int(tree), int(prec), int(extrap)
+    o.alpha, o.beta_fixed, o.seed = float(alpha), float(beta_fixed), int(seed)
+    if mlp_weights is not None:
+        w = np.ascontiguousarray(mlp_weights, dtype=np.float32)
+        o._keep = w  # keep alive while the struct is used
+        o.mlp_weights = w.ctypes.data_as(C.POINTER(C.c_float))
+    return o
+
+
+def cp_als_qr_init(dims: Sequence[int], R: int, X_dev: int, x_is_fp64: bool,
+                   A0: Optional[Sequence[np.ndarray]] = None, options: Optional[Options] = None,
+                   stream: int = 0) -> C.c_void_p:
+    ctx = C.c_void_p()
+    N = len(dims)
+    a0 = None
+    keep = []
+    if A0 is not None:
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in A0]
+        keep = arrs
+        a0 = (C.POINTER(C.c_double) * N)(*[_dptr(a) for a in arrs])
+    st = lib().cp_als_qr_init(C.byref(ctx), N, _i64(dims), int(R), C.c_void_p(int(X_dev)), int(bool(x_is_fp64)),
+                              a0, C.byref(options) if options is not None else None, C.c_void_p(int(stream)))
+    del keep
+    _check(st, "cp_als_qr_init")
+    return ctx
+
+
+def cp_als_qr_sweep(ctx, nsweeps: int) -> np.ndarray:
+    fits = np.zeros(max(int(nsweeps), 1))
+    _check(lib().cp_als_qr_sweep(ctx, int(nsweeps), _dptr(fits)), "cp_als_qr_sweep")
+    return fits[:nsweeps]
+
+
+def cp_als_qr_fit(ctx, tol: float, max_sweeps: int) -> Tuple[bool, float, int]:
+    f = C.c_double()
+    n = C.c_int32()
+    st = _check(lib().cp_als_qr_fit(ctx, float(tol), int(max_sweeps), C.byref(f), C.byref(n)), "cp_als_qr_fit",
+                allow=(OK, ENOTCONV))
+    return st == OK, f.value, n.value
+
+
+def cp_als_qr_get(ctx, n: int, I: int, R: int):
+    A = np.zeros((I, R))
+    lam = np.zeros(R)
+    Q = np.zeros((I, R))
+    Rn = np.zeros((R, R))
+    _check(lib().cp_als_qr_get(ctx, int(n), _dptr(A), _dptr(lam), _dptr(Q), _dptr(Rn)), "cp_als_qr_get")
+    return A, lam, Q, Rn
+
+
+def cp_als_qr_stats(ctx) -> Stats:
+    s = Stats()
+    _check(lib().cp_als_qr_stats(ctx, C.byref(s)), "cp_als_qr_stats")
+    return s
+
+
+def cp_als_qr_fit_exact(ctx) -> float:
+    f = C.c_double()
+    _check(lib().cp_als_qr_fit_exact(ctx, C.byref(f)), "cp_als_qr_fit_exact")
+    return f.value
+
+
+def cp_als_qr_destroy(ctx) -> None:
+    if ctx:
+        lib().cp_als_qr_destroy(ctx)
+
+
+def cp_als_qr_schedule(dims: Sequence[int], R: int, tree: int, nsweeps: int) -> Tuple[np.ndarray, int]:
+    cnt = C.c_int64()
+    fl = C.c_int64()
+    _check(lib().cp_als_qr_schedule(len(dims), _i64(dims), int(R), int(tree), int(nsweeps), None, 0,
+                                    C.byref(cnt), C.byref(fl)), "cp_als_qr_schedule")
+    ops = np.zeros((cnt.value, 4), dtype=np.int32)
+    _check(lib().cp_als_qr_schedule(len(dims), _i64(dims), int(R), int(tree), int(nsweeps),
+                                    ops.ctypes.data_as(C.POINTER(C.c_int32)), cnt.value, C.byref(cnt),
+                                    C.byref(fl)), "cp_als_qr_schedule")
+    return ops, fl.value
+
+
+def cpqr_ttm(T_dev: int, tdims: Sequence[int], k: int, Q_dev: int, R: int, out_dev: int, dtype: int,
+             stream: int = 0) -> None:
+    _check(lib().cpqr_ttm(C.c_void_p(int(T_dev)), len(tdims), _i64(tdims), int(k), C.c_void_p(int(Q_dev)), int(R),
+                          C.c_void_p(int(out_dev)), int(dtype), C.c_void_p(int(stream))), "cpqr_ttm")
+
+
+def cpqr_house_qr(A_dev: int, M: int, R: int, Q_dev: int, R_dev: int, stream: int = 0) -> None:
+    _check(lib().cpqr_house_qr(C.c_void_p(int(A_dev)), int(M), int(R), C.c_void_p(int(Q_dev)),
+                               C.c_void_p(int(R_dev)), C.c_void_p(int(stream))), "cpqr_house_qr")
+
+
+def cpqr_krp_qr(Rs_dev: int, m: int, R: int, Q0_dev: int, R0_dev: int, stream: int = 0) -> None:
+    _check(lib().cpqr_krp_qr(C.c_void_p(int(Rs_dev)), int(m), int(R), C.c_void_p(int(Q0_dev)),
+                             C.c_void_p(int(R0_dev)), C.c_void_p(int(stream))), "cpqr_krp_qr")
+
+
+class Decomposition:
+    """Owns one context; X must stay alive (device memory) while it exists."""
+
+    def __init__(self, dims, R, X_dev: int, x_is_fp64: bool, A0=None, options: Optional[Options] = None,
+                 stream: int = 0):
+        self.dims = [int(d) for d in dims]
+        self.R = int(R)
+        self.ctx = cp_als_qr_init(self.dims, self.R, X_dev, x_is_fp64, A0, options, stream)
+
+    def sweep(self, n: int = 1) -> np.ndarray:
+        return cp_als_qr_sweep(self.ctx, n)
+
+    def fit(self, tol: float, max_sweeps: int):
+        return cp_als_qr_fit(self.ctx, tol, max_sweeps)
+
+    def factors(self):
+        out = [cp_als_qr_get(self.ctx, n, I, self.R) for n, I in enumerate(self.dims)]
+        return [o[0] for o in out], out[-1][1], [o[2] for o in out], [o[3] for o in out]
+
+    def stats(self) -> Stats:
+        return cp_als_qr_stats(self.ctx)
+
+    def fit_exact(self) -> float:
+        return cp_als_qr_fit_exact(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            cp_als_qr_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

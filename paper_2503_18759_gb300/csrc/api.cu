@@ -1,0 +1,693 @@
+// C ABI of the CP-ALS-QR library: context, sweep driver (Alg. 3 with the
+// schedules of Section 3.1) and the operation-level entry points.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <new>
+#include <stdexcept>
+#include <vector>
+
+#include "../../include/cpqr.h"
+#include "common.cuh"
+#include "schedule.h"
+
+using namespace cpqr;
+
+namespace {
+
+// Section 4.2: alpha = 1/10; beta picked by fit level once the change in fit drops below 0.03.
+constexpr double kAlphaDefault = 0.1;
+constexpr double kActivateDfit = 0.03;
+double beta_band(double fit) {
+  if (fit > 0.95) return 1.0 / 20000.0;
+  if (fit > 0.90) return 1.0 / 2000.0;
+  if (fit > 0.70) return 1.0 / 500.0;
+  return 1.0 / 250.0;
+}
+
+struct DeviceBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+// Caching pool for tree nodes: blocks are kept by size and reused.
+class Pool {
+ public:
+  ~Pool() { release(); }
+  cudaError_t get(size_t bytes, void** out) {
+    auto it = free_.find(bytes);
+    if (it != free_.end()) {
+      *out = it->second;
+      free_.erase(it);
+      return cudaSuccess;
+    }
+    cudaError_t e = cudaMalloc(out, bytes);
+    if (e == cudaSuccess) all_.push_back(*out);
+    return e;
+  }
+  void put(size_t bytes, void* p) { free_.emplace(bytes, p); }
+  void release() {
+    for (void* p : all_) cudaFree(p);
+    all_.clear();
+    free_.clear();
+  }
+
+ private:
+  std::multimap<size_t, void*> free_;
+  std::vector<void*> all_;
+};
+
+struct NodeBuf {
+  void* p;
+  size_t bytes;
+  uint32_t free_mask;
+  bool is_x;
+};
+
+uint64_t splitmix64(uint64_t& s) {
+  uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+}  // namespace
+
+struct cpqr_ctx {
+  int N = 0, R = 0;
+  std::vector<int64_t> dims;
+  int tree = 2, prec = 0, extrap = 1;
+  double alpha = kAlphaDefault, beta_fixed = 0.0;
+  cudaStream_t st = nullptr;
+  const void* X = nullptr;
+  bool x64 = false;
+  int64_t nX = 0;
+  cpqr_status err = CPQR_OK;
+
+  std::vector<void*> owned;  // cudaMalloc'd, freed at destroy
+  double* A[CPQR_MAXN] = {};
+  double* Q[CPQR_MAXN] = {};
+  double* Rf[CPQR_MAXN] = {};
+  float* Qf[CPQR_MAXN] = {};
+  double* Q0prev[CPQR_MAXN] = {};
+  bool has_prev[CPQR_MAXN] = {};
+  __nv_bfloat16* Qt[CPQR_MAXN] = {};
+  int Rp = 0;
+  int64_t Kp[CPQR_MAXN] = {};
+  __nv_bfloat16 *Xhi = nullptr, *Xlo = nullptr;
+  double* lambda = nullptr;
+  double* Q0 = nullptr;
+  double* R0 = nullptr;
+  double* V = nullptr;
+  double* qr_work = nullptr;
+  double* fit_terms = nullptr;
+  double* d_scalar = nullptr;
+  unsigned int* dstatus = nullptr;
+  double* h_pinned = nullptr;  // 4 doubles: fit terms, status
+  int32_t* d_perm = nullptr;
+  ZPlan zplan{};
+
+  std::unique_ptr<Schedule> sched;
+  std::vector<Op> ops;
+  std::map<int, NodeBuf> nodes;
+  Pool pool;
+
+  double normX2 = 0.0;
+  std::vector<double> fits;
+  double beta_active = 0.0;
+  bool activated = false;
+  double last_beta = 0.0;
+  int64_t sweeps = 0;
+  int64_t proposals = 0, accepted = 0;
+
+  ~cpqr_ctx() {
+    if (st) cudaStreamSynchronize(st);
+    pool.release();
+    for (void* p : owned) cudaFree(p);
+    if (h_pinned) cudaFreeHost(h_pinned);
+  }
+
+  template <typename T>
+  cudaError_t alloc(T** p, size_t count) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+    if (e == cudaSuccess) {
+      owned.push_back(q);
+      *p = static_cast<T*>(q);
+    }
+    return e;
+  }
+};
+
+#define CK(...)                                                           \
+  do {                                                                    \
+    cudaError_t e_ = (__VA_ARGS__);                                            \
+    if (e_ != cudaSuccess) {                                              \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? CPQR_ENOMEM : CPQR_ECUDA); \
+    }                                                                     \
+  } while (0)
+
+namespace {
+
+cpqr_status fail(cpqr_ctx* ctx, cpqr_status s) {
+  if (ctx && ctx->err == CPQR_OK) ctx->err = s;
+  return s;
+}
+
+int64_t ipow(int64_t b, int e) {
+  int64_t r = 1;
+  for (int i = 0; i < e; ++i) r *= b;
+  return r;
+}
+
+// Khatri-Rao row order for the staircase QR: rows sorted by their largest digit.
+std::vector<int32_t> krp_perm(int m, int R) {
+  int64_t M = ipow(R, m);
+  std::vector<std::vector<int32_t>> buckets(R);
+  for (int64_t idx = 0; idx < M; ++idx) {
+    int64_t x = idx;
+    int mx = 0;
+    for (int k = 0; k < m; ++k) {
+      mx = std::max<int>(mx, (int)(x % R));
+      x /= R;
+    }
+    buckets[mx].push_back((int32_t)idx);
+  }
+  std::vector<int32_t> perm;
+  perm.reserve(M);
+  for (auto& b : buckets) perm.insert(perm.end(), b.begin(), b.end());
+  return perm;
+}
+
+std::vector<int64_t> node_dims(const cpqr_ctx* ctx, uint32_t mask) {
+  std::vector<int64_t> d(ctx->N);
+  for (int k = 0; k < ctx->N; ++k) d[k] = (mask & (1u << k)) ? ctx->dims[k] : ctx->R;
+  return d;
+}
+
+size_t elem_size_of_nodes(const cpqr_ctx* ctx) { return ctx->prec == CPQR_PREC_FP64 ? 8 : 4; }
+
+cpqr_status run_ttm(cpqr_ctx* ctx, const Op& op) {
+  const int dst = op.a, src = op.b, k = op.c;
+  auto it = ctx->nodes.find(src);
+  if (it == ctx->nodes.end()) return fail(ctx, CPQR_EINVAL);
+  const NodeBuf sb = it->second;
+  std::vector<int64_t> d = node_dims(ctx, sb.free_mask);
+  int64_t P = 1, S = 1;
+  for (int j = 0; j < k; ++j) P *= d[j];
+  for (int j = k + 1; j < ctx->N; ++j) S *= d[j];
+  const int64_t K = d[k];
+  const int R = ctx->R;
+  const size_t es = elem_size_of_nodes(ctx);
+  const size_t bytes = (size_t)(P * R * S) * es;
+  void* out = nullptr;
+  CK(ctx->pool.get(bytes, &out));
+  cudaStream_t st = ctx->st;
+  if (ctx->prec == CPQR_PREC_FP64) {
+    if (sb.is_x && !ctx->x64)
+      CK(launch_ttm<float, double, double>((const float*)sb.p, ctx->Q[k], (double*)out, P, K, S, R, st));
+    else
+      CK(launch_ttm<double, double, double>((const double*)sb.p, ctx->Q[k], (double*)out, P, K, S, R, st));
+  } else {
+    if (sb.is_x && ttm_tc_supported(P, K, S, R)) {
+      CK(launch_ttm_tc(ctx->Xhi, ctx->Xlo, ctx->Qt[k], ctx->Rp, ctx->Kp[k], (float*)out, P, K, S, R,
+                       ctx->dstatus, st));
+    } else {
+      CK(launch_ttm<float, float, float>((const float*)sb.p, ctx->Qf[k], (float*)out, P, K, S, R, st));
+    }
+  }
+  ctx->nodes[dst] = NodeBuf{out, bytes, sb.free_mask & ~(1u << k), false};
+  return CPQR_OK;
+}
+
+void free_node(cpqr_ctx* ctx, int id) {
+  auto it = ctx->nodes.find(id);
+  if (it == ctx->nodes.end() || it->second.is_x) return;
+  ctx->pool.put(it->second.bytes, it->second.p);
+  ctx->nodes.erase(it);
+}
+
+cpqr_status stage_q(cpqr_ctx* ctx, int n) {
+  if (ctx->prec != CPQR_PREC_SPLIT_BF16) return CPQR_OK;
+  CK(launch_split_q(ctx->Q[n], ctx->dims[n], ctx->R, ctx->Qt[n], ctx->Rp, ctx->Kp[n], ctx->st));
+  return CPQR_OK;
+}
+
+cpqr_status run_update(cpqr_ctx* ctx, int n, int leaf, double beta) {
+  auto it = ctx->nodes.find(leaf);
+  if (it == ctx->nodes.end()) return fail(ctx, CPQR_EINVAL);
+  const NodeBuf lb = it->second;
+  const int N = ctx->N, R = ctx->R;
+  cudaStream_t st = ctx->st;
+  // Alg. 3 lines 3-4: QR of the Khatri-Rao product of the other triangles.
+  TriPtrs tri{};
+  int m = 0;
+  for (int k = 0; k < N; ++k)
+    if (k != n) tri.p[m++] = ctx->Rf[k];
+  CK(launch_krp_qr(ctx->zplan, tri, ctx->Q0, ctx->R0, ctx->qr_work, ctx->dstatus, st));
+  // Lines 5 and 7: V = Y_(n) [Q0 | Q0^{k-1}].
+  int64_t P = ipow(R, n), S = ipow(R, N - 1 - n);
+  const int64_t I = ctx->dims[n];
+  const bool ext = (beta != 0.0) && ctx->has_prev[n];
+  const int C = ext ? 2 * R : R;
+  if (ctx->prec == CPQR_PREC_FP64)
+    CK(launch_leaf_v<double>((const double*)lb.p, P, I, S, ctx->Q0, ctx->Q0prev[n], R, C, ctx->V, st));
+  else
+    CK(launch_leaf_v<float>((const float*)lb.p, P, I, S, ctx->Q0, ctx->Q0prev[n], R, C, ctx->V, st));
+  // Lines 8-10.
+  FinishOut fo{ctx->A[n], ctx->lambda, ctx->Q[n], ctx->Rf[n], ctx->Qf[n], ctx->fit_terms};
+  CK(launch_mode_finish(ctx->V, C, ctx->R0, ext ? beta : 0.0, ctx->alpha, I, R, fo, ctx->qr_work, ctx->dstatus,
+                        st));
+  cpqr_status s = stage_q(ctx, n);
+  if (s != CPQR_OK) return s;
+  std::swap(ctx->Q0, ctx->Q0prev[n]);
+  ctx->has_prev[n] = true;
+  return CPQR_OK;
+}
+
+cpqr_status read_fit(cpqr_ctx* ctx, double* fit) {
+  CK(cudaMemcpyAsync(ctx->h_pinned, ctx->fit_terms, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaMemcpyAsync(ctx->h_pinned + 2, ctx->dstatus, sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  unsigned int ds;
+  std::memcpy(&ds, ctx->h_pinned + 2, sizeof(ds));
+  if (ds & CPQR_DEV_TIMEOUT) return fail(ctx, CPQR_ETIMEOUT);
+  if (ds & CPQR_DEV_SINGULAR) return fail(ctx, CPQR_ESINGULAR);
+  double in = ctx->h_pinned[0], nn = ctx->h_pinned[1];
+  double r2 = ctx->normX2 - 2.0 * in + nn;
+  double f = 1.0 - std::sqrt(std::max(r2, 0.0)) / std::sqrt(ctx->normX2);
+  if (!std::isfinite(f)) return fail(ctx, CPQR_ENONFINITE);
+  *fit = f;
+  return CPQR_OK;
+}
+
+double beta_for_sweep(cpqr_ctx* ctx) {
+  switch (ctx->extrap) {
+    case CPQR_EXTRAP_NONE: return 0.0;
+    case CPQR_EXTRAP_FIXED: return ctx->sweeps >= 1 ? ctx->beta_fixed : 0.0;
+    default: return ctx->beta_active;
+  }
+}
+
+void observe_fit(cpqr_ctx* ctx, double fit) {
+  ctx->fits.push_back(fit);
+  size_t k = ctx->fits.size();
+  if (!ctx->activated && k >= 2 && std::fabs(ctx->fits[k - 1] - ctx->fits[k - 2]) < kActivateDfit) {
+    ctx->beta_active = beta_band(fit);
+    ctx->activated = true;
+  }
+}
+
+cpqr_status one_sweep(cpqr_ctx* ctx, double* fit_out) {
+  const double beta = beta_for_sweep(ctx);
+  ctx->ops.clear();
+  try {
+    ctx->sched->next_sweep(ctx->ops);
+  } catch (const std::exception&) {
+    return fail(ctx, CPQR_EINVAL);
+  }
+  for (const Op& op : ctx->ops) {
+    cpqr_status s = CPQR_OK;
+    if (op.kind == OP_TTM) s = run_ttm(ctx, op);
+    else if (op.kind == OP_UPDATE) s = run_update(ctx, op.a, op.b, beta);
+    else free_node(ctx, op.a);
+    if (s != CPQR_OK) return s;
+  }
+  double fit = 0.0;
+  cpqr_status s = read_fit(ctx, &fit);
+  if (s != CPQR_OK) return s;
+  ctx->last_beta = beta;
+  ++ctx->sweeps;
+  observe_fit(ctx, fit);
+  if (fit_out) *fit_out = fit;
+  return CPQR_OK;
+}
+
+bool valid_enum(int v, int lo, int hi) { return v >= lo && v <= hi; }
+
+}  // namespace
+
+extern "C" {
+
+void cp_als_qr_default_options(cpqr_options* opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->tree = CPQR_TREE_RESTRUCTURED;
+  opt->prec = CPQR_PREC_FP64;
+  opt->extrap = CPQR_EXTRAP_PAPER;
+  opt->alpha = kAlphaDefault;
+  opt->beta_fixed = 0.0;
+  opt->seed = 0;
+  opt->mlp_weights = nullptr;
+}
+
+const char* cp_als_qr_strerror(int32_t s) {
+  switch (s) {
+    case CPQR_OK: return "ok";
+    case CPQR_EINVAL: return "invalid argument";
+    case CPQR_ENOMEM: return "out of device memory";
+    case CPQR_ECUDA: return "CUDA error";
+    case CPQR_ESINGULAR: return "singular factor (zero column norm or zero R diagonal)";
+    case CPQR_ENONFINITE: return "non-finite fit";
+    case CPQR_ETIMEOUT: return "device wait timed out";
+    case CPQR_ENOTCONV: return "max_sweeps reached before tol";
+    case CPQR_EUNSUPPORTED: return "unsupported configuration";
+    default: return "unknown status";
+  }
+}
+
+cpqr_status cp_als_qr_init(cpqr_ctx** out, int32_t N, const int64_t* dims, int32_t R, const void* X_dev,
+                           int32_t x_is_fp64, const double* const* A0_host, const cpqr_options* opt_in,
+                           void* stream) {
+  if (!out) return CPQR_EINVAL;
+  *out = nullptr;
+  if (N < 3 || N > CPQR_MAXN || !dims || R < 1 || R > CPQR_MAXR || !X_dev) return CPQR_EINVAL;
+  cpqr_options opt;
+  if (opt_in) opt = *opt_in;
+  else cp_als_qr_default_options(&opt);
+  if (!valid_enum(opt.tree, 0, 2) || !valid_enum(opt.prec, 0, 1) || !valid_enum(opt.extrap, 0, 3))
+    return CPQR_EINVAL;
+  int64_t nX = 1;
+  for (int n = 0; n < N; ++n) {
+    if (dims[n] < R || dims[n] > (1 << 30)) return CPQR_EINVAL;
+    nX *= dims[n];
+    if (nX > (int64_t(1) << 40)) return CPQR_EINVAL;
+  }
+  if (opt.prec == CPQR_PREC_SPLIT_BF16 && x_is_fp64) return CPQR_EUNSUPPORTED;
+  if (ipow(R, N - 1) > (int64_t(1) << 30)) return CPQR_EINVAL;
+
+  std::unique_ptr<cpqr_ctx> c;
+  try {
+    c.reset(new cpqr_ctx());
+  } catch (...) {
+    return CPQR_ENOMEM;
+  }
+  cpqr_ctx* ctx = c.get();
+  ctx->N = N;
+  ctx->R = R;
+  ctx->dims.assign(dims, dims + N);
+  ctx->tree = opt.tree;
+  ctx->prec = opt.prec;
+  ctx->extrap = opt.extrap;
+  ctx->alpha = opt.alpha > 0 ? opt.alpha : kAlphaDefault;
+  ctx->beta_fixed = opt.beta_fixed;
+  ctx->st = (cudaStream_t)stream;
+  ctx->X = X_dev;
+  ctx->x64 = x_is_fp64 != 0;
+  ctx->nX = nX;
+  cudaStream_t st = ctx->st;
+
+  const int64_t M0 = ipow(R, N - 1);
+  int64_t Imax = 0;
+  for (int n = 0; n < N; ++n) Imax = std::max(Imax, dims[n]);
+  CK(cudaMallocHost(&ctx->h_pinned, 4 * sizeof(double)));
+  for (int n = 0; n < N; ++n) {
+    CK(ctx->alloc(&ctx->A[n], dims[n] * R));
+    CK(ctx->alloc(&ctx->Q[n], dims[n] * R));
+    CK(ctx->alloc(&ctx->Rf[n], (size_t)R * R));
+    CK(ctx->alloc(&ctx->Qf[n], dims[n] * R));
+    CK(ctx->alloc(&ctx->Q0prev[n], M0 * R));
+  }
+  CK(ctx->alloc(&ctx->lambda, R));
+  CK(ctx->alloc(&ctx->Q0, M0 * R));
+  CK(ctx->alloc(&ctx->R0, (size_t)R * R));
+  CK(ctx->alloc(&ctx->V, Imax * 2 * R));
+  CK(ctx->alloc(&ctx->qr_work, std::max<int64_t>(M0, Imax) * R));
+  CK(ctx->alloc(&ctx->fit_terms, 2));
+  CK(ctx->alloc(&ctx->d_scalar, 2));
+  CK(ctx->alloc(&ctx->dstatus, 1));
+  CK(cudaMemsetAsync(ctx->dstatus, 0, sizeof(unsigned int), st));
+  CK(cudaMemsetAsync(ctx->fit_terms, 0, 2 * sizeof(double), st));
+  CK(cudaMemsetAsync(ctx->lambda, 0, R * sizeof(double), st));
+
+  // Khatri-Rao row plan (identical for every mode: N-1 triangles of size R).
+  {
+    std::vector<int32_t> perm = krp_perm(N - 1, R);
+    CK(ctx->alloc(&ctx->d_perm, perm.size()));
+    CK(cudaMemcpyAsync(ctx->d_perm, perm.data(), perm.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    ctx->zplan.m = N - 1;
+    ctx->zplan.R = R;
+    ctx->zplan.M = M0;
+    ctx->zplan.perm = ctx->d_perm;
+    for (int j = 0; j < CPQR_MAXR; ++j) ctx->zplan.act[j] = (int32_t)std::min<int64_t>(M0, ipow(j + 1, N - 1));
+    CK(cudaStreamSynchronize(st));  // perm vector goes out of scope
+  }
+
+  // Starting factors (Alg. 2 "Initialize") and their QRs.
+  std::vector<double> host;
+  uint64_t seed = opt.seed;
+  for (int n = 0; n < N; ++n) {
+    host.resize(dims[n] * R);
+    if (A0_host && A0_host[n]) {
+      std::memcpy(host.data(), A0_host[n], host.size() * sizeof(double));
+    } else {
+      for (size_t i = 0; i < host.size(); ++i) {  // Box-Muller on SplitMix64
+        double u1 = ((splitmix64(seed) >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+        double u2 = ((splitmix64(seed) >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+        host[i] = std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+      }
+    }
+    CK(cudaMemcpyAsync(ctx->A[n], host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(launch_house_qr(ctx->A[n], dims[n], R, ctx->Q[n], ctx->Rf[n], ctx->qr_work, ctx->dstatus, st));
+    CK(launch_to_f32(ctx->Q[n], ctx->Qf[n], dims[n] * R, st));
+    CK(cudaStreamSynchronize(st));
+  }
+  // Split-precision staging.
+  if (ctx->prec == CPQR_PREC_SPLIT_BF16) {
+    ctx->Rp = ((R + 15) / 16) * 16;
+    for (int n = 0; n < N; ++n) {
+      ctx->Kp[n] = ((dims[n] + 63) / 64) * 64;
+      CK(ctx->alloc(&ctx->Qt[n], (size_t)2 * ctx->Rp * ctx->Kp[n]));
+      cpqr_status s = stage_q(ctx, n);
+      if (s != CPQR_OK) return s;
+    }
+    CK(ctx->alloc(&ctx->Xhi, nX));
+    CK(ctx->alloc(&ctx->Xlo, nX));
+    CK(launch_split_x((const float*)X_dev, ctx->Xhi, ctx->Xlo, nX, st));
+  }
+  // ||X||^2 (precomputed once, Section 4.1).
+  if (ctx->x64) CK(launch_norm2<double>((const double*)X_dev, nX, ctx->d_scalar, nullptr, st));
+  else CK(launch_norm2<float>((const float*)X_dev, nX, ctx->d_scalar, nullptr, st));
+  CK(cudaMemcpyAsync(ctx->h_pinned, ctx->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(ctx->h_pinned + 2, ctx->dstatus, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  ctx->normX2 = ctx->h_pinned[0];
+  {
+    unsigned int ds;
+    std::memcpy(&ds, ctx->h_pinned + 2, sizeof(ds));
+    if (ds & CPQR_DEV_SINGULAR) return CPQR_ESINGULAR;
+  }
+  if (!(ctx->normX2 > 0.0) || !std::isfinite(ctx->normX2)) return CPQR_EINVAL;
+
+  try {
+    ctx->sched.reset(new Schedule(ctx->dims, R, ctx->tree));
+  } catch (...) {
+    return CPQR_ENOMEM;
+  }
+  ctx->nodes[0] = NodeBuf{const_cast<void*>(X_dev), 0, (1u << N) - 1u, true};
+  *out = c.release();
+  return CPQR_OK;
+}
+
+cpqr_status cp_als_qr_sweep(cpqr_ctx* ctx, int32_t nsweeps, double* fits_host) {
+  if (!ctx) return CPQR_EINVAL;
+  if (ctx->err != CPQR_OK) return ctx->err;
+  if (nsweeps < 0) return CPQR_EINVAL;
+  for (int i = 0; i < nsweeps; ++i) {
+    double f = 0.0;
+    cpqr_status s = one_sweep(ctx, &f);
+    if (s != CPQR_OK) return s;
+    if (fits_host) fits_host[i] = f;
+  }
+  return CPQR_OK;
+}
+
+cpqr_status cp_als_qr_fit(cpqr_ctx* ctx, double tol, int32_t max_sweeps, double* final_fit, int32_t* sweeps_done) {
+  if (!ctx) return CPQR_EINVAL;
+  if (ctx->err != CPQR_OK) return ctx->err;
+  if (max_sweeps < 0) return CPQR_EINVAL;
+  double prev = NAN, f = NAN;
+  int done = 0;
+  bool conv = false;
+  for (int i = 0; i < max_sweeps; ++i) {
+    cpqr_status s = one_sweep(ctx, &f);
+    if (s != CPQR_OK) return s;
+    ++done;
+    if (i >= 1 && std::fabs(f - prev) < tol) {
+      conv = true;
+      break;
+    }
+    prev = f;
+  }
+  if (final_fit) *final_fit = f;
+  if (sweeps_done) *sweeps_done = done;
+  return (conv || max_sweeps == 0) ? CPQR_OK : CPQR_ENOTCONV;
+}
+
+cpqr_status cp_als_qr_get(cpqr_ctx* ctx, int32_t n, double* A_host, double* lambda_host, double* Q_host,
+                          double* R_host) {
+  if (!ctx) return CPQR_EINVAL;
+  if (ctx->err != CPQR_OK) return ctx->err;
+  if (n < 0 || n >= ctx->N) return CPQR_EINVAL;
+  const size_t I = ctx->dims[n], R = ctx->R;
+  cudaStream_t st = ctx->st;
+  if (A_host) CK(cudaMemcpyAsync(A_host, ctx->A[n], I * R * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (lambda_host) CK(cudaMemcpyAsync(lambda_host, ctx->lambda, R * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (Q_host) CK(cudaMemcpyAsync(Q_host, ctx->Q[n], I * R * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (R_host) CK(cudaMemcpyAsync(R_host, ctx->Rf[n], R * R * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return CPQR_OK;
+}
+
+cpqr_status cp_als_qr_stats(cpqr_ctx* ctx, cpqr_stats* out) {
+  if (!ctx || !out) return CPQR_EINVAL;
+  std::memset(out, 0, sizeof(*out));
+  out->sweeps = ctx->sweeps;
+  out->ttm_flops = ctx->sched ? ctx->sched->flops() : 0;
+  out->full_ttms = ctx->sched ? ctx->sched->full_ttms() : 0;
+  out->last_fit = ctx->fits.empty() ? 0.0 : ctx->fits.back();
+  out->beta = ctx->last_beta;
+  out->proposals = ctx->proposals;
+  out->accepted = ctx->accepted;
+  return ctx->err;
+}
+
+cpqr_status cp_als_qr_fit_exact(cpqr_ctx* ctx, double* fit) {
+  if (!ctx || !fit) return CPQR_EINVAL;
+  if (ctx->err != CPQR_OK) return ctx->err;
+  const double* A[CPQR_MAXN];
+  for (int n = 0; n < ctx->N; ++n) A[n] = ctx->A[n];
+  if (ctx->x64)
+    CK(launch_residual2<double>((const double*)ctx->X, ctx->N, ctx->dims.data(), A, ctx->lambda, ctx->R,
+                                ctx->d_scalar, nullptr, ctx->st));
+  else
+    CK(launch_residual2<float>((const float*)ctx->X, ctx->N, ctx->dims.data(), A, ctx->lambda, ctx->R,
+                               ctx->d_scalar, nullptr, ctx->st));
+  CK(cudaMemcpyAsync(ctx->h_pinned, ctx->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  *fit = 1.0 - std::sqrt(std::max(ctx->h_pinned[0], 0.0)) / std::sqrt(ctx->normX2);
+  return CPQR_OK;
+}
+
+void cp_als_qr_destroy(cpqr_ctx* ctx) { delete ctx; }
+
+cpqr_status cp_als_qr_schedule(int32_t N, const int64_t* dims, int32_t R, int32_t tree, int32_t nsweeps,
+                               int32_t* ops, int64_t cap, int64_t* count, int64_t* flops) {
+  if (N < 3 || N > CPQR_MAXN || !dims || R < 1 || tree < 0 || tree > 2 || nsweeps < 0) return CPQR_EINVAL;
+  try {
+    std::vector<int64_t> d(dims, dims + N);
+    Schedule s(d, R, tree);
+    std::vector<Op> all;
+    for (int i = 0; i < nsweeps; ++i) s.next_sweep(all);
+    if (count) *count = (int64_t)all.size();
+    if (flops) *flops = s.flops();
+    if (ops) {
+      int64_t n = std::min<int64_t>(cap, (int64_t)all.size());
+      for (int64_t i = 0; i < n; ++i) {
+        ops[4 * i] = all[i].kind;
+        ops[4 * i + 1] = all[i].a;
+        ops[4 * i + 2] = all[i].b;
+        ops[4 * i + 3] = all[i].c;
+      }
+    }
+  } catch (...) {
+    return CPQR_EINVAL;
+  }
+  return CPQR_OK;
+}
+
+cpqr_status cpqr_ttm(const void* T_dev, int32_t nd, const int64_t* tdims, int32_t k, const void* Q_dev, int32_t R,
+                     void* out_dev, int32_t dtype, void* stream) {
+  if (!T_dev || !Q_dev || !out_dev || !tdims || nd < 1 || nd > 8 || k < 0 || k >= nd || R < 1 || R > CPQR_MAXR)
+    return CPQR_EINVAL;
+  int64_t P = 1, S = 1;
+  for (int j = 0; j < k; ++j) P *= tdims[j];
+  for (int j = k + 1; j < nd; ++j) S *= tdims[j];
+  const int64_t K = tdims[k];
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e;
+  switch (dtype) {
+    case 0: e = launch_ttm<double, double, double>((const double*)T_dev, (const double*)Q_dev, (double*)out_dev, P, K, S, R, st); break;
+    case 1: e = launch_ttm<float, float, float>((const float*)T_dev, (const float*)Q_dev, (float*)out_dev, P, K, S, R, st); break;
+    case 2: e = launch_ttm<float, double, double>((const float*)T_dev, (const double*)Q_dev, (double*)out_dev, P, K, S, R, st); break;
+    case 3: {
+      if (!ttm_tc_supported(P, K, S, R)) return CPQR_EUNSUPPORTED;
+      const int Rp = ((R + 15) / 16) * 16;
+      const int64_t Kp = ((K + 63) / 64) * 64;
+      const int64_t n = P * K * S;
+      __nv_bfloat16 *xh = nullptr, *xl = nullptr, *qt = nullptr;
+      unsigned int* ds = nullptr;
+      if (cudaMalloc(&xh, n * 2) != cudaSuccess || cudaMalloc(&xl, n * 2) != cudaSuccess ||
+          cudaMalloc(&qt, (size_t)2 * Rp * Kp * 2) != cudaSuccess || cudaMalloc(&ds, 4) != cudaSuccess) {
+        cudaFree(xh); cudaFree(xl); cudaFree(qt); cudaFree(ds);
+        return CPQR_ENOMEM;
+      }
+      e = cudaMemsetAsync(ds, 0, 4, st);
+      if (e == cudaSuccess) e = launch_split_x((const float*)T_dev, xh, xl, n, st);
+      if (e == cudaSuccess) e = launch_split_q((const double*)Q_dev, K, R, qt, Rp, Kp, st);
+      if (e == cudaSuccess) e = launch_ttm_tc(xh, xl, qt, Rp, Kp, (float*)out_dev, P, K, S, R, ds, st);
+      unsigned int hs = 0;
+      if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, ds, 4, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      cudaFree(xh); cudaFree(xl); cudaFree(qt); cudaFree(ds);
+      if (e == cudaSuccess && (hs & CPQR_DEV_TIMEOUT)) return CPQR_ETIMEOUT;
+      break;
+    }
+    default: return CPQR_EINVAL;
+  }
+  return e == cudaSuccess ? CPQR_OK : CPQR_ECUDA;
+}
+
+cpqr_status cpqr_house_qr(const double* A_dev, int64_t M, int32_t R, double* Q_dev, double* R_dev, void* stream) {
+  if (!A_dev || !Q_dev || !R_dev || R < 1 || R > CPQR_MAXR || M < R) return CPQR_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  double* work = nullptr;
+  unsigned int* ds = nullptr;
+  if (cudaMalloc(&work, (size_t)M * R * sizeof(double)) != cudaSuccess || cudaMalloc(&ds, 4) != cudaSuccess) {
+    cudaFree(work); cudaFree(ds);
+    return CPQR_ENOMEM;
+  }
+  cudaError_t e = cudaMemsetAsync(ds, 0, 4, st);
+  if (e == cudaSuccess) e = launch_house_qr(A_dev, M, R, Q_dev, R_dev, work, ds, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(work);
+  cudaFree(ds);
+  return e == cudaSuccess ? CPQR_OK : CPQR_ECUDA;
+}
+
+cpqr_status cpqr_krp_qr(const double* Rs_dev, int32_t m, int32_t R, double* Q0_dev, double* R0_dev, void* stream) {
+  if (!Rs_dev || !Q0_dev || !R0_dev || m < 1 || m > CPQR_MAXN - 1 || R < 1 || R > CPQR_MAXR) return CPQR_EINVAL;
+  int64_t M = ipow(R, m);
+  if (M < R) return CPQR_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<int32_t> perm = krp_perm(m, R);
+  int32_t* dperm = nullptr;
+  double* work = nullptr;
+  unsigned int* ds = nullptr;
+  if (cudaMalloc(&dperm, perm.size() * 4) != cudaSuccess || cudaMalloc(&work, (size_t)M * R * 8) != cudaSuccess ||
+      cudaMalloc(&ds, 4) != cudaSuccess) {
+    cudaFree(dperm); cudaFree(work); cudaFree(ds);
+    return CPQR_ENOMEM;
+  }
+  ZPlan plan{};
+  plan.m = m;
+  plan.R = R;
+  plan.M = M;
+  plan.perm = dperm;
+  for (int j = 0; j < CPQR_MAXR; ++j) plan.act[j] = (int32_t)std::min<int64_t>(M, ipow(j + 1, m));
+  TriPtrs tri{};
+  for (int k = 0; k < m; ++k) tri.p[k] = Rs_dev + (size_t)k * R * R;
+  cudaError_t e = cudaMemcpyAsync(dperm, perm.data(), perm.size() * 4, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ds, 0, 4, st);
+  if (e == cudaSuccess) e = launch_krp_qr(plan, tri, Q0_dev, R0_dev, work, ds, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(dperm); cudaFree(work); cudaFree(ds);
+  return e == cudaSuccess ? CPQR_OK : CPQR_ECUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,97 @@
+// Shared device helpers and launch declarations of the CP-ALS-QR library.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+
+#define CPQR_MAXR 32
+#define CPQR_MAXN 5
+
+// Device-side error flags (bitwise OR into ctx status word).
+#define CPQR_DEV_SINGULAR 1u
+#define CPQR_DEV_NONFINITE 2u
+#define CPQR_DEV_TIMEOUT 4u
+
+namespace cpqr {
+
+// Cluster size of the FP64 small-QR kernels (CTAs per cluster) and their block size.
+constexpr int kQrCluster = 8;
+constexpr int kQrThreads = 256;
+
+// ----- TTM (ttm.cu) -----
+// out[p, r, s] = sum_i T[p, i, s] * Q[i, r] with T of shape (P, K, S), Q K x R row-major.
+// TT = element type of T, TQ = element type of Q and of the accumulator, TO = output type.
+template <typename TT, typename TQ, typename TO>
+cudaError_t launch_ttm(const TT* T, const TQ* Q, TO* out, int64_t P, int64_t K, int64_t S, int R,
+                       cudaStream_t st);
+
+// ----- split-precision tensor-core TTM (ttm_tc.cu) -----
+// Stages Q (K x R FP64 row-major) as bf16 hi/lo, transposed and padded for the MMA
+// B operand: Qt[2][Rp][Kp] with Rp = R rounded up to 16, Kp = K rounded up to 64.
+cudaError_t launch_split_q(const double* Q, int64_t K, int R, __nv_bfloat16* Qt, int Rp, int64_t Kp,
+                           cudaStream_t st);
+// X (n elements FP32) -> Xhi, Xlo bf16 with X = hi + lo + O(2^-16 |X|).
+cudaError_t launch_split_x(const float* X, __nv_bfloat16* Xhi, __nv_bfloat16* Xlo, int64_t n,
+                           cudaStream_t st);
+// out[p, r, s] = sum_i X[p, i, s] Q[i, r] from split operands; out FP32.
+// Returns cudaErrorNotSupported if the shape is outside the kernel's range.
+cudaError_t launch_ttm_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo, const __nv_bfloat16* Qt,
+                          int Rp, int64_t Kp, float* out, int64_t P, int64_t K, int64_t S, int R,
+                          unsigned int* dev_status, cudaStream_t st);
+bool ttm_tc_supported(int64_t P, int64_t K, int64_t S, int R);
+
+// ----- small FP64 kernels (smallqr.cu) -----
+struct ZPlan {          // row order of the Khatri-Rao product used by the staircase QR
+  int m;                // number of triangles in the product
+  int R;
+  int64_t M;            // R^m rows
+  const int32_t* perm;  // device: sorted row t -> original row index
+  int32_t act[CPQR_MAXR];  // column j is active on sorted rows [j, act[j])
+};
+
+// Plain QR of an M x R FP64 row-major matrix (device): Q (M x R), R (R x R), diag(R) > 0.
+cudaError_t launch_house_qr(const double* A, int64_t M, int R, double* Q, double* Rout, double* work,
+                            unsigned int* dev_status, cudaStream_t st);
+size_t house_qr_work_doubles(int64_t M, int R);
+
+// QR of Z = R_{k_1} (.) ... (.) R_{k_m}: Rs holds pointers to the m triangles (device).
+struct TriPtrs {
+  const double* p[CPQR_MAXN];
+};
+cudaError_t launch_krp_qr(const ZPlan& plan, TriPtrs Rs, double* Q0, double* R0, double* work,
+                          unsigned int* dev_status, cudaStream_t st);
+size_t krp_qr_work_doubles(const ZPlan& plan);
+
+// Finish of a mode update (Alg. 3 lines 5 and 7-10): V^ = (1+beta) V0 - alpha beta V1
+// (V = [V0 | V1], I x C, C = R or 2R), A^ = V^ R0^{-T}, lambda = column norms,
+// A = A^ / lambda, A = Q_n R_n; also the fit terms <V0, V^> and ||V^||^2.
+struct FinishOut {
+  double* A;        // I x R
+  double* lambda;   // R
+  double* Q;        // I x R
+  double* Rn;       // R x R
+  float* Qf;        // I x R FP32 copy (may be null)
+  double* fit_terms;  // 2 doubles
+};
+cudaError_t launch_mode_finish(const double* V, int C, const double* R0, double beta, double alpha,
+                               int64_t I, int R, FinishOut out, double* work, unsigned int* dev_status,
+                               cudaStream_t st);
+
+// V[i, c] = sum_{p, s} Y[p, i, s] * Qc[p*S + s, c], c < C, Qc = [Q0 | Q0prev] (K x C,
+// K = P*S) FP64; Y FP64 or FP32.  V is zeroed by the launcher.
+template <typename TY>
+cudaError_t launch_leaf_v(const TY* Y, int64_t P, int64_t I, int64_t S, const double* Q0,
+                          const double* Q0prev, int R, int C, double* V, cudaStream_t st);
+
+// ||X||^2 in FP64 (partials into work, final into out[0]).
+template <typename TX>
+cudaError_t launch_norm2(const TX* X, int64_t n, double* out, double* work, cudaStream_t st);
+
+// ||X - [[lambda; A]]||^2 with FP64 model entries; X dims d[0..N-1].
+template <typename TX>
+cudaError_t launch_residual2(const TX* X, int N, const int64_t* d, const double* const* A,
+                             const double* lambda, int R, double* out, double* work, cudaStream_t st);
+
+cudaError_t launch_to_f32(const double* a, float* b, int64_t n, cudaStream_t st);
+
+}  // namespace cpqr

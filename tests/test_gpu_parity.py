@@ -1,0 +1,160 @@
+"""GPU parity: every step of the CUDA path against the FP64 CPU oracle on the
+same seeded inputs, through the C ABI."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import cpqr_oracle as o
+from paper_2503_18759_gb300 import binding as b
+from paper_2503_18759_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2503_18759_gb300 import build
+    build.build()
+    b.lib()
+    assert torch.cuda.is_available()
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def _rel(a, ref):
+    return float(np.max(np.abs(a - ref)) / max(np.max(np.abs(ref)), 1e-300))
+
+
+TTM_SHAPES = [((37, 53, 29), 5), ((64, 65, 66), 32), ((9, 10, 11, 12), 7), ((3, 200, 2), 2), ((130, 7, 1, 5), 1),
+              ((5, 6, 7, 8, 9), 4), ((128, 128, 3), 24)]
+
+
+@pytest.mark.parametrize("dims,R", TTM_SHAPES)
+def test_ttm_fp64_every_mode(dims, R):
+    g = np.random.default_rng(sum(dims) + R)
+    T = g.standard_normal(dims)
+    for k in range(len(dims)):
+        if dims[k] < 1:
+            continue
+        Q = g.standard_normal((dims[k], R))
+        ref = o.ttm_qt(T, Q, k)
+        out = torch.empty(ref.shape, dtype=torch.float64, device=DEV)
+        Td, Qd = _dev(T), _dev(Q)  # keep the device copies alive across the call
+        b.cpqr_ttm(Td.data_ptr(), dims, k, Qd.data_ptr(), R, out.data_ptr(), b.TTM_F64)
+        torch.cuda.synchronize()
+        assert _rel(out.cpu().numpy(), ref) < 1e-13, (dims, k)
+
+
+@pytest.mark.parametrize("dims,R", TTM_SHAPES)
+def test_ttm_fp32_every_mode(dims, R):
+    g = np.random.default_rng(sum(dims) + R + 1)
+    T = g.standard_normal(dims).astype(np.float32)
+    for k in range(len(dims)):
+        Q = g.standard_normal((dims[k], R)).astype(np.float32)
+        ref = o.ttm_qt(T.astype(np.float64), Q.astype(np.float64), k)
+        Td, Qd = _dev(T), _dev(Q)
+        out = torch.empty(ref.shape, dtype=torch.float32, device=DEV)
+        b.cpqr_ttm(Td.data_ptr(), dims, k, Qd.data_ptr(), R, out.data_ptr(), b.TTM_F32)
+        out64 = torch.empty(ref.shape, dtype=torch.float64, device=DEV)
+        Q64 = _dev(Q.astype(np.float64))
+        b.cpqr_ttm(Td.data_ptr(), dims, k, Q64.data_ptr(), R, out64.data_ptr(), b.TTM_F32_IN_F64)
+        torch.cuda.synchronize()
+        # FP32 accumulation over K terms: |err| <= K * 2^-24 * sum|t q|, checked loosely against max|ref|
+        K = dims[k]
+        assert _rel(out.cpu().numpy(), ref) < 4 * math.sqrt(K) * 2 ** -24 * 8
+        assert _rel(out64.cpu().numpy(), ref) < 1e-13
+
+
+@pytest.mark.parametrize("M,R", [(400, 32), (60, 5), (33, 32), (1000, 17), (5, 5), (128, 24), (2049, 32)])
+def test_house_qr(M, R):
+    g = np.random.default_rng(M * 7 + R)
+    A = g.standard_normal((M, R))
+    Qr, Rr = o.householder_qr(A)
+    Q = torch.empty((M, R), dtype=torch.float64, device=DEV)
+    Rm = torch.empty((R, R), dtype=torch.float64, device=DEV)
+    Ad = _dev(A)
+    b.cpqr_house_qr(Ad.data_ptr(), M, R, Q.data_ptr(), Rm.data_ptr())
+    torch.cuda.synchronize()
+    assert np.allclose(Rm.cpu().numpy(), Rr, atol=1e-12 * np.linalg.norm(A))
+    assert np.allclose(Q.cpu().numpy(), Qr, atol=1e-12)
+
+
+@pytest.mark.parametrize("m,R", [(2, 5), (2, 32), (3, 24), (4, 16), (2, 1), (3, 7), (4, 5)])
+def test_krp_qr(m, R):
+    g = np.random.default_rng(m * 100 + R)
+    Rs = [o.householder_qr(g.standard_normal((R + 4, R)))[1] for _ in range(m)]
+    Z = o.khatri_rao(Rs)
+    Q0r, R0r = o.householder_qr(Z)
+    Q0 = torch.empty(Z.shape, dtype=torch.float64, device=DEV)
+    R0 = torch.empty((R, R), dtype=torch.float64, device=DEV)
+    Rd = _dev(np.stack(Rs))
+    b.cpqr_krp_qr(Rd.data_ptr(), m, R, Q0.data_ptr(), R0.data_ptr())
+    torch.cuda.synchronize()
+    assert np.allclose(R0.cpu().numpy(), R0r, atol=1e-12 * np.abs(R0r).max())
+    assert np.allclose(Q0.cpu().numpy(), Q0r, atol=1e-11)
+
+
+def _run_gpu(prob, tree, extrap, beta_fixed, sweeps, prec=b.PREC_FP64):
+    x64 = prob.X.dtype == np.float64
+    X = _dev(prob.X)
+    opts = b.make_options(tree=tree, prec=prec, extrap=extrap, beta_fixed=beta_fixed)
+    with b.Decomposition(prob.dims, prob.R, X.data_ptr(), x64, prob.A0, opts) as d:
+        fits = d.sweep(sweeps)
+        A, lam, Q, Rn = d.factors()
+        st = d.stats()
+    return fits, A, lam, Q, Rn, st
+
+
+def _run_oracle(prob, tree, extrap, beta_fixed, sweeps):
+    kw = dict(tree=tree, max_sweeps=sweeps)
+    if extrap == b.EXTRAP_NONE:
+        kw["extrapolate"] = False
+    elif extrap == b.EXTRAP_FIXED:
+        kw.update(extrapolate=True, beta_fixed=beta_fixed)
+    else:
+        kw["extrapolate"] = True
+    return o.cp_als_qr(prob.X, prob.R, prob.A0, **kw)
+
+
+CASES = [
+    ("cube60_std", dict(dims=[60, 60, 60], R=5, c=None, eta=1e-4, dtype=np.float64), b.TREE_STANDARD, b.EXTRAP_NONE, 0.0, 12),
+    ("order3_rest_fixed", dict(dims=[23, 19, 17], R=6, c=0.6, eta=1e-2, dtype=np.float64), b.TREE_RESTRUCTURED, b.EXTRAP_FIXED, 0.02, 8),
+    ("order3_rest_paper", dict(dims=[30, 31, 29], R=8, c=0.9, eta=1e-3, dtype=np.float32), b.TREE_RESTRUCTURED, b.EXTRAP_PAPER, 0.0, 10),
+    ("order4_rest", dict(dims=[11, 9, 10, 12], R=4, c=0.5, eta=1e-3, dtype=np.float64), b.TREE_RESTRUCTURED, b.EXTRAP_FIXED, 0.01, 7),
+    ("order4_std", dict(dims=[11, 9, 10, 12], R=4, c=0.5, eta=1e-3, dtype=np.float32), b.TREE_STANDARD, b.EXTRAP_NONE, 0.0, 5),
+    ("order5_rest", dict(dims=[6, 7, 5, 6, 7], R=3, c=None, eta=1e-3, dtype=np.float64), b.TREE_RESTRUCTURED, b.EXTRAP_FIXED, 0.01, 6),
+    ("order3_none", dict(dims=[15, 16, 17], R=5, c=0.3, eta=1e-3, dtype=np.float64), b.TREE_NONE, b.EXTRAP_NONE, 0.0, 5),
+    ("order3_r32", dict(dims=[40, 36, 33], R=32, c=0.5, eta=1e-3, dtype=np.float64), b.TREE_RESTRUCTURED, b.EXTRAP_FIXED, 0.001, 5),
+]
+
+
+@pytest.mark.parametrize("name,cfg,tree,extrap,beta,sweeps", CASES, ids=[c[0] for c in CASES])
+def test_fp64_solver_matches_oracle(name, cfg, tree, extrap, beta, sweeps):
+    cfg = dict(cfg)
+    prob = inputs.make_problem(name, cfg.pop("dims"), cfg.pop("R"), seed=3, **cfg)
+    fits, A, lam, Q, Rn, st = _run_gpu(prob, tree, extrap, beta, sweeps)
+    ref = _run_oracle(prob, tree, extrap, beta, sweeps)
+    assert np.max(np.abs(fits - np.array(ref.fits))) <= 1e-10, (fits, ref.fits)
+    for n in range(len(prob.dims)):
+        assert o.subspace_sine(A[n], ref.A[n]) <= 1e-10
+        assert np.allclose(A[n], ref.A[n], atol=1e-8)
+    assert np.allclose(lam, ref.lam, rtol=1e-8)
+    assert st.ttm_flops == ref.flops
+
+
+def test_cube60_fifty_sweeps_parity():
+    """The 60^3 FP64 rank-5 workload, standard tree, 50 sweeps: fit and factor subspaces <= 1e-10."""
+    prob = inputs.workload("cube60_r5_f64", seed=0)
+    fits, A, lam, Q, Rn, st = _run_gpu(prob, b.TREE_STANDARD, b.EXTRAP_NONE, 0.0, 50)
+    ref = _run_oracle(prob, b.TREE_STANDARD, b.EXTRAP_NONE, 0.0, 50)
+    assert np.max(np.abs(fits - np.array(ref.fits))) <= 1e-10
+    for n in range(3):
+        assert o.subspace_sine(A[n], ref.A[n]) <= 1e-10
+        assert np.allclose(Q[n].T @ Q[n], np.eye(5), atol=1e-13)
+    assert fits[-1] > 0.9998
