@@ -1,0 +1,287 @@
+#!/usr/bin/env python
+"""Benchmark: seconds per CP-ALS-QR sweep (ALS-QR-BRE: restructured dimension
+tree + customised extrapolation) on the 400 x 400 x 400 rank-32 workload.
+
+A step is one sweep (every mode updated once: TTM chain, Khatri-Rao QR,
+V = Y_(n) Q0, R0^{-T} solve, normalisation, factor QR, fit) on a seeded
+synthetic tensor resident in HBM.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--prec split|fp64] [--quick]
+
+N > 1 (torchrun): independent replicas, one per GPU (the solver has no
+cross-GPU exchange in this build); value = max-over-ranks time / sweeps of all
+ranks.  --impl reference times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "sec/CP-ALS-QR sweep & time-to-fit 1e-6 (mixed+learned vs FP64 GPU); TTM %peak"
+WORKLOAD = "cube400_r32_c09"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling in the background."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_sweep_times(prob, tree, sweeps):
+    """Wall time of each oracle sweep on the host cores (FP64 numpy/BLAS)."""
+    from oracle import cpqr_oracle as o
+    stamps = [time.perf_counter()]
+    o.cp_als_qr(prob.X, prob.R, prob.A0, tree=tree, extrapolate=True, max_sweeps=sweeps,
+                on_sweep=lambda k, f: stamps.append(time.perf_counter()))
+    return np.diff(stamps)
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return None
+    from oracle import cpqr_oracle as o
+    from paper_2503_18759_gb300 import inputs
+    prob = inputs.workload(WORKLOAD, seed=0)
+    t = oracle_sweep_times(prob, o.TREE_RESTRUCTURED, args.warmup + args.steps)
+    per = float(np.mean(t[args.warmup:])) if args.steps > 0 else float("nan")
+    cores = os.cpu_count()
+    return {"metric": METRIC, "value": per, "unit": "s/sweep", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "dims": prob.dims, "rank": prob.R, "tree": "restructured",
+                       "extrapolation": "paper rule", "l2": "no flush; 512 MB FP64 tensor > L2"},
+            "cpu_baseline": {"value": per, "unit": "s/sweep", "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} full-size oracle sweeps after {args.warmup} warm-up sweeps"},
+            "e2e": {"value": per, "unit": "s/sweep", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2503_18759_gb300 import binding as b
+    from paper_2503_18759_gb300 import build, inputs
+
+    build.build()
+    b.lib()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    prec = b.PREC_SPLIT_BF16 if args.prec == "split" else b.PREC_FP64
+    prob = inputs.workload(WORKLOAD, seed=rank)
+    X = torch.from_numpy(prob.X).to(dev)
+    xbytes = prob.X.nbytes
+    opts = b.make_options(tree=b.TREE_RESTRUCTURED, prec=prec, extrap=b.EXTRAP_PAPER)
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    dec = b.Decomposition(prob.dims, prob.R, X.data_ptr(), False, prob.A0, opts)
+    dec.sweep(args.warmup)
+    launches0 = dec.stats().launches
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    fits = dec.sweep(args.steps)
+    e1.record()
+    barrier()
+    ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    launches = dec.stats().launches - launches0
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    # per-kernel device time over the same number of sweeps (CUDA events around each launch)
+    dec.set_timing(True)
+    dec.sweep(args.steps)
+    st = dec.stats()
+    dec.set_timing(False)
+    buckets = {name: st.ms_bucket[i] / max(args.steps, 1) for i, name in enumerate(b.BUCKETS)}
+    n_full = st.n_bucket[0]
+    full_ms = st.ms_bucket[0] / max(n_full, 1)
+    out = None
+    if rank == 0:
+        hbm, peak_kind = _peaks()
+        # first-level TTM, algorithmic bytes: X once (FP32, or bf16 hi + lo: 4 B/element) + output (FP32/FP64)
+        out_elems = prob.X.size // prob.dims[0] * prob.R  # every full TTM here shrinks one side of 400 to R
+        ob = 4 if prec == b.PREC_SPLIT_BF16 else 8
+        alg_bytes = xbytes + out_elems * ob
+        achieved = alg_bytes / (full_ms * 1e-3) / 1e9 if n_full else None
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": (achieved / hbm) if achieved else None, "traffic": None,
+                "kernel": "first-level TTM (full tensor)", "peak_kind": f"{peak_kind} copy bandwidth (burst)",
+                "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": full_ms, "launches": int(n_full)}
+        if prec == b.PREC_FP64:
+            flops = 2 * prob.X.size * prob.R
+            roof.update({"bound": "alu", "achieved": flops / (full_ms * 1e-3) / 1e12, "peak": 1.2,
+                         "unit": "TFLOP/s", "peak_kind": "FP64 DFMA rate measured by a probe (1.2 TFLOP/s)"})
+            roof["frac"] = roof["achieved"] / roof["peak"]
+        out = {"metric": METRIC, "value": ms * 1e-3 / world, "unit": "s/sweep", "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+               "vs_baseline": None,
+               "dtype": "bf16x3+f32+f64" if prec == b.PREC_SPLIT_BF16 else "f64",
+               "data": "synthetic",
+               "config": {"workload": WORKLOAD, "dims": prob.dims, "rank": prob.R, "tree": "restructured",
+                          "extrapolation": "paper rule", "precision": args.prec,
+                          "l2": "no flush; inputs larger than L2 (256 MB tensor, 512 MB bf16 split)",
+                          "replicas": world},
+               "roofline": roof,
+               "buckets_ms_per_sweep": buckets,
+               "gpu_launches": int(launches),
+               "fit_last": float(fits[-1]) if len(fits) else None}
+    dec.close()
+    if rank == 0 and not args.quick:
+        out.update(extras(args, prob, X, dev, b))
+    out_clocks = clocks.stop()
+    if out is not None:
+        out["clocks"] = out_clocks
+        if not args.quick:
+            out["cpu_baseline"] = cpu_baseline(prob)
+    return out
+
+
+def extras(args, prob, X, dev, b):
+    """e2e through the host-buffer entry point, the FP64 GPU path, and time to the 1e-6 fit tolerance."""
+    import torch
+    res = {}
+    # e2e: pinned host tensor -> device -> init -> sweeps -> factors back, one C call
+    S = 30
+    Xh = torch.from_numpy(prob.X).pin_memory()
+    opts = b.make_options(tree=b.TREE_RESTRUCTURED, prec=b.PREC_SPLIT_BF16 if args.prec == "split" else b.PREC_FP64,
+                          extrap=b.EXTRAP_PAPER)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    _, _, _, ns, _ = b.cp_als_qr_run_host(prob.dims, prob.R, Xh.numpy(), prob.A0, opts, tol=0.0, max_sweeps=S)
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    fbytes = sum(d * prob.R * 8 for d in prob.dims) + prob.R * 8
+    res["e2e"] = {"value": e2e_ms * 1e-3 / ns, "unit": "s/sweep", "h2d_bytes_per_step": prob.X.nbytes / ns,
+                  "d2h_bytes_per_step": fbytes / ns + 24, "sweeps_per_call": ns,
+                  "note": "one cp_als_qr_run_host call (H2D of X from pinned memory, init, sweeps, factors D2H) / sweeps"}
+    # time to |delta fit| < 1e-6 from the same start, FP64 GPU path and this path
+    ttf = {}
+    for name, prec in (("fp64", b.PREC_FP64), (args.prec, b.PREC_SPLIT_BF16 if args.prec == "split" else b.PREC_FP64)):
+        if name in ttf:
+            continue
+        o = b.make_options(tree=b.TREE_RESTRUCTURED, prec=prec, extrap=b.EXTRAP_PAPER)
+        with b.Decomposition(prob.dims, prob.R, X.data_ptr(), False, prob.A0, o) as d:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            conv, f, ns = d.fit(1e-6, 400)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            fx = d.fit_exact()
+            ttf[name] = {"seconds": wall, "sweeps": ns, "converged": conv, "fit_reported": f, "fit_exact": fx,
+                         "s_per_sweep": wall / max(ns, 1)}
+    res["time_to_tol_1e-6"] = ttf
+    return res
+
+
+def cpu_baseline(prob):
+    from oracle import cpqr_oracle as o
+    t = oracle_sweep_times(prob, o.TREE_RESTRUCTURED, 4)
+    return {"value": float(np.mean(t[1:])), "unit": "s/sweep", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "3 full-size FP64 oracle sweeps (400^3, R=32) after its first sweep, numpy/BLAS on all host cores"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="split", choices=["split", "fp64"])
+    ap.add_argument("--quick", action="store_true", help="skip e2e, time-to-fit and the CPU baseline")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        out = run_reference(args, rank)
+    else:
+        if world > 1:
+            import torch
+            torch.cuda.set_device(local_rank)
+            torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+        out = run_ours(args, rank, world, local_rank)
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+    if out is not None and rank == 0:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

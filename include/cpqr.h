@@ -83,6 +83,18 @@ typedef struct {
                                the rule alone) */
 } cpqr_options;
 
+/* Time buckets of a sweep (the per-iteration breakdown of Section 4.3 plus the
+ * split of TTM time by tree level). */
+enum {
+  CPQR_BUCKET_TTM_FULL = 0,  /* TTMs that read all of X */
+  CPQR_BUCKET_TTM_DEEP = 1,  /* TTMs on cached intermediates */
+  CPQR_BUCKET_Q0 = 2,        /* Khatri-Rao product and its QR (computation of Q0) */
+  CPQR_BUCKET_APPLY_Q0 = 3,  /* V = Y_(n) [Q0 | Q0^{k-1}] (application of Q0) */
+  CPQR_BUCKET_QR = 4,        /* extrapolation, R0^{-T} solve, normalisation, factor QR */
+  CPQR_BUCKET_OTHER = 5,     /* operand staging, fit read-back */
+  CPQR_NBUCKETS = 6
+};
+
 /* Per-context counters. */
 typedef struct {
   int64_t sweeps;          /* sweeps done */
@@ -92,7 +104,13 @@ typedef struct {
   double beta;             /* beta used by the last sweep */
   int64_t proposals;       /* learned proposals evaluated */
   int64_t accepted;        /* learned proposals accepted by the judge */
+  int64_t launches;        /* kernels this context launched */
+  double ms_bucket[CPQR_NBUCKETS];   /* device time per bucket (only while timing is on) */
+  int64_t n_bucket[CPQR_NBUCKETS];   /* launches per bucket (only while timing is on) */
 } cpqr_stats;
+
+/* Turn per-launch CUDA-event timing on (1) or off (0); resets the bucket times. */
+cpqr_status cp_als_qr_set_timing(cpqr_ctx* ctx, int32_t on);
 
 /* Fill *opt with the defaults: restructured tree, FP64, paper extrapolation,
  * alpha = 0.1, beta_fixed = 0, seed = 0, no learned model. */
@@ -132,6 +150,17 @@ cpqr_status cp_als_qr_stats(cpqr_ctx* ctx, cpqr_stats* out);
 /* Exact fit of the current model by one pass over X: 1 - ||X - [[lambda; A]]|| / ||X|| with
  * every model entry and the residual sum in FP64.  Costs N*R flops per element of X. */
 cpqr_status cp_als_qr_fit_exact(cpqr_ctx* ctx, double* fit);
+
+/* End-to-end decomposition of a HOST tensor: copies X_host (C order, float32 or float64; pinned
+ * memory gives an asynchronous copy) to the device, runs cp_als_qr_init and cp_als_qr_fit(tol,
+ * max_sweeps), copies every factor to A_out_host[n] (I_n x R, host) and the weights to
+ * lambda_out_host (R, host), and releases everything.  final_fit / sweeps_done may be NULL.
+ * Returns CPQR_ENOTCONV if max_sweeps was reached before tol (results are still written). */
+cpqr_status cp_als_qr_run_host(int32_t N, const int64_t* dims, int32_t R, const void* X_host,
+                               int32_t x_is_fp64, const double* const* A0_host,
+                               const cpqr_options* opt, double tol, int32_t max_sweeps,
+                               double* const* A_out_host, double* lambda_out_host,
+                               double* final_fit, int32_t* sweeps_done, void* stream);
 
 /* Release every device allocation of ctx (NULL is ignored). */
 void cp_als_qr_destroy(cpqr_ctx* ctx);

@@ -435,7 +435,8 @@ class Result:
 def cp_als_qr(X: np.ndarray, R: int, A0: Sequence[np.ndarray], *, tree: int = TREE_RESTRUCTURED,
               extrapolate: bool = True, alpha: float = ALPHA, beta_fixed: Optional[float] = None,
               max_sweeps: int = 50, tol: float = 0.0, record: bool = False,
-              check_leaves: bool = False, beta_schedule: Optional[Sequence[float]] = None) -> Result:
+              check_leaves: bool = False, beta_schedule: Optional[Sequence[float]] = None,
+              on_sweep=None) -> Result:
     """CP-ALS-QR (Alg. 2) with a TTM schedule and optional customised extrapolation (Alg. 3).
 
     X is promoted to float64 exactly.  A0 are the starting factors (Alg. 2
@@ -443,6 +444,7 @@ def cp_als_qr(X: np.ndarray, R: int, A0: Sequence[np.ndarray], *, tree: int = TR
     beta from sweep 2 on (ablation); ``beta_schedule[k]`` forces the beta of
     sweep k (0-based) when given.  ``tol`` > 0 stops when |fit_k - fit_{k-1}| < tol.
     ``check_leaves`` asserts every scheduled leaf equals X x_{k != n} Q_k^T.
+    ``on_sweep(k, fit)`` is called after every sweep (timing hook; no effect on the result).
     """
     X = np.asarray(X, dtype=np.float64)
     N = X.ndim
@@ -525,6 +527,8 @@ def cp_als_qr(X: np.ndarray, R: int, A0: Sequence[np.ndarray], *, tree: int = TR
         fits.append(fit)
         # Section 4.2 activation rule.
         rule.observe(fit)
+        if on_sweep is not None:
+            on_sweep(k, fit)
         if tol > 0 and k >= 1 and abs(fits[-1] - fits[-2]) < tol:
             break
     return Result(A, lam, fits, betas, orders, sched.flops, len(fits), normX2, records)

@@ -36,10 +36,15 @@ class Options(C.Structure):
                 ("mlp_weights", C.POINTER(C.c_float))]
 
 
+NBUCKETS = 6
+BUCKETS = ("ttm_full", "ttm_deep", "q0", "apply_q0", "qr", "other")
+
+
 class Stats(C.Structure):
     _fields_ = [("sweeps", C.c_int64), ("ttm_flops", C.c_int64), ("full_ttms", C.c_int64),
                 ("last_fit", C.c_double), ("beta", C.c_double), ("proposals", C.c_int64),
-                ("accepted", C.c_int64)]
+                ("accepted", C.c_int64), ("launches", C.c_int64), ("ms_bucket", C.c_double * NBUCKETS),
+                ("n_bucket", C.c_int64 * NBUCKETS)]
 
 
 _lib = None
@@ -63,16 +68,19 @@ def lib() -> C.CDLL:
     L.cp_als_qr_get.argtypes = [vp, i32, P(dbl), P(dbl), P(dbl), P(dbl)]
     L.cp_als_qr_stats.argtypes = [vp, P(Stats)]
     L.cp_als_qr_fit_exact.argtypes = [vp, P(dbl)]
+    L.cp_als_qr_set_timing.argtypes = [vp, i32]
     L.cp_als_qr_destroy.argtypes = [vp]
     L.cp_als_qr_destroy.restype = None
     L.cp_als_qr_strerror.argtypes = [i32]
     L.cp_als_qr_strerror.restype = C.c_char_p
     L.cp_als_qr_schedule.argtypes = [i32, P(i64), i32, i32, i32, P(i32), i64, P(i64), P(i64)]
+    L.cp_als_qr_run_host.argtypes = [i32, P(i64), i32, vp, i32, P(P(dbl)), P(Options), dbl, i32, P(P(dbl)),
+                                     P(dbl), P(dbl), P(i32), vp]
     L.cpqr_ttm.argtypes = [vp, i32, P(i64), i32, vp, i32, vp, i32, vp]
     L.cpqr_house_qr.argtypes = [vp, i64, i32, vp, vp, vp]
     L.cpqr_krp_qr.argtypes = [vp, i32, i32, vp, vp, vp]
     for name in ("cp_als_qr_init", "cp_als_qr_sweep", "cp_als_qr_fit", "cp_als_qr_get", "cp_als_qr_stats",
-                 "cp_als_qr_fit_exact", "cp_als_qr_schedule", "cpqr_ttm", "cpqr_house_qr", "cpqr_krp_qr"):
+                 "cp_als_qr_fit_exact", "cp_als_qr_set_timing", "cp_als_qr_schedule", "cp_als_qr_run_host", "cpqr_ttm", "cpqr_house_qr", "cpqr_krp_qr"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -167,6 +175,34 @@ def cp_als_qr_fit_exact(ctx) -> float:
     return f.value
 
 
+def cp_als_qr_set_timing(ctx, on: bool) -> None:
+    _check(lib().cp_als_qr_set_timing(ctx, int(bool(on))), "cp_als_qr_set_timing")
+
+
+def cp_als_qr_run_host(dims: Sequence[int], R: int, X_host: np.ndarray, A0=None, options: Optional[Options] = None,
+                       tol: float = 1e-6, max_sweeps: int = 100, stream: int = 0):
+    """Host tensor in, host factors out (copies inside the call).  Returns (A list, lambda,
+    final_fit, sweeps, converged)."""
+    X_host = np.ascontiguousarray(X_host)
+    x64 = X_host.dtype == np.float64
+    N = len(dims)
+    a0 = None
+    keep = []
+    if A0 is not None:
+        keep = [np.ascontiguousarray(a, dtype=np.float64) for a in A0]
+        a0 = (C.POINTER(C.c_double) * N)(*[_dptr(a) for a in keep])
+    outs = [np.zeros((int(d), int(R))) for d in dims]
+    aout = (C.POINTER(C.c_double) * N)(*[_dptr(a) for a in outs])
+    lam = np.zeros(int(R))
+    f = C.c_double()
+    ns = C.c_int32()
+    st = lib().cp_als_qr_run_host(N, _i64(dims), int(R), C.c_void_p(X_host.ctypes.data), int(x64), a0,
+                                  C.byref(options) if options is not None else None, float(tol), int(max_sweeps),
+                                  aout, _dptr(lam), C.byref(f), C.byref(ns), C.c_void_p(int(stream)))
+    _check(st, "cp_als_qr_run_host", allow=(OK, ENOTCONV))
+    return outs, lam, f.value, ns.value, st == OK
+
+
 def cp_als_qr_destroy(ctx) -> None:
     if ctx:
         lib().cp_als_qr_destroy(ctx)
@@ -224,6 +260,9 @@ class Decomposition:
 
     def fit_exact(self) -> float:
         return cp_als_qr_fit_exact(self.ctx)
+
+    def set_timing(self, on: bool) -> None:
+        cp_als_qr_set_timing(self.ctx, on)
 
     def close(self):
         if self.ctx:

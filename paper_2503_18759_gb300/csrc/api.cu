@@ -84,6 +84,11 @@ struct cpqr_ctx {
   int tree = 2, prec = 0, extrap = 1;
   double alpha = kAlphaDefault, beta_fixed = 0.0;
   cudaStream_t st = nullptr;
+  cudaStream_t st2 = nullptr;      // side stream: Khatri-Rao QR overlapped with the TTM chain
+  cudaEvent_t ev_ready = nullptr;  // main stream: triangles R_k of the previous update ready
+  cudaEvent_t ev_z = nullptr;      // side stream: Q0, R0 of the upcoming update ready
+  bool z_pending = false;
+  int z_mode = -1;
   const void* X = nullptr;
   bool x64 = false;
   int64_t nX = 0;
@@ -105,6 +110,7 @@ struct cpqr_ctx {
   double* R0 = nullptr;
   double* V = nullptr;
   double* qr_work = nullptr;
+  double* zq_work = nullptr;
   double* fit_terms = nullptr;
   double* d_scalar = nullptr;
   unsigned int* dstatus = nullptr;
@@ -117,6 +123,14 @@ struct cpqr_ctx {
   std::map<int, NodeBuf> nodes;
   Pool pool;
 
+  // per-launch timing (CUDA events on st), buckets of cpqr.h
+  bool timing = false;
+  std::vector<cudaEvent_t> evpool;
+  std::vector<std::pair<int, int>> evused;  // (bucket, index of start event; end = +1)
+  double ms_bucket[CPQR_NBUCKETS] = {};
+  int64_t n_bucket[CPQR_NBUCKETS] = {};
+  int64_t launches = 0;
+
   double normX2 = 0.0;
   std::vector<double> fits;
   double beta_active = 0.0;
@@ -127,6 +141,11 @@ struct cpqr_ctx {
 
   ~cpqr_ctx() {
     if (st) cudaStreamSynchronize(st);
+    if (st2) cudaStreamSynchronize(st2);
+    for (cudaEvent_t e : evpool) cudaEventDestroy(e);
+    if (ev_ready) cudaEventDestroy(ev_ready);
+    if (ev_z) cudaEventDestroy(ev_z);
+    if (st2) cudaStreamDestroy(st2);
     pool.release();
     for (void* p : owned) cudaFree(p);
     if (h_pinned) cudaFreeHost(h_pinned);
@@ -157,6 +176,45 @@ namespace {
 cpqr_status fail(cpqr_ctx* ctx, cpqr_status s) {
   if (ctx && ctx->err == CPQR_OK) ctx->err = s;
   return s;
+}
+
+// Brackets one launch group with CUDA events when timing is on.
+struct Timed {
+  cpqr_ctx* ctx;
+  int bucket;
+  int idx = -1;
+  cudaStream_t s;
+  Timed(cpqr_ctx* c, int b, int nlaunch, cudaStream_t stream = nullptr) : ctx(c), bucket(b) {
+    s = stream ? stream : ctx->st;
+    ctx->launches += nlaunch;
+    if (!ctx->timing) return;
+    idx = (int)ctx->evused.size() * 2;
+    while ((int)ctx->evpool.size() < idx + 2) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) {
+        idx = -1;
+        return;
+      }
+      ctx->evpool.push_back(e);
+    }
+    cudaEventRecord(ctx->evpool[idx], s);
+  }
+  ~Timed() {
+    if (idx < 0) return;
+    cudaEventRecord(ctx->evpool[idx + 1], s);
+    ctx->evused.push_back({bucket, idx});
+  }
+};
+
+void collect_timing(cpqr_ctx* ctx) {
+  for (auto& u : ctx->evused) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ctx->evpool[u.second], ctx->evpool[u.second + 1]) == cudaSuccess) {
+      ctx->ms_bucket[u.first] += ms;
+      ctx->n_bucket[u.first] += 1;
+    }
+  }
+  ctx->evused.clear();
 }
 
 int64_t ipow(int64_t b, int e) {
@@ -208,6 +266,7 @@ cpqr_status run_ttm(cpqr_ctx* ctx, const Op& op) {
   void* out = nullptr;
   CK(ctx->pool.get(bytes, &out));
   cudaStream_t st = ctx->st;
+  Timed tm(ctx, sb.is_x ? CPQR_BUCKET_TTM_FULL : CPQR_BUCKET_TTM_DEEP, 1);
   if (ctx->prec == CPQR_PREC_FP64) {
     if (sb.is_x && !ctx->x64)
       CK(launch_ttm<float, double, double>((const float*)sb.p, ctx->Q[k], (double*)out, P, K, S, R, st));
@@ -234,7 +293,28 @@ void free_node(cpqr_ctx* ctx, int id) {
 
 cpqr_status stage_q(cpqr_ctx* ctx, int n) {
   if (ctx->prec != CPQR_PREC_SPLIT_BF16) return CPQR_OK;
+  Timed tm(ctx, CPQR_BUCKET_OTHER, 1);
   CK(launch_split_q(ctx->Q[n], ctx->dims[n], ctx->R, ctx->Qt[n], ctx->Rp, ctx->Kp[n], ctx->st));
+  return CPQR_OK;
+}
+
+// Alg. 3 lines 3-4 for mode n: QR of the Khatri-Rao product of the other triangles,
+// issued on the side stream as soon as the previous update has produced its R_k so
+// that it runs under the TTM chain of mode n.
+cpqr_status launch_z(cpqr_ctx* ctx, int n) {
+  TriPtrs tri{};
+  int m = 0;
+  for (int k = 0; k < ctx->N; ++k)
+    if (k != n) tri.p[m++] = ctx->Rf[k];
+  CK(cudaEventRecord(ctx->ev_ready, ctx->st));
+  CK(cudaStreamWaitEvent(ctx->st2, ctx->ev_ready, 0));
+  {
+    Timed tm(ctx, CPQR_BUCKET_Q0, 1, ctx->st2);
+    CK(launch_krp_qr(ctx->zplan, tri, ctx->Q0, ctx->R0, ctx->zq_work, ctx->dstatus, ctx->st2));
+  }
+  CK(cudaEventRecord(ctx->ev_z, ctx->st2));
+  ctx->z_pending = true;
+  ctx->z_mode = n;
   return CPQR_OK;
 }
 
@@ -244,25 +324,31 @@ cpqr_status run_update(cpqr_ctx* ctx, int n, int leaf, double beta) {
   const NodeBuf lb = it->second;
   const int N = ctx->N, R = ctx->R;
   cudaStream_t st = ctx->st;
-  // Alg. 3 lines 3-4: QR of the Khatri-Rao product of the other triangles.
-  TriPtrs tri{};
-  int m = 0;
-  for (int k = 0; k < N; ++k)
-    if (k != n) tri.p[m++] = ctx->Rf[k];
-  CK(launch_krp_qr(ctx->zplan, tri, ctx->Q0, ctx->R0, ctx->qr_work, ctx->dstatus, st));
+  if (!ctx->z_pending || ctx->z_mode != n) {
+    cpqr_status s = launch_z(ctx, n);
+    if (s != CPQR_OK) return s;
+  }
+  CK(cudaStreamWaitEvent(st, ctx->ev_z, 0));
+  ctx->z_pending = false;
   // Lines 5 and 7: V = Y_(n) [Q0 | Q0^{k-1}].
   int64_t P = ipow(R, n), S = ipow(R, N - 1 - n);
   const int64_t I = ctx->dims[n];
   const bool ext = (beta != 0.0) && ctx->has_prev[n];
   const int C = ext ? 2 * R : R;
-  if (ctx->prec == CPQR_PREC_FP64)
-    CK(launch_leaf_v<double>((const double*)lb.p, P, I, S, ctx->Q0, ctx->Q0prev[n], R, C, ctx->V, st));
-  else
-    CK(launch_leaf_v<float>((const float*)lb.p, P, I, S, ctx->Q0, ctx->Q0prev[n], R, C, ctx->V, st));
+  {
+    Timed tm(ctx, CPQR_BUCKET_APPLY_Q0, 2);
+    if (ctx->prec == CPQR_PREC_FP64)
+      CK(launch_leaf_v<double>((const double*)lb.p, P, I, S, ctx->Q0, ctx->Q0prev[n], R, C, ctx->V, st));
+    else
+      CK(launch_leaf_v<float>((const float*)lb.p, P, I, S, ctx->Q0, ctx->Q0prev[n], R, C, ctx->V, st));
+  }
   // Lines 8-10.
   FinishOut fo{ctx->A[n], ctx->lambda, ctx->Q[n], ctx->Rf[n], ctx->Qf[n], ctx->fit_terms};
-  CK(launch_mode_finish(ctx->V, C, ctx->R0, ext ? beta : 0.0, ctx->alpha, I, R, fo, ctx->qr_work, ctx->dstatus,
-                        st));
+  {
+    Timed tm(ctx, CPQR_BUCKET_QR, 1);
+    CK(launch_mode_finish(ctx->V, C, ctx->R0, ext ? beta : 0.0, ctx->alpha, I, R, fo, ctx->qr_work,
+                          ctx->dstatus, st));
+  }
   cpqr_status s = stage_q(ctx, n);
   if (s != CPQR_OK) return s;
   std::swap(ctx->Q0, ctx->Q0prev[n]);
@@ -271,9 +357,13 @@ cpqr_status run_update(cpqr_ctx* ctx, int n, int leaf, double beta) {
 }
 
 cpqr_status read_fit(cpqr_ctx* ctx, double* fit) {
-  CK(cudaMemcpyAsync(ctx->h_pinned, ctx->fit_terms, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
-  CK(cudaMemcpyAsync(ctx->h_pinned + 2, ctx->dstatus, sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->st));
+  {
+    Timed tm(ctx, CPQR_BUCKET_OTHER, 0);
+    CK(cudaMemcpyAsync(ctx->h_pinned, ctx->fit_terms, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaMemcpyAsync(ctx->h_pinned + 2, ctx->dstatus, sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->st));
+  }
   CK(cudaStreamSynchronize(ctx->st));
+  if (ctx->timing) collect_timing(ctx);
   unsigned int ds;
   std::memcpy(&ds, ctx->h_pinned + 2, sizeof(ds));
   if (ds & CPQR_DEV_TIMEOUT) return fail(ctx, CPQR_ETIMEOUT);
@@ -311,8 +401,18 @@ cpqr_status one_sweep(cpqr_ctx* ctx, double* fit_out) {
   } catch (const std::exception&) {
     return fail(ctx, CPQR_EINVAL);
   }
-  for (const Op& op : ctx->ops) {
+  for (size_t i = 0; i < ctx->ops.size(); ++i) {
+    const Op& op = ctx->ops[i];
     cpqr_status s = CPQR_OK;
+    if (op.kind == OP_TTM && !ctx->z_pending) {
+      // first TTM of the next mode's chain: start its Khatri-Rao QR alongside
+      for (size_t k = i + 1; k < ctx->ops.size(); ++k)
+        if (ctx->ops[k].kind == OP_UPDATE) {
+          s = launch_z(ctx, ctx->ops[k].a);
+          break;
+        }
+      if (s != CPQR_OK) return s;
+    }
     if (op.kind == OP_TTM) s = run_ttm(ctx, op);
     else if (op.kind == OP_UPDATE) s = run_update(ctx, op.a, op.b, beta);
     else free_node(ctx, op.a);
@@ -418,6 +518,10 @@ cpqr_status cp_als_qr_init(cpqr_ctx** out, int32_t N, const int64_t* dims, int32
   CK(ctx->alloc(&ctx->R0, (size_t)R * R));
   CK(ctx->alloc(&ctx->V, Imax * 2 * R));
   CK(ctx->alloc(&ctx->qr_work, std::max<int64_t>(M0, Imax) * R));
+  CK(ctx->alloc(&ctx->zq_work, M0 * R));
+  CK(cudaStreamCreateWithFlags(&ctx->st2, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&ctx->ev_ready, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&ctx->ev_z, cudaEventDisableTiming));
   CK(ctx->alloc(&ctx->fit_terms, 2));
   CK(ctx->alloc(&ctx->d_scalar, 2));
   CK(ctx->alloc(&ctx->dstatus, 1));
@@ -554,7 +658,25 @@ cpqr_status cp_als_qr_stats(cpqr_ctx* ctx, cpqr_stats* out) {
   out->beta = ctx->last_beta;
   out->proposals = ctx->proposals;
   out->accepted = ctx->accepted;
+  out->launches = ctx->launches;
+  for (int b = 0; b < CPQR_NBUCKETS; ++b) {
+    out->ms_bucket[b] = ctx->ms_bucket[b];
+    out->n_bucket[b] = ctx->n_bucket[b];
+  }
   return ctx->err;
+}
+
+cpqr_status cp_als_qr_set_timing(cpqr_ctx* ctx, int32_t on) {
+  if (!ctx) return CPQR_EINVAL;
+  if (ctx->err != CPQR_OK) return ctx->err;
+  CK(cudaStreamSynchronize(ctx->st));
+  ctx->evused.clear();
+  ctx->timing = on != 0;
+  for (int b = 0; b < CPQR_NBUCKETS; ++b) {
+    ctx->ms_bucket[b] = 0.0;
+    ctx->n_bucket[b] = 0;
+  }
+  return CPQR_OK;
 }
 
 cpqr_status cp_als_qr_fit_exact(cpqr_ctx* ctx, double* fit) {
@@ -575,6 +697,36 @@ cpqr_status cp_als_qr_fit_exact(cpqr_ctx* ctx, double* fit) {
 }
 
 void cp_als_qr_destroy(cpqr_ctx* ctx) { delete ctx; }
+
+cpqr_status cp_als_qr_run_host(int32_t N, const int64_t* dims, int32_t R, const void* X_host, int32_t x_is_fp64,
+                               const double* const* A0_host, const cpqr_options* opt, double tol,
+                               int32_t max_sweeps, double* const* A_out_host, double* lambda_out_host,
+                               double* final_fit, int32_t* sweeps_done, void* stream) {
+  if (N < 3 || N > CPQR_MAXN || !dims || !X_host || !A_out_host) return CPQR_EINVAL;
+  int64_t n = 1;
+  for (int k = 0; k < N; ++k) {
+    if (dims[k] < 1) return CPQR_EINVAL;
+    n *= dims[k];
+  }
+  const size_t bytes = (size_t)n * (x_is_fp64 ? 8 : 4);
+  cudaStream_t st = (cudaStream_t)stream;
+  void* X = nullptr;
+  if (cudaMalloc(&X, bytes) != cudaSuccess) return CPQR_ENOMEM;
+  cpqr_status s = CPQR_OK;
+  if (cudaMemcpyAsync(X, X_host, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) s = CPQR_ECUDA;
+  cpqr_ctx* ctx = nullptr;
+  if (s == CPQR_OK) s = cp_als_qr_init(&ctx, N, dims, R, X, x_is_fp64, A0_host, opt, stream);
+  if (s == CPQR_OK) {
+    cpqr_status fs = cp_als_qr_fit(ctx, tol, max_sweeps, final_fit, sweeps_done);
+    if (fs != CPQR_OK && fs != CPQR_ENOTCONV) s = fs;
+    for (int k = 0; k < N && s == CPQR_OK; ++k)
+      s = cp_als_qr_get(ctx, k, A_out_host[k], k == N - 1 ? lambda_out_host : nullptr, nullptr, nullptr);
+    if (s == CPQR_OK) s = fs;
+  }
+  cp_als_qr_destroy(ctx);
+  cudaFree(X);
+  return s;
+}
 
 cpqr_status cp_als_qr_schedule(int32_t N, const int64_t* dims, int32_t R, int32_t tree, int32_t nsweeps,
                                int32_t* ops, int64_t cap, int64_t* count, int64_t* flops) {

@@ -14,8 +14,7 @@
 
 namespace cpqr {
 
-// Cluster size of the FP64 small-QR kernels (CTAs per cluster) and their block size.
-constexpr int kQrCluster = 8;
+// Block size of the FP64 small-QR kernels.
 constexpr int kQrThreads = 256;
 
 // ----- TTM (ttm.cu) -----

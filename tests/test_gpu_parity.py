@@ -158,3 +158,23 @@ def test_cube60_fifty_sweeps_parity():
         assert o.subspace_sine(A[n], ref.A[n]) <= 1e-10
         assert np.allclose(Q[n].T @ Q[n], np.eye(5), atol=1e-13)
     assert fits[-1] > 0.9998
+
+
+MIXED = [
+    ("mixed_order3", dict(dims=[40, 36, 33], R=8, c=0.5, eta=1e-2), b.TREE_RESTRUCTURED, b.EXTRAP_FIXED, 0.01, 8),
+    ("mixed_order4", dict(dims=[14, 12, 13, 11], R=5, c=0.3, eta=1e-2), b.TREE_RESTRUCTURED, b.EXTRAP_NONE, 0.0, 6),
+    ("mixed_order5", dict(dims=[8, 7, 9, 8, 7], R=4, c=None, eta=1e-2), b.TREE_STANDARD, b.EXTRAP_FIXED, 0.01, 5),
+]
+
+
+@pytest.mark.parametrize("name,cfg,tree,extrap,beta,sweeps", MIXED, ids=[c[0] for c in MIXED])
+def test_split_precision_solver_tracks_oracle(name, cfg, tree, extrap, beta, sweeps):
+    """Mixed path (FP32 / split-bf16 TTMs, FP64 QRs): per-sweep fit within 1e-4 and factor
+    subspaces within 1e-4 of the FP64 oracle on the same FP32 tensor."""
+    cfg = dict(cfg)
+    prob = inputs.make_problem(name, cfg.pop("dims"), cfg.pop("R"), seed=4, dtype=np.float32, **cfg)
+    fits, A, lam, Q, Rn, st = _run_gpu(prob, tree, extrap, beta, sweeps, prec=b.PREC_SPLIT_BF16)
+    ref = _run_oracle(prob, tree, extrap, beta, sweeps)
+    assert np.max(np.abs(fits - np.array(ref.fits))) <= 1e-4, (fits, ref.fits)
+    for n in range(len(prob.dims)):
+        assert o.subspace_sine(A[n], ref.A[n]) <= 1e-4
