@@ -1,0 +1,42 @@
+"""GPU parity of the split-bf16 tensor-core TTM (tcgen05) against the FP64 oracle TTM."""
+import numpy as np
+import pytest
+
+from oracle import cpqr_oracle as o
+from paper_2503_18759_gb300 import binding as b
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2503_18759_gb300 import build
+    build.build()
+    b.lib()
+
+
+# (P, K, S, R): several tiles, ragged s blocks, odd half-tile counts, K not a multiple of 64,
+# R padded to 16 / 32, and the 400^3 mode-1 / mode-2 shapes.
+SHAPES = [(1, 64, 128, 32), (3, 64, 64, 16), (2, 50, 72, 5), (5, 37, 8, 24), (7, 129, 200, 32), (1, 400, 4096, 32),
+          (40, 48, 48, 16), (400, 400, 400, 32), (1, 400, 160000, 32), (3, 512, 136, 30)]
+
+
+@pytest.mark.parametrize("P,K,S,R", SHAPES)
+def test_ttm_split_bf16_tensor_cores(P, K, S, R):
+    g = np.random.default_rng(P * 1000 + K + S + R)
+    X = g.standard_normal((P, K, S)).astype(np.float32)
+    Q, _ = np.linalg.qr(g.standard_normal((K, R)))
+    ref = o.ttm_qt(X.astype(np.float64), Q, 1)
+    Xd = torch.from_numpy(X).to(DEV)
+    Qd = torch.from_numpy(np.ascontiguousarray(Q)).to(DEV)
+    out = torch.full(ref.shape, float("nan"), dtype=torch.float32, device=DEV)
+    b.cpqr_ttm(Xd.data_ptr(), [P, K, S], 1, Qd.data_ptr(), R, out.data_ptr(), b.TTM_SPLIT_BF16)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().astype(np.float64)
+    assert np.isfinite(got).all()
+    # hi*hi + hi*lo + lo*hi keeps ~16 significant bits of each operand: per-term relative error
+    # about 2^-16, summed with random signs over K terms, against outputs of size ~sqrt(K).
+    err = np.max(np.abs(got - ref)) / np.max(np.abs(ref))
+    assert err < 2e-4, err
