@@ -517,6 +517,7 @@ cudaError_t run(QrParams& p, cudaStream_t st) {
 }  // namespace
 
 #ifdef CPQR_QR_PHASES
+// Profiling build only: %globaltimer stamps of the last cluster-QR launch (rank 0).
 extern "C" void cpqr_debug_qr_phases(unsigned long long* out) {
   cudaMemcpyFromSymbol(out, g_qr_phase, sizeof(g_qr_phase));
 }
