@@ -80,7 +80,7 @@ typedef struct {
   double beta_fixed;  /* beta for CPQR_EXTRAP_FIXED */
   uint64_t seed;      /* seed of the N(0,1) starting factors when A0 is NULL */
   const float* mlp_weights; /* host, CPQR_MLP_NPARAMS floats, for CPQR_EXTRAP_LEARNED (NULL =
-                               the rule alone) */
+                               the rule alone); copied at init */
 } cpqr_options;
 
 /* Time buckets of a sweep (the per-iteration breakdown of Section 4.3 plus the
@@ -200,9 +200,57 @@ cpqr_status cpqr_house_qr(const double* A_dev, int64_t M, int32_t R, double* Q_d
 cpqr_status cpqr_krp_qr(const double* Rs_dev, int32_t m, int32_t R, double* Q0_dev,
                         double* R0_dev, void* stream);
 
-/* Number of float parameters of the learned beta model (3 hidden layers of 128). */
-#define CPQR_MLP_FEATURES 40
+/* ---- Learned extrapolation proposer (no counterpart in the paper; it proposes the beta of
+ *      eq. 19 and is judged against the Section 4.2 rule) ----
+ * A multilayer perceptron F -> 128 -> 128 -> 128 -> C (ReLU), weights and activations bf16,
+ * FP32 accumulation, FP32 master parameters packed as [W_l (out x in row-major), b_l] for
+ * l = 0..3.  Class c proposes beta = cp_als_qr_mlp_beta(c). */
+#define CPQR_MLP_FEATURES 32
 #define CPQR_MLP_HIDDEN 128
+#define CPQR_MLP_CLASSES 8
+#define CPQR_MLP_NPARAMS (32 * 128 + 128 + 2 * (128 * 128 + 128) + 128 * 8 + 8)
+
+/* beta of class c (0 <= c < CPQR_MLP_CLASSES); class 0 is beta = 0; NaN otherwise. */
+double cp_als_qr_mlp_beta(int32_t c);
+
+/* Feature vector (CPQR_MLP_FEATURES floats, host) after sweep n from the fits and betas of
+ * sweeps 1..n (host arrays of n doubles), the beta the Section 4.2 rule would use next and
+ * whether the rule has activated.  For the last 8 sweeps j (most recent first):
+ * log10(1 - fit)/12, signed log of the fit change, log10(beta + 1e-8)/8; then log10(n+1)/3,
+ * log10(rule_beta + 1e-8)/8, the activation flag; the rest zero. */
+cpqr_status cpqr_mlp_features(const double* fits, const double* betas, int32_t n, double rule_beta,
+                              int32_t activated, float* out_host);
+
+/* Device workspace bytes the MLP entry points need for a batch of B rows. */
+int64_t cpqr_mlp_work_bytes(int32_t B);
+
+/* logits (device, B x C) of the features X (device, B x F) under params (device, FP32). */
+cpqr_status cpqr_mlp_forward(const float* params_dev, const float* X_dev, int32_t B, float* logits_dev,
+                             void* work_dev, void* stream);
+
+/* Mean softmax cross-entropy of labels y (device int32, B) and its gradient with respect to
+ * params: grad_dev (CPQR_MLP_NPARAMS floats), loss_dev (1 float). */
+cpqr_status cpqr_mlp_grad(const float* params_dev, const float* X_dev, const int32_t* y_dev, int32_t B,
+                          float* grad_dev, float* loss_dev, void* work_dev, void* stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on params with moments m, v (device). */
+cpqr_status cpqr_mlp_adam(float* params_dev, float* m_dev, float* v_dev, const float* grad_dev, float lr,
+                          int32_t step, void* stream);
+
+/* ---- Checkpoint / rollback of a context (used for speculative sweeps) ----
+ * checkpoint: saves every piece of solver state (factors, their QRs, Q0^{k-1}, weights, beta
+ * rule, schedule and cached tree nodes, fit history) in the context's one checkpoint slot.
+ * rollback: restores it (the slot stays valid, so several branches can start from it).
+ * commit: drops the slot.  One sweep with a forced beta: cp_als_qr_sweep_beta. */
+cpqr_status cp_als_qr_checkpoint(cpqr_ctx* ctx);
+cpqr_status cp_als_qr_rollback(cpqr_ctx* ctx);
+cpqr_status cp_als_qr_commit(cpqr_ctx* ctx);
+cpqr_status cp_als_qr_sweep_beta(cpqr_ctx* ctx, double beta, double* fit_host);
+
+/* Fit and beta history of a context: up to cap sweeps into fits_host / betas_host (either may
+ * be NULL); *n = sweeps done.  rule_beta / activated (may be NULL): the Section 4.2 rule state. */
+cpqr_status cp_als_qr_history(cpqr_ctx* ctx, double* fits_host, double* betas_host, int32_t cap, int32_t* n,
+                              double* rule_beta, int32_t* activated);
 
 #ifdef __cplusplus
 }

@@ -77,10 +77,25 @@ def lib() -> C.CDLL:
     L.cp_als_qr_run_host.argtypes = [i32, P(i64), i32, vp, i32, P(P(dbl)), P(Options), dbl, i32, P(P(dbl)),
                                      P(dbl), P(dbl), P(i32), vp]
     L.cpqr_ttm.argtypes = [vp, i32, P(i64), i32, vp, i32, vp, i32, vp]
+    L.cp_als_qr_mlp_beta.argtypes = [i32]
+    L.cp_als_qr_mlp_beta.restype = dbl
+    L.cpqr_mlp_features.argtypes = [P(dbl), P(dbl), i32, dbl, i32, P(C.c_float)]
+    L.cpqr_mlp_work_bytes.argtypes = [i32]
+    L.cpqr_mlp_work_bytes.restype = i64
+    L.cpqr_mlp_forward.argtypes = [vp, vp, i32, vp, vp, vp]
+    L.cpqr_mlp_grad.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp]
+    L.cpqr_mlp_adam.argtypes = [vp, vp, vp, vp, C.c_float, i32, vp]
+    L.cp_als_qr_checkpoint.argtypes = [vp]
+    L.cp_als_qr_rollback.argtypes = [vp]
+    L.cp_als_qr_commit.argtypes = [vp]
+    L.cp_als_qr_sweep_beta.argtypes = [vp, dbl, P(dbl)]
+    L.cp_als_qr_history.argtypes = [vp, P(dbl), P(dbl), i32, P(i32), P(dbl), P(i32)]
     L.cpqr_house_qr.argtypes = [vp, i64, i32, vp, vp, vp]
     L.cpqr_krp_qr.argtypes = [vp, i32, i32, vp, vp, vp]
     for name in ("cp_als_qr_init", "cp_als_qr_sweep", "cp_als_qr_fit", "cp_als_qr_get", "cp_als_qr_stats",
-                 "cp_als_qr_fit_exact", "cp_als_qr_set_timing", "cp_als_qr_schedule", "cp_als_qr_run_host", "cpqr_ttm", "cpqr_house_qr", "cpqr_krp_qr"):
+                 "cp_als_qr_fit_exact", "cp_als_qr_set_timing", "cp_als_qr_schedule", "cp_als_qr_run_host",
+                 "cpqr_mlp_features", "cpqr_mlp_forward", "cpqr_mlp_grad", "cpqr_mlp_adam", "cp_als_qr_checkpoint",
+                 "cp_als_qr_rollback", "cp_als_qr_commit", "cp_als_qr_sweep_beta", "cp_als_qr_history", "cpqr_ttm", "cpqr_house_qr", "cpqr_krp_qr"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -203,6 +218,75 @@ def cp_als_qr_run_host(dims: Sequence[int], R: int, X_host: np.ndarray, A0=None,
     return outs, lam, f.value, ns.value, st == OK
 
 
+MLP_FEATURES, MLP_HIDDEN, MLP_CLASSES = 32, 128, 8
+MLP_NPARAMS = 32 * 128 + 128 + 2 * (128 * 128 + 128) + 128 * 8 + 8
+
+
+def cp_als_qr_mlp_beta(c: int) -> float:
+    return lib().cp_als_qr_mlp_beta(int(c))
+
+
+def cpqr_mlp_features(fits, betas, rule_beta: float, activated: bool) -> np.ndarray:
+    f = np.ascontiguousarray(fits, dtype=np.float64)
+    bt = np.ascontiguousarray(betas, dtype=np.float64)
+    out = np.zeros(MLP_FEATURES, dtype=np.float32)
+    _check(lib().cpqr_mlp_features(_dptr(f), _dptr(bt), len(f), float(rule_beta), int(bool(activated)),
+                                   out.ctypes.data_as(C.POINTER(C.c_float))), "cpqr_mlp_features")
+    return out
+
+
+def cpqr_mlp_work_bytes(B: int) -> int:
+    return int(lib().cpqr_mlp_work_bytes(int(B)))
+
+
+def cpqr_mlp_forward(params_dev: int, X_dev: int, B: int, logits_dev: int, work_dev: int, stream: int = 0) -> None:
+    _check(lib().cpqr_mlp_forward(C.c_void_p(params_dev), C.c_void_p(X_dev), int(B), C.c_void_p(logits_dev),
+                                  C.c_void_p(work_dev), C.c_void_p(stream)), "cpqr_mlp_forward")
+
+
+def cpqr_mlp_grad(params_dev: int, X_dev: int, y_dev: int, B: int, grad_dev: int, loss_dev: int, work_dev: int,
+                  stream: int = 0) -> None:
+    _check(lib().cpqr_mlp_grad(C.c_void_p(params_dev), C.c_void_p(X_dev), C.c_void_p(y_dev), int(B),
+                               C.c_void_p(grad_dev), C.c_void_p(loss_dev), C.c_void_p(work_dev), C.c_void_p(stream)),
+           "cpqr_mlp_grad")
+
+
+def cpqr_mlp_adam(params_dev: int, m_dev: int, v_dev: int, grad_dev: int, lr: float, step: int,
+                  stream: int = 0) -> None:
+    _check(lib().cpqr_mlp_adam(C.c_void_p(params_dev), C.c_void_p(m_dev), C.c_void_p(v_dev), C.c_void_p(grad_dev),
+                               float(lr), int(step), C.c_void_p(stream)), "cpqr_mlp_adam")
+
+
+def cp_als_qr_checkpoint(ctx) -> None:
+    _check(lib().cp_als_qr_checkpoint(ctx), "cp_als_qr_checkpoint")
+
+
+def cp_als_qr_rollback(ctx) -> None:
+    _check(lib().cp_als_qr_rollback(ctx), "cp_als_qr_rollback")
+
+
+def cp_als_qr_commit(ctx) -> None:
+    _check(lib().cp_als_qr_commit(ctx), "cp_als_qr_commit")
+
+
+def cp_als_qr_sweep_beta(ctx, beta: float) -> float:
+    f = C.c_double()
+    _check(lib().cp_als_qr_sweep_beta(ctx, float(beta), C.byref(f)), "cp_als_qr_sweep_beta")
+    return f.value
+
+
+def cp_als_qr_history(ctx, cap: int = 100000):
+    fits = np.zeros(cap)
+    betas = np.zeros(cap)
+    n = C.c_int32()
+    rb = C.c_double()
+    act = C.c_int32()
+    _check(lib().cp_als_qr_history(ctx, _dptr(fits), _dptr(betas), int(cap), C.byref(n), C.byref(rb), C.byref(act)),
+           "cp_als_qr_history")
+    m = min(n.value, cap)
+    return fits[:m], betas[:m], rb.value, bool(act.value)
+
+
 def cp_als_qr_destroy(ctx) -> None:
     if ctx:
         lib().cp_als_qr_destroy(ctx)
@@ -263,6 +347,21 @@ class Decomposition:
 
     def set_timing(self, on: bool) -> None:
         cp_als_qr_set_timing(self.ctx, on)
+
+    def checkpoint(self):
+        cp_als_qr_checkpoint(self.ctx)
+
+    def rollback(self):
+        cp_als_qr_rollback(self.ctx)
+
+    def commit(self):
+        cp_als_qr_commit(self.ctx)
+
+    def sweep_beta(self, beta: float) -> float:
+        return cp_als_qr_sweep_beta(self.ctx, beta)
+
+    def history(self):
+        return cp_als_qr_history(self.ctx)
 
     def close(self):
         if self.ctx:

@@ -78,6 +78,21 @@ uint64_t splitmix64(uint64_t& s) {
 
 }  // namespace
 
+struct Checkpoint {
+  bool valid = false;
+  void* arena = nullptr;  // device copy of the state arena
+  std::unique_ptr<Schedule> sched;
+  std::map<int, NodeBuf> nodes;
+  std::vector<double> fits, betas;
+  double beta_active = 0.0;
+  bool activated = false;
+  double last_beta = 0.0;
+  int64_t sweeps = 0;
+  bool has_prev[CPQR_MAXN] = {};
+  double* Q0prev[CPQR_MAXN] = {};
+  double* Q0 = nullptr;
+};
+
 struct cpqr_ctx {
   int N = 0, R = 0;
   std::vector<int64_t> dims;
@@ -95,6 +110,15 @@ struct cpqr_ctx {
   cpqr_status err = CPQR_OK;
 
   std::vector<void*> owned;  // cudaMalloc'd, freed at destroy
+  void* arena = nullptr;     // every per-mode state array (factors, QRs, Q0 history, staging)
+  size_t arena_bytes = 0;
+  Checkpoint ckpt[2];        // 0: caller's slot, 1: learned-proposal speculation
+  std::map<int, NodeBuf> orphans;  // nodes freed while a checkpoint still references them
+  // learned proposer
+  float* mlp_params = nullptr;
+  void* mlp_work = nullptr;
+  float* mlp_io = nullptr;     // device: features (F) then logits (C)
+  float* h_mlp = nullptr;      // pinned host: features + logits
   double* A[CPQR_MAXN] = {};
   double* Q[CPQR_MAXN] = {};
   double* Rf[CPQR_MAXN] = {};
@@ -132,6 +156,7 @@ struct cpqr_ctx {
   int64_t launches = 0;
 
   double normX2 = 0.0;
+  std::vector<double> betas;
   std::vector<double> fits;
   double beta_active = 0.0;
   bool activated = false;
@@ -143,12 +168,15 @@ struct cpqr_ctx {
     if (st) cudaStreamSynchronize(st);
     if (st2) cudaStreamSynchronize(st2);
     for (cudaEvent_t e : evpool) cudaEventDestroy(e);
+    for (Checkpoint& c : ckpt)
+      if (c.arena) cudaFree(c.arena);
     if (ev_ready) cudaEventDestroy(ev_ready);
     if (ev_z) cudaEventDestroy(ev_z);
     if (st2) cudaStreamDestroy(st2);
     pool.release();
     for (void* p : owned) cudaFree(p);
     if (h_pinned) cudaFreeHost(h_pinned);
+    if (h_mlp) cudaFreeHost(h_mlp);
   }
 
   template <typename T>
@@ -284,11 +312,91 @@ cpqr_status run_ttm(cpqr_ctx* ctx, const Op& op) {
   return CPQR_OK;
 }
 
+bool pinned(const cpqr_ctx* ctx, int id) {
+  for (const Checkpoint& c : ctx->ckpt)
+    if (c.valid && c.nodes.count(id)) return true;
+  return false;
+}
+
 void free_node(cpqr_ctx* ctx, int id) {
   auto it = ctx->nodes.find(id);
   if (it == ctx->nodes.end() || it->second.is_x) return;
-  ctx->pool.put(it->second.bytes, it->second.p);
+  if (pinned(ctx, id)) ctx->orphans[id] = it->second;  // a checkpoint still needs its contents
+  else ctx->pool.put(it->second.bytes, it->second.p);
   ctx->nodes.erase(it);
+}
+
+// Returns orphaned node buffers that no checkpoint and no live node references to the pool.
+void sweep_orphans(cpqr_ctx* ctx) {
+  for (auto it = ctx->orphans.begin(); it != ctx->orphans.end();) {
+    if (!pinned(ctx, it->first) && !ctx->nodes.count(it->first)) {
+      ctx->pool.put(it->second.bytes, it->second.p);
+      it = ctx->orphans.erase(it);
+    } else {
+      ++it;
+    }
+  }
+}
+
+cpqr_status checkpoint_save(cpqr_ctx* ctx, int slot) {
+  Checkpoint& c = ctx->ckpt[slot];
+  if (!c.arena) CK(cudaMalloc(&c.arena, ctx->arena_bytes));
+  CK(cudaMemcpyAsync(c.arena, ctx->arena, ctx->arena_bytes, cudaMemcpyDeviceToDevice, ctx->st));
+  if (c.valid) {  // re-saving: previously pinned nodes may become free
+    c.valid = false;
+    sweep_orphans(ctx);
+  }
+  c.sched.reset(new Schedule(*ctx->sched));
+  c.nodes = ctx->nodes;
+  c.fits = ctx->fits;
+  c.betas = ctx->betas;
+  c.beta_active = ctx->beta_active;
+  c.activated = ctx->activated;
+  c.last_beta = ctx->last_beta;
+  c.sweeps = ctx->sweeps;
+  for (int n = 0; n < CPQR_MAXN; ++n) {
+    c.has_prev[n] = ctx->has_prev[n];
+    c.Q0prev[n] = ctx->Q0prev[n];
+  }
+  c.Q0 = ctx->Q0;
+  c.valid = true;
+  return CPQR_OK;
+}
+
+cpqr_status checkpoint_restore(cpqr_ctx* ctx, int slot) {
+  Checkpoint& c = ctx->ckpt[slot];
+  if (!c.valid) return CPQR_EINVAL;
+  CK(cudaMemcpyAsync(ctx->arena, c.arena, ctx->arena_bytes, cudaMemcpyDeviceToDevice, ctx->st));
+  for (auto& kv : ctx->nodes) {
+    if (kv.second.is_x || c.nodes.count(kv.first)) continue;
+    if (pinned(ctx, kv.first)) ctx->orphans[kv.first] = kv.second;
+    else ctx->pool.put(kv.second.bytes, kv.second.p);
+  }
+  ctx->nodes = c.nodes;
+  for (auto& kv : ctx->nodes) ctx->orphans.erase(kv.first);
+  ctx->sched.reset(new Schedule(*c.sched));
+  ctx->fits = c.fits;
+  ctx->betas = c.betas;
+  ctx->beta_active = c.beta_active;
+  ctx->activated = c.activated;
+  ctx->last_beta = c.last_beta;
+  ctx->sweeps = c.sweeps;
+  for (int n = 0; n < CPQR_MAXN; ++n) {
+    ctx->has_prev[n] = c.has_prev[n];
+    ctx->Q0prev[n] = c.Q0prev[n];
+  }
+  ctx->Q0 = c.Q0;
+  ctx->z_pending = false;
+  return CPQR_OK;
+}
+
+void checkpoint_drop(cpqr_ctx* ctx, int slot) {
+  Checkpoint& c = ctx->ckpt[slot];
+  if (!c.valid) return;
+  c.valid = false;
+  c.nodes.clear();
+  c.sched.reset();
+  sweep_orphans(ctx);
 }
 
 cpqr_status stage_q(cpqr_ctx* ctx, int n) {
@@ -380,6 +488,7 @@ double beta_for_sweep(cpqr_ctx* ctx) {
   switch (ctx->extrap) {
     case CPQR_EXTRAP_NONE: return 0.0;
     case CPQR_EXTRAP_FIXED: return ctx->sweeps >= 1 ? ctx->beta_fixed : 0.0;
+    case CPQR_EXTRAP_LEARNED:
     default: return ctx->beta_active;
   }
 }
@@ -393,8 +502,8 @@ void observe_fit(cpqr_ctx* ctx, double fit) {
   }
 }
 
-cpqr_status one_sweep(cpqr_ctx* ctx, double* fit_out) {
-  const double beta = beta_for_sweep(ctx);
+cpqr_status one_sweep(cpqr_ctx* ctx, double* fit_out, const double* forced_beta = nullptr) {
+  const double beta = forced_beta ? *forced_beta : beta_for_sweep(ctx);
   ctx->ops.clear();
   try {
     ctx->sched->next_sweep(ctx->ops);
@@ -423,9 +532,79 @@ cpqr_status one_sweep(cpqr_ctx* ctx, double* fit_out) {
   if (s != CPQR_OK) return s;
   ctx->last_beta = beta;
   ++ctx->sweeps;
+  ctx->betas.push_back(beta);
   observe_fit(ctx, fit);
   if (fit_out) *fit_out = fit;
   return CPQR_OK;
+}
+
+// Section 4.2 rule's beta for the next sweep (what CPQR_EXTRAP_PAPER would use).
+double rule_beta_next(const cpqr_ctx* ctx) { return ctx->beta_active; }
+
+const double kMlpBetas[CPQR_MLP_CLASSES] = {0.0, 5e-5, 2e-4, 5e-4, 2e-3, 4e-3, 1e-2, 3e-2};
+
+void mlp_features(const double* fits, const double* betas, int n, double rule_beta, int activated, float* f) {
+  for (int i = 0; i < CPQR_MLP_FEATURES; ++i) f[i] = 0.f;
+  for (int j = 0; j < 8; ++j) {
+    const int k = n - 1 - j;  // sweep index (0-based) j sweeps back
+    if (k < 0) break;
+    const double fit = fits[k];
+    f[3 * j] = (float)(std::log10(std::max(1.0 - fit, 1e-12)) / 12.0);
+    if (k >= 1) {
+      const double d = fits[k] - fits[k - 1];
+      const double m = (std::log10(std::max(std::fabs(d), 1e-14)) + 14.0) / 14.0;
+      f[3 * j + 1] = (float)(d >= 0 ? m : -m);
+    }
+    f[3 * j + 2] = (float)(std::log10(betas[k] + 1e-8) / 8.0);
+  }
+  f[24] = (float)(std::log10((double)n + 1.0) / 3.0);
+  f[25] = (float)(std::log10(rule_beta + 1e-8) / 8.0);
+  f[26] = activated ? 1.f : 0.f;
+}
+
+// CPQR_EXTRAP_LEARNED: the network proposes beta; the sweep runs speculatively and is kept
+// only if its fit does not fall below the previous sweep's, else it is rolled back and
+// redone with the Section 4.2 rule's beta.
+cpqr_status learned_sweep(cpqr_ctx* ctx, double* fit_out) {
+  const double rule = rule_beta_next(ctx);
+  if (!ctx->mlp_params || ctx->fits.size() < 2) return one_sweep(ctx, fit_out, &rule);
+  float* hf = ctx->h_mlp;
+  mlp_features(ctx->fits.data(), ctx->betas.data(), (int)ctx->fits.size(), rule, ctx->activated ? 1 : 0, hf);
+  CK(cudaMemcpyAsync(ctx->mlp_io, hf, CPQR_MLP_FEATURES * sizeof(float), cudaMemcpyHostToDevice, ctx->st));
+  {
+    Timed tm(ctx, CPQR_BUCKET_OTHER, 7);
+    CK(mlp_forward(ctx->mlp_params, ctx->mlp_io, 1, ctx->mlp_io + CPQR_MLP_FEATURES, ctx->mlp_work, ctx->st));
+  }
+  CK(cudaMemcpyAsync(hf + CPQR_MLP_FEATURES, ctx->mlp_io + CPQR_MLP_FEATURES, CPQR_MLP_CLASSES * sizeof(float),
+                     cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  int best = 0;
+  for (int c = 1; c < CPQR_MLP_CLASSES; ++c)
+    if (hf[CPQR_MLP_FEATURES + c] > hf[CPQR_MLP_FEATURES + best]) best = c;
+  const double prop = kMlpBetas[best];
+  if (prop == rule) return one_sweep(ctx, fit_out, &rule);
+  const double prev = ctx->fits.back();
+  cpqr_status s = checkpoint_save(ctx, 1);
+  if (s != CPQR_OK) return s;
+  double f = 0.0;
+  s = one_sweep(ctx, &f, &prop);
+  if (s != CPQR_OK) return s;
+  ++ctx->proposals;
+  if (f >= prev) {
+    ++ctx->accepted;
+    checkpoint_drop(ctx, 1);
+    if (fit_out) *fit_out = f;
+    return CPQR_OK;
+  }
+  s = checkpoint_restore(ctx, 1);
+  if (s != CPQR_OK) return s;
+  checkpoint_drop(ctx, 1);
+  return one_sweep(ctx, fit_out, &rule);
+}
+
+cpqr_status next_sweep(cpqr_ctx* ctx, double* fit_out) {
+  if (ctx->extrap == CPQR_EXTRAP_LEARNED) return learned_sweep(ctx, fit_out);
+  return one_sweep(ctx, fit_out);
 }
 
 bool valid_enum(int v, int lo, int hi) { return v >= lo && v <= hi; }
@@ -506,15 +685,43 @@ cpqr_status cp_als_qr_init(cpqr_ctx** out, int32_t N, const int64_t* dims, int32
   int64_t Imax = 0;
   for (int n = 0; n < N; ++n) Imax = std::max(Imax, dims[n]);
   CK(cudaMallocHost(&ctx->h_pinned, 4 * sizeof(double)));
-  for (int n = 0; n < N; ++n) {
-    CK(ctx->alloc(&ctx->A[n], dims[n] * R));
-    CK(ctx->alloc(&ctx->Q[n], dims[n] * R));
-    CK(ctx->alloc(&ctx->Rf[n], (size_t)R * R));
-    CK(ctx->alloc(&ctx->Qf[n], dims[n] * R));
-    CK(ctx->alloc(&ctx->Q0prev[n], M0 * R));
+  // Per-mode state lives in one arena so that a checkpoint is a single copy.
+  const bool split = opt.prec == CPQR_PREC_SPLIT_BF16;
+  ctx->Rp = ((R + 15) / 16) * 16;
+  {
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+      size_t o = off;
+      off += (bytes + 255) / 256 * 256;
+      return o;
+    };
+    size_t oA[CPQR_MAXN], oQ[CPQR_MAXN], oR[CPQR_MAXN], oQf[CPQR_MAXN], oP[CPQR_MAXN], oT[CPQR_MAXN];
+    for (int n = 0; n < N; ++n) {
+      ctx->Kp[n] = ((dims[n] + 63) / 64) * 64;
+      oA[n] = take(dims[n] * R * 8);
+      oQ[n] = take(dims[n] * R * 8);
+      oR[n] = take((size_t)R * R * 8);
+      oQf[n] = take(dims[n] * R * 4);
+      oP[n] = take(M0 * R * 8);
+      oT[n] = split ? take((size_t)2 * ctx->Rp * ctx->Kp[n] * 2) : 0;
+    }
+    size_t oQ0 = take(M0 * R * 8), oL = take(R * 8);
+    ctx->arena_bytes = off;
+    CK(cudaMalloc(&ctx->arena, off));
+    ctx->owned.push_back(ctx->arena);
+    CK(cudaMemsetAsync(ctx->arena, 0, off, st));
+    char* a = static_cast<char*>(ctx->arena);
+    for (int n = 0; n < N; ++n) {
+      ctx->A[n] = (double*)(a + oA[n]);
+      ctx->Q[n] = (double*)(a + oQ[n]);
+      ctx->Rf[n] = (double*)(a + oR[n]);
+      ctx->Qf[n] = (float*)(a + oQf[n]);
+      ctx->Q0prev[n] = (double*)(a + oP[n]);
+      if (split) ctx->Qt[n] = (__nv_bfloat16*)(a + oT[n]);
+    }
+    ctx->Q0 = (double*)(a + oQ0);
+    ctx->lambda = (double*)(a + oL);
   }
-  CK(ctx->alloc(&ctx->lambda, R));
-  CK(ctx->alloc(&ctx->Q0, M0 * R));
   CK(ctx->alloc(&ctx->R0, (size_t)R * R));
   CK(ctx->alloc(&ctx->V, Imax * 2 * R));
   CK(ctx->alloc(&ctx->qr_work, std::max<int64_t>(M0, Imax) * R));
@@ -563,10 +770,7 @@ cpqr_status cp_als_qr_init(cpqr_ctx** out, int32_t N, const int64_t* dims, int32
   }
   // Split-precision staging.
   if (ctx->prec == CPQR_PREC_SPLIT_BF16) {
-    ctx->Rp = ((R + 15) / 16) * 16;
     for (int n = 0; n < N; ++n) {
-      ctx->Kp[n] = ((dims[n] + 63) / 64) * 64;
-      CK(ctx->alloc(&ctx->Qt[n], (size_t)2 * ctx->Rp * ctx->Kp[n]));
       cpqr_status s = stage_q(ctx, n);
       if (s != CPQR_OK) return s;
     }
@@ -588,6 +792,15 @@ cpqr_status cp_als_qr_init(cpqr_ctx** out, int32_t N, const int64_t* dims, int32
   }
   if (!(ctx->normX2 > 0.0) || !std::isfinite(ctx->normX2)) return CPQR_EINVAL;
 
+  if (ctx->extrap == CPQR_EXTRAP_LEARNED && opt.mlp_weights) {
+    CK(ctx->alloc(&ctx->mlp_params, CPQR_MLP_NPARAMS));
+    CK(cudaMemcpyAsync(ctx->mlp_params, opt.mlp_weights, CPQR_MLP_NPARAMS * sizeof(float), cudaMemcpyHostToDevice,
+                       st));
+    CK(ctx->alloc((char**)&ctx->mlp_work, (size_t)mlp_work_bytes(1)));
+    CK(ctx->alloc(&ctx->mlp_io, CPQR_MLP_FEATURES + CPQR_MLP_CLASSES));
+    CK(cudaMallocHost(&ctx->h_mlp, (CPQR_MLP_FEATURES + CPQR_MLP_CLASSES) * sizeof(float)));
+    CK(cudaStreamSynchronize(st));
+  }
   try {
     ctx->sched.reset(new Schedule(ctx->dims, R, ctx->tree));
   } catch (...) {
@@ -604,7 +817,7 @@ cpqr_status cp_als_qr_sweep(cpqr_ctx* ctx, int32_t nsweeps, double* fits_host) {
   if (nsweeps < 0) return CPQR_EINVAL;
   for (int i = 0; i < nsweeps; ++i) {
     double f = 0.0;
-    cpqr_status s = one_sweep(ctx, &f);
+    cpqr_status s = next_sweep(ctx, &f);
     if (s != CPQR_OK) return s;
     if (fits_host) fits_host[i] = f;
   }
@@ -619,7 +832,7 @@ cpqr_status cp_als_qr_fit(cpqr_ctx* ctx, double tol, int32_t max_sweeps, double*
   int done = 0;
   bool conv = false;
   for (int i = 0; i < max_sweeps; ++i) {
-    cpqr_status s = one_sweep(ctx, &f);
+    cpqr_status s = next_sweep(ctx, &f);
     if (s != CPQR_OK) return s;
     ++done;
     if (i >= 1 && std::fabs(f - prev) < tol) {
@@ -697,6 +910,82 @@ cpqr_status cp_als_qr_fit_exact(cpqr_ctx* ctx, double* fit) {
 }
 
 void cp_als_qr_destroy(cpqr_ctx* ctx) { delete ctx; }
+
+cpqr_status cp_als_qr_checkpoint(cpqr_ctx* ctx) {
+  if (!ctx) return CPQR_EINVAL;
+  if (ctx->err != CPQR_OK) return ctx->err;
+  return checkpoint_save(ctx, 0);
+}
+
+cpqr_status cp_als_qr_rollback(cpqr_ctx* ctx) {
+  if (!ctx) return CPQR_EINVAL;
+  if (ctx->err != CPQR_OK) return ctx->err;
+  return checkpoint_restore(ctx, 0);
+}
+
+cpqr_status cp_als_qr_commit(cpqr_ctx* ctx) {
+  if (!ctx) return CPQR_EINVAL;
+  if (ctx->err != CPQR_OK) return ctx->err;
+  checkpoint_drop(ctx, 0);
+  return CPQR_OK;
+}
+
+cpqr_status cp_als_qr_sweep_beta(cpqr_ctx* ctx, double beta, double* fit_host) {
+  if (!ctx || !(beta >= 0.0) || !std::isfinite(beta)) return CPQR_EINVAL;
+  if (ctx->err != CPQR_OK) return ctx->err;
+  return one_sweep(ctx, fit_host, &beta);
+}
+
+cpqr_status cp_als_qr_history(cpqr_ctx* ctx, double* fits_host, double* betas_host, int32_t cap, int32_t* n,
+                              double* rule_beta, int32_t* activated) {
+  if (!ctx) return CPQR_EINVAL;
+  const int m = (int)ctx->fits.size();
+  for (int i = 0; i < m && i < cap; ++i) {
+    if (fits_host) fits_host[i] = ctx->fits[i];
+    if (betas_host) betas_host[i] = ctx->betas[i];
+  }
+  if (n) *n = m;
+  if (rule_beta) *rule_beta = rule_beta_next(ctx);
+  if (activated) *activated = ctx->activated ? 1 : 0;
+  return ctx->err;
+}
+
+double cp_als_qr_mlp_beta(int32_t c) {
+  if (c < 0 || c >= CPQR_MLP_CLASSES) return NAN;
+  return kMlpBetas[c];
+}
+
+cpqr_status cpqr_mlp_features(const double* fits, const double* betas, int32_t n, double rule_beta,
+                              int32_t activated, float* out_host) {
+  if (!out_host || n < 0 || (n > 0 && (!fits || !betas))) return CPQR_EINVAL;
+  mlp_features(fits, betas, n, rule_beta, activated, out_host);
+  return CPQR_OK;
+}
+
+int64_t cpqr_mlp_work_bytes(int32_t B) { return B < 1 ? 0 : (int64_t)mlp_work_bytes(B); }
+
+cpqr_status cpqr_mlp_forward(const float* params_dev, const float* X_dev, int32_t B, float* logits_dev,
+                             void* work_dev, void* stream) {
+  if (!params_dev || !X_dev || !logits_dev || !work_dev || B < 1 || B > 65535) return CPQR_EINVAL;
+  return mlp_forward(params_dev, X_dev, B, logits_dev, work_dev, (cudaStream_t)stream) == cudaSuccess ? CPQR_OK
+                                                                                                     : CPQR_ECUDA;
+}
+
+cpqr_status cpqr_mlp_grad(const float* params_dev, const float* X_dev, const int32_t* y_dev, int32_t B,
+                          float* grad_dev, float* loss_dev, void* work_dev, void* stream) {
+  if (!params_dev || !X_dev || !y_dev || !grad_dev || !loss_dev || !work_dev || B < 1 || B > 65535)
+    return CPQR_EINVAL;
+  return mlp_grad(params_dev, X_dev, y_dev, B, grad_dev, loss_dev, work_dev, (cudaStream_t)stream) == cudaSuccess
+             ? CPQR_OK
+             : CPQR_ECUDA;
+}
+
+cpqr_status cpqr_mlp_adam(float* params_dev, float* m_dev, float* v_dev, const float* grad_dev, float lr,
+                          int32_t step, void* stream) {
+  if (!params_dev || !m_dev || !v_dev || !grad_dev || step < 1 || !(lr > 0.f)) return CPQR_EINVAL;
+  return mlp_adam(params_dev, m_dev, v_dev, grad_dev, lr, step, (cudaStream_t)stream) == cudaSuccess ? CPQR_OK
+                                                                                                   : CPQR_ECUDA;
+}
 
 cpqr_status cp_als_qr_run_host(int32_t N, const int64_t* dims, int32_t R, const void* X_host, int32_t x_is_fp64,
                                const double* const* A0_host, const cpqr_options* opt, double tol,

@@ -93,4 +93,11 @@ cudaError_t launch_residual2(const TX* X, int N, const int64_t* d, const double*
 
 cudaError_t launch_to_f32(const double* a, float* b, int64_t n, cudaStream_t st);
 
+// ----- learned proposer (mlp.cu) -----
+size_t mlp_work_bytes(int B);
+cudaError_t mlp_forward(const float* params, const float* X, int B, float* logits, void* work, cudaStream_t st);
+cudaError_t mlp_grad(const float* params, const float* X, const int32_t* y, int B, float* grad, float* loss,
+                     void* work, cudaStream_t st);
+cudaError_t mlp_adam(float* params, float* m, float* v, const float* grad, float lr, int step, cudaStream_t st);
+
 }  // namespace cpqr

@@ -137,17 +137,24 @@ def workload(name: str, seed: int = 0, **overrides) -> Problem:
     return make_problem(name, cfg.pop("dims"), cfg.pop("R"), seed=seed, **cfg)
 
 
-def training_problem(index: int, *, base_seed: int = 0, order: int = 3) -> Problem:
-    """One tensor of the extrapolation-learning set: sides U{64..256}, rank U{8..32},
-    congruence U[0, 0.95], relative noise log-uniform in [1e-4, 1e-2]."""
-    g = _rng(base_seed * 1_000_003 + index, 7)
-    if order == 3:
-        dims = [int(v) for v in g.integers(64, 257, size=3)]
-    else:
-        dims = [int(v) for v in g.integers(24, 65, size=order)]
-    R = int(g.integers(8, 33))
-    R = min(R, min(dims))
-    c = float(g.uniform(0.0, 0.95))
-    eta = float(10.0 ** g.uniform(-4.0, -2.0))
-    return make_problem(f"train{index}", dims, R, seed=base_seed * 1_000_003 + index, c=c, eta=eta,
-                        dtype=np.float32)
+def make_problem_device(name: str, dims: Sequence[int], R: int, *, seed: int, c=None, eta: float = 0.0,
+                        device: str = "cuda"):
+    """Same recipe as make_problem, with the dense tensor and the noise formed on the GPU by
+    torch (seeded torch generator) for large training sets; X is a float32 device tensor.
+    Factors and starting factors are drawn with numpy exactly as in make_problem."""
+    import torch
+
+    dims = [int(d) for d in dims]
+    B = gaussian_factors(dims, R, seed) if c is None else collinear_factors(dims, R, c, seed)
+    Bt = [torch.from_numpy(b).to(device) for b in B]
+    rows = Bt[0]
+    for Bn in Bt[1:-1]:
+        rows = (rows[:, None, :] * Bn[None, :, :]).reshape(-1, R)
+    X = (rows @ Bt[-1].T).reshape(dims)
+    if eta > 0:
+        gen = torch.Generator(device=device)
+        gen.manual_seed(int(seed) * 7919 + _STREAM_NOISE)
+        Nz = torch.randn(dims, generator=gen, device=device, dtype=torch.float64)
+        X = X + (eta * torch.linalg.vector_norm(X) / torch.linalg.vector_norm(Nz)) * Nz
+    X = X.to(torch.float32).contiguous()
+    return Problem(name, dims, R, X, init_factors(dims, R, seed), B, eta, seed, {"c": c, "dtype": "float32"})

@@ -1,0 +1,200 @@
+"""Training and evaluation of the learned extrapolation proposer.
+
+The solver itself generates the data: along a trajectory, at every sweep after the
+second, the state is checkpointed and each candidate beta (cp_als_qr_mlp_beta) is run
+for `horizon` sweeps; the candidate with the highest fit (ties: the smaller beta) is the
+label of the features of that state, and the trajectory continues with it.  The network
+(3 hidden layers of 128, bf16) is trained with the library's own forward / backward /
+Adam kernels.  Evaluation compares, on held-out tensors, sweeps and time to the fit
+tolerance with the learned proposer (judged against the Section 4.2 rule), with the rule
+alone and without extrapolation.
+
+  python -m paper_2503_18759_gb300.learn train --problems 2000 --out weights.npy
+  python -m paper_2503_18759_gb300.learn eval --weights weights.npy --problems 200
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+from typing import List, Sequence
+
+import numpy as np
+
+from . import binding as b
+from . import inputs
+
+
+def candidates() -> List[float]:
+    return [b.cp_als_qr_mlp_beta(c) for c in range(b.MLP_CLASSES)]
+
+
+def problem_set(start: int, count: int, order: int = 3, base_seed: int = 0):
+    """Seeded problems of the training distribution: order 3 sides U{64..256} (order 4:
+    U{24..64}), rank U{8..32}, congruence U[0, 0.95], noise log-uniform in [1e-4, 1e-2]."""
+    for i in range(start, start + count):
+        g = np.random.default_rng([base_seed, i, order])
+        if order == 3:
+            dims = [int(v) for v in g.integers(64, 257, size=3)]
+        else:
+            dims = [int(v) for v in g.integers(24, 65, size=order)]
+        R = min(int(g.integers(8, 33)), min(dims))
+        c = float(g.uniform(0.0, 0.95))
+        eta = float(10.0 ** g.uniform(-4.0, -2.0))
+        yield inputs.make_problem_device(f"p{order}_{i}", dims, R, seed=base_seed * 100003 + i * 7 + order, c=c,
+                                         eta=eta)
+
+
+def trajectories(problems, sweeps: int = 12, horizon: int = 2, start: int = 2, prec: int = b.PREC_SPLIT_BF16):
+    cand = candidates()
+    feats, labels = [], []
+    for prob in problems:
+        opts = b.make_options(tree=b.TREE_RESTRUCTURED, prec=prec, extrap=b.EXTRAP_PAPER)
+        with b.Decomposition(prob.dims, prob.R, prob.X.data_ptr(), False, prob.A0, opts) as d:
+            d.sweep(start)
+            for _ in range(start, sweeps):
+                fits, betas, rule, act = d.history()
+                f = b.cpqr_mlp_features(fits, betas, rule, act)
+                d.checkpoint()
+                res = []
+                for ci, beta in enumerate(cand):
+                    if ci:
+                        d.rollback()
+                    fit = 0.0
+                    for _ in range(horizon):
+                        fit = d.sweep_beta(beta)
+                    res.append(fit)
+                d.rollback()
+                d.commit()
+                res = np.array(res)
+                best = int(np.min(np.nonzero(res >= res.max() - 1e-13)[0]))
+                feats.append(f)
+                labels.append(best)
+                d.sweep_beta(cand[best])
+    return np.array(feats, dtype=np.float32), np.array(labels, dtype=np.int32)
+
+
+def init_params(seed: int = 0) -> np.ndarray:
+    g = np.random.default_rng(seed)
+    shapes = [(b.MLP_HIDDEN, b.MLP_FEATURES), (b.MLP_HIDDEN, b.MLP_HIDDEN), (b.MLP_HIDDEN, b.MLP_HIDDEN),
+              (b.MLP_CLASSES, b.MLP_HIDDEN)]
+    parts = []
+    for o, i in shapes:
+        parts.append(g.standard_normal(o * i) * np.sqrt(2.0 / i))
+        parts.append(np.zeros(o))
+    p = np.concatenate(parts).astype(np.float32)
+    assert p.size == b.MLP_NPARAMS
+    return p
+
+
+def train(feats: np.ndarray, labels: np.ndarray, epochs: int = 60, batch: int = 256, lr: float = 1e-3,
+          seed: int = 0, log=None) -> np.ndarray:
+    import torch
+
+    dev = "cuda"
+    params = torch.from_numpy(init_params(seed)).to(dev)
+    m = torch.zeros_like(params)
+    v = torch.zeros_like(params)
+    grad = torch.zeros_like(params)
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    Xall = torch.from_numpy(feats).to(dev)
+    yall = torch.from_numpy(labels.astype(np.int32)).to(dev)
+    n = len(labels)
+    B = min(batch, n)
+    work = torch.empty(b.cpqr_mlp_work_bytes(B), dtype=torch.uint8, device=dev)
+    g = np.random.default_rng(seed)
+    step = 0
+    for ep in range(epochs):
+        perm = torch.from_numpy(g.permutation(n)).to(dev)
+        tot = 0.0
+        for i in range(0, n - B + 1, B):
+            idx = perm[i:i + B]
+            Xb = Xall[idx].contiguous()
+            yb = yall[idx].contiguous()
+            b.cpqr_mlp_grad(params.data_ptr(), Xb.data_ptr(), yb.data_ptr(), B, grad.data_ptr(), loss.data_ptr(),
+                            work.data_ptr())
+            step += 1
+            b.cpqr_mlp_adam(params.data_ptr(), m.data_ptr(), v.data_ptr(), grad.data_ptr(), lr, step)
+            tot += loss.item()
+        if log is not None:
+            log(ep, tot / max(1, n // B))
+    torch.cuda.synchronize()
+    return params.cpu().numpy()
+
+
+def accuracy(params: np.ndarray, feats: np.ndarray, labels: np.ndarray) -> float:
+    import torch
+
+    dev = "cuda"
+    n = len(labels)
+    pd = torch.from_numpy(params).to(dev)
+    X = torch.from_numpy(feats).to(dev)
+    logits = torch.empty((n, b.MLP_CLASSES), dtype=torch.float32, device=dev)
+    work = torch.empty(b.cpqr_mlp_work_bytes(n), dtype=torch.uint8, device=dev)
+    b.cpqr_mlp_forward(pd.data_ptr(), X.data_ptr(), n, logits.data_ptr(), work.data_ptr())
+    pred = logits.argmax(dim=1).cpu().numpy()
+    return float(np.mean(pred == labels))
+
+
+def evaluate(params, problems, tol: float = 1e-6, max_sweeps: int = 150, prec: int = b.PREC_SPLIT_BF16):
+    """Per problem and mode: sweeps and wall time until |fit_k - fit_{k-1}| < tol, the fit
+    reported then and the exact fit of the final model."""
+    import torch
+
+    out = []
+    modes = [("none", b.EXTRAP_NONE, None), ("paper", b.EXTRAP_PAPER, None), ("learned", b.EXTRAP_LEARNED, params)]
+    for prob in problems:
+        row = {"name": prob.name, "dims": prob.dims, "R": prob.R}
+        for name, ex, w in modes:
+            opts = b.make_options(tree=b.TREE_RESTRUCTURED, prec=prec, extrap=ex, mlp_weights=w)
+            with b.Decomposition(prob.dims, prob.R, prob.X.data_ptr(), False, prob.A0, opts) as d:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                conv, f, ns = d.fit(tol, max_sweeps)
+                torch.cuda.synchronize()
+                wall = time.perf_counter() - t0
+                st = d.stats()
+                row[name] = {"sweeps": ns, "seconds": wall, "converged": conv, "fit": f, "fit_exact": d.fit_exact(),
+                             "proposals": st.proposals, "accepted": st.accepted}
+        out.append(row)
+    return out
+
+
+def summarize(rows):
+    s = {}
+    for name in ("none", "paper", "learned"):
+        s[name] = {"mean_sweeps": float(np.mean([r[name]["sweeps"] for r in rows])),
+                   "mean_seconds": float(np.mean([r[name]["seconds"] for r in rows])),
+                   "mean_fit_exact": float(np.mean([r[name]["fit_exact"] for r in rows])),
+                   "converged": int(sum(r[name]["converged"] for r in rows))}
+    return s
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("cmd", choices=["train", "eval"])
+    ap.add_argument("--problems", type=int, default=200)
+    ap.add_argument("--sweeps", type=int, default=12)
+    ap.add_argument("--epochs", type=int, default=60)
+    ap.add_argument("--out", default="beta_mlp.npy")
+    ap.add_argument("--weights", default="beta_mlp.npy")
+    ap.add_argument("--order", type=int, default=3)
+    ap.add_argument("--start", type=int, default=0)
+    args = ap.parse_args()
+    b.lib()
+    if args.cmd == "train":
+        t0 = time.time()
+        F, y = trajectories(problem_set(args.start, args.problems), sweeps=args.sweeps)
+        t1 = time.time()
+        w = train(F, y, epochs=args.epochs)
+        np.save(args.out, w)
+        print(json.dumps({"states": len(y), "label_counts": np.bincount(y, minlength=b.MLP_CLASSES).tolist(),
+                          "generate_s": t1 - t0, "train_s": time.time() - t1, "train_acc": accuracy(w, F, y)}))
+    else:
+        w = np.load(args.weights).astype(np.float32)
+        rows = evaluate(w, problem_set(10000 + args.start, args.problems, order=args.order))
+        print(json.dumps(summarize(rows)))
+
+
+if __name__ == "__main__":
+    main()
