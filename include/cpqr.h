@@ -193,6 +193,22 @@ cpqr_status cpqr_ttm(const void* T_dev, int32_t nd, const int64_t* tdims, int32_
 cpqr_status cpqr_house_qr(const double* A_dev, int64_t M, int32_t R, double* Q_dev,
                           double* R_dev, void* stream);
 
+/* Same QR as cpqr_house_qr without any device allocation.  The paper has no counterpart; it
+ * is for callers that may not allocate device memory (a host application that owns all device
+ * memory through its own pool, a latency-critical loop that cannot afford cudaMalloc/cudaFree
+ * and the device synchronisation they can cause, a deployment with a fixed memory footprint).
+ * Scratch lives in one statically allocated device array of CPQR_NOALLOC_QR_MAX_ELEMS + 32
+ * doubles (8 MiB) that every GPU loading the library holds until the process exits.
+ * - M * R must not exceed CPQR_NOALLOC_QR_MAX_ELEMS; larger problems return CPQR_EINVAL.
+ * - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ *   that device current; make that first call before any stream capture.
+ * - All calls share the one array and it keeps the last call's contents: calls whose GPU work
+ *   overlaps (other streams, other host threads) race and must be serialised by the caller.
+ * Synchronises the stream before returning. */
+#define CPQR_NOALLOC_QR_MAX_ELEMS (1 << 20)
+cpqr_status cpqr_house_qr_noalloc(const double* A_dev, int64_t M, int32_t R, double* Q_dev,
+                                  double* R_dev, void* stream);
+
 /* QR of Z = R_1 (.) ... (.) R_m, the Khatri-Rao product of m upper-triangular R x R
  * matrices (Alg. 2 lines 3-4), rows (r_1, ..., r_m) with r_m fastest: Rs_dev holds the m
  * triangles back to back (device, FP64).  Q0_dev (R^m x R) and R0_dev (R x R) receive the

@@ -92,10 +92,11 @@ def lib() -> C.CDLL:
     L.cp_als_qr_history.argtypes = [vp, P(dbl), P(dbl), i32, P(i32), P(dbl), P(i32)]
     L.cpqr_house_qr.argtypes = [vp, i64, i32, vp, vp, vp]
     L.cpqr_krp_qr.argtypes = [vp, i32, i32, vp, vp, vp]
+    L.cpqr_house_qr_noalloc.argtypes = [vp, i64, i32, vp, vp, vp]
     for name in ("cp_als_qr_init", "cp_als_qr_sweep", "cp_als_qr_fit", "cp_als_qr_get", "cp_als_qr_stats",
                  "cp_als_qr_fit_exact", "cp_als_qr_set_timing", "cp_als_qr_schedule", "cp_als_qr_run_host",
                  "cpqr_mlp_features", "cpqr_mlp_forward", "cpqr_mlp_grad", "cpqr_mlp_adam", "cp_als_qr_checkpoint",
-                 "cp_als_qr_rollback", "cp_als_qr_commit", "cp_als_qr_sweep_beta", "cp_als_qr_history", "cpqr_ttm", "cpqr_house_qr", "cpqr_krp_qr"):
+                 "cp_als_qr_rollback", "cp_als_qr_commit", "cp_als_qr_sweep_beta", "cp_als_qr_history", "cpqr_ttm", "cpqr_house_qr", "cpqr_krp_qr", "cpqr_house_qr_noalloc"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -313,6 +314,16 @@ def cpqr_ttm(T_dev: int, tdims: Sequence[int], k: int, Q_dev: int, R: int, out_d
 def cpqr_house_qr(A_dev: int, M: int, R: int, Q_dev: int, R_dev: int, stream: int = 0) -> None:
     _check(lib().cpqr_house_qr(C.c_void_p(int(A_dev)), int(M), int(R), C.c_void_p(int(Q_dev)),
                                C.c_void_p(int(R_dev)), C.c_void_p(int(stream))), "cpqr_house_qr")
+
+
+NOALLOC_QR_MAX_ELEMS = 1 << 20
+
+
+def cpqr_house_qr_noalloc(A_dev: int, M: int, R: int, Q_dev: int, R_dev: int, stream: int = 0) -> None:
+    """cpqr_house_qr without device allocation (fixed static scratch; M * R <= NOALLOC_QR_MAX_ELEMS;
+    calls that overlap on the GPU race)."""
+    _check(lib().cpqr_house_qr_noalloc(C.c_void_p(int(A_dev)), int(M), int(R), C.c_void_p(int(Q_dev)),
+                                       C.c_void_p(int(R_dev)), C.c_void_p(int(stream))), "cpqr_house_qr_noalloc")
 
 
 def cpqr_krp_qr(Rs_dev: int, m: int, R: int, Q0_dev: int, R0_dev: int, stream: int = 0) -> None:
