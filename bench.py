@@ -32,6 +32,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "sec/CP-ALS-QR sweep & time-to-fit 1e-6 (mixed+learned vs FP64 GPU); TTM %peak"
 WORKLOAD = "cube400_r32_c09"
+# dram__bytes_read.sum + dram__bytes_write.sum of one ttm_tc_kernel launch on the 400^3 mode-1 shape
+# (ncu capture summarised in profiles/ttm_tc_cube400_mode1.md); None once that kernel changes
+TTM_TC_TRAFFIC = 270.94e6
+# whole-GPU FP64 DFMA rate measured by a probe on the GB300s (TFLOP/s)
+FP64_PEAK_TFLOPS = 1.20
 
 
 def _peaks():
@@ -176,15 +181,33 @@ def run_ours(args, rank, world, local_rank):
         ob = 4 if prec == b.PREC_SPLIT_BF16 else 8
         alg_bytes = xbytes + out_elems * ob
         achieved = alg_bytes / (full_ms * 1e-3) / 1e9 if n_full else None
-        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": (achieved / hbm) if achieved else None, "traffic": None,
-                "kernel": "first-level TTM (full tensor)", "peak_kind": f"{peak_kind} copy bandwidth (burst)",
-                "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": full_ms, "launches": int(n_full)}
+        roof_ttm = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                    "frac": (achieved / hbm) if achieved else None,
+                    "traffic": TTM_TC_TRAFFIC if prec == b.PREC_SPLIT_BF16 else None,
+                    "kernel": "ttm_tc_kernel (first-level TTM, full tensor)",
+                    "peak_kind": f"{peak_kind} copy bandwidth (burst)",
+                    "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": full_ms, "launches": int(n_full)}
         if prec == b.PREC_FP64:
             flops = 2 * prob.X.size * prob.R
-            roof.update({"bound": "alu", "achieved": flops / (full_ms * 1e-3) / 1e12, "peak": 1.2,
-                         "unit": "TFLOP/s", "peak_kind": "FP64 DFMA rate measured by a probe (1.2 TFLOP/s)"})
-            roof["frac"] = roof["achieved"] / roof["peak"]
+            roof_ttm.update({"bound": "alu", "achieved": flops / (full_ms * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                             "unit": "TFLOP/s", "kernel": "ttm_kernel<float,double,double> (first-level TTM, FP64)",
+                             "peak_kind": "FP64 DFMA rate measured by a probe", "alg_flops_per_launch": flops})
+            roof_ttm["frac"] = roof_ttm["achieved"] / roof_ttm["peak"]
+        # the factor-QR finish kernel (Alg. 3 lines 8-10 on one 16-CTA cluster): FP64, latency bound
+        n_qr = st.n_bucket[4]
+        qr_ms = st.ms_bucket[4] / max(n_qr, 1)
+        I, R = prob.dims[0], prob.R
+        qr_flops = 5 * I * R * R - (2 * R ** 3) // 3
+        roof_qr = {"bound": "alu", "achieved": qr_flops / (qr_ms * 1e-3) / 1e12 if n_qr else None,
+                   "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "traffic": None,
+                   "kernel": "qr_cluster_kernel<16> (finish: solve, normalise, Householder QR, Q)",
+                   "peak_kind": "FP64 DFMA rate of the whole GPU measured by a probe; the kernel runs on one "
+                                "16-SM cluster and is bound by serial FP64 latency",
+                   "alg_flops_per_launch": qr_flops, "avg_launch_ms": qr_ms, "launches": int(n_qr)}
+        roof_qr["frac"] = roof_qr["achieved"] / roof_qr["peak"] if n_qr else None
+        # dominant kernel by device time per sweep
+        qr_share = st.ms_bucket[4] + st.ms_bucket[2]
+        roof = roof_qr if (prec == b.PREC_SPLIT_BF16 and qr_share > st.ms_bucket[0]) else roof_ttm
         out = {"metric": METRIC, "value": ms * 1e-3 / world, "unit": "s/sweep", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
                "vs_baseline": None,
@@ -195,6 +218,7 @@ def run_ours(args, rank, world, local_rank):
                           "l2": "no flush; inputs larger than L2 (256 MB tensor, 512 MB bf16 split)",
                           "replicas": world},
                "roofline": roof,
+               "roofline_ttm_full": roof_ttm,
                "buckets_ms_per_sweep": buckets,
                "gpu_launches": int(launches),
                "fit_last": float(fits[-1]) if len(fits) else None}
@@ -229,21 +253,40 @@ def extras(args, prob, X, dev, b):
     res["e2e"] = {"value": e2e_ms * 1e-3 / ns, "unit": "s/sweep", "h2d_bytes_per_step": prob.X.nbytes / ns,
                   "d2h_bytes_per_step": fbytes / ns + 24, "sweeps_per_call": ns,
                   "note": "one cp_als_qr_run_host call (H2D of X from pinned memory, init, sweeps, factors D2H) / sweeps"}
-    # time to |delta fit| < 1e-6 from the same start, FP64 GPU path and this path
+    # time to |delta fit| < 1e-6 from the same start: plain FP64 CP-ALS-QR (Alg. 2: no tree,
+    # no extrapolation) and ALS-QR-BRE on both paths, with the rule and with the learned proposer
+    from paper_2503_18759_gb300 import learn
+    w = learn.load_weights()
     ttf = {}
-    for name, prec in (("fp64", b.PREC_FP64), (args.prec, b.PREC_SPLIT_BF16 if args.prec == "split" else b.PREC_FP64)):
-        if name in ttf:
-            continue
-        o = b.make_options(tree=b.TREE_RESTRUCTURED, prec=prec, extrap=b.EXTRAP_PAPER)
+    variants = [("fp64_plain_cpalsqr", b.PREC_FP64, b.TREE_NONE, b.EXTRAP_NONE, None),
+                ("fp64_bre_rule", b.PREC_FP64, b.TREE_RESTRUCTURED, b.EXTRAP_PAPER, None),
+                ("split_bre_rule", b.PREC_SPLIT_BF16, b.TREE_RESTRUCTURED, b.EXTRAP_PAPER, None),
+                ("split_bre_learned", b.PREC_SPLIT_BF16, b.TREE_RESTRUCTURED, b.EXTRAP_LEARNED, w),
+                ("split_br_none", b.PREC_SPLIT_BF16, b.TREE_RESTRUCTURED, b.EXTRAP_NONE, None)]
+    for name, prec, tree, ex, wt in variants:
+        o = b.make_options(tree=tree, prec=prec, extrap=ex, mlp_weights=wt)
         with b.Decomposition(prob.dims, prob.R, X.data_ptr(), False, prob.A0, o) as d:
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            conv, f, ns = d.fit(1e-6, 400)
+            conv, f, ns = d.fit(1e-6, 300)
             torch.cuda.synchronize()
             wall = time.perf_counter() - t0
             fx = d.fit_exact()
+            st = d.stats()
+            hist = d.history()[0]
             ttf[name] = {"seconds": wall, "sweeps": ns, "converged": conv, "fit_reported": f, "fit_exact": fx,
-                         "s_per_sweep": wall / max(ns, 1)}
+                         "s_per_sweep": wall / max(ns, 1), "proposals": st.proposals, "accepted": st.accepted,
+                         "_hist": hist}
+    # the variants stop at different fits (the tree changes the mode order, hence the
+    # trajectory): also time each to the lowest final fit any of them reached
+    target = min(v["fit_exact"] for v in ttf.values()) - 1e-6
+    for v in ttf.values():
+        h = v.pop("_hist")
+        hit = np.nonzero(h >= target)[0]
+        k = int(hit[0]) + 1 if len(hit) else None
+        v["sweeps_to_common_target"] = k
+        v["seconds_to_common_target"] = k * v["s_per_sweep"] if k else None
+    res["common_fit_target"] = target
     res["time_to_tol_1e-6"] = ttf
     return res
 

@@ -128,8 +128,10 @@ cpqr_status cp_als_qr_init(cpqr_ctx** out, int32_t N, const int64_t* dims, int32
 
 /* Run nsweeps sweeps (outer iterations of Alg. 3: every mode updated once, TTMs per the
  * schedule, customised extrapolation per the options).  fits_host (nsweeps doubles, may be
- * NULL) receives the fit after each sweep, computed as in Section 4.1 from the last mode of
- * the sweep: 1 - sqrt(max(||X||^2 - 2<V0, V^> + ||V^||^2, 0)) / ||X||. */
+ * NULL) receives the fit after each sweep.  FP64 contexts compute it as in Section 4.1 from the
+ * last mode of the sweep: 1 - sqrt(max(||X||^2 - 2<V0, V^> + ||V^||^2, 0)) / ||X||; split-
+ * precision contexts from an explicit residual pass (see cp_als_qr_fit_exact), because the
+ * reduced form's cancellation would expose the split operands' error. */
 cpqr_status cp_als_qr_sweep(cpqr_ctx* ctx, int32_t nsweeps, double* fits_host);
 
 /* Sweep until |fit_k - fit_{k-1}| < tol (the stopping test of Alg. 2/3, read as a change in
@@ -147,8 +149,11 @@ cpqr_status cp_als_qr_get(cpqr_ctx* ctx, int32_t n, double* A_host, double* lamb
 /* Counters since init. */
 cpqr_status cp_als_qr_stats(cpqr_ctx* ctx, cpqr_stats* out);
 
-/* Exact fit of the current model by one pass over X: 1 - ||X - [[lambda; A]]|| / ||X|| with
- * every model entry and the residual sum in FP64.  Costs N*R flops per element of X. */
+/* Fit of the current model from an explicit pass over X: 1 - ||X - [[lambda; A]]|| / ||X||.  The
+ * model entries are formed in FP32 from the FP64 factors and the squared residual is summed in
+ * FP64, so the result does not suffer the cancellation of ||X||^2 - 2<X,K> + ||K||^2 (relative
+ * error ~1e-7 in ||X - K||).  One read of X plus R FMAs per element; rows of X (product of all
+ * but the last dimension) < 2^31. */
 cpqr_status cp_als_qr_fit_exact(cpqr_ctx* ctx, double* fit);
 
 /* End-to-end decomposition of a HOST tensor: copies X_host (C order, float32 or float64; pinned

@@ -135,6 +135,8 @@ struct cpqr_ctx {
   double* V = nullptr;
   double* qr_work = nullptr;
   double* zq_work = nullptr;
+  double* v_work = nullptr;
+  double* res_work = nullptr;
   double* fit_terms = nullptr;
   double* d_scalar = nullptr;
   unsigned int* dstatus = nullptr;
@@ -305,7 +307,10 @@ cpqr_status run_ttm(cpqr_ctx* ctx, const Op& op) {
       CK(launch_ttm_tc(ctx->Xhi, ctx->Xlo, ctx->Qt[k], ctx->Rp, ctx->Kp[k], (float*)out, P, K, S, R,
                        ctx->dstatus, st));
     } else {
-      CK(launch_ttm<float, float, float>((const float*)sb.p, ctx->Qf[k], (float*)out, P, K, S, R, st));
+      cudaError_t e = launch_ttm_f32_tiled((const float*)sb.p, ctx->Qf[k], (float*)out, P, K, S, R, st);
+      if (e == cudaErrorNotSupported) e = launch_ttm<float, float, float>((const float*)sb.p, ctx->Qf[k], (float*)out,
+                                                                           P, K, S, R, st);
+      CK(e);
     }
   }
   ctx->nodes[dst] = NodeBuf{out, bytes, sb.free_mask & ~(1u << k), false};
@@ -446,9 +451,10 @@ cpqr_status run_update(cpqr_ctx* ctx, int n, int leaf, double beta) {
   {
     Timed tm(ctx, CPQR_BUCKET_APPLY_Q0, 2);
     if (ctx->prec == CPQR_PREC_FP64)
-      CK(launch_leaf_v<double>((const double*)lb.p, P, I, S, ctx->Q0, ctx->Q0prev[n], R, C, ctx->V, st));
+      CK(launch_leaf_v<double>((const double*)lb.p, P, I, S, ctx->Q0, ctx->Q0prev[n], R, C, ctx->V, ctx->v_work,
+                               st));
     else
-      CK(launch_leaf_v<float>((const float*)lb.p, P, I, S, ctx->Q0, ctx->Q0prev[n], R, C, ctx->V, st));
+      CK(launch_leaf_v<float>((const float*)lb.p, P, I, S, ctx->Q0, ctx->Q0prev[n], R, C, ctx->V, ctx->v_work, st));
   }
   // Lines 8-10.
   FinishOut fo{ctx->A[n], ctx->lambda, ctx->Q[n], ctx->Rf[n], ctx->Qf[n], ctx->fit_terms};
@@ -464,9 +470,23 @@ cpqr_status run_update(cpqr_ctx* ctx, int n, int leaf, double beta) {
   return CPQR_OK;
 }
 
+// Fit after a sweep.  FP64 path: Section 4.1's reduced form from the last mode's V0, V^.
+// Split path: the reduced form cancels ||X||^2 against terms that carry the split operands'
+// ~2^-16 relative error, which can exceed a 1e-6 change in fit, so the fit comes from an
+// explicit residual pass over X with the current factors instead (one read of X).
 cpqr_status read_fit(cpqr_ctx* ctx, double* fit) {
+  const bool explicit_fit = (ctx->prec == CPQR_PREC_SPLIT_BF16);
+  if (explicit_fit) {
+    Timed tm(ctx, CPQR_BUCKET_OTHER, 1);
+    const double* A[CPQR_MAXN];
+    for (int n = 0; n < ctx->N; ++n) A[n] = ctx->A[n];
+    CK(launch_residual2<float>((const float*)ctx->X, ctx->N, ctx->dims.data(), A, ctx->lambda, ctx->R,
+                               ctx->d_scalar, ctx->res_work, ctx->st));
+  }
   {
     Timed tm(ctx, CPQR_BUCKET_OTHER, 0);
+    if (explicit_fit)
+      CK(cudaMemcpyAsync(ctx->h_pinned + 3, ctx->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaMemcpyAsync(ctx->h_pinned, ctx->fit_terms, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaMemcpyAsync(ctx->h_pinned + 2, ctx->dstatus, sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->st));
   }
@@ -477,7 +497,7 @@ cpqr_status read_fit(cpqr_ctx* ctx, double* fit) {
   if (ds & CPQR_DEV_TIMEOUT) return fail(ctx, CPQR_ETIMEOUT);
   if (ds & CPQR_DEV_SINGULAR) return fail(ctx, CPQR_ESINGULAR);
   double in = ctx->h_pinned[0], nn = ctx->h_pinned[1];
-  double r2 = ctx->normX2 - 2.0 * in + nn;
+  double r2 = explicit_fit ? ctx->h_pinned[3] : ctx->normX2 - 2.0 * in + nn;
   double f = 1.0 - std::sqrt(std::max(r2, 0.0)) / std::sqrt(ctx->normX2);
   if (!std::isfinite(f)) return fail(ctx, CPQR_ENONFINITE);
   *fit = f;
@@ -562,8 +582,8 @@ void mlp_features(const double* fits, const double* betas, int n, double rule_be
   f[26] = activated ? 1.f : 0.f;
 }
 
-// CPQR_EXTRAP_LEARNED: the network proposes beta; the sweep runs speculatively and is kept
-// only if its fit does not fall below the previous sweep's, else it is rolled back and
+// CPQR_EXTRAP_LEARNED: the network proposes beta; a sweep with beta > 0 runs speculatively and
+// is kept only if its fit does not fall below the previous sweep's, else it is rolled back and
 // redone with the Section 4.2 rule's beta.
 cpqr_status learned_sweep(cpqr_ctx* ctx, double* fit_out) {
   const double rule = rule_beta_next(ctx);
@@ -583,6 +603,13 @@ cpqr_status learned_sweep(cpqr_ctx* ctx, double* fit_out) {
     if (hf[CPQR_MLP_FEATURES + c] > hf[CPQR_MLP_FEATURES + best]) best = c;
   const double prop = kMlpBetas[best];
   if (prop == rule) return one_sweep(ctx, fit_out, &rule);
+  if (prop == 0.0) {
+    // without extrapolation every mode update is an exact least-squares step, so the fit
+    // cannot drop: nothing to judge
+    ++ctx->proposals;
+    ++ctx->accepted;
+    return one_sweep(ctx, fit_out, &prop);
+  }
   const double prev = ctx->fits.back();
   cpqr_status s = checkpoint_save(ctx, 1);
   if (s != CPQR_OK) return s;
@@ -726,6 +753,12 @@ cpqr_status cp_als_qr_init(cpqr_ctx** out, int32_t N, const int64_t* dims, int32
   CK(ctx->alloc(&ctx->V, Imax * 2 * R));
   CK(ctx->alloc(&ctx->qr_work, std::max<int64_t>(M0, Imax) * R));
   CK(ctx->alloc(&ctx->zq_work, M0 * R));
+  CK(ctx->alloc((char**)&ctx->res_work, residual2_work_bytes(N, dims, R)));
+  {
+    int64_t vw = 0;
+    for (int n = 0; n < N; ++n) vw = std::max<int64_t>(vw, (int64_t)leaf_v_splits(dims[n], M0) * dims[n] * 2 * R);
+    CK(ctx->alloc(&ctx->v_work, vw));
+  }
   CK(cudaStreamCreateWithFlags(&ctx->st2, cudaStreamNonBlocking));
   CK(cudaEventCreateWithFlags(&ctx->ev_ready, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&ctx->ev_z, cudaEventDisableTiming));
@@ -899,10 +932,10 @@ cpqr_status cp_als_qr_fit_exact(cpqr_ctx* ctx, double* fit) {
   for (int n = 0; n < ctx->N; ++n) A[n] = ctx->A[n];
   if (ctx->x64)
     CK(launch_residual2<double>((const double*)ctx->X, ctx->N, ctx->dims.data(), A, ctx->lambda, ctx->R,
-                                ctx->d_scalar, nullptr, ctx->st));
+                                ctx->d_scalar, ctx->res_work, ctx->st));
   else
     CK(launch_residual2<float>((const float*)ctx->X, ctx->N, ctx->dims.data(), A, ctx->lambda, ctx->R,
-                               ctx->d_scalar, nullptr, ctx->st));
+                               ctx->d_scalar, ctx->res_work, ctx->st));
   CK(cudaMemcpyAsync(ctx->h_pinned, ctx->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
   *fit = 1.0 - std::sqrt(std::max(ctx->h_pinned[0], 0.0)) / std::sqrt(ctx->normX2);
@@ -1054,7 +1087,11 @@ cpqr_status cpqr_ttm(const void* T_dev, int32_t nd, const int64_t* tdims, int32_
   cudaError_t e;
   switch (dtype) {
     case 0: e = launch_ttm<double, double, double>((const double*)T_dev, (const double*)Q_dev, (double*)out_dev, P, K, S, R, st); break;
-    case 1: e = launch_ttm<float, float, float>((const float*)T_dev, (const float*)Q_dev, (float*)out_dev, P, K, S, R, st); break;
+    case 1:
+      e = launch_ttm_f32_tiled((const float*)T_dev, (const float*)Q_dev, (float*)out_dev, P, K, S, R, st);
+      if (e == cudaErrorNotSupported)
+        e = launch_ttm<float, float, float>((const float*)T_dev, (const float*)Q_dev, (float*)out_dev, P, K, S, R, st);
+      break;
     case 2: e = launch_ttm<float, double, double>((const float*)T_dev, (const double*)Q_dev, (double*)out_dev, P, K, S, R, st); break;
     case 3: {
       if (!ttm_tc_supported(P, K, S, R)) return CPQR_EUNSUPPORTED;

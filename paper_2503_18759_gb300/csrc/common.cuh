@@ -24,6 +24,11 @@ template <typename TT, typename TQ, typename TO>
 cudaError_t launch_ttm(const TT* T, const TQ* Q, TO* out, int64_t P, int64_t K, int64_t S, int R,
                        cudaStream_t st);
 
+// FP32 register-tiled TTM for S == 1 (K % 4 == 0) or S % 4 == 0; cudaErrorNotSupported
+// for other shapes (use launch_ttm<float, float, float>).
+cudaError_t launch_ttm_f32_tiled(const float* T, const float* Q, float* out, int64_t P, int64_t K, int64_t S, int R,
+                                 cudaStream_t st);
+
 // ----- split-precision tensor-core TTM (ttm_tc.cu) -----
 // Stages Q (K x R FP64 row-major) as bf16 hi/lo, transposed and padded for the MMA
 // B operand: Qt[2][Rp][Kp] with Rp = R rounded up to 16, Kp = K rounded up to 64.
@@ -77,16 +82,19 @@ cudaError_t launch_mode_finish(const double* V, int C, const double* R0, double 
                                cudaStream_t st);
 
 // V[i, c] = sum_{p, s} Y[p, i, s] * Qc[p*S + s, c], c < C, Qc = [Q0 | Q0prev] (K x C,
-// K = P*S) FP64; Y FP64 or FP32.  V is zeroed by the launcher.
+// K = P*S) FP64; Y FP64 or FP32.  work: leaf_v_splits(I, K) * I * C doubles.
+int leaf_v_splits(int64_t I, int64_t K);
 template <typename TY>
 cudaError_t launch_leaf_v(const TY* Y, int64_t P, int64_t I, int64_t S, const double* Q0,
-                          const double* Q0prev, int R, int C, double* V, cudaStream_t st);
+                          const double* Q0prev, int R, int C, double* V, double* work, cudaStream_t st);
 
 // ||X||^2 in FP64 (partials into work, final into out[0]).
 template <typename TX>
 cudaError_t launch_norm2(const TX* X, int64_t n, double* out, double* work, cudaStream_t st);
 
-// ||X - [[lambda; A]]||^2 with FP64 model entries; X dims d[0..N-1].
+// ||X - [[lambda; A]]||^2 (FP32 model entries, FP64 total); X dims d[0..N-1]; A: host array of N
+// device pointers; work: device scratch of residual2_work_bytes(N, d, R).
+size_t residual2_work_bytes(int N, const int64_t* d, int R);
 template <typename TX>
 cudaError_t launch_residual2(const TX* X, int N, const int64_t* d, const double* const* A,
                              const double* lambda, int R, double* out, double* work, cudaStream_t st);

@@ -5,6 +5,9 @@
 //  * V = Y_(n) [Q0 | Q0^{k-1}] (Alg. 3 line 7; eq. 19 is applied to V by
 //    linearity in the finish kernel);
 //  * ||X||^2 and the explicit residual ||X - [[lambda; A]]||^2 (Section 4.1).
+#include <algorithm>
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace cpqr {
@@ -95,66 +98,208 @@ __global__ void __launch_bounds__(NT) ttm_kernel(const TT* __restrict__ T, const
 }
 
 // ----------------------------------------------------------------------------
+// FP32 mode-k product for the deeper tree levels, register-tiled: a CTA computes
+// 128 output rows x 32 columns with a 4 x 4 tile per thread from KC-deep shared
+// memory chunks (A stored k-major, B = Q rows), double buffered through registers.
+// Rows are s (S % 4 == 0, one p per tile, float4 loads along s) or p (S == 1, the
+// plain GEMM out[p, :] = T[p, :] Q, float4 loads along i, K % 4 == 0).
+// ----------------------------------------------------------------------------
+constexpr int TBM = 128, TKC = 16, TNT = 256;
+
+template <bool LASTMODE>
+__global__ void __launch_bounds__(TNT) ttm_f32_tiled_kernel(const float* __restrict__ T, const float* __restrict__ Q,
+                                                             float* __restrict__ out, int64_t P, int64_t K, int64_t S,
+                                                             int R, int64_t sblocks) {
+  __shared__ __align__(16) float sA[2][TKC][TBM];
+  __shared__ __align__(16) float sB[2][TKC][CPQR_MAXR];
+  const int tid = threadIdx.x;
+  const int tx = tid & 7, ty = tid >> 3;  // columns tx*4.., rows ty*4..
+  int64_t p = 0, m0 = 0;
+  if (LASTMODE) {
+    m0 = (int64_t)blockIdx.x * TBM;  // rows are p
+  } else {
+    p = (int64_t)blockIdx.x / sblocks;
+    m0 = ((int64_t)blockIdx.x % sblocks) * TBM;  // rows are s
+  }
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+
+  // loader mapping: A chunk = TKC x TBM floats = 512 float4, 2 per thread; B chunk 128 float4
+  float4 ra[2], rb;
+  auto load = [&](int64_t i0) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int e = tid + TNT * q;  // 0..511
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (LASTMODE) {
+        const int m = e >> 2, kq = (e & 3) * 4;  // row m, k = kq..kq+3
+        const int64_t row = m0 + m, ii = i0 + kq;
+        if (row < P && ii < K) v = *reinterpret_cast<const float4*>(T + row * K + ii);
+      } else {
+        const int k = e >> 5, mq = (e & 31) * 4;  // k, rows mq..mq+3 (s)
+        const int64_t ii = i0 + k, ss = m0 + mq;
+        if (ii < K && ss < S) v = *reinterpret_cast<const float4*>(T + (p * K + ii) * S + ss);
+      }
+      ra[q] = v;
+    }
+    {
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (tid < TKC * CPQR_MAXR / 4) {
+        const int k = tid >> 3, rq = (tid & 7) * 4;
+        const int64_t ii = i0 + k;
+        if (ii < K) {
+          const float* q = Q + ii * R + rq;
+          v.x = (rq + 0 < R) ? q[0] : 0.f;
+          v.y = (rq + 1 < R) ? q[1] : 0.f;
+          v.z = (rq + 2 < R) ? q[2] : 0.f;
+          v.w = (rq + 3 < R) ? q[3] : 0.f;
+        }
+      }
+      rb = v;
+    }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int e = tid + TNT * q;
+      if (LASTMODE) {
+        const int m = e >> 2, kq = (e & 3) * 4;
+        sA[buf][kq + 0][m] = ra[q].x;
+        sA[buf][kq + 1][m] = ra[q].y;
+        sA[buf][kq + 2][m] = ra[q].z;
+        sA[buf][kq + 3][m] = ra[q].w;
+      } else {
+        const int k = e >> 5, mq = (e & 31) * 4;
+        *reinterpret_cast<float4*>(&sA[buf][k][mq]) = ra[q];
+      }
+    }
+    if (tid < TKC * CPQR_MAXR / 4) {
+      const int k = tid >> 3, rq = (tid & 7) * 4;
+      *reinterpret_cast<float4*>(&sB[buf][k][rq]) = rb;
+    }
+  };
+  const int nchunks = (int)((K + TKC - 1) / TKC);
+  load(0);
+  store(0);
+  __syncthreads();
+  for (int c = 0; c < nchunks; ++c) {
+    const int buf = c & 1;
+    if (c + 1 < nchunks) load((int64_t)(c + 1) * TKC);
+#pragma unroll
+    for (int k = 0; k < TKC; ++k) {
+      const float4 a = *reinterpret_cast<const float4*>(&sA[buf][k][ty * 4]);
+      const float4 bq = *reinterpret_cast<const float4*>(&sB[buf][k][tx * 4]);
+      const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {bq.x, bq.y, bq.z, bq.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+    }
+    if (c + 1 < nchunks) store(buf ^ 1);
+    __syncthreads();
+  }
+  if (LASTMODE) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int64_t row = m0 + ty * 4 + i;
+      const int r0 = tx * 4;
+      if (row >= P) continue;
+      if (r0 + 3 < R && (R % 4) == 0) {
+        *reinterpret_cast<float4*>(out + row * R + r0) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (r0 + j < R) out[row * R + r0 + j] = acc[i][j];
+      }
+    }
+  } else {
+    const int64_t s0 = m0 + ty * 4;
+    if (s0 < S) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int r = tx * 4 + j;
+        if (r < R)
+          *reinterpret_cast<float4*>(out + (p * R + r) * S + s0) =
+              make_float4(acc[0][j], acc[1][j], acc[2][j], acc[3][j]);
+      }
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
 // V[i, c] = sum_k Y[p, i, s] Qc[k, c], k = p*S + s, Qc = [Q0 | Q0prev].
-// CTA tile: 32 rows i x C <= 64 columns x one K chunk; partial sums are added
-// to V with FP64 atomics.
+// CTA tile: 32 rows i x C <= 64 columns x one K chunk.  Every chunk writes its
+// partial sums (FP64) to its own slice of a workspace; a second kernel adds the
+// slices in a fixed order (deterministic, no atomics).
 // ----------------------------------------------------------------------------
 constexpr int VI = 32, VK = 32;
 
 template <typename TY, typename TA>
-__global__ void __launch_bounds__(256) leaf_v_kernel(const TY* __restrict__ Y, int64_t P, int64_t I, int64_t S,
+__global__ void __launch_bounds__(256) leaf_v_kernel(const TY* __restrict__ Y, int P, int I, int S,
                                                      const double* __restrict__ Q0,
-                                                     const double* __restrict__ Q0p, int R, int C,
-                                                     int64_t kchunk, double* __restrict__ V) {
+                                                     const double* __restrict__ Q0p, int R, int C, int kchunk,
+                                                     double* __restrict__ part) {
   __shared__ TA sY[VK][VI + 1];
   __shared__ TA sQ[VK][2 * CPQR_MAXR];
   const int tid = threadIdx.x;
   const int il = tid % VI, cgp = tid / VI;  // row il, columns cgp*8 .. cgp*8+7
-  const int64_t i0 = (int64_t)blockIdx.x * VI;
-  const int64_t K = P * S;
-  const int64_t kbeg = (int64_t)blockIdx.y * kchunk;
-  const int64_t kend = (kbeg + kchunk < K) ? kbeg + kchunk : K;
+  const int i0 = blockIdx.x * VI;
+  const int K = P * S;
+  const int kbeg = blockIdx.y * kchunk;
+  const int kend = (kbeg + kchunk < K) ? kbeg + kchunk : K;
   TA acc[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) acc[j] = TA(0);
-  for (int64_t k0 = kbeg; k0 < kend; k0 += VK) {
+  for (int k0 = kbeg; k0 < kend; k0 += VK) {
 #pragma unroll
     for (int q = 0; q < (VK * VI) / 256; ++q) {
-      int e = tid + 256 * q;
-      int kk = e % VK, ii = e / VK;
-      int64_t k = k0 + kk, i = i0 + ii;
+      const int e = tid + 256 * q;
+      const int kk = e % VK, ii = e / VK;
+      const int k = k0 + kk, i = i0 + ii;
       TA v = TA(0);
       if (k < kend && i < I) {
-        int64_t p = k / S, s = k - p * S;
-        v = (TA)Y[(p * I + i) * S + s];
+        const int p = k / S, s = k - p * S;
+        v = (TA)Y[((int64_t)p * I + i) * S + s];
       }
       sY[kk][ii] = v;
     }
 #pragma unroll
     for (int q = 0; q < (VK * 2 * CPQR_MAXR) / 256; ++q) {
-      int e = tid + 256 * q;
-      int kk = e / (2 * CPQR_MAXR), c = e % (2 * CPQR_MAXR);
-      int64_t k = k0 + kk;
+      const int e = tid + 256 * q;
+      const int kk = e / (2 * CPQR_MAXR), c = e % (2 * CPQR_MAXR);
+      const int k = k0 + kk;
       TA v = TA(0);
-      if (k < kend && c < C) v = (TA)((c < R) ? Q0[k * R + c] : Q0p[k * R + (c - R)]);
+      if (k < kend && c < C) v = (TA)((c < R) ? Q0[(int64_t)k * R + c] : Q0p[(int64_t)k * R + (c - R)]);
       sQ[kk][c] = v;
     }
     __syncthreads();
 #pragma unroll 8
     for (int kk = 0; kk < VK; ++kk) {
-      TA y = sY[kk][il];
+      const TA y = sY[kk][il];
 #pragma unroll
       for (int j = 0; j < 8; ++j) acc[j] += y * sQ[kk][cgp * 8 + j];
     }
     __syncthreads();
   }
-  const int64_t i = i0 + il;
+  const int i = i0 + il;
   if (i < I) {
+    double* dst = part + ((size_t)blockIdx.y * I + i) * C;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      int c = cgp * 8 + j;
-      if (c < C) atomicAdd(&V[i * C + c], (double)acc[j]);
+      const int c = cgp * 8 + j;
+      if (c < C) dst[c] = (double)acc[j];
     }
+  }
+}
+
+__global__ void sum_parts_kernel(const double* __restrict__ part, int nparts, int64_t n, double* __restrict__ V) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int q = 0; q < nparts; ++q) s += part[(size_t)q * n + e];
+    V[e] = s;
   }
 }
 
@@ -186,43 +331,186 @@ __global__ void norm2_kernel(const TX* __restrict__ X, int64_t n, double* __rest
   if (threadIdx.x == 0) atomicAdd(out, t);
 }
 
-// Explicit residual: X viewed as (rows = prod of modes 0..N-2) x (I_last); every
-// CTA takes one row, forms w_r = lambda_r prod_{n<N-1} A_n[i_n, r] in FP64 and the
-// model entries k = sum_r w_r A_last[l, r] in FP64; (x - k)^2 summed in FP64.
+// Explicit residual ||X - [[lambda; A]]||^2.  X is viewed as rows (modes 0..N-2) x I_last.
+// The factors are first copied to FP32 (lambda folded into the first).  A CTA takes tiles of
+// RT rows: the Khatri-Rao weights w[row, r] = prod_{n<N-1} A_n[i_n, r] go to shared memory,
+// every thread holds one column l of A_last (R values) in registers and forms the model
+// entries k = sum_r w[row, r] A_last[l, r] of its column for the RT rows, all in FP32; (x - k)^2
+// is summed in FP32 per thread and the per-thread totals in FP64 (FP64 runs at 1/64 of FP32 on
+// GB300: it stays out of the per-element work).  Rounding of w and k (~(N + R) 2^-24 |k|)
+// perturbs ||X - K||^2 by a relative ~1e-6 at a 1e-3 residual, the fit by ~1e-9.
 struct ResParams {
   int N, R;
-  int64_t d[CPQR_MAXN];
-  const double* A[CPQR_MAXN];
-  const double* lambda;
+  int d[CPQR_MAXN];
+  const float* A[CPQR_MAXN];  // FP32 copies, lambda folded into A[0]
 };
 
+__global__ void factors_to_f32_kernel(ResParams rp, const double* const* A64, const double* __restrict__ lambda,
+                                      float* __restrict__ dst, int total) {
+  // dst holds A_0 .. A_{N-2} back to back (I_n x R each), then A_{N-1} transposed (R x I_{N-1})
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    int off = 0, n = 0;
+    while (e >= off + rp.d[n] * rp.R) {
+      off += rp.d[n] * rp.R;
+      ++n;
+    }
+    const int loc = e - off;
+    double v = A64[n][loc];
+    if (n == 0) v *= lambda[loc % rp.R];
+    int o = e;
+    if (n == rp.N - 1) {
+      const int i = loc / rp.R, r = loc % rp.R;
+      o = off + r * rp.d[n] + i;
+    }
+    dst[o] = (float)v;
+  }
+}
+
+// Work items of 128 rows x 64 columns of X, numbered row tile major; every CTA takes one
+// contiguous range of items, so all CTAs get the same number of items (to within one).
+// The Khatri-Rao weights w[row, r] = prod_{n<N-1} A_n[i_n, r] of a row tile are formed in
+// shared memory when the CTA enters the tile and are reused by all of its column items:
+// lane = r, so every factor row is one coalesced 128-byte load, and every thread writes four
+// rows at once into sW[r][row], the row index XOR-swizzled by (r mod 8) * 4 (groups of four
+// rows stay contiguous; the 128-bit stores and reads are conflict-free).  The A_last^T chunk
+// of the next item is prefetched into registers during the product and stored into the other
+// of two buffers.  Each warp computes a 32 x 32 block of model entries K = W A_last^T, 8 rows x
+// 4 columns per thread (three 128-bit shared loads per 32 FMAs), with the thread's X values
+// loaded before the product, and accumulates (x - k)^2.
+constexpr int RM = 128, RC = 64, RNT = 256;
+
+__device__ __forceinline__ int wswz(int r, int row) { return row ^ ((r & 7) << 2); }
+
 template <typename TX>
-__global__ void residual2_kernel(const TX* __restrict__ X, ResParams rp, int64_t rows, double* __restrict__ out) {
-  __shared__ double w[CPQR_MAXR];
+__global__ void __launch_bounds__(RNT, 2) residual2_kernel(const TX* __restrict__ X, const __grid_constant__ ResParams rp,
+                                                           int rows, double* __restrict__ out) {
+  __shared__ __align__(16) float sW[CPQR_MAXR][RM];
+  __shared__ __align__(16) float sA[2][CPQR_MAXR][RC];
   __shared__ double sh[32];
   const int R = rp.R, N = rp.N;
-  const int64_t Il = rp.d[N - 1];
+  const int Il = rp.d[N - 1];
+  const int nchunks = (Il + RC - 1) / RC;
+  const int64_t total = (int64_t)((rows + RM - 1) / RM) * nchunks;
+  const int64_t u0 = total * blockIdx.x / gridDim.x, u1 = total * (blockIdx.x + 1) / gridDim.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int tx = lane & 7, ty = lane >> 3;
+  const int rloc = (warp >> 1) * 32 + ty * 8;  // first of this thread's 8 rows in the tile
+  const int cloc = (warp & 1) * 32 + tx * 4;   // first of its 4 columns in the item
+  const bool vec4 = std::is_same<TX, float>::value && (Il % 4) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+  const float* AlT = rp.A[N - 1];  // R x I_last
+
+  // A_last^T chunk q: element e = threadIdx.x + 256 j is (r = e / 64, column e % 64)
+  // element j of a thread: r = threadIdx.x / 64 + 4 j, column threadIdx.x % 64 of the chunk
+  const int ar = threadIdx.x / RC, ac = threadIdx.x % RC;
+  float an[8];
+  auto loadA = [&](int q) {
+    const int col = q * RC + ac;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int r = ar + 4 * j;
+      an[j] = (r < R && col < Il) ? AlT[(int64_t)r * Il + col] : 0.f;
+    }
+  };
+  auto storeA = [&](int buf) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) sA[buf][ar + 4 * j][ac] = an[j];
+  };
+  // rows of sW and sA beyond R hold zeros, so the product may run over R rounded up to 8
+  const int R8 = (R + 7) & ~7;
   double acc = 0.0;
-  for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
-    if (threadIdx.x < R) {
-      double v = rp.lambda[threadIdx.x];
-      int64_t x = row;
-      for (int n = N - 2; n >= 0; --n) {
-        int64_t in = x % rp.d[n];
-        x /= rp.d[n];
-        v *= rp.A[n][in * R + threadIdx.x];
+  int cur_rt = -1, buf = 0;
+  int rt = (int)(u0 / nchunks), q = (int)(u0 % nchunks);  // item u0; advanced incrementally
+  if (u0 < u1) {
+    loadA(q);
+    storeA(0);
+  }
+  for (int64_t u = u0; u < u1; ++u) {
+    const int r0 = rt * RM;
+    if (rt != cur_rt) {
+      __syncthreads();  // every warp is done with the previous tile's weights
+      // rows r0 + 4g .. r0 + 4g + 3 for g = warp, warp + 8, warp + 16, warp + 24; r = lane
+#pragma unroll
+      for (int gg = 0; gg < 4; ++gg) {
+        const int g = warp + 8 * gg;
+        float w[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int row = r0 + 4 * g + i;
+          float v = 0.f;
+          if (row < rows && lane < R) {
+            v = 1.f;
+            int x = row;
+            for (int n = N - 2; n > 0; --n) {
+              const int qd = x / rp.d[n];
+              v *= rp.A[n][(int64_t)(x - qd * rp.d[n]) * R + lane];
+              x = qd;
+            }
+            v *= rp.A[0][(int64_t)x * R + lane];
+          }
+          w[i] = v;
+        }
+        *reinterpret_cast<float4*>(&sW[lane][wswz(lane, 4 * g)]) = make_float4(w[0], w[1], w[2], w[3]);
       }
-      w[threadIdx.x] = v;
+      cur_rt = rt;
     }
-    __syncthreads();
-    for (int64_t l = threadIdx.x; l < Il; l += blockDim.x) {
-      double k = 0.0;
-      const double* al = rp.A[N - 1] + l * R;
-      for (int r = 0; r < R; ++r) k += w[r] * al[r];
-      double e = (double)X[row * Il + l] - k;
-      acc += e * e;
+    __syncthreads();  // weights and sA[buf] complete
+    // X values of this thread's 8 x 4 block, issued before the product
+    const int cb = q * RC + cloc;
+    float xv[8][4];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int xrow = r0 + rloc + i;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) xv[i][j] = 0.f;
+      if (xrow >= rows) continue;
+      const TX* xr = X + (int64_t)xrow * Il + cb;
+      if (vec4) {
+        if (cb < Il) {  // Il % 4 == 0: the whole float4 is inside the row
+          const float4 x4 = *reinterpret_cast<const float4*>(xr);
+          xv[i][0] = x4.x; xv[i][1] = x4.y; xv[i][2] = x4.z; xv[i][3] = x4.w;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (cb + j < Il) xv[i][j] = (float)xr[j];
+      }
     }
-    __syncthreads();
+    const bool more = u + 1 < u1;
+    const int qn = (q + 1 == nchunks) ? 0 : q + 1;
+    if (more) loadA(qn);
+    float k[8][4];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) k[i][j] = 0.f;
+    for (int rb = 0; rb < R8; rb += 8) {
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {  // r = rb + t, so r mod 8 = t is known here
+        const int r = rb + t;
+        const float4 w0 = *reinterpret_cast<const float4*>(&sW[r][wswz(t, rloc)]);
+        const float4 w1 = *reinterpret_cast<const float4*>(&sW[r][wswz(t, rloc + 4)]);
+        const float4 a4 = *reinterpret_cast<const float4*>(&sA[buf][r][cloc]);
+        const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w}, av[4] = {a4.x, a4.y, a4.z, a4.w};
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) k[i][j] = fmaf(wv[i], av[j], k[i][j]);
+      }
+    }
+    // entries outside X have x = 0 and k = 0 (zero weights / zero A_last columns)
+    float racc = 0.f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float e = xv[i][j] - k[i][j];
+        racc = fmaf(e, e, racc);
+      }
+    acc += (double)racc;
+    if (more) storeA(buf ^ 1);  // that buffer was last read in the previous item, before this item's barrier
+    buf ^= 1;
+    q = qn;
+    if (q == 0) ++rt;
   }
   double t = block_sum(acc, sh);
   if (threadIdx.x == 0) atomicAdd(out, t);
@@ -259,29 +547,62 @@ template cudaError_t launch_ttm<float, double, double>(const float*, const doubl
 template cudaError_t launch_ttm<float, float, float>(const float*, const float*, float*, int64_t, int64_t, int64_t,
                                                      int, cudaStream_t);
 
+cudaError_t launch_ttm_f32_tiled(const float* T, const float* Q, float* out, int64_t P, int64_t K, int64_t S, int R,
+                                 cudaStream_t st) {
+  if (R < 1 || R > CPQR_MAXR || P < 1 || K < 1 || S < 1) return cudaErrorInvalidValue;
+  // float4 accesses: the tensor and the output must be 16-byte aligned
+  if ((reinterpret_cast<uintptr_t>(T) & 15) || (reinterpret_cast<uintptr_t>(out) & 15)) return cudaErrorNotSupported;
+  if (S == 1) {
+    if (K % 4) return cudaErrorNotSupported;
+    const int64_t blocks = (P + TBM - 1) / TBM;
+    if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
+    ttm_f32_tiled_kernel<true><<<(unsigned)blocks, TNT, 0, st>>>(T, Q, out, P, K, S, R, 1);
+  } else {
+    if (S % 4) return cudaErrorNotSupported;
+    const int64_t sb = (S + TBM - 1) / TBM;
+    const int64_t blocks = P * sb;
+    if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
+    ttm_f32_tiled_kernel<false><<<(unsigned)blocks, TNT, 0, st>>>(T, Q, out, P, K, S, R, sb);
+  }
+  return cudaGetLastError();
+}
+
+int leaf_v_splits(int64_t I, int64_t K) {
+  // split K so that the grid covers the GPU about twice, with at least two VK chunks per split
+  const int64_t itiles = (I + VI - 1) / VI;
+  int64_t want = (2 * 152 + itiles - 1) / itiles;
+  const int64_t maxs = (K + 2 * VK - 1) / (2 * VK);
+  if (want > maxs) want = maxs;
+  if (want < 1) want = 1;
+  return (int)want;
+}
+
 template <typename TY>
 cudaError_t launch_leaf_v(const TY* Y, int64_t P, int64_t I, int64_t S, const double* Q0, const double* Q0prev,
-                          int R, int C, double* V, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(V, 0, sizeof(double) * I * C, st);
-  if (e != cudaSuccess) return e;
+                          int R, int C, double* V, double* work, cudaStream_t st) {
   const int64_t K = P * S;
+  if (K > 0x7fffffff || I > 0x7fffffff) return cudaErrorInvalidValue;
+  if (C < 1 || C > 2 * CPQR_MAXR || R < 1 || R > CPQR_MAXR) return cudaErrorInvalidValue;
   const int64_t itiles = (I + VI - 1) / VI;
-  // split K so that the grid covers the GPU about twice
-  int64_t want = (2 * 152 + itiles - 1) / itiles;
-  int64_t kchunk = (K + want - 1) / want;
+  const int splits = leaf_v_splits(I, K);
+  int64_t kchunk = (K + splits - 1) / splits;
   kchunk = ((kchunk + VK - 1) / VK) * VK;
   if (kchunk < VK) kchunk = VK;
-  const int64_t ktiles = (K + kchunk - 1) / kchunk;
+  const int64_t ktiles = (K + kchunk - 1) / kchunk;  // <= splits: fits the work slices
   dim3 grid((unsigned)itiles, (unsigned)ktiles);
   using TA = typename std::conditional<std::is_same<TY, double>::value, double, float>::type;
-  leaf_v_kernel<TY, TA><<<grid, 256, 0, st>>>(Y, P, I, S, Q0, Q0prev, R, C, kchunk, V);
+  leaf_v_kernel<TY, TA><<<grid, 256, 0, st>>>(Y, (int)P, (int)I, (int)S, Q0, Q0prev, R, C, (int)kchunk, work);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int64_t n = I * C;
+  sum_parts_kernel<<<(int)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, st>>>(work, (int)ktiles, n, V);
   return cudaGetLastError();
 }
 
 template cudaError_t launch_leaf_v<double>(const double*, int64_t, int64_t, int64_t, const double*, const double*,
-                                           int, int, double*, cudaStream_t);
+                                           int, int, double*, double*, cudaStream_t);
 template cudaError_t launch_leaf_v<float>(const float*, int64_t, int64_t, int64_t, const double*, const double*,
-                                          int, int, double*, cudaStream_t);
+                                          int, int, double*, double*, cudaStream_t);
 
 template <typename TX>
 cudaError_t launch_norm2(const TX* X, int64_t n, double* out, double* /*work*/, cudaStream_t st) {
@@ -293,23 +614,44 @@ cudaError_t launch_norm2(const TX* X, int64_t n, double* out, double* /*work*/, 
 template cudaError_t launch_norm2<float>(const float*, int64_t, double*, double*, cudaStream_t);
 template cudaError_t launch_norm2<double>(const double*, int64_t, double*, double*, cudaStream_t);
 
+size_t residual2_work_bytes(int N, const int64_t* d, int R) {
+  int64_t total = 0;
+  for (int n = 0; n < N; ++n) total += d[n] * R;
+  return (size_t)((total + 3) / 4) * 16 + CPQR_MAXN * sizeof(double*) + 64;
+}
+
 template <typename TX>
 cudaError_t launch_residual2(const TX* X, int N, const int64_t* d, const double* const* A, const double* lambda,
-                             int R, double* out, double* /*work*/, cudaStream_t st) {
+                             int R, double* out, double* work, cudaStream_t st) {
+  // work: >= sum_n d[n] * R floats + N pointers (device)
   ResParams rp{};
   rp.N = N;
   rp.R = R;
-  int64_t rows = 1;
+  int64_t rows = 1, total = 0;
   for (int n = 0; n < N; ++n) {
-    rp.d[n] = d[n];
-    rp.A[n] = A[n];
+    if (d[n] > 0x7fffffff) return cudaErrorInvalidValue;
+    rp.d[n] = (int)d[n];
     if (n < N - 1) rows *= d[n];
+    total += d[n] * R;
   }
-  rp.lambda = lambda;
-  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), st);
+  if (rows > 0x7fffffff || total > 0x7fffffff) return cudaErrorInvalidValue;
+  float* f32 = reinterpret_cast<float*>(work);
+  const double** ptrs = reinterpret_cast<const double**>(f32 + ((total + 3) / 4) * 4);
+  int64_t off = 0;
+  for (int n = 0; n < N; ++n) {
+    rp.A[n] = f32 + off;
+    off += d[n] * R;
+  }
+  cudaError_t e = cudaMemcpyAsync(ptrs, A, N * sizeof(double*), cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return e;
-  int grid = (int)((rows < 152 * 16) ? rows : 152 * 16);
-  residual2_kernel<TX><<<grid, 256, 0, st>>>(X, rp, rows, out);
+  factors_to_f32_kernel<<<(int)std::min<int64_t>((total + 255) / 256, 512), 256, 0, st>>>(rp, ptrs, lambda, f32,
+                                                                                         (int)total);
+  e = cudaMemsetAsync(out, 0, sizeof(double), st);
+  if (e != cudaSuccess) return e;
+  // contiguous ranges of (row tile, column chunk) items, two CTAs per SM
+  const int64_t items = ((rows + RM - 1) / RM) * ((d[N - 1] + RC - 1) / RC);
+  const int grid = (int)std::min<int64_t>(items, 152 * 2);
+  residual2_kernel<TX><<<grid, RNT, 0, st>>>(X, rp, (int)rows, out);
   return cudaGetLastError();
 }
 template cudaError_t launch_residual2<float>(const float*, int, const int64_t*, const double* const*, const double*,

@@ -31,8 +31,11 @@ def _rel(a, ref):
     return float(np.max(np.abs(a - ref)) / max(np.max(np.abs(ref)), 1e-300))
 
 
+# ragged tails; S == 1 with K % 4 == 0 and S % 4 == 0 reach the register-tiled FP32 kernel,
+# the other shapes the generic one
 TTM_SHAPES = [((37, 53, 29), 5), ((64, 65, 66), 32), ((9, 10, 11, 12), 7), ((3, 200, 2), 2), ((130, 7, 1, 5), 1),
-              ((5, 6, 7, 8, 9), 4), ((128, 128, 3), 24)]
+              ((5, 6, 7, 8, 9), 4), ((128, 128, 3), 24), ((300, 32, 400), 32), ((32, 400, 132), 24),
+              ((9, 8, 12, 20), 16)]
 
 
 @pytest.mark.parametrize("dims,R", TTM_SHAPES)
@@ -178,3 +181,18 @@ def test_split_precision_solver_tracks_oracle(name, cfg, tree, extrap, beta, swe
     assert np.max(np.abs(fits - np.array(ref.fits))) <= 1e-4, (fits, ref.fits)
     for n in range(len(prob.dims)):
         assert o.subspace_sine(A[n], ref.A[n]) <= 1e-4
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_fit_exact_matches_dense_residual(dtype):
+    """cp_als_qr_fit_exact against the oracle's dense ||X - [[lambda; A]]|| with the GPU's own factors."""
+    prob = inputs.make_problem("fx", [31, 29, 33], 6, seed=12, c=0.4, eta=3e-3, dtype=dtype)
+    X = _dev(prob.X)
+    opts = b.make_options(tree=b.TREE_RESTRUCTURED, prec=b.PREC_FP64, extrap=b.EXTRAP_NONE)
+    with b.Decomposition(prob.dims, prob.R, X.data_ptr(), dtype == np.float64, prob.A0, opts) as d:
+        fits = d.sweep(15)
+        A, lam, _, _ = d.factors()
+        fx = d.fit_exact()
+    ref = o.fit_explicit(prob.X, lam, A)
+    assert abs(fx - ref) <= 1e-8
+    assert abs(fits[-1] - ref) <= 1e-8
