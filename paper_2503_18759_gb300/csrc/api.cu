@@ -481,7 +481,7 @@ cpqr_status read_fit(cpqr_ctx* ctx, double* fit) {
     const double* A[CPQR_MAXN];
     for (int n = 0; n < ctx->N; ++n) A[n] = ctx->A[n];
     CK(launch_residual2<float>((const float*)ctx->X, ctx->N, ctx->dims.data(), A, ctx->lambda, ctx->R,
-                               ctx->d_scalar, ctx->res_work, ctx->st));
+                               ctx->d_scalar, ctx->res_work, ctx->dstatus, ctx->st));
   }
   {
     Timed tm(ctx, CPQR_BUCKET_OTHER, 0);
@@ -932,12 +932,16 @@ cpqr_status cp_als_qr_fit_exact(cpqr_ctx* ctx, double* fit) {
   for (int n = 0; n < ctx->N; ++n) A[n] = ctx->A[n];
   if (ctx->x64)
     CK(launch_residual2<double>((const double*)ctx->X, ctx->N, ctx->dims.data(), A, ctx->lambda, ctx->R,
-                                ctx->d_scalar, ctx->res_work, ctx->st));
+                                ctx->d_scalar, ctx->res_work, ctx->dstatus, ctx->st));
   else
     CK(launch_residual2<float>((const float*)ctx->X, ctx->N, ctx->dims.data(), A, ctx->lambda, ctx->R,
-                               ctx->d_scalar, ctx->res_work, ctx->st));
+                               ctx->d_scalar, ctx->res_work, ctx->dstatus, ctx->st));
   CK(cudaMemcpyAsync(ctx->h_pinned, ctx->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaMemcpyAsync(ctx->h_pinned + 2, ctx->dstatus, sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
+  unsigned int ds;
+  std::memcpy(&ds, ctx->h_pinned + 2, sizeof(ds));
+  if (ds & CPQR_DEV_TIMEOUT) return fail(ctx, CPQR_ETIMEOUT);
   *fit = 1.0 - std::sqrt(std::max(ctx->h_pinned[0], 0.0)) / std::sqrt(ctx->normX2);
   return CPQR_OK;
 }

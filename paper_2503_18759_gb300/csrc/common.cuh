@@ -93,11 +93,21 @@ template <typename TX>
 cudaError_t launch_norm2(const TX* X, int64_t n, double* out, double* work, cudaStream_t st);
 
 // ||X - [[lambda; A]]||^2 (FP32 model entries, FP64 total); X dims d[0..N-1]; A: host array of N
-// device pointers; work: device scratch of residual2_work_bytes(N, d, R).
+// device pointers; work: device scratch of residual2_work_bytes(N, d, R).  FP32 tensors whose
+// last dimension is a multiple of 4 go to the tensor-core kernel (residual_tc.cu), the rest to
+// a CUDA-core kernel.  dev_status collects CPQR_DEV_TIMEOUT of the tensor-core kernel.
 size_t residual2_work_bytes(int N, const int64_t* d, int R);
 template <typename TX>
 cudaError_t launch_residual2(const TX* X, int N, const int64_t* d, const double* const* A,
-                             const double* lambda, int R, double* out, double* work, cudaStream_t st);
+                             const double* lambda, int R, double* out, double* work, unsigned int* dev_status,
+                             cudaStream_t st);
+
+// ----- tensor-core explicit residual (residual_tc.cu) -----
+// Af: host array of N device pointers to the FP32 factors (lambda folded into Af[0], Af[N-1]
+// stored transposed, R x I_last); accumulates ||X - K||^2 into *out (not cleared).
+bool residual_tc_supported(int N, const int64_t* d, int R, const void* X);
+cudaError_t launch_residual_tc(const float* X, int N, const int64_t* d, const float* const* Af, int R, double* out,
+                               unsigned int* dev_status, cudaStream_t st);
 
 cudaError_t launch_to_f32(const double* a, float* b, int64_t n, cudaStream_t st);
 

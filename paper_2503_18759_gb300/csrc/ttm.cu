@@ -622,7 +622,7 @@ size_t residual2_work_bytes(int N, const int64_t* d, int R) {
 
 template <typename TX>
 cudaError_t launch_residual2(const TX* X, int N, const int64_t* d, const double* const* A, const double* lambda,
-                             int R, double* out, double* work, cudaStream_t st) {
+                             int R, double* out, double* work, unsigned int* dev_status, cudaStream_t st) {
   // work: >= sum_n d[n] * R floats + N pointers (device)
   ResParams rp{};
   rp.N = N;
@@ -648,6 +648,10 @@ cudaError_t launch_residual2(const TX* X, int N, const int64_t* d, const double*
                                                                                          (int)total);
   e = cudaMemsetAsync(out, 0, sizeof(double), st);
   if (e != cudaSuccess) return e;
+  if (std::is_same<TX, float>::value && residual_tc_supported(N, d, R, X)) {
+    e = launch_residual_tc(reinterpret_cast<const float*>(X), N, d, rp.A, R, out, dev_status, st);
+    if (e != cudaErrorNotSupported) return e;
+  }
   // contiguous ranges of (row tile, column chunk) items, two CTAs per SM
   const int64_t items = ((rows + RM - 1) / RM) * ((d[N - 1] + RC - 1) / RC);
   const int grid = (int)std::min<int64_t>(items, 152 * 2);
@@ -655,9 +659,9 @@ cudaError_t launch_residual2(const TX* X, int N, const int64_t* d, const double*
   return cudaGetLastError();
 }
 template cudaError_t launch_residual2<float>(const float*, int, const int64_t*, const double* const*, const double*,
-                                             int, double*, double*, cudaStream_t);
+                                             int, double*, double*, unsigned int*, cudaStream_t);
 template cudaError_t launch_residual2<double>(const double*, int, const int64_t*, const double* const*,
-                                              const double*, int, double*, double*, cudaStream_t);
+                                              const double*, int, double*, double*, unsigned int*, cudaStream_t);
 
 cudaError_t launch_to_f32(const double* a, float* b, int64_t n, cudaStream_t st) {
   to_f32_kernel<<<grid_for(n, 256 * 4), 256, 0, st>>>(a, b, n);

@@ -4,11 +4,9 @@
 // hi = bf16(X), lo = bf16(X - hi).  Each Q_k (FP64) is staged after its QR as
 // bf16 hi/lo of Q_k^T, zero-padded to Rp x Kp (the MMA's N x K operand, K
 // contiguous).  The product keeps hi*hi + hi*lo + lo*hi and drops lo*lo.
-#include <cuda.h>
-
 #include <algorithm>
 
-#include "common.cuh"
+#include "tc_common.cuh"
 
 namespace cpqr {
 
@@ -107,7 +105,6 @@ constexpr int TC_HALF_BYTES = 64 * 64 * 2;  // one 64 x 64 bf16 box
 constexpr int TC_STAGE_BYTES = 4 * TC_HALF_BYTES;  // hi h0, hi h1, lo h0, lo h1
 constexpr int TC_MAX_KB = 8;                // K <= 512
 constexpr int TC_TMEM_COLS = 64;            // two accumulators of up to 32 columns
-constexpr unsigned long long TC_TIMEOUT_NS = 2000000000ull;
 
 struct TcParams {
   int64_t P, K, S;
@@ -132,130 +129,7 @@ struct TcSmemTail {
   int consumed[TC_NST];
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ unsigned long long gtimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t a) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(a), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait: false on timeout or (honor_abort) when another role has aborted.
-__device__ bool mbar_wait(uint32_t a, uint32_t parity, TcSmemTail* tail, unsigned int* status,
-                          bool honor_abort = true) {
-  unsigned long long t0 = 0;
-  for (int it = 0;; ++it) {
-    if (mbar_try(a, parity)) return true;
-    if ((it & 255) == 255) {
-      if (honor_abort && *(volatile int*)&tail->abort_flag) return false;
-      unsigned long long now = gtimer();
-      if (t0 == 0) t0 = now;
-      else if (now - t0 > TC_TIMEOUT_NS) {
-        atomicOr(status, CPQR_DEV_TIMEOUT);
-        *(volatile int*)&tail->abort_flag = 1;
-        return false;
-      }
-    }
-  }
-}
-
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* tm, int c0, int c1, int c2,
-                                            uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
-      : "memory");
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm, int c0, int c1, uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(bar)
-      : "memory");
-}
-
-// Shared-memory matrix descriptor (tcgen05): start, leading / stride byte offsets,
-// descriptor version 1, 128-byte swizzle.  Atoms are 1024-byte aligned.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-  d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
-  return d;
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accum) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-      ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-               : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
+using namespace tc;
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
     ttm_tc_kernel(const __grid_constant__ CUtensorMap tmXhi, const __grid_constant__ CUtensorMap tmXlo,
@@ -293,9 +167,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  tc_fence_before();
+  fence_before();
   __syncthreads();
-  tc_fence_after();
+  fence_after();
   const uint32_t tmem = tail->tmem_base;
 
   const int64_t ntile_local = (p.T > (int64_t)blockIdx.x) ? (p.T - 1 - blockIdx.x) / gridDim.x + 1 : 0;
@@ -322,7 +196,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           sb1 = (int)(h1 % p.nsb);
         }
         for (int kb = 0; kb < p.nkb; ++kb) {
-          if (!mbar_wait(smem_u32(&tail->empty[stage]), phase ^ 1u, tail, p.status)) {
+          if (!mbar_wait(smem_u32(&tail->empty[stage]), phase ^ 1u, &tail->abort_flag, p.status)) {
             ok = false;
             break;
           }
@@ -346,23 +220,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       // ---------------- MMA issuer ----------------
       const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | ((uint32_t)(p.Rp >> 3) << 17) |
                              ((uint32_t)(128 >> 4) << 24);
-      bool ok = mbar_wait(smem_u32(&tail->bfull), 0, tail, p.status);
-      tc_fence_after();
+      bool ok = mbar_wait(smem_u32(&tail->bfull), 0, &tail->abort_flag, p.status);
+      fence_after();
       int stage = 0;
       uint32_t phase = 0;
       for (int64_t lt = 0; lt < ntile_local && ok; ++lt) {
         const int acc = (int)(lt & 1);
         const uint32_t use = (uint32_t)(lt >> 1);
-        if (!mbar_wait(smem_u32(&tail->tempty[acc]), (use & 1u) ^ 1u, tail, p.status)) break;
-        tc_fence_after();
+        if (!mbar_wait(smem_u32(&tail->tempty[acc]), (use & 1u) ^ 1u, &tail->abort_flag, p.status)) break;
+        fence_after();
         const uint32_t d = tmem + (uint32_t)(acc * 32);
         for (int kb = 0; kb < p.nkb; ++kb) {
-          if (!mbar_wait(smem_u32(&tail->full[stage]), phase, tail, p.status)) {
+          if (!mbar_wait(smem_u32(&tail->full[stage]), phase, &tail->abort_flag, p.status)) {
             ok = false;
             break;
           }
           tail->consumed[stage] += 1;
-          tc_fence_after();
+          fence_after();
           const uint32_t a_hi = sA + stage * TC_STAGE_BYTES;
           const uint32_t a_lo = a_hi + 2 * TC_HALF_BYTES;
           const uint32_t b_hi = sB + (2 * kb) * bsub, b_lo = b_hi + bsub;
@@ -387,7 +261,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
       // every MMA issued above has completed once tdown flips
       mma_commit(smem_u32(&tail->tdown));
-      mbar_wait(smem_u32(&tail->tdown), 0, tail, p.status, false);
+      mbar_wait(smem_u32(&tail->tdown), 0, &tail->abort_flag, p.status, false);
     }
   } else {
     // ---------------- epilogue: warps 0-3, tensor-memory lanes 32w .. 32w+31 ----------------
@@ -395,13 +269,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     for (int64_t lt = 0; lt < ntile_local; ++lt) {
       const int acc = (int)(lt & 1);
       const uint32_t use = (uint32_t)(lt >> 1);
-      if (!mbar_wait(smem_u32(&tail->tfull[acc]), use & 1u, tail, p.status)) break;
-      tc_fence_after();
+      if (!mbar_wait(smem_u32(&tail->tfull[acc]), use & 1u, &tail->abort_flag, p.status)) break;
+      fence_after();
       float v[32];
       const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc * 32);
       if (p.Rp == 32) tmem_ld32(taddr, v);
       else tmem_ld16(taddr, v);
-      tc_fence_before();
+      fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&tail->tempty[acc]));
       const int64_t tile = blockIdx.x + lt * gridDim.x;
@@ -427,37 +301,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const int pending = tail->issued[st] - tail->consumed[st];
       if (pending > 0) {
         const uint32_t par = (uint32_t)((tail->issued[st] - 1) & 1);
-        mbar_wait(smem_u32(&tail->full[st]), par, tail, p.status, false);
+        mbar_wait(smem_u32(&tail->full[st]), par, &tail->abort_flag, p.status, false);
       }
     }
   }
   __syncthreads();
   if (warp == 4) {
-    tc_fence_after();
+    fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
   }
 }
-
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
-    void* ptr = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(ptr);
-  }
-  return fn;
-}
-
-int g_num_sms = 0;
 
 }  // namespace
 
@@ -475,7 +328,7 @@ cudaError_t launch_ttm_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo, co
   if (!ttm_tc_supported(P, K, S, R) || (Rp != 16 && Rp != 32) || Rp < R || Kp < K || (Kp % 64) != 0)
     return cudaErrorNotSupported;
   if (((uintptr_t)Xhi & 15) || ((uintptr_t)Xlo & 15) || ((uintptr_t)Qt & 15)) return cudaErrorMisalignedAddress;
-  EncodeTiledFn enc = encode_fn();
+  tc::EncodeTiledFn enc = tc::encode_tiled_fn();
   if (!enc) return cudaErrorNotSupported;
   CUtensorMap tmh, tml, tmq;
   {
@@ -515,18 +368,42 @@ cudaError_t launch_ttm_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo, co
   prm.out = out;
   prm.status = dev_status;
   if (prm.nkb * 64 > Kp) return cudaErrorInvalidValue;
-  if (!g_num_sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_num_sms <= 0) g_num_sms = 148;
-  }
   const size_t smem = 1024 + (size_t)TC_NST * TC_STAGE_BYTES + (size_t)prm.nkb * 2 * Rp * 128 + sizeof(TcSmemTail);
   cudaError_t e = cudaFuncSetAttribute(ttm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int64_t grid = std::min<int64_t>(prm.T, g_num_sms);
+  const int64_t grid = std::min<int64_t>(prm.T, tc::num_sms());
   ttm_tc_kernel<<<(unsigned)grid, TC_THREADS, smem, st>>>(tmh, tml, tmq, prm);
   return cudaGetLastError();
 }
+
+namespace tc {
+
+EncodeTiledFn encode_tiled_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(ptr);
+  }
+  return fn;
+}
+
+int num_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 148;
+  }
+  return n;
+}
+
+}  // namespace tc
 
 }  // namespace cpqr

@@ -196,3 +196,19 @@ def test_fit_exact_matches_dense_residual(dtype):
     ref = o.fit_explicit(prob.X, lam, A)
     assert abs(fx - ref) <= 1e-8
     assert abs(fits[-1] - ref) <= 1e-8
+
+
+@pytest.mark.parametrize("dims,R", [([37, 29, 36], 6), ([20, 30, 260], 8), ([36, 33, 40, 64], 32)])
+def test_fit_exact_tensor_core_residual(dims, R):
+    """FP32 tensors whose last dimension is a multiple of 4 take the tensor-core residual (3xTF32):
+    ragged row tiles (37 * 29 = 1073 rows), a masked column tail (36 of 64 MMA columns), two
+    column groups (I_last = 260), order 4 with R = 32.  Fit against the oracle's dense residual."""
+    prob = inputs.make_problem("fxtc", dims, R, seed=13, c=0.5, eta=2e-3, dtype=np.float32)
+    X = _dev(prob.X)
+    opts = b.make_options(tree=b.TREE_RESTRUCTURED, prec=b.PREC_FP64, extrap=b.EXTRAP_NONE)
+    with b.Decomposition(prob.dims, prob.R, X.data_ptr(), False, prob.A0, opts) as d:
+        d.sweep(6)
+        A, lam, _, _ = d.factors()
+        fx = d.fit_exact()
+    ref = o.fit_explicit(prob.X, lam, A)
+    assert abs(fx - ref) <= 1e-8
