@@ -9,13 +9,22 @@
 //
 // GB300 has ~8 GFLOP/s of FP64 per SM, so these run on one thread-block
 // cluster of 16 CTAs (8 where 16 cannot be scheduled) that own the rows
-// round-robin.  Each Householder column costs one cluster barrier: every CTA
-// reduces [x^T a_c (c >= j), pivot row] over its rows and pushes the sums into
-// every peer's shared memory before the barrier, so after it the reduction is
-// local; every CTA then applies the reflector to its rows.  Q is formed with
-// the compact-WY (UT) representation: Q = E - V T V_top^T with
-// T^{-1} = striu(V^T V) + diag(V^T V)/2 (reduce-scatter + all-gather of V^T V
-// over the cluster, two more barriers).
+// round-robin; every row stays with one warp from start to end.  The 32
+// Householder columns form a serial chain, so the kernel is built around the
+// latency of one column:
+//  * one exchange per column: every CTA reduces x_j^T a_c over its rows for
+//    all c (c >= j gives the norm and the reflector products, c < j gives the
+//    entries v_c^T v_j of V^T V for the compact-WY form at no extra cost) and
+//    stores the sums into every peer's shared memory with st.async, which
+//    completes the bytes on the peer's mbarrier: no cluster barrier, and the
+//    pivot row, pushed by its owner, also gives the top block of V;
+//  * the reflector of column j-1 is applied row by row in the same pass that
+//    forms the products of column j;
+//  * the norm uses the 53-bit rsqrt.approx.f64 and the reflector scale a
+//    reciprocal from rcp.approx.f64 refined by two Newton-Raphson steps.
+// Q is formed with the compact-WY (UT) representation: Q = E - V T V_top^T with
+// T^{-1} = striu(V^T V) + diag(V^T V)/2; the columns of W2 = T V_top^T are
+// back-substituted by different CTAs and all-gathered with st.async.
 //
 // Khatri-Rao rows are processed sorted by the largest index among their
 // digits: a row whose digits are <= m is zero in columns < m because every
@@ -26,6 +35,7 @@
 #include <cstdlib>
 
 #include "common.cuh"
+#include "tc_common.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -49,11 +59,15 @@ namespace cpqr {
 
 namespace {
 
+using tc::smem_u32;
+
 constexpr int NT = kQrThreads;
 constexpr int NW = NT / 32;
 constexpr int MAXCL = 16;
-constexpr int PSLOT = 2 * CPQR_MAXR + 2;  // partial-sum slots per step
+constexpr int PSLOT = 2 * CPQR_MAXR + 2;  // partial-sum slots of the finish prologue exchange
 constexpr int RR = CPQR_MAXR * CPQR_MAXR;
+constexpr int W2LD = CPQR_MAXR + 2;       // row stride of W2T (16-byte aligned rows, few bank conflicts)
+constexpr unsigned FULL = 0xffffffffu;
 
 enum { MODE_PLAIN = 0, MODE_KRP = 1, MODE_FINISH = 2 };
 
@@ -84,21 +98,23 @@ struct QrParams {
 };
 
 struct SmemLayout {
-  double inbox[2][MAXCL][PSLOT];  // partial sums pushed by every CTA of the cluster (double buffered)
-  double pivbox[2][CPQR_MAXR];    // pivot row of the current column, pushed by its owner CTA
-  double pivloc[CPQR_MAXR];       // pivot row as seen by the owning warp
-  double dvec[CPQR_MAXR];         // cluster-wide x^T a_c of the current column
-  double red[NW][PSLOT];          // per-warp partial sums
-  double bcw[CPQR_MAXR];          // broadcast w_c of the current step
+  alignas(16) double cbox[2][MAXCL][CPQR_MAXR];  // per-column sums of every CTA (st.async, 2 buffers)
+  alignas(16) double pbox[2][CPQR_MAXR];         // pivot row of the column (st.async by its owner)
+  alignas(16) double W2T[CPQR_MAXR][W2LD];       // W2T[c][a] = (T V_top^T)[a][c] (st.async all-gather)
+  unsigned long long bar[3];                     // mbarriers: cbox/pbox buffer 0, 1; W2T
+  int abort_flag;
+  int pad_;
+  double inbox1[MAXCL][PSLOT];  // finish prologue: partial sums pushed by every CTA (cluster barrier)
+  double red[NW][PSLOT];        // per-warp partial sums
+  double pivloc[CPQR_MAXR];     // pivot row as seen by the owning warp
+  double dvec[CPQR_MAXR];       // cluster-wide x_j^T a_c of the current column
+  double bcw[CPQR_MAXR];        // tau (x_j^T a_c - alpha a_jc): reflector product per column
   double alpha[CPQR_MAXR];
   double tau[CPQR_MAXR];
   double vpiv[CPQR_MAXR];
-  double spart[RR];               // this CTA's partial V^T V (upper entries), then scratch
-  double sinbox[MAXCL][RR / 8];   // reduce-scatter inbox: entries i with i % CL == rank
-  double Ssum[RR];                // total V^T V
-  double vtop[RR];                // v_a[t] for t < R (row-major [t][a]) of the whole cluster
-  double W2[RR];
-  double R0[RR];                  // finish: R0
+  double ST[CPQR_MAXR][CPQR_MAXR];  // ST[b][a] = v_a^T v_b, a < b
+  double VT[CPQR_MAXR][CPQR_MAXR];  // VT[c][a] = v_a[c], a <= c (top block of V, transposed)
+  double R0[RR];                    // finish: R0
   double rdiag[CPQR_MAXR];
 };
 
@@ -127,6 +143,33 @@ __device__ __forceinline__ double tree8(const double* v, int stride) {
          ((v[4 * stride] + v[5 * stride]) + (v[6 * stride] + v[7 * stride]));
 }
 
+// 1/sqrt(s) for the column norm: rsqrt.approx.f64 (measured to 53 bits on sm_103) inside the
+// normal range, the IEEE path outside it.
+__device__ __forceinline__ double col_rsqrt(double s) {
+  if (s > 1e-280 && s < 1e280) {
+    double y;
+    asm("rsqrt.approx.f64 %0, %1;" : "=d"(y) : "d"(s));
+    return y;
+  }
+  return 1.0 / sqrt(s);
+}
+
+// 1/d: rcp.approx.ftz.f64 (about 20 bits) refined by two Newton-Raphson steps
+// z <- z + z (1 - d z), each squaring the relative error; IEEE division outside the normal range.
+__device__ __forceinline__ double col_rcp(double d) {
+  if (d > 1e-280 && d < 1e280) {
+    double z;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(z) : "d"(d));
+    z = fma(z, fma(-d, z, 1.0), z);
+    z = fma(z, fma(-d, z, 1.0), z);
+    return z;
+  }
+  return 1.0 / d;
+}
+
+// Named barrier for warps 0..3 (128 threads).
+__device__ __forceinline__ void sync_warps0to3() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
 template <int CL>
 __global__ void __launch_bounds__(NT, 1) qr_cluster_kernel(QrParams p) {
   cg::cluster_group cluster = cg::this_cluster();
@@ -134,9 +177,12 @@ __global__ void __launch_bounds__(NT, 1) qr_cluster_kernel(QrParams p) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int R = p.R;
   const int M = p.M;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   SmemLayout& sm = *reinterpret_cast<SmemLayout*>(smem_raw);
   double* rows_smem = reinterpret_cast<double*>(smem_raw + ((sizeof(SmemLayout) + 15) / 16) * 16);
+  // bytes that complete one column exchange on each CTA: CL partial-sum vectors + the pivot row
+  constexpr uint32_t kColBytes = (uint32_t)((CL + 1) * CPQR_MAXR * sizeof(double));
+  const uint32_t kW2Bytes = (uint32_t)(R * CPQR_MAXR * sizeof(double));
 
   const int L = (M > rank) ? (M - rank + CL - 1) / CL : 0;  // local rows: t = rank + CL * u
   double* Wb;
@@ -151,30 +197,18 @@ __global__ void __launch_bounds__(NT, 1) qr_cluster_kernel(QrParams p) {
   auto W = [&](int u) -> double* { return Wb + (size_t)u * ldw; };
   auto grow = [&](int u) -> int { return rank + CL * u; };
 
-  // Warp 0 sums the per-warp vectors red[*][0..n) and pushes the CTA total into
-  // inbox[buf][rank] of every CTA of the cluster.
-  auto push_partials = [&](int buf, int n0, int n1) {
-    __syncthreads();
-    if (warp == 0) {
-      for (int i = n0 + lane; i < n1; i += 32) {
-        double v = tree8(&sm.red[0][i], PSLOT);
-        for (int r = 0; r < CL; ++r) cluster.map_shared_rank(&sm.inbox[buf][rank][0], r)[i] = v;
-      }
-    }
-    cluster.sync();
-  };
-  auto inbox_sum = [&](int buf, int i) -> double {
-    double s[MAXCL / 2];
-#pragma unroll
-    for (int h = 0; h < CL / 2; ++h) s[h] = sm.inbox[buf][2 * h][i] + sm.inbox[buf][2 * h + 1][i];
-#pragma unroll
-    for (int w = CL / 4; w >= 1; w >>= 1)
-#pragma unroll
-      for (int h = 0; h < w; ++h) s[h] += s[h + w];
-    return s[0];
-  };
-
   QR_PHASE(0);
+  // mbarriers of the st.async exchanges, armed for their first phase before any peer can send
+  if (tid == 0) {
+    for (int b = 0; b < 3; ++b) tc::mbar_init(smem_u32(&sm.bar[b]), 1);
+    tc::fence_mbar_init_cluster();
+    tc::mbar_expect_tx(smem_u32(&sm.bar[0]), kColBytes);
+    if (R > 1) tc::mbar_expect_tx(smem_u32(&sm.bar[1]), kColBytes);
+    tc::mbar_expect_tx(smem_u32(&sm.bar[2]), kW2Bytes);
+    sm.abort_flag = 0;
+  }
+  cluster.sync();
+
   // ---------------- prologue: fill the local rows ----------------
   if (p.mode == MODE_PLAIN) {
     for (int u = warp; u < L; u += NW)
@@ -206,7 +240,7 @@ __global__ void __launch_bounds__(NT, 1) qr_cluster_kernel(QrParams p) {
       f_nn += vh * vh;
       double res = vh, ahat = 0.0;
       for (int c = R - 1; c >= 0; --c) {
-        double a_c = __shfl_sync(0xffffffffu, res, c) * sm.rdiag[c];
+        double a_c = __shfl_sync(FULL, res, c) * sm.rdiag[c];
         if (lane == c) ahat = a_c;
         if (lane < c) res -= sm.R0[lane * CPQR_MAXR + c] * a_c;
       }
@@ -214,25 +248,42 @@ __global__ void __launch_bounds__(NT, 1) qr_cluster_kernel(QrParams p) {
       nrm += ahat * ahat;
     }
     for (int o = 16; o > 0; o >>= 1) {
-      f_in += __shfl_xor_sync(0xffffffffu, f_in, o);
-      f_nn += __shfl_xor_sync(0xffffffffu, f_nn, o);
+      f_in += __shfl_xor_sync(FULL, f_in, o);
+      f_nn += __shfl_xor_sync(FULL, f_nn, o);
     }
     sm.red[warp][lane] = nrm;
     if (lane == 0) {
       sm.red[warp][2 * CPQR_MAXR] = f_in;
       sm.red[warp][2 * CPQR_MAXR + 1] = f_nn;
     }
-    push_partials(1, 0, PSLOT);
+    __syncthreads();
     if (warp == 0) {
-      double lam = sqrt(inbox_sum(1, lane));
+      for (int i = lane; i < PSLOT; i += 32) {
+        double v = tree8(&sm.red[0][i], PSLOT);
+        for (int r = 0; r < CL; ++r) cluster.map_shared_rank(&sm.inbox1[rank][0], r)[i] = v;
+      }
+    }
+    cluster.sync();
+    auto inbox_sum = [&](int i) -> double {
+      double s[MAXCL / 2];
+#pragma unroll
+      for (int h = 0; h < CL / 2; ++h) s[h] = sm.inbox1[2 * h][i] + sm.inbox1[2 * h + 1][i];
+#pragma unroll
+      for (int w = CL / 4; w >= 1; w >>= 1)
+#pragma unroll
+        for (int h = 0; h < w; ++h) s[h] += s[h + w];
+      return s[0];
+    };
+    if (warp == 0) {
+      double lam = sqrt(inbox_sum(lane));
       if (lane < R) {
         sm.bcw[lane] = (lam > 0.0) ? 1.0 / lam : 0.0;
         if (lam == 0.0 && rank == 0) atomicOr(p.status, CPQR_DEV_SINGULAR);
         if (rank == 0) p.fin.lambda[lane] = lam;
       }
       if (lane == 0 && rank == 0) {
-        p.fin.fit_terms[0] = inbox_sum(1, 2 * CPQR_MAXR);
-        p.fin.fit_terms[1] = inbox_sum(1, 2 * CPQR_MAXR + 1);
+        p.fin.fit_terms[0] = inbox_sum(2 * CPQR_MAXR);
+        p.fin.fit_terms[1] = inbox_sum(2 * CPQR_MAXR + 1);
       }
     }
     __syncthreads();
@@ -244,93 +295,105 @@ __global__ void __launch_bounds__(NT, 1) qr_cluster_kernel(QrParams p) {
       }
     }
   }
-  __syncwarp();
+  __syncthreads();
   QR_PHASE(1);
 
-  // ---------------- Householder steps: one cluster barrier per column ----------------
-  // FP64 instructions cost ~64 cycles per warp on GB300, so the reductions are
-  // split over warps 0..3 (one per SM sub-partition) and the pivot row, owned by
-  // a single CTA, is pushed instead of reduced.
-  constexpr int IPG = CL / 4;  // inboxes summed by each of the 4 lane groups
+  // ---------------- Householder columns: one st.async exchange per column ----------------
+  // Step j applies reflector j-1 to the rows it touches and, in the same pass, accumulates
+  // x_j^T a_c (x_j = column j after that update) over the rows [j, act[j]) for every c.
   for (int j = 0; j < R; ++j) {
     const int buf = j & 1;
-    const int actj = p.act[j];
-    const int u0 = (j <= rank) ? 0 : (j - rank + CL - 1) / CL;
-    const int u1 = (actj > rank) ? (actj - rank + CL - 1) / CL : 0;
+    const int pj = j - 1;
+    const bool upd = (j > 0);
+    const int t_lo = upd ? pj : 0;
+    const int t_hi = p.act[j];
+    const int act_prev = upd ? p.act[pj] : 0;
+    const double tw = upd ? sm.bcw[lane] : 0.0;  // zero outside pj < lane < R
+    const double vpp = upd ? sm.vpiv[pj] : 0.0;
+    const double alp = upd ? sm.alpha[pj] : 0.0;
+    const int u0 = (t_lo <= rank) ? 0 : (t_lo - rank + CL - 1) / CL;
+    const int u1 = (t_hi > rank) ? (t_hi - rank + CL - 1) / CL : 0;
     const int us = u0 + ((warp - (u0 % NW)) + NW) % NW;
     double acc = 0.0;
     for (int u = us; u < u1; u += NW) {
-      const double* w = W(u);
-      double x = w[j];
+      double* w = W(u);
+      const int t = grow(u);
       double a = (lane < R) ? w[lane] : 0.0;
-      if (lane >= j) acc += x * a;
-      if (grow(u) == j) sm.pivloc[lane] = a;
+      if (t < act_prev) {  // reflector j-1 touches this row
+        const bool pivrow = (t == pj);
+        const double v = pivrow ? vpp : w[pj];
+        a = fma(-tw, v, a);
+        if (lane > pj && lane < R) w[lane] = a;
+        if (pivrow && lane == pj) w[lane] = alp;
+      }
+      if (t >= j) {
+        const double x = __shfl_sync(FULL, a, j);
+        acc = fma(x, a, acc);
+        if (t == j) sm.pivloc[lane] = a;
+      }
     }
     sm.red[warp][lane] = acc;
     __syncthreads();
     if (warp < 4) {
+      // CTA sums of 8 columns per warp, stored into every CTA of the cluster
       const int slot = 8 * warp + (lane & 7), g = lane >> 3;
       double v = sm.red[2 * g][slot] + sm.red[2 * g + 1][slot];
-      v += __shfl_xor_sync(0xffffffffu, v, 8);
-      v += __shfl_xor_sync(0xffffffffu, v, 16);
-      for (int r = g; r < CL; r += 4) cluster.map_shared_rank(&sm.inbox[buf][rank][0], r)[slot] = v;
+      v += __shfl_xor_sync(FULL, v, 8);
+      v += __shfl_xor_sync(FULL, v, 16);
+      const int pr = lane & 3;
+      const double lo = __shfl_sync(FULL, v, 2 * pr), hi = __shfl_sync(FULL, v, 2 * pr + 1);
+      const uint32_t src = smem_u32(&sm.cbox[buf][rank][8 * warp + 2 * pr]);
+      const uint32_t bar = smem_u32(&sm.bar[buf]);
+      for (int r = lane >> 2; r < CL; r += 8) tc::st_async_v2(tc::mapa(src, r), lo, hi, tc::mapa(bar, r));
     } else if (warp == 4 && rank == j % CL) {
-      const double pvv = sm.pivloc[lane];
-      for (int r = 0; r < CL; ++r) cluster.map_shared_rank(&sm.pivbox[buf][0], r)[lane] = pvv;
+      // the pivot row, owned here
+      const int pr = lane & 15;
+      const double lo = sm.pivloc[2 * pr], hi = sm.pivloc[2 * pr + 1];
+      const uint32_t src = smem_u32(&sm.pbox[buf][2 * pr]);
+      const uint32_t bar = smem_u32(&sm.bar[buf]);
+      for (int r = lane >> 4; r < CL; r += 2) tc::st_async_v2(tc::mapa(src, r), lo, hi, tc::mapa(bar, r));
     }
-    cluster.sync();
     if (warp < 4) {
+      tc::mbar_wait_cluster(smem_u32(&sm.bar[buf]), (uint32_t)((j >> 1) & 1), &sm.abort_flag, p.status);
+      // re-arm this buffer for column j + 2: its bytes can only come after this CTA's column j + 1
+      // sums, which it sends after every read of this buffer
+      if (tid == 0 && j + 2 < R) tc::mbar_expect_tx(smem_u32(&sm.bar[buf]), kColBytes);
+      constexpr int IPG = CL / 4;  // partial vectors summed by each of the 4 lane groups
       const int slot = 8 * warp + (lane & 7), g = lane >> 3;
-      double v = sm.inbox[buf][g * IPG][slot];
+      double v = sm.cbox[buf][g * IPG][slot];
 #pragma unroll
-      for (int q = 1; q < IPG; ++q) v += sm.inbox[buf][g * IPG + q][slot];
-      v += __shfl_xor_sync(0xffffffffu, v, 8);
-      v += __shfl_xor_sync(0xffffffffu, v, 16);
+      for (int q = 1; q < IPG; ++q) v += sm.cbox[buf][g * IPG + q][slot];
+      v += __shfl_xor_sync(FULL, v, 8);
+      v += __shfl_xor_sync(FULL, v, 16);
       if (g == 0) sm.dvec[slot] = v;
+      sync_warps0to3();
+      if (warp == 0) {
+        const double s = sm.dvec[j], xj = sm.pbox[buf][j];
+        double alpha = 0.0, tau = 0.0, vp = 0.0;
+        if (s > 0.0) {
+          const double nx = s * col_rsqrt(s);
+          alpha = (xj >= 0.0) ? -nx : nx;
+          vp = xj - alpha;
+          tau = col_rcp(s - alpha * xj);  // 2 / ||v||^2 with ||v||^2 = 2 (s - alpha xj)
+        }
+        const double pl = sm.pbox[buf][lane];
+        const double num = sm.dvec[lane] - alpha * pl;  // v_j^T a_lane (lane > j), v_lane^T v_j (lane < j)
+        sm.bcw[lane] = (lane > j && lane < R) ? tau * num : 0.0;
+        sm.ST[j][lane] = (lane < j) ? num : 0.0;
+        sm.VT[j][lane] = (lane < j) ? pl : (lane == j ? vp : 0.0);
+        if (lane == 0) {
+          sm.alpha[j] = alpha;
+          sm.tau[j] = tau;
+          sm.vpiv[j] = vp;
+          if (rank == 0 && !(s > 0.0)) atomicOr(p.status, CPQR_DEV_SINGULAR);
+        }
+      }
     }
     __syncthreads();
-    if (warp == 0) {
-      const double s = sm.dvec[j], xj = sm.pivbox[buf][j];
-      double alpha = 0.0, tau = 0.0, vp = 0.0;
-      if (s > 0.0) {
-        double nx = sqrt(s);
-        alpha = (xj >= 0.0) ? -nx : nx;
-        vp = xj - alpha;
-        tau = 1.0 / (s - alpha * xj);  // 2 / ||v||^2 with ||v||^2 = 2 (s - alpha xj)
-      }
-      sm.bcw[lane] = (lane > j && lane < R) ? tau * (sm.dvec[lane] - alpha * sm.pivbox[buf][lane]) : 0.0;
-      if (lane == 0 && rank == 0 && !(s > 0.0)) atomicOr(p.status, CPQR_DEV_SINGULAR);
-      if (lane == 0) {
-        sm.alpha[j] = alpha;
-        sm.tau[j] = tau;
-        sm.vpiv[j] = vp;
-      }
-    }
-    __syncthreads();
-    {
-      const double tw = sm.bcw[lane], vp = sm.vpiv[j], al = sm.alpha[j];
-      for (int u = us; u < u1; u += NW) {
-        double* w = W(u);
-        const bool pivrow = (grow(u) == j);
-        double v = pivrow ? vp : w[j];
-        if (lane > j && lane < R) w[lane] -= tw * v;
-        __syncwarp();
-        if (pivrow && lane == j) w[j] = al;
-      }
-    }
-    __syncwarp();
   }
-
-  // reflector entry v_a[t] of local row u (t = grow(u))
-  auto vref = [&](int u, int t, int a) -> double {
-    if (t < a || t >= p.act[a]) return 0.0;
-    if (t == a) return sm.vpiv[a];
-    return W(u)[a];
-  };
+  QR_PHASE(2);
 
   // ---------------- R factor (positive diagonal) ----------------
-  __syncthreads();
-  QR_PHASE(2);
   for (int u = warp; u < L; u += NW) {
     int t = grow(u);
     if (t >= R) break;
@@ -340,102 +403,63 @@ __global__ void __launch_bounds__(NT, 1) qr_cluster_kernel(QrParams p) {
       p.Rout[t * R + lane] = sg * v;
     }
   }
-
-  // ---------------- compact WY: S = V^T V (reduce-scatter, then all-gather) ----------------
-  // upper entries (a, b), a <= b < R, packed densely over the threads
-  for (int e = tid; e < RR; e += NT) sm.spart[e] = 0.0;
-  __syncthreads();
-  {
-    const int nup = R * (R + 1) / 2;
-    for (int k = tid; k < nup; k += NT) {
-      // k -> (a, b): rows a have R - a entries
-      int a = 0, rem = k;
-      while (rem >= R - a) {
-        rem -= R - a;
-        ++a;
-      }
-      const int b = a + rem;
-      double acc = 0.0;
-      // v_a[t] is nonzero only for a <= t < act[a]; v_b[t] needs t >= b
-      const int ulo = (b <= rank) ? 0 : (b - rank + CL - 1) / CL;
-      const int uhi = (p.act[a] > rank) ? (p.act[a] - rank + CL - 1) / CL : 0;
-      for (int u = ulo; u < uhi; ++u) {
-        const int t = grow(u);
-        acc += vref(u, t, a) * vref(u, t, b);
-      }
-      sm.spart[a * CPQR_MAXR + b] = acc;
-    }
-  }
-  // vtop rows owned here, zero elsewhere (summed over the cluster below)
-  __syncthreads();
   QR_PHASE(3);
-  for (int e = tid; e < RR; e += NT) {
-    const int r = e % CL, k = e / CL;
-    cluster.map_shared_rank(&sm.sinbox[rank][0], r)[k] = sm.spart[e];
+
+  // ---------------- W2 = T V_top^T: column cc by warp cc / CL of CTA cc % CL ----------------
+  // Tinv W2 = V_top^T with Tinv = striu(S) + diag(S)/2 upper triangular and diag(S)/2 = 1/tau;
+  // column cc has nonzeros in rows a <= cc, found by back substitution (lane = row).
+  {
+    const int cc = rank + CL * warp;
+    if (cc < R) {
+      double rhs = (lane <= cc) ? sm.VT[cc][lane] : 0.0;
+      double mine = 0.0;
+      for (int a = cc; a >= 0; --a) {
+        const double w = __shfl_sync(FULL, rhs, a) * sm.tau[a];
+        if (lane == a) mine = w;
+        if (lane < a) rhs = fma(-sm.ST[a][lane], w, rhs);
+      }
+      const int pr = lane & 15;
+      const double lo = __shfl_sync(FULL, mine, 2 * pr), hi = __shfl_sync(FULL, mine, 2 * pr + 1);
+      const uint32_t src = smem_u32(&sm.W2T[cc][2 * pr]);
+      const uint32_t bar = smem_u32(&sm.bar[2]);
+      for (int r = lane >> 4; r < CL; r += 2) tc::st_async_v2(tc::mapa(src, r), lo, hi, tc::mapa(bar, r));
+    }
   }
-  cluster.sync();
-  for (int k = tid; k < RR / CL; k += NT) {
-    const int e = k * CL + rank;
-    double v = 0.0;
-    for (int r = 0; r < CL; ++r) v += sm.sinbox[r][k];
-    for (int r = 0; r < CL; ++r) cluster.map_shared_rank(&sm.Ssum[0], r)[e] = v;
-  }
-  for (int u = warp; u < L; u += NW) {
-    int t = grow(u);
-    if (t >= R) break;
-    double v = (lane < R) ? vref(u, t, lane) : 0.0;
-    for (int r = 0; r < CL; ++r) cluster.map_shared_rank(&sm.vtop[0], r)[t * CPQR_MAXR + lane] = v;
-  }
-  cluster.sync();  // every remote write is done: no DSMEM access after this point
   QR_PHASE(4);
-  // W2 = T V_top^T, i.e. solve Tinv W2 = V_top^T, Tinv = striu(S) + diag(S)/2 (upper),
-  // blocked by 8 rows: off-block products on all warps, 8 x 8 diagonal solves on warp 0.
-  if (warp == 0) {
-    const int c = lane;
-    double dg = (c < R) ? 0.5 * sm.Ssum[c * CPQR_MAXR + c] : 0.0;
-    sm.rdiag[c] = (dg > 0.0) ? 1.0 / dg : 0.0;
-  }
-  for (int e = tid; e < RR; e += NT) sm.W2[e] = 0.0;
-  __syncthreads();
-  for (int kb = (R - 1) / 8; kb >= 0; --kb) {
-    const int a0 = kb * 8, a1 = (a0 + 8 < R) ? a0 + 8 : R;
-    {
-      const int a = a0 + warp, c = lane;  // one row of the block per warp
-      if (a < a1 && c < R) {
-        double rhs = (c >= a) ? sm.vtop[c * CPQR_MAXR + a] : 0.0;  // V_top^T[a][c] = v_a[c]
-        for (int b = a1; b < R; ++b) rhs -= sm.Ssum[a * CPQR_MAXR + b] * sm.W2[b * CPQR_MAXR + c];
-        sm.spart[a * CPQR_MAXR + c] = rhs;
-      }
-    }
-    __syncthreads();
-    if (warp == 0 && lane < R) {
-      const int c = lane;
-      for (int a = a1 - 1; a >= a0; --a) {
-        double rhs = sm.spart[a * CPQR_MAXR + c];
-        for (int b = a + 1; b < a1; ++b) rhs -= sm.Ssum[a * CPQR_MAXR + b] * sm.W2[b * CPQR_MAXR + c];
-        sm.W2[a * CPQR_MAXR + c] = rhs * sm.rdiag[a];
-      }
-    }
-    __syncthreads();
-  }
+  tc::mbar_wait_cluster(smem_u32(&sm.bar[2]), 0u, &sm.abort_flag, p.status);
   QR_PHASE(5);
 
   // ---------------- Q rows: Q[t, c] = sign_c (delta_tc - sum_a v_a[t] W2[a][c]) ----------------
-  for (int u = warp; u < L; u += NW) {
-    const int t = grow(u);
-    if (lane >= R) continue;
+  {
     const int c = lane;
-    const int alo = row_alo(p, t);
-    const int ahi = (t < c) ? t : c;
-    double q = (t == c) ? 1.0 : 0.0;
-    for (int a = alo; a <= ahi; ++a) q -= vref(u, t, a) * sm.W2[a * CPQR_MAXR + c];
-    q *= (sm.alpha[c] < 0.0) ? -1.0 : 1.0;
-    const size_t orow = (p.mode == MODE_KRP) ? (size_t)p.perm[t] : (size_t)t;
-    p.Q[orow * R + c] = q;
-    if (p.mode == MODE_FINISH && p.fin.Qf) p.fin.Qf[orow * R + c] = (float)q;
+    double w2[CPQR_MAXR];
+#pragma unroll
+    for (int a = 0; a < CPQR_MAXR; ++a) w2[a] = (c < R) ? sm.W2T[c][a] : 0.0;
+    const double sg = (c < R && sm.alpha[c] < 0.0) ? -1.0 : 1.0;
+    for (int u = warp; u < L; u += NW) {
+      const int t = grow(u);
+      const double* w = W(u);
+      const int alo = row_alo(p, t);
+      const int ahi = (t < R - 1) ? t : R - 1;
+      double q = (t == c) ? 1.0 : 0.0;
+#pragma unroll
+      for (int a = 0; a < CPQR_MAXR; ++a) {
+        if (a >= alo && a <= ahi) {
+          const double va = (a == t) ? sm.vpiv[a] : w[a];
+          q = fma(-va, w2[a], q);
+        }
+      }
+      q *= sg;
+      if (c < R) {
+        const size_t orow = (p.mode == MODE_KRP) ? (size_t)p.perm[t] : (size_t)t;
+        p.Q[orow * R + c] = q;
+        if (p.mode == MODE_FINISH && p.fin.Qf) p.fin.Qf[orow * R + c] = (float)q;
+      }
+    }
   }
-  __syncthreads();
   QR_PHASE(6);
+  // no CTA leaves while a peer may still store into its shared memory
+  cluster.sync();
 }
 
 size_t smem_bytes(int M, int R, int CL, bool use_smem) {

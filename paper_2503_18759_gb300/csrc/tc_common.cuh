@@ -168,6 +168,61 @@ static __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// ----- distributed shared memory of a thread-block cluster -----
+// Address of the same shared-memory location in the CTA of the given cluster rank.
+static __device__ __forceinline__ uint32_t mapa(uint32_t a, uint32_t rank) {
+  uint32_t o;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(o) : "r"(a), "r"(rank));
+  return o;
+}
+
+// 16-byte store into a peer CTA's shared memory that completes 16 bytes of the transaction
+// count of the peer's mbarrier (both addresses from mapa, the store address 16-byte aligned).
+static __device__ __forceinline__ void st_async_v2(uint32_t raddr, double lo, double hi, uint32_t rbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f64 [%0], {%1, %2}, [%3];" ::"r"(raddr),
+               "d"(lo), "d"(hi), "r"(rbar)
+               : "memory");
+}
+
+// Makes mbarrier initialisations visible to the other CTAs of the cluster.
+static __device__ __forceinline__ void fence_mbar_init_cluster() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// try_wait with acquire at cluster scope: data written by peers' st.async is visible after it.
+static __device__ __forceinline__ bool mbar_try_cluster(uint32_t a, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on a cluster-fed mbarrier phase: false (and CPQR_DEV_TIMEOUT, and the CTA's
+// abort flag set) after kTimeoutNs, or at once if the abort flag is already set.
+static __device__ bool mbar_wait_cluster(uint32_t a, uint32_t parity, int* abort_flag, unsigned int* status) {
+  if (*(volatile int*)abort_flag) return false;
+  unsigned long long t0 = 0;
+  for (int it = 0;; ++it) {
+    if (mbar_try_cluster(a, parity)) return true;
+    if ((it & 255) == 255) {
+      if (*(volatile int*)abort_flag) return false;
+      const unsigned long long now = gtimer();
+      if (t0 == 0) {
+        t0 = now;
+      } else if (now - t0 > kTimeoutNs) {
+        atomicOr(status, CPQR_DEV_TIMEOUT);
+        *(volatile int*)abort_flag = 1;
+        return false;
+      }
+    }
+  }
+}
+
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link).
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,

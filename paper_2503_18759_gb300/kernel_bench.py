@@ -70,7 +70,7 @@ def main(argv):
         buf = (ctypes.c_ulonglong * 8)()
         L.cpqr_debug_qr_phases(buf)
         t = [buf[i] for i in range(7)]
-        names = ["prologue", "householder", "R+VtV", "VtV reduce", "T solve", "Q rows"]
+        names = ["prologue", "householder", "R out", "T solve", "W2 gather", "Q rows"]
         print(" ".join(f"{n} {(t[i + 1] - t[i]) / 1000:.1f}us" for i, n in enumerate(names)),
               f"total {(t[6] - t[0]) / 1000:.1f}us")
 
