@@ -91,8 +91,9 @@ enum {
   CPQR_BUCKET_Q0 = 2,        /* Khatri-Rao product and its QR (computation of Q0) */
   CPQR_BUCKET_APPLY_Q0 = 3,  /* V = Y_(n) [Q0 | Q0^{k-1}] (application of Q0) */
   CPQR_BUCKET_QR = 4,        /* extrapolation, R0^{-T} solve, normalisation, factor QR */
-  CPQR_BUCKET_OTHER = 5,     /* operand staging, fit read-back */
-  CPQR_NBUCKETS = 6
+  CPQR_BUCKET_OTHER = 5,     /* operand staging, fit read-back, learned proposal */
+  CPQR_BUCKET_FIT = 6,       /* explicit residual ||X - K||^2 of the split-precision path */
+  CPQR_NBUCKETS = 7
 };
 
 /* Per-context counters. */

@@ -36,8 +36,8 @@ class Options(C.Structure):
                 ("mlp_weights", C.POINTER(C.c_float))]
 
 
-NBUCKETS = 6
-BUCKETS = ("ttm_full", "ttm_deep", "q0", "apply_q0", "qr", "other")
+NBUCKETS = 7
+BUCKETS = ("ttm_full", "ttm_deep", "q0", "apply_q0", "qr", "other", "fit")
 
 
 class Stats(C.Structure):

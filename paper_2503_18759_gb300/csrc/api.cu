@@ -91,6 +91,8 @@ struct Checkpoint {
   bool has_prev[CPQR_MAXN] = {};
   double* Q0prev[CPQR_MAXN] = {};
   double* Q0 = nullptr;
+  float* Q0fprev[CPQR_MAXN] = {};
+  float* Q0f = nullptr;
 };
 
 struct cpqr_ctx {
@@ -131,8 +133,11 @@ struct cpqr_ctx {
   __nv_bfloat16 *Xhi = nullptr, *Xlo = nullptr;
   double* lambda = nullptr;
   double* Q0 = nullptr;
+  float* Q0f = nullptr;                // split path: FP32 copy of Q0 for V = Y_(n) Q0
+  float* Q0fprev[CPQR_MAXN] = {};      // split path: FP32 copies of Q0^{k-1}
   double* R0 = nullptr;
-  double* V = nullptr;
+  double* V = nullptr;                 // rows of A^ = V^ R0^{-T}
+  double* fitpart = nullptr;           // per-block partial fit terms of the finish preparation
   double* qr_work = nullptr;
   double* zq_work = nullptr;
   double* v_work = nullptr;
@@ -304,8 +309,11 @@ cpqr_status run_ttm(cpqr_ctx* ctx, const Op& op) {
       CK(launch_ttm<double, double, double>((const double*)sb.p, ctx->Q[k], (double*)out, P, K, S, R, st));
   } else {
     if (sb.is_x && ttm_tc_supported(P, K, S, R)) {
+      // a Khatri-Rao QR running on the side stream holds one cluster of SMs: the persistent
+      // grid leaves those free so that the two overlap instead of queueing behind each other
+      const int reserve = ctx->z_pending ? qr_cluster_sms() : 0;
       CK(launch_ttm_tc(ctx->Xhi, ctx->Xlo, ctx->Qt[k], ctx->Rp, ctx->Kp[k], (float*)out, P, K, S, R,
-                       ctx->dstatus, st));
+                       ctx->dstatus, st, reserve));
     } else {
       cudaError_t e = launch_ttm_f32_tiled((const float*)sb.p, ctx->Qf[k], (float*)out, P, K, S, R, st);
       if (e == cudaErrorNotSupported) e = launch_ttm<float, float, float>((const float*)sb.p, ctx->Qf[k], (float*)out,
@@ -362,8 +370,10 @@ cpqr_status checkpoint_save(cpqr_ctx* ctx, int slot) {
   for (int n = 0; n < CPQR_MAXN; ++n) {
     c.has_prev[n] = ctx->has_prev[n];
     c.Q0prev[n] = ctx->Q0prev[n];
+    c.Q0fprev[n] = ctx->Q0fprev[n];
   }
   c.Q0 = ctx->Q0;
+  c.Q0f = ctx->Q0f;
   c.valid = true;
   return CPQR_OK;
 }
@@ -389,8 +399,10 @@ cpqr_status checkpoint_restore(cpqr_ctx* ctx, int slot) {
   for (int n = 0; n < CPQR_MAXN; ++n) {
     ctx->has_prev[n] = c.has_prev[n];
     ctx->Q0prev[n] = c.Q0prev[n];
+    ctx->Q0fprev[n] = c.Q0fprev[n];
   }
   ctx->Q0 = c.Q0;
+  ctx->Q0f = c.Q0f;
   ctx->z_pending = false;
   return CPQR_OK;
 }
@@ -423,7 +435,7 @@ cpqr_status launch_z(cpqr_ctx* ctx, int n) {
   CK(cudaStreamWaitEvent(ctx->st2, ctx->ev_ready, 0));
   {
     Timed tm(ctx, CPQR_BUCKET_Q0, 1, ctx->st2);
-    CK(launch_krp_qr(ctx->zplan, tri, ctx->Q0, ctx->R0, ctx->zq_work, ctx->dstatus, ctx->st2));
+    CK(launch_krp_qr(ctx->zplan, tri, ctx->Q0, ctx->R0, ctx->zq_work, ctx->dstatus, ctx->st2, ctx->Q0f));
   }
   CK(cudaEventRecord(ctx->ev_z, ctx->st2));
   ctx->z_pending = true;
@@ -443,29 +455,39 @@ cpqr_status run_update(cpqr_ctx* ctx, int n, int leaf, double beta) {
   }
   CK(cudaStreamWaitEvent(st, ctx->ev_z, 0));
   ctx->z_pending = false;
-  // Lines 5 and 7: V = Y_(n) [Q0 | Q0^{k-1}].
+  // Lines 5 and 7: V = Y_(n) [Q0 | Q0^{k-1}] as split-K slices.
   int64_t P = ipow(R, n), S = ipow(R, N - 1 - n);
   const int64_t I = ctx->dims[n];
   const bool ext = (beta != 0.0) && ctx->has_prev[n];
   const int C = ext ? 2 * R : R;
+  const bool fp64 = ctx->prec == CPQR_PREC_FP64;
+  int nparts = 0;
   {
-    Timed tm(ctx, CPQR_BUCKET_APPLY_Q0, 2);
-    if (ctx->prec == CPQR_PREC_FP64)
-      CK(launch_leaf_v<double>((const double*)lb.p, P, I, S, ctx->Q0, ctx->Q0prev[n], R, C, ctx->V, ctx->v_work,
-                               st));
+    Timed tm(ctx, CPQR_BUCKET_APPLY_Q0, 1);
+    if (fp64)
+      CK(launch_leaf_v<double, double>((const double*)lb.p, P, I, S, ctx->Q0, ctx->Q0prev[n], R, C, ctx->v_work,
+                                       &nparts, st));
     else
-      CK(launch_leaf_v<float>((const float*)lb.p, P, I, S, ctx->Q0, ctx->Q0prev[n], R, C, ctx->V, ctx->v_work, st));
+      CK(launch_leaf_v<float, float>((const float*)lb.p, P, I, S, ctx->Q0f, ctx->Q0fprev[n], R, C,
+                                     (float*)ctx->v_work, &nparts, st));
   }
-  // Lines 8-10.
+  // Lines 8-10: eq. 19 and the R0^{-T} solve over all SMs, then normalisation and the factor QR.
   FinishOut fo{ctx->A[n], ctx->lambda, ctx->Q[n], ctx->Rf[n], ctx->Qf[n], ctx->fit_terms};
   {
-    Timed tm(ctx, CPQR_BUCKET_QR, 1);
-    CK(launch_mode_finish(ctx->V, C, ctx->R0, ext ? beta : 0.0, ctx->alpha, I, R, fo, ctx->qr_work,
-                          ctx->dstatus, st));
+    Timed tm(ctx, CPQR_BUCKET_QR, 2);
+    const double b = ext ? beta : 0.0;
+    if (fp64)
+      CK(launch_finish_prep<double>(ctx->v_work, nparts, I, C, R, ctx->R0, b, ctx->alpha, ctx->V, ctx->fitpart,
+                                    ctx->dstatus, st));
+    else
+      CK(launch_finish_prep<float>((const float*)ctx->v_work, nparts, I, C, R, ctx->R0, b, ctx->alpha, ctx->V,
+                                   ctx->fitpart, ctx->dstatus, st));
+    CK(launch_mode_finish(ctx->V, ctx->fitpart, finish_prep_blocks(I), I, R, fo, ctx->qr_work, ctx->dstatus, st));
   }
   cpqr_status s = stage_q(ctx, n);
   if (s != CPQR_OK) return s;
   std::swap(ctx->Q0, ctx->Q0prev[n]);
+  std::swap(ctx->Q0f, ctx->Q0fprev[n]);
   ctx->has_prev[n] = true;
   return CPQR_OK;
 }
@@ -477,7 +499,7 @@ cpqr_status run_update(cpqr_ctx* ctx, int n, int leaf, double beta) {
 cpqr_status read_fit(cpqr_ctx* ctx, double* fit) {
   const bool explicit_fit = (ctx->prec == CPQR_PREC_SPLIT_BF16);
   if (explicit_fit) {
-    Timed tm(ctx, CPQR_BUCKET_OTHER, 1);
+    Timed tm(ctx, CPQR_BUCKET_FIT, 1);
     const double* A[CPQR_MAXN];
     for (int n = 0; n < ctx->N; ++n) A[n] = ctx->A[n];
     CK(launch_residual2<float>((const float*)ctx->X, ctx->N, ctx->dims.data(), A, ctx->lambda, ctx->R,
@@ -722,7 +744,7 @@ cpqr_status cp_als_qr_init(cpqr_ctx** out, int32_t N, const int64_t* dims, int32
       off += (bytes + 255) / 256 * 256;
       return o;
     };
-    size_t oA[CPQR_MAXN], oQ[CPQR_MAXN], oR[CPQR_MAXN], oQf[CPQR_MAXN], oP[CPQR_MAXN], oT[CPQR_MAXN];
+    size_t oA[CPQR_MAXN], oQ[CPQR_MAXN], oR[CPQR_MAXN], oQf[CPQR_MAXN], oP[CPQR_MAXN], oT[CPQR_MAXN], oPf[CPQR_MAXN];
     for (int n = 0; n < N; ++n) {
       ctx->Kp[n] = ((dims[n] + 63) / 64) * 64;
       oA[n] = take(dims[n] * R * 8);
@@ -731,8 +753,9 @@ cpqr_status cp_als_qr_init(cpqr_ctx** out, int32_t N, const int64_t* dims, int32
       oQf[n] = take(dims[n] * R * 4);
       oP[n] = take(M0 * R * 8);
       oT[n] = split ? take((size_t)2 * ctx->Rp * ctx->Kp[n] * 2) : 0;
+      oPf[n] = split ? take(M0 * R * 4) : 0;
     }
-    size_t oQ0 = take(M0 * R * 8), oL = take(R * 8);
+    size_t oQ0 = take(M0 * R * 8), oL = take(R * 8), oQ0f = split ? take(M0 * R * 4) : 0;
     ctx->arena_bytes = off;
     CK(cudaMalloc(&ctx->arena, off));
     ctx->owned.push_back(ctx->arena);
@@ -745,12 +768,15 @@ cpqr_status cp_als_qr_init(cpqr_ctx** out, int32_t N, const int64_t* dims, int32
       ctx->Qf[n] = (float*)(a + oQf[n]);
       ctx->Q0prev[n] = (double*)(a + oP[n]);
       if (split) ctx->Qt[n] = (__nv_bfloat16*)(a + oT[n]);
+      if (split) ctx->Q0fprev[n] = (float*)(a + oPf[n]);
     }
     ctx->Q0 = (double*)(a + oQ0);
+    if (split) ctx->Q0f = (float*)(a + oQ0f);
     ctx->lambda = (double*)(a + oL);
   }
   CK(ctx->alloc(&ctx->R0, (size_t)R * R));
   CK(ctx->alloc(&ctx->V, Imax * 2 * R));
+  CK(ctx->alloc(&ctx->fitpart, 2 * (size_t)finish_prep_blocks(Imax)));
   CK(ctx->alloc(&ctx->qr_work, std::max<int64_t>(M0, Imax) * R));
   CK(ctx->alloc(&ctx->zq_work, M0 * R));
   CK(ctx->alloc((char**)&ctx->res_work, residual2_work_bytes(N, dims, R)));

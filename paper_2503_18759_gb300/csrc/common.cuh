@@ -39,9 +39,10 @@ cudaError_t launch_split_x(const float* X, __nv_bfloat16* Xhi, __nv_bfloat16* Xl
                            cudaStream_t st);
 // out[p, r, s] = sum_i X[p, i, s] Q[i, r] from split operands; out FP32.
 // Returns cudaErrorNotSupported if the shape is outside the kernel's range.
+// reserve_sms: SMs the persistent grid leaves free for concurrent work (a cluster QR).
 cudaError_t launch_ttm_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo, const __nv_bfloat16* Qt,
                           int Rp, int64_t Kp, float* out, int64_t P, int64_t K, int64_t S, int R,
-                          unsigned int* dev_status, cudaStream_t st);
+                          unsigned int* dev_status, cudaStream_t st, int reserve_sms = 0);
 bool ttm_tc_supported(int64_t P, int64_t K, int64_t S, int R);
 
 // ----- small FP64 kernels (smallqr.cu) -----
@@ -53,6 +54,9 @@ struct ZPlan {          // row order of the Khatri-Rao product used by the stair
   int32_t act[CPQR_MAXR];  // column j is active on sorted rows [j, act[j])
 };
 
+// SMs one cluster QR occupies (its cluster size).
+int qr_cluster_sms();
+
 // Plain QR of an M x R FP64 row-major matrix (device): Q (M x R), R (R x R), diag(R) > 0.
 cudaError_t launch_house_qr(const double* A, int64_t M, int R, double* Q, double* Rout, double* work,
                             unsigned int* dev_status, cudaStream_t st);
@@ -63,12 +67,28 @@ struct TriPtrs {
   const double* p[CPQR_MAXN];
 };
 cudaError_t launch_krp_qr(const ZPlan& plan, TriPtrs Rs, double* Q0, double* R0, double* work,
-                          unsigned int* dev_status, cudaStream_t st);
+                          unsigned int* dev_status, cudaStream_t st, float* Q0f = nullptr);
 size_t krp_qr_work_doubles(const ZPlan& plan);
 
-// Finish of a mode update (Alg. 3 lines 5 and 7-10): V^ = (1+beta) V0 - alpha beta V1
-// (V = [V0 | V1], I x C, C = R or 2R), A^ = V^ R0^{-T}, lambda = column norms,
-// A = A^ / lambda, A = Q_n R_n; also the fit terms <V0, V^> and ||V^||^2.
+// V[i, c] = sum_{p, s} Y[p, i, s] * Qc[p*S + s, c], c < C, Qc = [Q0 | Q0prev] (K x C,
+// K = P*S), as *nparts split-K slices of I x C in work (leaf_v_splits(I, K) * I * C
+// elements).  FP64 path: Y, Q0, slices FP64; split path: Y, Q0 copies, slices FP32.
+int leaf_v_splits(int64_t I, int64_t K);
+template <typename TY, typename TQ>
+cudaError_t launch_leaf_v(const TY* Y, int64_t P, int64_t I, int64_t S, const TQ* Q0, const TQ* Q0prev, int R, int C,
+                          TQ* work, int* nparts, cudaStream_t st);
+
+// Mode update, Alg. 3 lines 5 and 7-8: adds the nparts slices of V = [V0 | V1] (I x C,
+// C = R or 2R), V^ = (1+beta) V0 - alpha beta V1 (eq. 19), A^ = V^ R0^{-T} into Ahat (I x R),
+// and per-block partials of <V0, V^>, ||V^||^2 into fitpart (finish_prep_blocks(I) x 2).
+int finish_prep_blocks(int64_t I);
+template <typename TP>
+cudaError_t launch_finish_prep(const TP* parts, int nparts, int64_t I, int C, int R, const double* R0, double beta,
+                               double alpha, double* Ahat, double* fitpart, unsigned int* dev_status,
+                               cudaStream_t st);
+
+// Finish of a mode update (Alg. 3 lines 9-10): lambda = column norms of A^, A = A^ / lambda,
+// A = Q_n R_n; the fit terms <V0, V^>, ||V^||^2 from the nfit block partials.
 struct FinishOut {
   double* A;        // I x R
   double* lambda;   // R
@@ -77,16 +97,8 @@ struct FinishOut {
   float* Qf;        // I x R FP32 copy (may be null)
   double* fit_terms;  // 2 doubles
 };
-cudaError_t launch_mode_finish(const double* V, int C, const double* R0, double beta, double alpha,
-                               int64_t I, int R, FinishOut out, double* work, unsigned int* dev_status,
-                               cudaStream_t st);
-
-// V[i, c] = sum_{p, s} Y[p, i, s] * Qc[p*S + s, c], c < C, Qc = [Q0 | Q0prev] (K x C,
-// K = P*S) FP64; Y FP64 or FP32.  work: leaf_v_splits(I, K) * I * C doubles.
-int leaf_v_splits(int64_t I, int64_t K);
-template <typename TY>
-cudaError_t launch_leaf_v(const TY* Y, int64_t P, int64_t I, int64_t S, const double* Q0,
-                          const double* Q0prev, int R, int C, double* V, double* work, cudaStream_t st);
+cudaError_t launch_mode_finish(const double* Ahat, const double* fitpart, int nfit, int64_t I, int R, FinishOut out,
+                               double* work, unsigned int* dev_status, cudaStream_t st);
 
 // ||X||^2 in FP64 (partials into work, final into out[0]).
 template <typename TX>

@@ -41,6 +41,7 @@ namespace cg = cooperative_groups;
 
 #ifdef CPQR_QR_PHASES
 __device__ unsigned long long g_qr_phase[8];
+__device__ long long g_qr_col[2][8];  // per-column sub-phase cycles (clock64) summed over columns, ranks 0 and CL-1
 #define QR_PHASE(i)                                                              \
   do {                                                                           \
     if (threadIdx.x == 0 && cluster.block_rank() == 0) {                         \
@@ -49,9 +50,18 @@ __device__ unsigned long long g_qr_phase[8];
       g_qr_phase[i] = t_;                                                        \
     }                                                                            \
   } while (0)
+#define QR_COL(k)                   \
+  do {                              \
+    const long long t_ = clock64(); \
+    col_acc[k] += t_ - col_prev;    \
+    col_prev = t_;                  \
+  } while (0)
 #else
 #define QR_PHASE(i) \
   do {              \
+  } while (0)
+#define QR_COL(k) \
+  do {            \
   } while (0)
 #endif
 
@@ -86,13 +96,13 @@ struct QrParams {
   int krp_m;
   TriPtrs tri;
   // MODE_FINISH
-  const double* V;
-  int C;
-  const double* R0;
-  double beta, alpha;
+  const double* Ahat;      // I x R rows of A^ = V^ R0^{-T} (finish_prep_kernel)
+  const double* fitpart;   // nfit x 2 per-block partial fit terms (finish_prep_kernel)
+  int nfit;
   FinishOut fin;
   // outputs
   double* Q;
+  float* Qf;  // FP32 copy of Q (may be null)
   double* Rout;
   unsigned int* status;
 };
@@ -112,10 +122,9 @@ struct SmemLayout {
   double alpha[CPQR_MAXR];
   double tau[CPQR_MAXR];
   double vpiv[CPQR_MAXR];
-  double ST[CPQR_MAXR][CPQR_MAXR];  // ST[b][a] = v_a^T v_b, a < b
-  double VT[CPQR_MAXR][CPQR_MAXR];  // VT[c][a] = v_a[c], a <= c (top block of V, transposed)
-  double R0[RR];                    // finish: R0
-  double rdiag[CPQR_MAXR];
+  // ST[b][a] = v_a^T v_b (a < b) in [0, RR), VT[c][a] = v_a[c] (a <= c, top block of V) in
+  // [RR, 2 RR); before the Householder columns: the Khatri-Rao triangles (up to 3 RR doubles)
+  double big[3 * RR];
 };
 
 // Row t's lowest column with a nonzero reflector entry (staircase) for KRP mode.
@@ -126,14 +135,16 @@ __device__ __forceinline__ int row_alo(const QrParams& p, int t) {
   return a;
 }
 
-__device__ __forceinline__ double krp_value(const QrParams& p, int orig, int c) {
-  // orig = digits (r_1 .. r_m) base R, r_m fastest
+// Entry (orig, c) of Z = R_{k1} (.) ... (.) R_{km}; orig = digits (r_1 .. r_m) base R, r_m
+// fastest; tri = the m triangles back to back (R x R each) in shared memory, or null (global).
+__device__ __forceinline__ double krp_value(const QrParams& p, const double* tri, int orig, int c) {
   double v = 1.0;
   int x = orig;
+  const int RR2 = p.R * p.R;
   for (int k = p.krp_m - 1; k >= 0; --k) {
     int r = x % p.R;
     x /= p.R;
-    v *= p.tri.p[k][r * p.R + c];
+    v *= tri ? tri[k * RR2 + r * p.R + c] : p.tri.p[k][r * p.R + c];
   }
   return v;
 }
@@ -143,28 +154,37 @@ __device__ __forceinline__ double tree8(const double* v, int stride) {
          ((v[4 * stride] + v[5 * stride]) + (v[6 * stride] + v[7 * stride]));
 }
 
-// 1/sqrt(s) for the column norm: rsqrt.approx.f64 (measured to 53 bits on sm_103) inside the
-// normal range, the IEEE path outside it.
-__device__ __forceinline__ double col_rsqrt(double s) {
-  if (s > 1e-280 && s < 1e280) {
+// Householder scalars of a column with squared norm s and pivot entry xj:
+// alpha = -sign(xj) sqrt(s), tau = 2 / ||v||^2 = 1 / (s - alpha xj).  Inside the normal range
+// the square root comes from rsqrt.approx.f64 (measured to 53 bits on sm_103) and the reciprocal
+// from rcp.approx.ftz.f64 (about 20 bits) refined by two Newton-Raphson steps
+// z <- z + z (1 - d z), each squaring the relative error; outside it the IEEE operations.  The
+// range and sign tests are integer tests on the bit patterns: FP64 compares would sit on the
+// column's critical path at FP64 latency.
+__device__ __forceinline__ void house_scalars(double s, double xj, double& alpha, double& tau) {
+  const long long sb = __double_as_longlong(s), xb = __double_as_longlong(xj);
+  const bool xpos = (xb >= 0) || (xb == (long long)0x8000000000000000ull);  // xj >= 0, including -0
+  alpha = 0.0;
+  tau = 0.0;
+  if (sb <= 0) return;  // s == 0 (a zero column); s is a sum of squares, so never negative
+  // [1e-280, 1e280]: s * (1 + |xj| / sqrt(s)) <= 2 s stays normal for the reciprocal
+  constexpr long long kLo = 0x05CD0B15A491EB84LL;  // bit pattern of 1e-280
+  constexpr long long kHi = 0x7A11A0FC668AAC70LL;  // bit pattern of 1e280
+  if (sb > kLo && sb < kHi) {
     double y;
     asm("rsqrt.approx.f64 %0, %1;" : "=d"(y) : "d"(s));
-    return y;
-  }
-  return 1.0 / sqrt(s);
-}
-
-// 1/d: rcp.approx.ftz.f64 (about 20 bits) refined by two Newton-Raphson steps
-// z <- z + z (1 - d z), each squaring the relative error; IEEE division outside the normal range.
-__device__ __forceinline__ double col_rcp(double d) {
-  if (d > 1e-280 && d < 1e280) {
+    const double nx = s * y;
+    alpha = xpos ? -nx : nx;
+    const double d = fma(-alpha, xj, s);
     double z;
     asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(z) : "d"(d));
     z = fma(z, fma(-d, z, 1.0), z);
-    z = fma(z, fma(-d, z, 1.0), z);
-    return z;
+    tau = fma(z, fma(-d, z, 1.0), z);
+  } else {
+    const double nx = sqrt(s);
+    alpha = xpos ? -nx : nx;
+    tau = 1.0 / (s - alpha * xj);
   }
-  return 1.0 / d;
 }
 
 // Named barrier for warps 0..3 (128 threads).
@@ -196,6 +216,8 @@ __global__ void __launch_bounds__(NT, 1) qr_cluster_kernel(QrParams p) {
   }
   auto W = [&](int u) -> double* { return Wb + (size_t)u * ldw; };
   auto grow = [&](int u) -> int { return rank + CL * u; };
+  double (*ST)[CPQR_MAXR] = reinterpret_cast<double (*)[CPQR_MAXR]>(&sm.big[0]);
+  double (*VT)[CPQR_MAXR] = reinterpret_cast<double (*)[CPQR_MAXR]>(&sm.big[RR]);
 
   QR_PHASE(0);
   // mbarriers of the st.async exchanges, armed for their first phase before any peer can send
@@ -214,76 +236,44 @@ __global__ void __launch_bounds__(NT, 1) qr_cluster_kernel(QrParams p) {
     for (int u = warp; u < L; u += NW)
       if (lane < R) W(u)[lane] = p.A_in[(size_t)grow(u) * R + lane];
   } else if (p.mode == MODE_KRP) {
+    // the triangles are read R times each: one copy into shared memory first when they fit
+    double* tri = nullptr;
+    if (p.krp_m * R * R <= 3 * RR) {
+      tri = sm.big;
+      for (int e = tid; e < p.krp_m * R * R; e += NT) tri[e] = p.tri.p[e / (R * R)][e % (R * R)];
+      __syncthreads();
+    }
     for (int u = warp; u < L; u += NW)
-      if (lane < R) W(u)[lane] = krp_value(p, p.perm[grow(u)], lane);
+      if (lane < R) W(u)[lane] = krp_value(p, tri, p.perm[grow(u)], lane);
   } else {
-    // MODE_FINISH: V^ per row, back substitution A^ R0^T = V^, column norms.
-    for (int i = tid; i < R * R; i += NT) sm.R0[(i / R) * CPQR_MAXR + i % R] = p.R0[i];
-    __syncthreads();
-    if (tid < R) {
-      double d = sm.R0[tid * CPQR_MAXR + tid];
-      sm.rdiag[tid] = (d != 0.0) ? 1.0 / d : 0.0;
-      if (d == 0.0 && rank == 0) atomicOr(p.status, CPQR_DEV_SINGULAR);
-    }
-    __syncthreads();
-    const bool ext = (p.C == 2 * R);
-    const double c0 = 1.0 + p.beta, c1 = -p.alpha * p.beta;
-    double nrm = 0.0, f_in = 0.0, f_nn = 0.0;
+    // MODE_FINISH: rows of A^ (Alg. 2 line 8, solved by finish_prep_kernel), column norms
+    // lambda_r = ||a^_r|| over the cluster and the normalisation A = A^ / lambda (line 9).
+    double nrm = 0.0;
     for (int u = warp; u < L; u += NW) {
-      const size_t t = (size_t)grow(u);
-      double v0 = 0.0, vh = 0.0;
-      if (lane < R) {
-        v0 = p.V[t * p.C + lane];
-        vh = ext ? (c0 * v0 + c1 * p.V[t * p.C + R + lane]) : v0;
-      }
-      f_in += v0 * vh;
-      f_nn += vh * vh;
-      double res = vh, ahat = 0.0;
-      for (int c = R - 1; c >= 0; --c) {
-        double a_c = __shfl_sync(FULL, res, c) * sm.rdiag[c];
-        if (lane == c) ahat = a_c;
-        if (lane < c) res -= sm.R0[lane * CPQR_MAXR + c] * a_c;
-      }
-      if (lane < R) W(u)[lane] = ahat;
-      nrm += ahat * ahat;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      f_in += __shfl_xor_sync(FULL, f_in, o);
-      f_nn += __shfl_xor_sync(FULL, f_nn, o);
+      const double a = (lane < R) ? p.Ahat[(size_t)grow(u) * R + lane] : 0.0;
+      if (lane < R) W(u)[lane] = a;
+      nrm = fma(a, a, nrm);
     }
     sm.red[warp][lane] = nrm;
-    if (lane == 0) {
-      sm.red[warp][2 * CPQR_MAXR] = f_in;
-      sm.red[warp][2 * CPQR_MAXR + 1] = f_nn;
-    }
     __syncthreads();
     if (warp == 0) {
-      for (int i = lane; i < PSLOT; i += 32) {
-        double v = tree8(&sm.red[0][i], PSLOT);
-        for (int r = 0; r < CL; ++r) cluster.map_shared_rank(&sm.inbox1[rank][0], r)[i] = v;
-      }
+      const double v = tree8(&sm.red[0][lane], PSLOT);
+      for (int r = 0; r < CL; ++r) cluster.map_shared_rank(&sm.inbox1[rank][0], r)[lane] = v;
     }
     cluster.sync();
-    auto inbox_sum = [&](int i) -> double {
+    if (warp == 0) {
       double s[MAXCL / 2];
 #pragma unroll
-      for (int h = 0; h < CL / 2; ++h) s[h] = sm.inbox1[2 * h][i] + sm.inbox1[2 * h + 1][i];
+      for (int h = 0; h < CL / 2; ++h) s[h] = sm.inbox1[2 * h][lane] + sm.inbox1[2 * h + 1][lane];
 #pragma unroll
       for (int w = CL / 4; w >= 1; w >>= 1)
 #pragma unroll
         for (int h = 0; h < w; ++h) s[h] += s[h + w];
-      return s[0];
-    };
-    if (warp == 0) {
-      double lam = sqrt(inbox_sum(lane));
+      const double lam = sqrt(s[0]);
       if (lane < R) {
         sm.bcw[lane] = (lam > 0.0) ? 1.0 / lam : 0.0;
         if (lam == 0.0 && rank == 0) atomicOr(p.status, CPQR_DEV_SINGULAR);
         if (rank == 0) p.fin.lambda[lane] = lam;
-      }
-      if (lane == 0 && rank == 0) {
-        p.fin.fit_terms[0] = inbox_sum(2 * CPQR_MAXR);
-        p.fin.fit_terms[1] = inbox_sum(2 * CPQR_MAXR + 1);
       }
     }
     __syncthreads();
@@ -301,7 +291,12 @@ __global__ void __launch_bounds__(NT, 1) qr_cluster_kernel(QrParams p) {
   // ---------------- Householder columns: one st.async exchange per column ----------------
   // Step j applies reflector j-1 to the rows it touches and, in the same pass, accumulates
   // x_j^T a_c (x_j = column j after that update) over the rows [j, act[j]) for every c.
+#ifdef CPQR_QR_PHASES
+  long long col_acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  long long col_prev = clock64();
+#endif
   for (int j = 0; j < R; ++j) {
+    QR_COL(0);
     const int buf = j & 1;
     const int pj = j - 1;
     const bool upd = (j > 0);
@@ -332,8 +327,10 @@ __global__ void __launch_bounds__(NT, 1) qr_cluster_kernel(QrParams p) {
         if (t == j) sm.pivloc[lane] = a;
       }
     }
+    QR_COL(1);
     sm.red[warp][lane] = acc;
     __syncthreads();
+    QR_COL(2);
     if (warp < 4) {
       // CTA sums of 8 columns per warp, stored into every CTA of the cluster
       const int slot = 8 * warp + (lane & 7), g = lane >> 3;
@@ -353,8 +350,10 @@ __global__ void __launch_bounds__(NT, 1) qr_cluster_kernel(QrParams p) {
       const uint32_t bar = smem_u32(&sm.bar[buf]);
       for (int r = lane >> 4; r < CL; r += 2) tc::st_async_v2(tc::mapa(src, r), lo, hi, tc::mapa(bar, r));
     }
+    QR_COL(3);
     if (warp < 4) {
       tc::mbar_wait_cluster(smem_u32(&sm.bar[buf]), (uint32_t)((j >> 1) & 1), &sm.abort_flag, p.status);
+      QR_COL(4);
       // re-arm this buffer for column j + 2: its bytes can only come after this CTA's column j + 1
       // sums, which it sends after every read of this buffer
       if (tid == 0 && j + 2 < R) tc::mbar_expect_tx(smem_u32(&sm.bar[buf]), kColBytes);
@@ -367,30 +366,33 @@ __global__ void __launch_bounds__(NT, 1) qr_cluster_kernel(QrParams p) {
       v += __shfl_xor_sync(FULL, v, 16);
       if (g == 0) sm.dvec[slot] = v;
       sync_warps0to3();
+      QR_COL(5);
       if (warp == 0) {
         const double s = sm.dvec[j], xj = sm.pbox[buf][j];
-        double alpha = 0.0, tau = 0.0, vp = 0.0;
-        if (s > 0.0) {
-          const double nx = s * col_rsqrt(s);
-          alpha = (xj >= 0.0) ? -nx : nx;
-          vp = xj - alpha;
-          tau = col_rcp(s - alpha * xj);  // 2 / ||v||^2 with ||v||^2 = 2 (s - alpha xj)
-        }
+        double alpha, tau;
+        house_scalars(s, xj, alpha, tau);
+        const double vp = xj - alpha;
         const double pl = sm.pbox[buf][lane];
         const double num = sm.dvec[lane] - alpha * pl;  // v_j^T a_lane (lane > j), v_lane^T v_j (lane < j)
         sm.bcw[lane] = (lane > j && lane < R) ? tau * num : 0.0;
-        sm.ST[j][lane] = (lane < j) ? num : 0.0;
-        sm.VT[j][lane] = (lane < j) ? pl : (lane == j ? vp : 0.0);
+        ST[j][lane] = (lane < j) ? num : 0.0;
+        VT[j][lane] = (lane < j) ? pl : (lane == j ? vp : 0.0);
         if (lane == 0) {
           sm.alpha[j] = alpha;
           sm.tau[j] = tau;
           sm.vpiv[j] = vp;
-          if (rank == 0 && !(s > 0.0)) atomicOr(p.status, CPQR_DEV_SINGULAR);
+          if (rank == 0 && tau == 0.0) atomicOr(p.status, CPQR_DEV_SINGULAR);
         }
       }
+      QR_COL(6);
     }
     __syncthreads();
+    QR_COL(7);
   }
+#ifdef CPQR_QR_PHASES
+  if (tid == 0 && (rank == 0 || rank == CL - 1))
+    for (int k = 0; k < 8; ++k) g_qr_col[rank == 0 ? 0 : 1][k] = col_acc[k];
+#endif
   QR_PHASE(2);
 
   // ---------------- R factor (positive diagonal) ----------------
@@ -411,12 +413,12 @@ __global__ void __launch_bounds__(NT, 1) qr_cluster_kernel(QrParams p) {
   {
     const int cc = rank + CL * warp;
     if (cc < R) {
-      double rhs = (lane <= cc) ? sm.VT[cc][lane] : 0.0;
+      double rhs = (lane <= cc) ? VT[cc][lane] : 0.0;
       double mine = 0.0;
       for (int a = cc; a >= 0; --a) {
         const double w = __shfl_sync(FULL, rhs, a) * sm.tau[a];
         if (lane == a) mine = w;
-        if (lane < a) rhs = fma(-sm.ST[a][lane], w, rhs);
+        if (lane < a) rhs = fma(-ST[a][lane], w, rhs);
       }
       const int pr = lane & 15;
       const double lo = __shfl_sync(FULL, mine, 2 * pr), hi = __shfl_sync(FULL, mine, 2 * pr + 1);
@@ -453,13 +455,102 @@ __global__ void __launch_bounds__(NT, 1) qr_cluster_kernel(QrParams p) {
       if (c < R) {
         const size_t orow = (p.mode == MODE_KRP) ? (size_t)p.perm[t] : (size_t)t;
         p.Q[orow * R + c] = q;
-        if (p.mode == MODE_FINISH && p.fin.Qf) p.fin.Qf[orow * R + c] = (float)q;
+        if (p.Qf) p.Qf[orow * R + c] = (float)q;
       }
     }
   }
   QR_PHASE(6);
+  if (p.mode == MODE_FINISH && rank == 0 && warp == 0) {
+    // <V0, V^> and ||V^||^2: per-block partials of finish_prep_kernel, added in a fixed order
+    double a = 0.0, b = 0.0;
+    for (int k = lane; k < p.nfit; k += 32) {
+      a += p.fitpart[2 * k];
+      b += p.fitpart[2 * k + 1];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(FULL, a, o);
+      b += __shfl_xor_sync(FULL, b, o);
+    }
+    if (lane == 0) {
+      p.fin.fit_terms[0] = a;
+      p.fin.fit_terms[1] = b;
+    }
+  }
   // no CTA leaves while a peer may still store into its shared memory
   cluster.sync();
+}
+
+// Alg. 2 line 8 with eq. 19, one warp per row of V and one row per SM sub-partition (the
+// 32-step back substitution is FP64-bound): the split-K slices of V = Y_(n) [Q0 | Q0^{k-1}]
+// are added in a fixed order (FP32 slices in FP32: the split path's V carries the split TTMs'
+// ~2^-16 relative error), V^ = (1 + beta) V0 - alpha beta V1, and A^ R0^T = V^ is solved by
+// back substitution with lane = column.  Each block also adds up <V0, V^> and ||V^||^2 over
+// its rows; the finish kernel adds the block partials.
+constexpr int PREP_WARPS = 4;
+
+template <typename TP>
+__global__ void __launch_bounds__(PREP_WARPS * 32) finish_prep_kernel(const TP* __restrict__ part, int nparts, int I,
+                                                                      int C, int R, const double* __restrict__ R0,
+                                                                      double c0, double c1, double* __restrict__ Ahat,
+                                                                      double* __restrict__ fitpart,
+                                                                      unsigned int* status) {
+  __shared__ double sR0[CPQR_MAXR][CPQR_MAXR + 1];
+  __shared__ double rdiag[CPQR_MAXR];
+  __shared__ double red[PREP_WARPS][2];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int e = tid; e < R * R; e += PREP_WARPS * 32) sR0[e / R][e % R] = R0[e];
+  __syncthreads();
+  if (tid < R) {
+    const double d = sR0[tid][tid];
+    rdiag[tid] = (d != 0.0) ? 1.0 / d : 0.0;
+    if (d == 0.0 && blockIdx.x == 0) atomicOr(status, CPQR_DEV_SINGULAR);
+  }
+  __syncthreads();
+  const bool ext = (C == 2 * R);
+  const size_t n = (size_t)I * C;
+  double f_in = 0.0, f_nn = 0.0;
+  const int i = blockIdx.x * PREP_WARPS + warp;
+  if (i < I) {
+    double v0 = 0.0, v1 = 0.0;
+    if (lane < R) {
+      const TP* p0 = part + (size_t)i * C + lane;
+      TP s0 = TP(0), s1 = TP(0);
+      for (int q = 0; q < nparts; ++q) {
+        s0 += p0[(size_t)q * n];
+        if (ext) s1 += p0[(size_t)q * n + R];
+      }
+      v0 = (double)s0;
+      v1 = (double)s1;
+    }
+    const double vh = ext ? fma(c0, v0, c1 * v1) : v0;
+    f_in = v0 * vh;
+    f_nn = vh * vh;
+    double res = vh, ahat = 0.0;
+    for (int c = R - 1; c >= 0; --c) {
+      const double a_c = __shfl_sync(FULL, res, c) * rdiag[c];
+      if (lane == c) ahat = a_c;
+      if (lane < c) res = fma(-sR0[lane][c], a_c, res);
+    }
+    if (lane < R) Ahat[(size_t)i * R + lane] = ahat;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    f_in += __shfl_xor_sync(FULL, f_in, o);
+    f_nn += __shfl_xor_sync(FULL, f_nn, o);
+  }
+  if (lane == 0) {
+    red[warp][0] = f_in;
+    red[warp][1] = f_nn;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < PREP_WARPS; ++w) {
+      a += red[w][0];
+      b += red[w][1];
+    }
+    fitpart[2 * blockIdx.x] = a;
+    fitpart[2 * blockIdx.x + 1] = b;
+  }
 }
 
 size_t smem_bytes(int M, int R, int CL, bool use_smem) {
@@ -473,23 +564,38 @@ constexpr size_t kSmemMax = 227 * 1024;
 
 int g_cluster = 0;  // cluster size in use (16 if the device allows it, else 8)
 
+// Function attributes of qr_cluster_kernel<CL>, set once per device.
 template <int CL>
-cudaError_t launch_cl(QrParams& p, cudaStream_t st) {
-  size_t base = smem_bytes(p.M, p.R, CL, false);
-  size_t full = smem_bytes(p.M, p.R, CL, true);
-  p.use_smem = (full <= kSmemMax) ? 1 : 0;
-  if (!p.use_smem && p.work == nullptr) return cudaErrorInvalidValue;
-  size_t sm = p.use_smem ? full : base;
-  cudaError_t e = cudaFuncSetAttribute(qr_cluster_kernel<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+cudaError_t ensure_attributes() {
+  static bool done[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+  e = cudaFuncSetAttribute(qr_cluster_kernel<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
   if (e != cudaSuccess) return e;
   if (CL > 8) {
     e = cudaFuncSetAttribute(qr_cluster_kernel<CL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
   }
+  if (dev >= 0 && dev < 64) done[dev] = true;
+  return cudaSuccess;
+}
+
+// Every launch takes the whole shared memory of its SMs: no other kernel's CTA can share an SM
+// with the QR, whose serial FP64 chain would otherwise compete for issue slots (the Khatri-Rao
+// QR runs beside the TTM chain on another stream).
+template <int CL>
+cudaError_t launch_cl(QrParams& p, cudaStream_t st) {
+  const size_t full = smem_bytes(p.M, p.R, CL, true);
+  p.use_smem = (full <= kSmemMax) ? 1 : 0;
+  if (!p.use_smem && p.work == nullptr) return cudaErrorInvalidValue;
+  cudaError_t e = ensure_attributes<CL>();
+  if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(CL, 1, 1);
   cfg.blockDim = dim3(NT, 1, 1);
-  cfg.dynamicSmemBytes = sm;
+  cfg.dynamicSmemBytes = kSmemMax;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -540,10 +646,17 @@ cudaError_t run(QrParams& p, cudaStream_t st) {
 
 }  // namespace
 
+int qr_cluster_sms() { return cluster_size(); }
+
 #ifdef CPQR_QR_PHASES
 // Profiling build only: %globaltimer stamps of the last cluster-QR launch (rank 0).
 extern "C" void cpqr_debug_qr_phases(unsigned long long* out) {
   cudaMemcpyFromSymbol(out, g_qr_phase, sizeof(g_qr_phase));
+}
+// Profiling build only: clock64 cycles per sub-phase of the Householder columns, summed over
+// columns, for cluster ranks 0 and CL-1 (2 x 8 values).
+extern "C" void cpqr_debug_qr_columns(long long* out) {
+  cudaMemcpyFromSymbol(out, g_qr_col, sizeof(g_qr_col));
 }
 #endif
 
@@ -568,7 +681,7 @@ cudaError_t launch_house_qr(const double* A, int64_t M, int R, double* Q, double
 }
 
 cudaError_t launch_krp_qr(const ZPlan& plan, TriPtrs Rs, double* Q0, double* R0, double* work,
-                          unsigned int* dev_status, cudaStream_t st) {
+                          unsigned int* dev_status, cudaStream_t st, float* Q0f) {
   QrParams p{};
   p.mode = MODE_KRP;
   if (plan.M > (int64_t(1) << 30)) return cudaErrorInvalidValue;
@@ -580,14 +693,32 @@ cudaError_t launch_krp_qr(const ZPlan& plan, TriPtrs Rs, double* Q0, double* R0,
   p.krp_m = plan.m;
   p.tri = Rs;
   p.Q = Q0;
+  p.Qf = Q0f;
   p.Rout = R0;
   p.status = dev_status;
   return run(p, st);
 }
 
-cudaError_t launch_mode_finish(const double* V, int C, const double* R0, double beta, double alpha,
-                               int64_t I, int R, FinishOut out, double* work, unsigned int* dev_status,
+int finish_prep_blocks(int64_t I) { return (int)((I + PREP_WARPS - 1) / PREP_WARPS); }
+
+template <typename TP>
+cudaError_t launch_finish_prep(const TP* parts, int nparts, int64_t I, int C, int R, const double* R0, double beta,
+                               double alpha, double* Ahat, double* fitpart, unsigned int* dev_status,
                                cudaStream_t st) {
+  if (I < 1 || I > (int64_t(1) << 30) || R < 1 || R > CPQR_MAXR || (C != R && C != 2 * R) || nparts < 1)
+    return cudaErrorInvalidValue;
+  const double c0 = 1.0 + beta, c1 = -alpha * beta;
+  finish_prep_kernel<TP><<<finish_prep_blocks(I), PREP_WARPS * 32, 0, st>>>(parts, nparts, (int)I, C, R, R0, c0, c1,
+                                                                          Ahat, fitpart, dev_status);
+  return cudaGetLastError();
+}
+template cudaError_t launch_finish_prep<double>(const double*, int, int64_t, int, int, const double*, double, double,
+                                                double*, double*, unsigned int*, cudaStream_t);
+template cudaError_t launch_finish_prep<float>(const float*, int, int64_t, int, int, const double*, double, double,
+                                               double*, double*, unsigned int*, cudaStream_t);
+
+cudaError_t launch_mode_finish(const double* Ahat, const double* fitpart, int nfit, int64_t I, int R, FinishOut out,
+                               double* work, unsigned int* dev_status, cudaStream_t st) {
   QrParams p{};
   p.mode = MODE_FINISH;
   if (I > (int64_t(1) << 30)) return cudaErrorInvalidValue;
@@ -595,13 +726,12 @@ cudaError_t launch_mode_finish(const double* V, int C, const double* R0, double 
   p.R = R;
   p.work = work;
   for (int j = 0; j < CPQR_MAXR; ++j) p.act[j] = (int32_t)I;
-  p.V = V;
-  p.C = C;
-  p.R0 = R0;
-  p.beta = beta;
-  p.alpha = alpha;
+  p.Ahat = Ahat;
+  p.fitpart = fitpart;
+  p.nfit = nfit;
   p.fin = out;
   p.Q = out.Q;
+  p.Qf = out.Qf;
   p.Rout = out.Rn;
   p.status = dev_status;
   return run(p, st);

@@ -231,75 +231,100 @@ __global__ void __launch_bounds__(TNT) ttm_f32_tiled_kernel(const float* __restr
 
 // ----------------------------------------------------------------------------
 // V[i, c] = sum_k Y[p, i, s] Qc[k, c], k = p*S + s, Qc = [Q0 | Q0prev].
-// CTA tile: 32 rows i x C <= 64 columns x one K chunk.  Every chunk writes its
-// partial sums (FP64) to its own slice of a workspace; a second kernel adds the
-// slices in a fixed order (deterministic, no atomics).
+// CTA tile: 64 rows i x 64 columns c (C <= 64) x one K chunk, staged through
+// shared memory 32 k at a time; each thread keeps a 4 x 4 register tile.  Every
+// chunk writes its partial sums to its own slice of a workspace; the finish
+// preparation kernel adds the slices in a fixed order (deterministic, no
+// atomics).  TQ = type of Q0 and of the slices (FP64 on the FP64 path; FP32
+// copies on the split path, whose Y carries the split TTMs' 2^-16 relative
+// error anyway).
 // ----------------------------------------------------------------------------
-constexpr int VI = 32, VK = 32;
+constexpr int VI = 64, VC = 64, VK = 32;
 
-template <typename TY, typename TA>
+template <typename TY, typename TA, typename TQ>
 __global__ void __launch_bounds__(256) leaf_v_kernel(const TY* __restrict__ Y, int P, int I, int S,
-                                                     const double* __restrict__ Q0,
-                                                     const double* __restrict__ Q0p, int R, int C, int kchunk,
-                                                     double* __restrict__ part) {
-  __shared__ TA sY[VK][VI + 1];
-  __shared__ TA sQ[VK][2 * CPQR_MAXR];
+                                                     const TQ* __restrict__ Q0,
+                                                     const TQ* __restrict__ Q0p, int R, int C, int kchunk,
+                                                     TQ* __restrict__ part) {
+  __shared__ TA sY[VK][VI + 1];  // padded: the S > 1 fill walks k fastest
+  __shared__ __align__(16) TA sQ[VK][VC];
+  constexpr int NLY = (VK * VI) / 256, NLQ = (VK * VC) / 256;
   const int tid = threadIdx.x;
-  const int il = tid % VI, cgp = tid / VI;  // row il, columns cgp*8 .. cgp*8+7
+  const int ty = tid >> 4, tx = tid & 15;  // rows ty*4 .. +3, columns tx*4 .. +3
   const int i0 = blockIdx.x * VI;
   const int K = P * S;
   const int kbeg = blockIdx.y * kchunk;
   const int kend = (kbeg + kchunk < K) ? kbeg + kchunk : K;
-  TA acc[8];
+  TA acc[4][4];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) acc[j] = TA(0);
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = TA(0);
+  // the next chunk's operands are loaded into registers while the current one is multiplied
+  TY ybuf[NLY];
+  TQ qbuf[NLQ];
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int q = 0; q < NLY; ++q) {
+      const int e = tid + 256 * q;
+      // consecutive threads along the contiguous index: s (S > 1) or i (S == 1)
+      const int kk = (S > 1) ? e % VK : e / VI, ii = (S > 1) ? e / VK : e % VI;
+      const int k = k0 + kk, i = i0 + ii;
+      ybuf[q] = TY(0);
+      if (k < kend && i < I) {
+        const int pp = k / S, ss = k - pp * S;
+        ybuf[q] = Y[((int64_t)pp * I + i) * S + ss];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NLQ; ++q) {
+      const int e = tid + 256 * q;
+      const int kk = e / VC, c = e % VC;
+      const int k = k0 + kk;
+      qbuf[q] = TQ(0);
+      if (k < kend && c < C) qbuf[q] = (c < R) ? Q0[(int64_t)k * R + c] : Q0p[(int64_t)k * R + (c - R)];
+    }
+  };
+  if (kbeg < kend) fetch(kbeg);
   for (int k0 = kbeg; k0 < kend; k0 += VK) {
 #pragma unroll
-    for (int q = 0; q < (VK * VI) / 256; ++q) {
+    for (int q = 0; q < NLY; ++q) {
       const int e = tid + 256 * q;
-      const int kk = e % VK, ii = e / VK;
-      const int k = k0 + kk, i = i0 + ii;
-      TA v = TA(0);
-      if (k < kend && i < I) {
-        const int p = k / S, s = k - p * S;
-        v = (TA)Y[((int64_t)p * I + i) * S + s];
-      }
-      sY[kk][ii] = v;
+      const int kk = (S > 1) ? e % VK : e / VI, ii = (S > 1) ? e / VK : e % VI;
+      sY[kk][ii] = (TA)ybuf[q];
     }
 #pragma unroll
-    for (int q = 0; q < (VK * 2 * CPQR_MAXR) / 256; ++q) {
+    for (int q = 0; q < NLQ; ++q) {
       const int e = tid + 256 * q;
-      const int kk = e / (2 * CPQR_MAXR), c = e % (2 * CPQR_MAXR);
-      const int k = k0 + kk;
-      TA v = TA(0);
-      if (k < kend && c < C) v = (TA)((c < R) ? Q0[(int64_t)k * R + c] : Q0p[(int64_t)k * R + (c - R)]);
-      sQ[kk][c] = v;
+      sQ[e / VC][e % VC] = (TA)qbuf[q];
     }
     __syncthreads();
-#pragma unroll 8
+    if (k0 + VK < kend) fetch(k0 + VK);
+#pragma unroll 4
     for (int kk = 0; kk < VK; ++kk) {
-      const TA y = sY[kk][il];
+      TA y[4], qv[4];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) acc[j] += y * sQ[kk][cgp * 8 + j];
+      for (int a = 0; a < 4; ++a) {
+        y[a] = sY[kk][ty * 4 + a];
+        qv[a] = sQ[kk][tx * 4 + a];
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] += y[a] * qv[b];
     }
     __syncthreads();
   }
-  const int i = i0 + il;
-  if (i < I) {
-    double* dst = part + ((size_t)blockIdx.y * I + i) * C;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int c = cgp * 8 + j;
-      if (c < C) dst[c] = (double)acc[j];
+  for (int a = 0; a < 4; ++a) {
+    const int i = i0 + ty * 4 + a;
+    if (i >= I) continue;
+    TQ* dst = part + ((size_t)blockIdx.y * I + i) * C;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int c = tx * 4 + b;
+      if (c < C) dst[c] = (TQ)acc[a][b];
     }
-  }
-}
-
-__global__ void sum_parts_kernel(const double* __restrict__ part, int nparts, int64_t n, double* __restrict__ V) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int q = 0; q < nparts; ++q) s += part[(size_t)q * n + e];
-    V[e] = s;
   }
 }
 
@@ -568,18 +593,18 @@ cudaError_t launch_ttm_f32_tiled(const float* T, const float* Q, float* out, int
 }
 
 int leaf_v_splits(int64_t I, int64_t K) {
-  // split K so that the grid covers the GPU about twice, with at least two VK chunks per split
+  // split K so that the grid covers the GPU about twice (at least one VK chunk per split)
   const int64_t itiles = (I + VI - 1) / VI;
   int64_t want = (2 * 152 + itiles - 1) / itiles;
-  const int64_t maxs = (K + 2 * VK - 1) / (2 * VK);
+  const int64_t maxs = (K + VK - 1) / VK;
   if (want > maxs) want = maxs;
   if (want < 1) want = 1;
   return (int)want;
 }
 
-template <typename TY>
-cudaError_t launch_leaf_v(const TY* Y, int64_t P, int64_t I, int64_t S, const double* Q0, const double* Q0prev,
-                          int R, int C, double* V, double* work, cudaStream_t st) {
+template <typename TY, typename TQ>
+cudaError_t launch_leaf_v(const TY* Y, int64_t P, int64_t I, int64_t S, const TQ* Q0, const TQ* Q0prev, int R, int C,
+                          TQ* work, int* nparts, cudaStream_t st) {
   const int64_t K = P * S;
   if (K > 0x7fffffff || I > 0x7fffffff) return cudaErrorInvalidValue;
   if (C < 1 || C > 2 * CPQR_MAXR || R < 1 || R > CPQR_MAXR) return cudaErrorInvalidValue;
@@ -591,18 +616,15 @@ cudaError_t launch_leaf_v(const TY* Y, int64_t P, int64_t I, int64_t S, const do
   const int64_t ktiles = (K + kchunk - 1) / kchunk;  // <= splits: fits the work slices
   dim3 grid((unsigned)itiles, (unsigned)ktiles);
   using TA = typename std::conditional<std::is_same<TY, double>::value, double, float>::type;
-  leaf_v_kernel<TY, TA><<<grid, 256, 0, st>>>(Y, (int)P, (int)I, (int)S, Q0, Q0prev, R, C, (int)kchunk, work);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  const int64_t n = I * C;
-  sum_parts_kernel<<<(int)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, st>>>(work, (int)ktiles, n, V);
+  leaf_v_kernel<TY, TA, TQ><<<grid, 256, 0, st>>>(Y, (int)P, (int)I, (int)S, Q0, Q0prev, R, C, (int)kchunk, work);
+  *nparts = (int)ktiles;
   return cudaGetLastError();
 }
 
-template cudaError_t launch_leaf_v<double>(const double*, int64_t, int64_t, int64_t, const double*, const double*,
-                                           int, int, double*, double*, cudaStream_t);
-template cudaError_t launch_leaf_v<float>(const float*, int64_t, int64_t, int64_t, const double*, const double*,
-                                          int, int, double*, double*, cudaStream_t);
+template cudaError_t launch_leaf_v<double, double>(const double*, int64_t, int64_t, int64_t, const double*,
+                                                   const double*, int, int, double*, int*, cudaStream_t);
+template cudaError_t launch_leaf_v<float, float>(const float*, int64_t, int64_t, int64_t, const float*, const float*,
+                                                 int, int, float*, int*, cudaStream_t);
 
 template <typename TX>
 cudaError_t launch_norm2(const TX* X, int64_t n, double* out, double* /*work*/, cudaStream_t st) {

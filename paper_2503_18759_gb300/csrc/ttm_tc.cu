@@ -324,7 +324,7 @@ bool ttm_tc_supported(int64_t P, int64_t K, int64_t S, int R) {
 
 cudaError_t launch_ttm_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo, const __nv_bfloat16* Qt, int Rp,
                           int64_t Kp, float* out, int64_t P, int64_t K, int64_t S, int R, unsigned int* dev_status,
-                          cudaStream_t st) {
+                          cudaStream_t st, int reserve_sms) {
   if (!ttm_tc_supported(P, K, S, R) || (Rp != 16 && Rp != 32) || Rp < R || Kp < K || (Kp % 64) != 0)
     return cudaErrorNotSupported;
   if (((uintptr_t)Xhi & 15) || ((uintptr_t)Xlo & 15) || ((uintptr_t)Qt & 15)) return cudaErrorMisalignedAddress;
@@ -371,7 +371,7 @@ cudaError_t launch_ttm_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo, co
   const size_t smem = 1024 + (size_t)TC_NST * TC_STAGE_BYTES + (size_t)prm.nkb * 2 * Rp * 128 + sizeof(TcSmemTail);
   cudaError_t e = cudaFuncSetAttribute(ttm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int64_t grid = std::min<int64_t>(prm.T, tc::num_sms());
+  const int64_t grid = std::min<int64_t>(prm.T, std::max(1, tc::num_sms() - std::max(0, reserve_sms)));
   ttm_tc_kernel<<<(unsigned)grid, TC_THREADS, smem, st>>>(tmh, tml, tmq, prm);
   return cudaGetLastError();
 }

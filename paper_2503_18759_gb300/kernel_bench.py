@@ -73,6 +73,14 @@ def main(argv):
         names = ["prologue", "householder", "R out", "T solve", "W2 gather", "Q rows"]
         print(" ".join(f"{n} {(t[i + 1] - t[i]) / 1000:.1f}us" for i, n in enumerate(names)),
               f"total {(t[6] - t[0]) / 1000:.1f}us")
+        cb = (ctypes.c_longlong * 16)()
+        L.cpqr_debug_qr_columns(cb)
+        R = int(argv[2])
+        cn = ["loop-top", "update+dots", "sync", "send", "wait", "consume", "scalars", "step-sync"]
+        for rk in range(2):
+            print(f"  rank {'0' if rk == 0 else 'last'} cycles/column:",
+                  " ".join(f"{cn[i]} {cb[8 * rk + i] / R:.0f}" for i in range(8)),
+                  f"sum {sum(cb[8 * rk + i] for i in range(8)) / R:.0f}")
 
 
 if __name__ == "__main__":
