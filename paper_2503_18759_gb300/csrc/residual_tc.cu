@@ -10,11 +10,12 @@
 // product against ~1e-3 residuals.  The residual (x - k)^2 is summed in FP32 per 32 columns
 // and in FP64 across them.
 //
-// CTA roles (192 threads, one CTA per SM): warp 0 streams X tiles (128 rows x 32 columns,
-// 128-byte swizzle) through a 4-stage TMA ring; warp 1 owns tensor memory and issues the MMAs;
-// warps 2-5 build W for the next tile (one row per thread) while the MMAs of the current tile
-// run, then read the accumulator (tensor-memory lane = row) and the X ring.  Two W buffers and
-// two accumulators of 256 columns let the MMAs of tile t+1 overlap the epilogue of tile t.
+// CTA roles (320 threads, one CTA per SM): warp 0 streams X tiles (128 rows x 32 columns,
+// 128-byte swizzle) through a 6-stage TMA ring; warp 1 owns tensor memory and issues the MMAs;
+// warps 6-9 build W one tile ahead (one row per thread; their factor loads never stall the
+// stream); warps 2-5 read the accumulator (tensor-memory lane = row) and the X ring.  Two W
+// buffers and two accumulators of 256 columns let the MMAs of tile t+1 overlap the epilogue of
+// tile t.
 // Every CTA owns one group of at most 256 columns (A_last^T of the group split into hi / lo
 // once, in shared memory) and a contiguous range of row tiles.  All mbarrier waits are bounded
 // (CPQR_DEV_TIMEOUT, then every role leaves; in-flight copies are drained and tensor memory is
@@ -29,9 +30,9 @@ namespace {
 
 using namespace tc;
 
-constexpr int RT_THREADS = 192;
+constexpr int RT_THREADS = 320;
 constexpr int RT_M = 128;                // rows per tile: MMA M, tensor-memory lanes
-constexpr int RT_NXS = 4;                // X ring stages
+constexpr int RT_NXS = 6;                // X ring stages
 constexpr int RT_XBOX = RT_M * 128;      // 128 rows x 32 FP32 columns
 constexpr int RT_WBYTES = RT_M * 128;    // 128 rows x 32 FP32 weights, one of hi / lo
 constexpr int RT_MAXW = 256;             // columns per CTA: one accumulator
@@ -193,12 +194,17 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
       mma_commit(smem_u32(&tail->tdown));
       mbar_wait(smem_u32(&tail->tdown), 0, abort_flag, p.status, false);
     }
-  } else {
-    // ---------------- weights + epilogue: warps 2-5, row m = tensor-memory lane ----------------
-    const int m = (warp & 3) * 32 + lane;
+  } else if (warp >= 6) {
+    // ---------------- Khatri-Rao weights: warps 6-9, row m of the tile ----------------
+    const int m = (warp - 6) * 32 + lane;
     const bool avec = (p.R & 3) == 0;
-    auto build = [&](int lt) {
+    for (int lt = 0; lt < ntl; ++lt) {
       const int b = lt & 1;
+      if (lt >= 2) {
+        // buffer b was last read by the MMAs of tile lt - 2
+        const uint32_t use = (uint32_t)((lt - 2) >> 1);
+        if (!warp_wait(smem_u32(&tail->mdone[b]), use & 1u, abort_flag, p.status)) break;
+      }
       const int row = (t0 + lt) * RT_M + m;
       float w[32];
 #pragma unroll
@@ -243,16 +249,14 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
       fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&tail->wfull[b]));
-    };
-
+    }
+  } else {
+    // ---------------- epilogue: warps 2-5, row m = tensor-memory lane ----------------
+    const int m = (warp & 3) * 32 + lane;
     double acc = 0.0;
     int stage = 0;
     uint32_t phase = 0;
-    if (ntl > 0) build(0);
     for (int lt = 0; lt < ntl; ++lt) {
-      // W buffer (lt + 1) & 1 was last read by the MMAs of tile lt - 1, complete since the
-      // previous iteration's wait on mdone
-      if (lt + 1 < ntl) build(lt + 1);
       const int b = lt & 1;
       const uint32_t use = (uint32_t)(lt >> 1);
       if (!warp_wait(smem_u32(&tail->mdone[b]), use & 1u, abort_flag, p.status)) break;
