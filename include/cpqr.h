@@ -57,7 +57,7 @@ typedef enum {
 typedef enum {
   CPQR_PREC_FP64 = 0,      /* every TTM in FP64 (X promoted exactly) */
   CPQR_PREC_SPLIT_BF16 = 1 /* full-tensor TTMs on tcgen05 tensor cores with X and Q split
-                              into bf16 hi + lo (hi*hi + hi*lo + lo*hi, FP32 accumulate);
+                              into bf16 hi + lo (all four products, FP32 accumulate);
                               deeper TTMs in FP32; V = Y_(n) Q0 with FP64 accumulation */
 } cpqr_prec;
 

@@ -67,6 +67,9 @@ struct NodeBuf {
   size_t bytes;
   uint32_t free_mask;
   bool is_x;
+  // split path: which copies the node holds, back to back in p: FP32, then bf16 hi, lo
+  bool has_f32 = true;
+  bool has_split = false;
 };
 
 uint64_t splitmix64(uint64_t& s) {
@@ -285,6 +288,20 @@ std::vector<int64_t> node_dims(const cpqr_ctx* ctx, uint32_t mask) {
 
 size_t elem_size_of_nodes(const cpqr_ctx* ctx) { return ctx->prec == CPQR_PREC_FP64 ? 8 : 4; }
 
+size_t align16(size_t b) { return (b + 15) / 16 * 16; }
+
+// Split-path tree nodes hold what their consumers read: the bf16 hi / lo split (the operand
+// of the tensor-core TTMs) for a node with two or more uncontracted modes, the FP32 tensor for
+// a leaf (V = Y_(n) Q0) and for a node that a CUDA-core TTM will read.
+size_t split_node_bytes(int64_t n, bool f32, bool split) {
+  return (f32 ? align16((size_t)n * 4) : 0) + (split ? 2 * align16((size_t)n * 2) : 0);
+}
+void split_views(void* base, int64_t n, bool f32, __nv_bfloat16** hi, __nv_bfloat16** lo) {
+  char* b = static_cast<char*>(base) + (f32 ? align16((size_t)n * 4) : 0);
+  *hi = reinterpret_cast<__nv_bfloat16*>(b);
+  *lo = reinterpret_cast<__nv_bfloat16*>(b + align16((size_t)n * 2));
+}
+
 cpqr_status run_ttm(cpqr_ctx* ctx, const Op& op) {
   const int dst = op.a, src = op.b, k = op.c;
   auto it = ctx->nodes.find(src);
@@ -297,31 +314,76 @@ cpqr_status run_ttm(cpqr_ctx* ctx, const Op& op) {
   const int64_t K = d[k];
   const int R = ctx->R;
   const size_t es = elem_size_of_nodes(ctx);
-  const size_t bytes = (size_t)(P * R * S) * es;
+  const bool split = ctx->prec == CPQR_PREC_SPLIT_BF16;
+  const int64_t n_out = P * R * S;
+  const uint32_t out_mask = sb.free_mask & ~(1u << k);
+  // split path: which copies the output needs (see split_node_bytes)
+  bool need_f32 = true, need_split = false;
+  if (split) {
+    const std::vector<int64_t> od = node_dims(ctx, out_mask);
+    int nfree = 0;
+    bool cuda_core_consumer = false;
+    for (int j = 0; j < ctx->N; ++j) {
+      if (!(out_mask & (1u << j))) continue;
+      ++nfree;
+      int64_t Pj = 1, Sj = 1;
+      for (int q = 0; q < j; ++q) Pj *= od[q];
+      for (int q = j + 1; q < ctx->N; ++q) Sj *= od[q];
+      if (!ttm_tc_supported(Pj, od[j], Sj, R)) cuda_core_consumer = true;
+    }
+    need_split = nfree >= 2;
+    need_f32 = nfree < 2 || cuda_core_consumer;
+  }
+  const size_t bytes = split ? split_node_bytes(n_out, need_f32, need_split) : (size_t)n_out * es;
   void* out = nullptr;
   CK(ctx->pool.get(bytes, &out));
   cudaStream_t st = ctx->st;
   Timed tm(ctx, sb.is_x ? CPQR_BUCKET_TTM_FULL : CPQR_BUCKET_TTM_DEEP, 1);
-  if (ctx->prec == CPQR_PREC_FP64) {
+  if (!split) {
     if (sb.is_x && !ctx->x64)
       CK(launch_ttm<float, double, double>((const float*)sb.p, ctx->Q[k], (double*)out, P, K, S, R, st));
     else
       CK(launch_ttm<double, double, double>((const double*)sb.p, ctx->Q[k], (double*)out, P, K, S, R, st));
   } else {
-    if (sb.is_x && ttm_tc_supported(P, K, S, R)) {
+    __nv_bfloat16 *ohi = nullptr, *olo = nullptr;
+    if (need_split) split_views(out, n_out, need_f32, &ohi, &olo);
+    float* of = need_f32 ? static_cast<float*>(out) : nullptr;
+    if (ttm_tc_supported(P, K, S, R) && (sb.is_x || sb.has_split)) {
+      const __nv_bfloat16 *shi = ctx->Xhi, *slo = ctx->Xlo;
+      if (!sb.is_x) {
+        __nv_bfloat16 *h, *l;
+        split_views(sb.p, P * K * S, sb.has_f32, &h, &l);
+        shi = h;
+        slo = l;
+      }
       // a Khatri-Rao QR running on the side stream holds one cluster of SMs: the persistent
       // grid leaves those free so that the two overlap instead of queueing behind each other
       const int reserve = ctx->z_pending ? qr_cluster_sms() : 0;
-      CK(launch_ttm_tc(ctx->Xhi, ctx->Xlo, ctx->Qt[k], ctx->Rp, ctx->Kp[k], (float*)out, P, K, S, R,
-                       ctx->dstatus, st, reserve));
+      CK(launch_ttm_tc(shi, slo, ctx->Qt[k], ctx->Rp, ctx->Kp[k], of, P, K, S, R, ctx->dstatus, st, reserve, ohi,
+                       olo));
     } else {
-      cudaError_t e = launch_ttm_f32_tiled((const float*)sb.p, ctx->Qf[k], (float*)out, P, K, S, R, st);
-      if (e == cudaErrorNotSupported) e = launch_ttm<float, float, float>((const float*)sb.p, ctx->Qf[k], (float*)out,
-                                                                           P, K, S, R, st);
+      if (!sb.has_f32) return fail(ctx, CPQR_EINVAL);  // not produced for a CUDA-core consumer
+      float* o32 = of;
+      if (!o32) {  // scratch FP32 output from the pool, split below
+        void* tmp = nullptr;
+        CK(ctx->pool.get((size_t)n_out * 4, &tmp));
+        o32 = static_cast<float*>(tmp);
+      }
+      cudaError_t e = launch_ttm_f32_tiled((const float*)sb.p, ctx->Qf[k], o32, P, K, S, R, st);
+      if (e == cudaErrorNotSupported) e = launch_ttm<float, float, float>((const float*)sb.p, ctx->Qf[k], o32, P, K,
+                                                                           S, R, st);
       CK(e);
+      if (need_split) {
+        CK(launch_split_x(o32, ohi, olo, n_out, st));
+        ctx->launches += 1;
+      }
+      if (!of) ctx->pool.put((size_t)n_out * 4, o32);  // stream order protects it until the split ran
     }
   }
-  ctx->nodes[dst] = NodeBuf{out, bytes, sb.free_mask & ~(1u << k), false};
+  NodeBuf nb{out, bytes, out_mask, false};
+  nb.has_f32 = need_f32;
+  nb.has_split = need_split;
+  ctx->nodes[dst] = nb;
   return CPQR_OK;
 }
 

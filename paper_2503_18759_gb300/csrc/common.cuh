@@ -37,12 +37,15 @@ cudaError_t launch_split_q(const double* Q, int64_t K, int R, __nv_bfloat16* Qt,
 // X (n elements FP32) -> Xhi, Xlo bf16 with X = hi + lo + O(2^-16 |X|).
 cudaError_t launch_split_x(const float* X, __nv_bfloat16* Xhi, __nv_bfloat16* Xlo, int64_t n,
                            cudaStream_t st);
-// out[p, r, s] = sum_i X[p, i, s] Q[i, r] from split operands; out FP32.
-// Returns cudaErrorNotSupported if the shape is outside the kernel's range.
+// out[p, r, s] = sum_i X[p, i, s] Q[i, r] from split operands; out FP32 and, if out_hi /
+// out_lo are given, its bf16 split (the operand format of a following tensor-core TTM).
+// S % 8 == 0 (MN-major) or S == 1 with K % 8 == 0 (K-major); K <= 512.  Returns
+// cudaErrorNotSupported if the shape is outside the kernel's range.
 // reserve_sms: SMs the persistent grid leaves free for concurrent work (a cluster QR).
 cudaError_t launch_ttm_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo, const __nv_bfloat16* Qt,
                           int Rp, int64_t Kp, float* out, int64_t P, int64_t K, int64_t S, int R,
-                          unsigned int* dev_status, cudaStream_t st, int reserve_sms = 0);
+                          unsigned int* dev_status, cudaStream_t st, int reserve_sms = 0,
+                          __nv_bfloat16* out_hi = nullptr, __nv_bfloat16* out_lo = nullptr);
 bool ttm_tc_supported(int64_t P, int64_t K, int64_t S, int R);
 
 // ----- small FP64 kernels (smallqr.cu) -----

@@ -494,17 +494,17 @@ __global__ void __launch_bounds__(PREP_WARPS * 32) finish_prep_kernel(const TP* 
                                                                       double c0, double c1, double* __restrict__ Ahat,
                                                                       double* __restrict__ fitpart,
                                                                       unsigned int* status) {
-  __shared__ double sR0[CPQR_MAXR][CPQR_MAXR + 1];
+  __shared__ double sM[CPQR_MAXR][CPQR_MAXR + 1];  // sM[l][c] = R0[l][c] / R0[c][c], l < c
   __shared__ double rdiag[CPQR_MAXR];
   __shared__ double red[PREP_WARPS][2];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  for (int e = tid; e < R * R; e += PREP_WARPS * 32) sR0[e / R][e % R] = R0[e];
-  __syncthreads();
   if (tid < R) {
-    const double d = sR0[tid][tid];
+    const double d = R0[tid * R + tid];
     rdiag[tid] = (d != 0.0) ? 1.0 / d : 0.0;
     if (d == 0.0 && blockIdx.x == 0) atomicOr(status, CPQR_DEV_SINGULAR);
   }
+  __syncthreads();
+  for (int e = tid; e < R * R; e += PREP_WARPS * 32) sM[e / R][e % R] = R0[e] * rdiag[e % R];
   __syncthreads();
   const bool ext = (C == 2 * R);
   const size_t n = (size_t)I * C;
@@ -513,23 +513,36 @@ __global__ void __launch_bounds__(PREP_WARPS * 32) finish_prep_kernel(const TP* 
   if (i < I) {
     double v0 = 0.0, v1 = 0.0;
     if (lane < R) {
+      // eight independent partial sums keep eight loads in flight; fixed order, deterministic
       const TP* p0 = part + (size_t)i * C + lane;
-      TP s0 = TP(0), s1 = TP(0);
-      for (int q = 0; q < nparts; ++q) {
-        s0 += p0[(size_t)q * n];
-        if (ext) s1 += p0[(size_t)q * n + R];
+      TP a0[8], a1[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) a0[u] = a1[u] = TP(0);
+      int q = 0;
+      for (; q + 8 <= nparts; q += 8) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          a0[u] += p0[(size_t)(q + u) * n];
+          if (ext) a1[u] += p0[(size_t)(q + u) * n + R];
+        }
       }
-      v0 = (double)s0;
-      v1 = (double)s1;
+      for (; q < nparts; ++q) {  // fixed registers: a runtime index would move the arrays to local memory
+        a0[0] += p0[(size_t)q * n];
+        if (ext) a1[0] += p0[(size_t)q * n + R];
+      }
+      v0 = (double)(((a0[0] + a0[1]) + (a0[2] + a0[3])) + ((a0[4] + a0[5]) + (a0[6] + a0[7])));
+      v1 = (double)(((a1[0] + a1[1]) + (a1[2] + a1[3])) + ((a1[4] + a1[5]) + (a1[6] + a1[7])));
     }
     const double vh = ext ? fma(c0, v0, c1 * v1) : v0;
     f_in = v0 * vh;
     f_nn = vh * vh;
+    // column c of the back substitution: a^_c = res_c / R0[c][c], res_l -= R0[l][c] a^_c (l < c);
+    // with the scaled R0 the serial chain is one shuffle and one FMA per column
     double res = vh, ahat = 0.0;
     for (int c = R - 1; c >= 0; --c) {
-      const double a_c = __shfl_sync(FULL, res, c) * rdiag[c];
-      if (lane == c) ahat = a_c;
-      if (lane < c) res = fma(-sR0[lane][c], a_c, res);
+      const double x = __shfl_sync(FULL, res, c);
+      if (lane == c) ahat = x * rdiag[c];
+      if (lane < c) res = fma(-sM[lane][c], x, res);
     }
     if (lane < R) Ahat[(size_t)i * R + lane] = ahat;
   }

@@ -3,7 +3,7 @@
 // X (FP32) is stored once as two bf16 arrays, X = hi + lo + O(2^-16 |X|):
 // hi = bf16(X), lo = bf16(X - hi).  Each Q_k (FP64) is staged after its QR as
 // bf16 hi/lo of Q_k^T, zero-padded to Rp x Kp (the MMA's N x K operand, K
-// contiguous).  The product keeps hi*hi + hi*lo + lo*hi and drops lo*lo.
+// contiguous).  The product keeps all four terms hi*hi + hi*lo + lo*hi + lo*lo.
 #include <algorithm>
 
 #include "tc_common.cuh"
@@ -78,16 +78,24 @@ cudaError_t launch_split_q(const double* Q, int64_t K, int R, __nv_bfloat16* Qt,
 }
 
 // ---------------------------------------------------------------------------
-// Tensor-core TTM of the full tensor (tcgen05, sm_103a).
+// Tensor-core TTM (tcgen05, sm_103a) of the full tensor and of the tree's
+// intermediates, from operands split into bf16 hi/lo.
 //
-// out[p, r, s] = sum_i X[p, i, s] Q[i, r] for S a multiple of 8.  Viewed per p,
-// D (S x R) = X_p^T (S x K, s contiguous: an MN-major A operand) * Q (K x R).
-// A 128-row MMA tile is two 64-row "half tiles" (p, block of 64 s) taken in
-// (p, s-block) order, each loaded by TMA as a 64 (s) x 64 (i) bf16 box with
-// 128-byte swizzle; rows beyond S or P are zero-filled by TMA and masked in the
-// epilogue.  Q^T (bf16 hi/lo, K-major, zero padded to Rp x Kp) stays resident
-// in shared memory.  Per 16-deep K step three MMAs accumulate hi*hi + hi*lo +
-// lo*hi into an FP32 accumulator in tensor memory (M = 128, N = Rp).
+// out[p, r, s] = sum_i X[p, i, s] Q[i, r].
+//  * S a multiple of 8 (MN-major A): viewed per p, D (S x R) = X_p^T (S x K,
+//    s contiguous) * Q (K x R).  A 128-row MMA tile is two 64-row "half tiles"
+//    (p, block of 64 s) taken in (p, s-block) order, each loaded by TMA as a
+//    64 (s) x 64 (i) bf16 box with 128-byte swizzle.
+//  * S == 1 (K-major A, the contracted mode is the contiguous one): D (P x R) =
+//    X (P x K, i contiguous) * Q; a tile is 128 rows p, loaded as one 64 (i) x
+//    128 (p) box per 64-deep K block.
+// Rows beyond S or P are zero-filled by TMA and masked in the epilogue.  Q^T
+// (bf16 hi/lo, K-major, zero padded to Rp x Kp) stays resident in shared
+// memory.  Per 16-deep K step four MMAs accumulate hi*hi + hi*lo + lo*hi + lo*lo
+// into an FP32 accumulator in tensor memory (M = 128, N = Rp): the products are
+// exact, so the error is that of the operands' two-term bf16 representations
+// (~2^-17 each); the tensor pipe is far from busy at these ranks.  The epilogue writes
+// the FP32 result and, when asked, its own bf16 hi/lo split for the next TTM.
 //
 // Warp roles (192 threads): warps 0-3 epilogue (tensor-memory lanes 32w..32w+31),
 // warp 4 TMA producer + tensor-memory allocation, warp 5 MMA issuer.  Stages of
@@ -109,10 +117,12 @@ constexpr int TC_TMEM_COLS = 64;            // two accumulators of up to 32 colu
 struct TcParams {
   int64_t P, K, S;
   int R, Rp, nkb;
-  int64_t nsb;  // 64-wide s blocks per p
-  int64_t H;    // half tiles = P * nsb
-  int64_t T;    // tiles = ceil(H / 2)
-  float* out;
+  int64_t nsb;  // 64-wide s blocks per p (MN-major)
+  int64_t H;    // half tiles = P * nsb (MN-major)
+  int64_t T;    // tiles: ceil(H / 2) (MN-major), ceil(P / 128) (K-major)
+  float* out;             // FP32 result (may be null when only the split is wanted)
+  __nv_bfloat16* out_hi;  // optional split copy of out (hi + lo = out to ~2^-16)
+  __nv_bfloat16* out_lo;
   unsigned int* status;
 };
 
@@ -131,6 +141,16 @@ struct TcSmemTail {
 
 using namespace tc;
 
+__device__ __forceinline__ void store_out(const TcParams& p, int64_t idx, float v) {
+  if (p.out) p.out[idx] = v;
+  if (p.out_hi) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    p.out_hi[idx] = h;
+    p.out_lo[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
+}
+
+template <bool KM>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     ttm_tc_kernel(const __grid_constant__ CUtensorMap tmXhi, const __grid_constant__ CUtensorMap tmXlo,
                   const __grid_constant__ CUtensorMap tmQ, TcParams p) {
@@ -143,6 +163,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const uint32_t sB = sA + TC_NST * TC_STAGE_BYTES;              // nkb x {hi, lo} x (Rp x 128 B)
   const uint32_t bsub = (uint32_t)p.Rp * 128u;
   TcSmemTail* tail = reinterpret_cast<TcSmemTail*>(base + TC_NST * TC_STAGE_BYTES + (size_t)p.nkb * 2 * bsub);
+  // K-major epilogue: each warp's 32 rows x R results pass through shared memory so that the
+  // rows (R contiguous floats each) are written with coalesced stores
+  float* epi = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(tail) + ((sizeof(TcSmemTail) + 15) / 16) * 16);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -189,11 +212,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       for (int64_t lt = 0; lt < ntile_local && ok; ++lt) {
         const int64_t tile = blockIdx.x + lt * gridDim.x;
         const int64_t h0 = 2 * tile, h1 = 2 * tile + 1;
-        const int p0 = (int)(h0 / p.nsb), sb0 = (int)(h0 % p.nsb);
-        int p1 = (int)p.P, sb1 = 0;  // past the last half tile: an all-out-of-bounds box (zeros)
-        if (h1 < p.H) {
-          p1 = (int)(h1 / p.nsb);
-          sb1 = (int)(h1 % p.nsb);
+        int p0 = 0, sb0 = 0, p1 = (int)p.P, sb1 = 0;  // past the last half tile: an all-out-of-bounds box
+        if (!KM) {
+          p0 = (int)(h0 / p.nsb);
+          sb0 = (int)(h0 % p.nsb);
+          if (h1 < p.H) {
+            p1 = (int)(h1 / p.nsb);
+            sb1 = (int)(h1 % p.nsb);
+          }
         }
         for (int kb = 0; kb < p.nkb; ++kb) {
           if (!mbar_wait(smem_u32(&tail->empty[stage]), phase ^ 1u, &tail->abort_flag, p.status)) {
@@ -203,10 +229,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           const uint32_t fb = smem_u32(&tail->full[stage]);
           const uint32_t dst = sA + stage * TC_STAGE_BYTES;
           mbar_expect_tx(fb, TC_STAGE_BYTES);
-          tma_load_3d(dst, &tmXhi, sb0 * 64, kb * 64, p0, fb);
-          tma_load_3d(dst + TC_HALF_BYTES, &tmXhi, sb1 * 64, kb * 64, p1, fb);
-          tma_load_3d(dst + 2 * TC_HALF_BYTES, &tmXlo, sb0 * 64, kb * 64, p0, fb);
-          tma_load_3d(dst + 3 * TC_HALF_BYTES, &tmXlo, sb1 * 64, kb * 64, p1, fb);
+          if (KM) {
+            // 128 rows p x 64 i of hi, then of lo
+            tma_load_2d(dst, &tmXhi, kb * 64, (int)(tile * 128), fb);
+            tma_load_2d(dst + 2 * TC_HALF_BYTES, &tmXlo, kb * 64, (int)(tile * 128), fb);
+          } else {
+            tma_load_3d(dst, &tmXhi, sb0 * 64, kb * 64, p0, fb);
+            tma_load_3d(dst + TC_HALF_BYTES, &tmXhi, sb1 * 64, kb * 64, p1, fb);
+            tma_load_3d(dst + 2 * TC_HALF_BYTES, &tmXlo, sb0 * 64, kb * 64, p0, fb);
+            tma_load_3d(dst + 3 * TC_HALF_BYTES, &tmXlo, sb1 * 64, kb * 64, p1, fb);
+          }
           tail->issued[stage] += 1;
           if (++stage == TC_NST) {
             stage = 0;
@@ -218,8 +250,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   } else if (warp == 5) {
     if (lane == 0) {
       // ---------------- MMA issuer ----------------
-      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | ((uint32_t)(p.Rp >> 3) << 17) |
-                             ((uint32_t)(128 >> 4) << 24);
+      // F32 accumulate, bf16 A and B, B K-major, A MN-major (bit 15) or K-major
+      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (KM ? 0u : (1u << 15)) |
+                             ((uint32_t)(p.Rp >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
       bool ok = mbar_wait(smem_u32(&tail->bfull), 0, &tail->abort_flag, p.status);
       fence_after();
       int stage = 0;
@@ -242,13 +275,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           const uint32_t b_hi = sB + (2 * kb) * bsub, b_lo = b_hi + bsub;
 #pragma unroll
           for (int ks = 0; ks < 4; ++ks) {
-            const uint64_t ah = smem_desc(a_hi + ks * 2048, TC_HALF_BYTES, 1024);
-            const uint64_t al = smem_desc(a_lo + ks * 2048, TC_HALF_BYTES, 1024);
+            // MN-major: 16 i-rows of 128 bytes per K step, the two 64-row halves TC_HALF_BYTES apart;
+            // K-major: 32 bytes (16 bf16) along each 128-byte row, 8-row groups 1024 bytes apart
+            const uint64_t ah = KM ? smem_desc(a_hi + ks * 32, 16, 1024) : smem_desc(a_hi + ks * 2048, TC_HALF_BYTES, 1024);
+            const uint64_t al = KM ? smem_desc(a_lo + ks * 32, 16, 1024) : smem_desc(a_lo + ks * 2048, TC_HALF_BYTES, 1024);
             const uint64_t bh = smem_desc(b_hi + ks * 32, 16, 1024);
             const uint64_t bl = smem_desc(b_lo + ks * 32, 16, 1024);
             mma_bf16(d, ah, bh, idesc, (kb | ks) != 0 ? 1u : 0u);
             mma_bf16(d, ah, bl, idesc, 1u);
             mma_bf16(d, al, bh, idesc, 1u);
+            mma_bf16(d, al, bl, idesc, 1u);
           }
           mma_commit(smem_u32(&tail->empty[stage]));
           if (++stage == TC_NST) {
@@ -279,15 +315,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&tail->tempty[acc]));
       const int64_t tile = blockIdx.x + lt * gridDim.x;
-      const int64_t h = 2 * tile + (m >> 6);
-      if (h < p.H) {
-        const int64_t pp = h / p.nsb, sb = h % p.nsb;
-        const int64_t sidx = sb * 64 + (m & 63);
-        if (sidx < p.S) {
-          float* o = p.out + (pp * p.R) * p.S + sidx;
+      if (KM) {
+        float* stg = epi + warp * (32 * 33);
 #pragma unroll
-          for (int r = 0; r < 32; ++r)
-            if (r < p.R) o[(int64_t)r * p.S] = v[r];
+        for (int r = 0; r < 32; ++r) stg[lane * 33 + r] = v[r];
+        __syncwarp();
+        const int64_t p0 = tile * 128 + warp * 32;  // this warp's rows, contiguous in out
+        const int nrows = (int)std::min<int64_t>(32, p.P - p0);
+        for (int e = lane; e < nrows * p.R; e += 32) {
+          const int row = e / p.R, r = e - row * p.R;
+          store_out(p, p0 * p.R + e, stg[row * 33 + r]);
+        }
+        __syncwarp();
+      } else {
+        const int64_t h = 2 * tile + (m >> 6);
+        if (h < p.H) {
+          const int64_t pp = h / p.nsb, sb = h % p.nsb;
+          const int64_t sidx = sb * 64 + (m & 63);
+          if (sidx < p.S) {
+            const int64_t o = (pp * p.R) * p.S + sidx;
+#pragma unroll
+            for (int r = 0; r < 32; ++r)
+              if (r < p.R) store_out(p, o + (int64_t)r * p.S, v[r]);
+          }
         }
       }
     }
@@ -315,8 +365,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 }  // namespace
 
 bool ttm_tc_supported(int64_t P, int64_t K, int64_t S, int R) {
-  if (R < 1 || R > 32 || K < 1 || K > 64 * TC_MAX_KB || P < 1 || S < 8 || (S % 8) != 0) return false;
-  if (P > 0x7fffffff || S > 0x7fffffff) return false;
+  if (R < 1 || R > 32 || K < 1 || K > 64 * TC_MAX_KB || P < 1 || P > 0x7fffffff || S > 0x7fffffff) return false;
+  if (S == 1) return (K % 8) == 0 && (P + 127) / 128 < (int64_t(1) << 31);  // K-major: 16-byte row stride
+  if (S < 8 || (S % 8) != 0) return false;
   const int64_t nsb = (S + 63) / 64;
   if (P * nsb > (int64_t(1) << 40)) return false;
   return true;
@@ -324,14 +375,29 @@ bool ttm_tc_supported(int64_t P, int64_t K, int64_t S, int R) {
 
 cudaError_t launch_ttm_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo, const __nv_bfloat16* Qt, int Rp,
                           int64_t Kp, float* out, int64_t P, int64_t K, int64_t S, int R, unsigned int* dev_status,
-                          cudaStream_t st, int reserve_sms) {
+                          cudaStream_t st, int reserve_sms, __nv_bfloat16* out_hi, __nv_bfloat16* out_lo) {
   if (!ttm_tc_supported(P, K, S, R) || (Rp != 16 && Rp != 32) || Rp < R || Kp < K || (Kp % 64) != 0)
     return cudaErrorNotSupported;
   if (((uintptr_t)Xhi & 15) || ((uintptr_t)Xlo & 15) || ((uintptr_t)Qt & 15)) return cudaErrorMisalignedAddress;
+  if ((out_hi == nullptr) != (out_lo == nullptr)) return cudaErrorInvalidValue;
+  const bool km = (S == 1);
   tc::EncodeTiledFn enc = tc::encode_tiled_fn();
   if (!enc) return cudaErrorNotSupported;
   CUtensorMap tmh, tml, tmq;
-  {
+  if (km) {
+    cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)P};
+    cuuint64_t strides[1] = {(cuuint64_t)K * 2};
+    cuuint32_t box[2] = {64, 128};
+    cuuint32_t es[2] = {1, 1};
+    if (enc(&tmh, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)Xhi, dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+    if (enc(&tml, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)Xlo, dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  } else {
     cuuint64_t dims[3] = {(cuuint64_t)S, (cuuint64_t)K, (cuuint64_t)P};
     cuuint64_t strides[2] = {(cuuint64_t)S * 2, (cuuint64_t)S * K * 2};
     cuuint32_t box[3] = {64, 64, 1};
@@ -362,17 +428,21 @@ cudaError_t launch_ttm_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo, co
   prm.R = R;
   prm.Rp = Rp;
   prm.nkb = (int)((K + 63) / 64);
-  prm.nsb = (S + 63) / 64;
+  prm.nsb = km ? 1 : (S + 63) / 64;
   prm.H = P * prm.nsb;
-  prm.T = (prm.H + 1) / 2;
+  prm.T = km ? (P + 127) / 128 : (prm.H + 1) / 2;
   prm.out = out;
+  prm.out_hi = out_hi;
+  prm.out_lo = out_lo;
   prm.status = dev_status;
   if (prm.nkb * 64 > Kp) return cudaErrorInvalidValue;
-  const size_t smem = 1024 + (size_t)TC_NST * TC_STAGE_BYTES + (size_t)prm.nkb * 2 * Rp * 128 + sizeof(TcSmemTail);
-  cudaError_t e = cudaFuncSetAttribute(ttm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = 1024 + (size_t)TC_NST * TC_STAGE_BYTES + (size_t)prm.nkb * 2 * Rp * 128 +
+                      ((sizeof(TcSmemTail) + 15) / 16) * 16 + (km ? 4 * 32 * 33 * sizeof(float) : 0);
+  auto kern = km ? ttm_tc_kernel<true> : ttm_tc_kernel<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int64_t grid = std::min<int64_t>(prm.T, std::max(1, tc::num_sms() - std::max(0, reserve_sms)));
-  ttm_tc_kernel<<<(unsigned)grid, TC_THREADS, smem, st>>>(tmh, tml, tmq, prm);
+  kern<<<(unsigned)grid, TC_THREADS, smem, st>>>(tmh, tml, tmq, prm);
   return cudaGetLastError();
 }
 

@@ -21,9 +21,14 @@ def _lib():
 # R padded to 16 / 32, and the 400^3 mode-1 / mode-2 shapes.
 SHAPES = [(1, 64, 128, 32), (3, 64, 64, 16), (2, 50, 72, 5), (5, 37, 8, 24), (7, 129, 200, 32), (1, 400, 4096, 32),
           (40, 48, 48, 16), (400, 400, 400, 32), (1, 400, 160000, 32), (3, 512, 136, 30)]
+# S == 1 (the contracted mode is the contiguous one: K-major operand): one row, a ragged last
+# 128-row tile, K a multiple of 8 but not of 64, R padded to 16 / 32, K at its 512 maximum,
+# and the 400^3 R = 32 deeper-level shape
+SHAPES_KMAJOR = [(1, 64, 1, 8), (1000, 400, 1, 32), (130, 48, 1, 24), (77, 72, 1, 16), (128, 512, 1, 32),
+                 (12800, 400, 1, 32)]
 
 
-@pytest.mark.parametrize("P,K,S,R", SHAPES)
+@pytest.mark.parametrize("P,K,S,R", SHAPES + SHAPES_KMAJOR)
 def test_ttm_split_bf16_tensor_cores(P, K, S, R):
     g = np.random.default_rng(P * 1000 + K + S + R)
     X = g.standard_normal((P, K, S)).astype(np.float32)
@@ -36,7 +41,7 @@ def test_ttm_split_bf16_tensor_cores(P, K, S, R):
     torch.cuda.synchronize()
     got = out.cpu().numpy().astype(np.float64)
     assert np.isfinite(got).all()
-    # hi*hi + hi*lo + lo*hi keeps ~16 significant bits of each operand: per-term relative error
+    # hi + lo keeps ~16 significant bits of each operand (all four products kept): per-term error
     # about 2^-16, summed with random signs over K terms, against outputs of size ~sqrt(K).
     err = np.max(np.abs(got - ref)) / np.max(np.abs(ref))
     assert err < 2e-4, err
