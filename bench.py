@@ -32,9 +32,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "sec/CP-ALS-QR sweep & time-to-fit 1e-6 (mixed+learned vs FP64 GPU); TTM %peak"
 WORKLOAD = "cube400_r32_c09"
-# dram__bytes_read.sum + dram__bytes_write.sum of one ttm_tc_kernel launch on the 400^3 mode-1 shape
-# (ncu capture summarised in profiles/ttm_tc_cube400_mode1.md); None once that kernel changes
-TTM_TC_TRAFFIC = 270.94e6
+# dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture of the current kernels
+# on this workload (profiles/ttm_tc_cube400_r32.md, profiles/qr_cluster_cube400_r32.md); None where a
+# kernel changed after its capture
+TTM_TC_TRAFFIC = None
+TTM_DEEP_TRAFFIC = None
+QR_TRAFFIC = None
 # whole-GPU FP64 DFMA rate measured by a probe on the GB300s (TFLOP/s)
 FP64_PEAK_TFLOPS = 1.20
 
@@ -173,6 +176,8 @@ def run_ours(args, rank, world, local_rank):
     buckets = {name: st.ms_bucket[i] / max(args.steps, 1) for i, name in enumerate(b.BUCKETS)}
     n_full = st.n_bucket[0]
     full_ms = st.ms_bucket[0] / max(n_full, 1)
+    n_deep = st.n_bucket[1]
+    deep_ms = st.ms_bucket[1] / max(n_deep, 1)
     out = None
     if rank == 0:
         hbm, peak_kind = _peaks()
@@ -187,6 +192,17 @@ def run_ours(args, rank, world, local_rank):
                     "kernel": "ttm_tc_kernel (first-level TTM, full tensor)",
                     "peak_kind": f"{peak_kind} copy bandwidth (burst)",
                     "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": full_ms, "launches": int(n_full)}
+        # deeper TTMs (every one on this workload contracts a 400 x 400 x 32 node to 400 x 32 x 32):
+        # node read once (4 B per element: FP32, or bf16 hi + lo) + result written once (4 B per element)
+        deep_in, deep_out = 400 * 400 * prob.R, 400 * prob.R * prob.R
+        deep_bytes = (deep_in + deep_out) * (4 if prec == b.PREC_SPLIT_BF16 else 8)
+        roof_deep = {"bound": "hbm", "achieved": deep_bytes / (deep_ms * 1e-3) / 1e9 if n_deep else None,
+                     "peak": hbm, "unit": "GB/s", "traffic": TTM_DEEP_TRAFFIC if prec == b.PREC_SPLIT_BF16 else None,
+                     "kernel": "ttm_tc_kernel (deeper tree levels, MN- and K-major)",
+                     "peak_kind": f"{peak_kind} copy bandwidth (burst)", "alg_bytes_per_launch": deep_bytes,
+                     "avg_launch_ms": deep_ms, "launches": int(n_deep),
+                     "note": "launches run beside the Khatri-Rao QR on another stream; the 20.5 MB node can be L2-resident"}
+        roof_deep["frac"] = roof_deep["achieved"] / hbm if n_deep else None
         if prec == b.PREC_FP64:
             flops = 2 * prob.X.size * prob.R
             roof_ttm.update({"bound": "alu", "achieved": flops / (full_ms * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS,
@@ -199,12 +215,18 @@ def run_ours(args, rank, world, local_rank):
         I, R = prob.dims[0], prob.R
         qr_flops = 5 * I * R * R - (2 * R ** 3) // 3
         roof_qr = {"bound": "alu", "achieved": qr_flops / (qr_ms * 1e-3) / 1e12 if n_qr else None,
-                   "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "traffic": None,
-                   "kernel": "qr_cluster_kernel<16> (finish: solve, normalise, Householder QR, Q)",
-                   "peak_kind": "FP64 DFMA rate of the whole GPU measured by a probe; the kernel runs on one "
-                                "16-SM cluster and is bound by serial FP64 latency",
-                   "alg_flops_per_launch": qr_flops, "avg_launch_ms": qr_ms, "launches": int(n_qr)}
-        roof_qr["frac"] = roof_qr["achieved"] / roof_qr["peak"] if n_qr else None
+                   "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "traffic": QR_TRAFFIC,
+                   "kernel": "finish_prep_kernel + qr_cluster_kernel<16> (eq. 19, R0^{-T} solve, normalise, "
+                             "Householder QR, Q)",
+                   "peak_kind": "FP64 DFMA rate of the whole GPU measured by a probe; the QR runs on one "
+                                "16-SM cluster and is bound by the latency of its 32 serial Householder columns",
+                   "alg_flops_per_launch": qr_flops, "avg_launch_ms": qr_ms, "launches": int(n_qr),
+                   "cluster_peak_tflops": FP64_PEAK_TFLOPS * 16 / 152}
+        if n_qr:
+            roof_qr["frac"] = roof_qr["achieved"] / roof_qr["peak"]
+            roof_qr["frac_of_cluster_peak"] = roof_qr["achieved"] / roof_qr["cluster_peak_tflops"]
+        else:
+            roof_qr["frac"] = None
         # dominant kernel by device time per sweep
         qr_share = st.ms_bucket[4] + st.ms_bucket[2]
         roof = roof_qr if (prec == b.PREC_SPLIT_BF16 and qr_share > st.ms_bucket[0]) else roof_ttm
@@ -219,6 +241,7 @@ def run_ours(args, rank, world, local_rank):
                           "replicas": world},
                "roofline": roof,
                "roofline_ttm_full": roof_ttm,
+               "roofline_ttm_deep": roof_deep,
                "buckets_ms_per_sweep": buckets,
                "gpu_launches": int(launches),
                "fit_last": float(fits[-1]) if len(fits) else None}
