@@ -35,9 +35,9 @@ WORKLOAD = "cube400_r32_c09"
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture of the current kernels
 # on this workload (profiles/ttm_tc_cube400_r32.md, profiles/qr_cluster_cube400_r32.md); None where a
 # kernel changed after its capture
-TTM_TC_TRAFFIC = None
-TTM_DEEP_TRAFFIC = None
-QR_TRAFFIC = None
+TTM_TC_TRAFFIC = 270.5e6    # ttm_tc_kernel<0>, 1 x 400 x 160000 -> R = 32 (256.1 MB read + 14.4 MB written)
+TTM_DEEP_TRAFFIC = 20.6e6   # ttm_tc_kernel<1>, 12800 x 400 x 1 -> R = 32 (20.6 MB read, output left in L2)
+QR_TRAFFIC = 168.2e3        # qr_cluster_kernel<16>, 400 x 32 plain QR (168 KB read, output left in L2)
 # whole-GPU FP64 DFMA rate measured by a probe on the GB300s (TFLOP/s)
 FP64_PEAK_TFLOPS = 1.20
 
@@ -221,7 +221,8 @@ def run_ours(args, rank, world, local_rank):
                    "peak_kind": "FP64 DFMA rate of the whole GPU measured by a probe; the QR runs on one "
                                 "16-SM cluster and is bound by the latency of its 32 serial Householder columns",
                    "alg_flops_per_launch": qr_flops, "avg_launch_ms": qr_ms, "launches": int(n_qr),
-                   "cluster_peak_tflops": FP64_PEAK_TFLOPS * 16 / 152}
+                   "cluster_peak_tflops": FP64_PEAK_TFLOPS * 16 / 152,
+                   "traffic_note": "ncu capture of the same cluster kernel on the 400 x 32 plain QR"}
         if n_qr:
             roof_qr["frac"] = roof_qr["achieved"] / roof_qr["peak"]
             roof_qr["frac_of_cluster_peak"] = roof_qr["achieved"] / roof_qr["cluster_peak_tflops"]

@@ -56,9 +56,10 @@ typedef enum {
  * factor QRs are FP64 in both modes. */
 typedef enum {
   CPQR_PREC_FP64 = 0,      /* every TTM in FP64 (X promoted exactly) */
-  CPQR_PREC_SPLIT_BF16 = 1 /* full-tensor TTMs on tcgen05 tensor cores with X and Q split
-                              into bf16 hi + lo (all four products, FP32 accumulate);
-                              deeper TTMs in FP32; V = Y_(n) Q0 with FP64 accumulation */
+  CPQR_PREC_SPLIT_BF16 = 1 /* TTMs at every tree level on tcgen05 tensor cores with the
+                              operands split into bf16 hi + lo (all four products, FP32
+                              accumulate; shapes outside the kernel's range on FP32 CUDA
+                              cores); V = Y_(n) Q0 in FP32; fit from an explicit residual */
 } cpqr_prec;
 
 /* Extrapolation on Q0 (eq. 19). */
@@ -190,7 +191,9 @@ cpqr_status cp_als_qr_schedule(int32_t N, const int64_t* dims, int32_t R, int32_
  * tdims[0..nd-1] and Q (I_k x R, row-major, I_k = tdims[k]).  out has dims tdims with
  * tdims[k] replaced by R.  dtype: 0 = FP64 T, Q, out; 1 = FP32 T, Q, out (FFMA, FP32
  * accumulate); 2 = FP32 T, FP64 Q, FP64 out; 3 = split-bf16 tensor-core path: T FP32, Q FP64,
- * out FP32 (tcgen05; T and Q are split into bf16 hi + lo internally).  stream: cudaStream_t. */
+ * out FP32 (tcgen05; T and Q are split into bf16 hi + lo internally; needs K <= 512 and either
+ * S a multiple of 8 or S == 1 with K a multiple of 8, S = prod of the dims after k, else
+ * CPQR_EUNSUPPORTED).  stream: cudaStream_t. */
 cpqr_status cpqr_ttm(const void* T_dev, int32_t nd, const int64_t* tdims, int32_t k,
                      const void* Q_dev, int32_t R, void* out_dev, int32_t dtype, void* stream);
 
