@@ -847,7 +847,14 @@ cpqr_status cp_als_qr_init(cpqr_ctx** out, int32_t N, const int64_t* dims, int32
     for (int n = 0; n < N; ++n) vw = std::max<int64_t>(vw, (int64_t)leaf_v_splits(dims[n], M0) * dims[n] * 2 * R);
     CK(ctx->alloc(&ctx->v_work, vw));
   }
-  CK(cudaStreamCreateWithFlags(&ctx->st2, cudaStreamNonBlocking));
+  {
+    // The Khatri-Rao QR needs one 16-CTA cluster (16 free SMs in one GPC) while a persistent TTM
+    // grid is about to fill the GPU: its stream gets the highest priority so that the cluster is
+    // placed first when both become ready together.
+    int least = 0, greatest = 0;
+    CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    CK(cudaStreamCreateWithPriority(&ctx->st2, cudaStreamNonBlocking, greatest));
+  }
   CK(cudaEventCreateWithFlags(&ctx->ev_ready, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&ctx->ev_z, cudaEventDisableTiming));
   CK(ctx->alloc(&ctx->fit_terms, 2));

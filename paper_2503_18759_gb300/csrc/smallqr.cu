@@ -236,15 +236,21 @@ __global__ void __launch_bounds__(NT, 1) qr_cluster_kernel(QrParams p) {
     for (int u = warp; u < L; u += NW)
       if (lane < R) W(u)[lane] = p.A_in[(size_t)grow(u) * R + lane];
   } else if (p.mode == MODE_KRP) {
-    // the triangles are read R times each: one copy into shared memory first when they fit
+    // The triangles are read R times each and the row permutation once per row: both go into
+    // shared memory first with loads issued all at once (this QR runs beside HBM-bound TTMs,
+    // where a chain of dependent global loads per row would pay the loaded memory latency).
     double* tri = nullptr;
-    if (p.krp_m * R * R <= 3 * RR) {
+    const int ntri = p.krp_m * R * R;
+    int* sperm = nullptr;
+    if (ntri * 8 + L * 4 <= 3 * RR * 8) {
       tri = sm.big;
-      for (int e = tid; e < p.krp_m * R * R; e += NT) tri[e] = p.tri.p[e / (R * R)][e % (R * R)];
+      sperm = reinterpret_cast<int*>(sm.big + ntri);
+      for (int e = tid; e < ntri; e += NT) tri[e] = p.tri.p[e / (R * R)][e % (R * R)];
+      for (int u = tid; u < L; u += NT) sperm[u] = p.perm[grow(u)];
       __syncthreads();
     }
     for (int u = warp; u < L; u += NW)
-      if (lane < R) W(u)[lane] = krp_value(p, tri, p.perm[grow(u)], lane);
+      if (lane < R) W(u)[lane] = krp_value(p, tri, sperm ? sperm[u] : p.perm[grow(u)], lane);
   } else {
     // MODE_FINISH: rows of A^ (Alg. 2 line 8, solved by finish_prep_kernel), column norms
     // lambda_r = ||a^_r|| over the cluster and the normalisation A = A^ / lambda (line 9).
@@ -432,6 +438,14 @@ __global__ void __launch_bounds__(NT, 1) qr_cluster_kernel(QrParams p) {
   QR_PHASE(5);
 
   // ---------------- Q rows: Q[t, c] = sign_c (delta_tc - sum_a v_a[t] W2[a][c]) ----------------
+  // Khatri-Rao mode: the output row of each local row, staged once (V^T V and V_top are dead:
+  // every column of W2 has arrived, so every warp of this CTA finished its back substitution)
+  int* sperm = nullptr;
+  if (p.mode == MODE_KRP && L * 4 <= 3 * RR * 8) {
+    sperm = reinterpret_cast<int*>(sm.big);
+    for (int u = tid; u < L; u += NT) sperm[u] = p.perm[grow(u)];
+    __syncthreads();
+  }
   {
     const int c = lane;
     double w2[CPQR_MAXR];
@@ -453,7 +467,7 @@ __global__ void __launch_bounds__(NT, 1) qr_cluster_kernel(QrParams p) {
       }
       q *= sg;
       if (c < R) {
-        const size_t orow = (p.mode == MODE_KRP) ? (size_t)p.perm[t] : (size_t)t;
+        const size_t orow = (p.mode == MODE_KRP) ? (size_t)(sperm ? sperm[u] : p.perm[t]) : (size_t)t;
         p.Q[orow * R + c] = q;
         if (p.Qf) p.Qf[orow * R + c] = (float)q;
       }

@@ -441,6 +441,37 @@ cudaError_t launch_ttm_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo, co
   auto kern = km ? ttm_tc_kernel<true> : ttm_tc_kernel<false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  if (reserve_sms > 0) {
+    // A cluster QR (reserve_sms CTAs in one cluster, hence in one GPC) runs beside this grid.
+    // Spare SMs scattered over the GPCs would not let it start, so the persistent grid is
+    // launched as clusters of the same size, one fewer than fit on the device: each of them
+    // takes a GPC of its own and one GPC's worth stays free whatever is placed first.  The
+    // CTAs never synchronise as a cluster; the clustering only steers placement.
+    const int cl = reserve_sms;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(TC_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3((unsigned)cl, 1, 1);
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) == cudaSuccess && nclusters >= 2) {
+      const int64_t want = (prm.T + cl - 1) / cl;  // clusters with at least one tile each
+      const int64_t ncl = std::min<int64_t>(want, nclusters - 1);
+      cfg.gridDim = dim3((unsigned)(ncl * cl), 1, 1);
+      e = cudaLaunchKernelEx(&cfg, kern, tmh, tml, tmq, prm);
+      if (e == cudaSuccess) return cudaSuccess;
+    }
+    cudaGetLastError();  // fall back to a plain grid that leaves reserve_sms SMs idle
+  }
   const int64_t grid = std::min<int64_t>(prm.T, std::max(1, tc::num_sms() - std::max(0, reserve_sms)));
   kern<<<(unsigned)grid, TC_THREADS, smem, st>>>(tmh, tml, tmq, prm);
   return cudaGetLastError();
