@@ -172,15 +172,18 @@ MIXED = [
 
 @pytest.mark.parametrize("name,cfg,tree,extrap,beta,sweeps", MIXED, ids=[c[0] for c in MIXED])
 def test_split_precision_solver_tracks_oracle(name, cfg, tree, extrap, beta, sweeps):
-    """Mixed path (FP32 / split-bf16 TTMs, FP64 QRs): per-sweep fit within 1e-4 and factor
-    subspaces within 1e-4 of the FP64 oracle on the same FP32 tensor."""
+    """Mixed path (split-bf16 TTMs at up to two tree levels, FP64 QRs): per-sweep fit within 1e-4
+    and factor subspaces within 3e-4 of the FP64 oracle on the same FP32 tensor.  Each split level
+    carries ~2^-17 relative operand error; two levels times the conditioning of the Hadamard
+    Grams of congruence-0.5 rank-8 factors (kappa ~ 9) give ~1.4e-4, and the bf16 rounding of
+    the operands makes the exact value jump by ~1e-5 under 1-ulp FP64 changes upstream."""
     cfg = dict(cfg)
     prob = inputs.make_problem(name, cfg.pop("dims"), cfg.pop("R"), seed=4, dtype=np.float32, **cfg)
     fits, A, lam, Q, Rn, st = _run_gpu(prob, tree, extrap, beta, sweeps, prec=b.PREC_SPLIT_BF16)
     ref = _run_oracle(prob, tree, extrap, beta, sweeps)
     assert np.max(np.abs(fits - np.array(ref.fits))) <= 1e-4, (fits, ref.fits)
     for n in range(len(prob.dims)):
-        assert o.subspace_sine(A[n], ref.A[n]) <= 1e-4
+        assert o.subspace_sine(A[n], ref.A[n]) <= 3e-4
 
 
 @pytest.mark.parametrize("dtype", [np.float32, np.float64])
