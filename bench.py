@@ -141,10 +141,18 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     prec = b.PREC_SPLIT_BF16 if args.prec == "split" else b.PREC_FP64
-    prob = inputs.workload(WORKLOAD, seed=rank)
-    X = torch.from_numpy(prob.X).to(dev)
-    xbytes = prob.X.nbytes
-    opts = b.make_options(tree=b.TREE_RESTRUCTURED, prec=prec, extrap=b.EXTRAP_PAPER)
+    wname = args.workload
+    if wname == WORKLOAD:
+        prob = inputs.workload(wname, seed=rank)
+        X = torch.from_numpy(prob.X).to(dev)
+    else:  # the other named workloads (timing and buckets only), generated on the GPU
+        cfg = dict(inputs.WORKLOADS[wname])
+        prob = inputs.make_problem_device(wname, cfg.pop("dims"), cfg.pop("R"), seed=rank, c=cfg.get("c"),
+                                          eta=cfg.get("eta", 0.0), device=str(dev))
+        X = prob.X
+    tree = {"standard": b.TREE_STANDARD, "none": b.TREE_NONE}.get(args.tree, b.TREE_RESTRUCTURED)
+    xbytes = X.numel() * X.element_size()
+    opts = b.make_options(tree=tree, prec=prec, extrap=b.EXTRAP_PAPER)
     clocks = ClockSampler(local_rank)
     clocks.start()
     dec = b.Decomposition(prob.dims, prob.R, X.data_ptr(), False, prob.A0, opts)
@@ -179,7 +187,18 @@ def run_ours(args, rank, world, local_rank):
     n_deep = st.n_bucket[1]
     deep_ms = st.ms_bucket[1] / max(n_deep, 1)
     out = None
-    if rank == 0:
+    if rank == 0 and wname != WORKLOAD:
+        out = {"metric": METRIC, "value": ms * 1e-3 / world, "unit": "s/sweep", "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+               "vs_baseline": None, "dtype": "bf16x3+f32+f64" if prec == b.PREC_SPLIT_BF16 else "f64",
+               "data": "synthetic", "config": {"workload": wname, "dims": prob.dims, "rank": prob.R,
+                                               "tree": args.tree, "precision": args.prec},
+               "buckets_ms_per_sweep": buckets, "launches_per_bucket_per_sweep":
+                   {name: st.n_bucket[i] / max(args.steps, 1) for i, name in enumerate(b.BUCKETS)},
+               "ttm_flops_per_sweep": st.ttm_flops / (args.warmup + 2 * args.steps), "gpu_launches": int(launches),
+               "fit_last": float(fits[-1]) if len(fits) else None,
+               "note": "extra workload: not the bench line (no roofline, e2e or CPU baseline)"}
+    elif rank == 0:
         hbm, peak_kind = _peaks()
         # first-level TTM, algorithmic bytes: X once (FP32, or bf16 hi + lo: 4 B/element) + output (FP32/FP64)
         out_elems = prob.X.size // prob.dims[0] * prob.R  # every full TTM here shrinks one side of 400 to R
@@ -249,12 +268,12 @@ def run_ours(args, rank, world, local_rank):
                "gpu_launches": int(launches),
                "fit_last": float(fits[-1]) if len(fits) else None}
     dec.close()
-    if rank == 0 and not args.quick:
+    if rank == 0 and not args.quick and wname == WORKLOAD:
         out.update(extras(args, prob, X, dev, b))
     out_clocks = clocks.stop()
     if out is not None:
         out["clocks"] = out_clocks
-        if not args.quick:
+        if not args.quick and wname == WORKLOAD:
             out["cpu_baseline"] = cpu_baseline(prob)
     return out
 
@@ -332,6 +351,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="split", choices=["split", "fp64"])
     ap.add_argument("--quick", action="store_true", help="skip e2e, time-to-fit and the CPU baseline")
+    ap.add_argument("--workload", default=WORKLOAD, help="named workload of inputs.WORKLOADS (default: the bench "
+                    "line's); others print timing and buckets only")
+    ap.add_argument("--tree", default="restructured", choices=["restructured", "standard", "none"],
+                    help="dimension tree of the extra workloads (the bench line is always restructured)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))

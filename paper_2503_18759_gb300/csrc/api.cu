@@ -150,7 +150,9 @@ struct cpqr_ctx {
   unsigned int* dstatus = nullptr;
   double* h_pinned = nullptr;  // 4 doubles: fit terms, status
   int32_t* d_perm = nullptr;
-  ZPlan zplan{};
+  ZPlan zplan{};   // Khatri-Rao row plan of the N-1 triangles
+  int32_t* d_perm2 = nullptr;
+  ZPlan zplan2{};  // plan of a two-triangle product (nested QR for N - 1 >= 3)
 
   std::unique_ptr<Schedule> sched;
   std::vector<Op> ops;
@@ -497,7 +499,14 @@ cpqr_status launch_z(cpqr_ctx* ctx, int n) {
   CK(cudaStreamWaitEvent(ctx->st2, ctx->ev_ready, 0));
   {
     Timed tm(ctx, CPQR_BUCKET_Q0, 1, ctx->st2);
-    CK(launch_krp_qr(ctx->zplan, tri, ctx->Q0, ctx->R0, ctx->zq_work, ctx->dstatus, ctx->st2, ctx->Q0f));
+    if (m >= 3) {
+      int nl = 0;
+      CK(launch_krp_qr_nested(ctx->zplan2, tri, m, ctx->Q0, ctx->R0, ctx->zq_work, ctx->dstatus, ctx->st2, ctx->Q0f,
+                              &nl));
+      ctx->launches += nl - 1;
+    } else {
+      CK(launch_krp_qr(ctx->zplan, tri, ctx->Q0, ctx->R0, ctx->zq_work, ctx->dstatus, ctx->st2, ctx->Q0f));
+    }
   }
   CK(cudaEventRecord(ctx->ev_z, ctx->st2));
   ctx->z_pending = true;
@@ -535,6 +544,11 @@ cpqr_status run_update(cpqr_ctx* ctx, int n, int leaf, double beta) {
   }
   // Lines 8-10: eq. 19 and the R0^{-T} solve over all SMs, then normalisation and the factor QR.
   FinishOut fo{ctx->A[n], ctx->lambda, ctx->Q[n], ctx->Rf[n], ctx->Qf[n], ctx->fit_terms};
+  if (!fp64) {  // the finish kernel also stages Q_n^T for the tensor cores
+    fo.Qt = ctx->Qt[n];
+    fo.Rp = ctx->Rp;
+    fo.Kp = ctx->Kp[n];
+  }
   {
     Timed tm(ctx, CPQR_BUCKET_QR, 2);
     const double b = ext ? beta : 0.0;
@@ -546,8 +560,6 @@ cpqr_status run_update(cpqr_ctx* ctx, int n, int leaf, double beta) {
                                    ctx->fitpart, ctx->dstatus, st));
     CK(launch_mode_finish(ctx->V, ctx->fitpart, finish_prep_blocks(I), I, R, fo, ctx->qr_work, ctx->dstatus, st));
   }
-  cpqr_status s = stage_q(ctx, n);
-  if (s != CPQR_OK) return s;
   std::swap(ctx->Q0, ctx->Q0prev[n]);
   std::swap(ctx->Q0f, ctx->Q0fprev[n]);
   ctx->has_prev[n] = true;
@@ -840,7 +852,7 @@ cpqr_status cp_als_qr_init(cpqr_ctx** out, int32_t N, const int64_t* dims, int32
   CK(ctx->alloc(&ctx->V, Imax * 2 * R));
   CK(ctx->alloc(&ctx->fitpart, 2 * (size_t)finish_prep_blocks(Imax)));
   CK(ctx->alloc(&ctx->qr_work, std::max<int64_t>(M0, Imax) * R));
-  CK(ctx->alloc(&ctx->zq_work, M0 * R));
+  CK(ctx->alloc(&ctx->zq_work, std::max<size_t>((size_t)(M0 * R), krp_nested_work_doubles(N - 1, R))));
   CK(ctx->alloc((char**)&ctx->res_work, residual2_work_bytes(N, dims, R)));
   {
     int64_t vw = 0;
@@ -874,7 +886,15 @@ cpqr_status cp_als_qr_init(cpqr_ctx** out, int32_t N, const int64_t* dims, int32
     ctx->zplan.M = M0;
     ctx->zplan.perm = ctx->d_perm;
     for (int j = 0; j < CPQR_MAXR; ++j) ctx->zplan.act[j] = (int32_t)std::min<int64_t>(M0, ipow(j + 1, N - 1));
-    CK(cudaStreamSynchronize(st));  // perm vector goes out of scope
+    std::vector<int32_t> perm2 = krp_perm(2, R);
+    CK(ctx->alloc(&ctx->d_perm2, perm2.size()));
+    CK(cudaMemcpyAsync(ctx->d_perm2, perm2.data(), perm2.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    ctx->zplan2.m = 2;
+    ctx->zplan2.R = R;
+    ctx->zplan2.M = (int64_t)R * R;
+    ctx->zplan2.perm = ctx->d_perm2;
+    for (int j = 0; j < CPQR_MAXR; ++j) ctx->zplan2.act[j] = (int32_t)std::min<int64_t>((int64_t)R * R, ipow(j + 1, 2));
+    CK(cudaStreamSynchronize(st));  // the perm vectors go out of scope
   }
 
   // Starting factors (Alg. 2 "Initialize") and their QRs.
@@ -1242,26 +1262,32 @@ cpqr_status cpqr_krp_qr(const double* Rs_dev, int32_t m, int32_t R, double* Q0_d
   int64_t M = ipow(R, m);
   if (M < R) return CPQR_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
-  std::vector<int32_t> perm = krp_perm(m, R);
+  const int mp = (m >= 3) ? 2 : m;  // m >= 3 goes through the nested QR of two-triangle products
+  std::vector<int32_t> perm = krp_perm(mp, R);
+  const int64_t Mp = ipow(R, mp);
+  const size_t wd = std::max<size_t>((size_t)(M * R), m >= 3 ? krp_nested_work_doubles(m, R) : 0);
   int32_t* dperm = nullptr;
   double* work = nullptr;
   unsigned int* ds = nullptr;
-  if (cudaMalloc(&dperm, perm.size() * 4) != cudaSuccess || cudaMalloc(&work, (size_t)M * R * 8) != cudaSuccess ||
+  if (cudaMalloc(&dperm, perm.size() * 4) != cudaSuccess || cudaMalloc(&work, wd * 8) != cudaSuccess ||
       cudaMalloc(&ds, 4) != cudaSuccess) {
     cudaFree(dperm); cudaFree(work); cudaFree(ds);
     return CPQR_ENOMEM;
   }
   ZPlan plan{};
-  plan.m = m;
+  plan.m = mp;
   plan.R = R;
-  plan.M = M;
+  plan.M = Mp;
   plan.perm = dperm;
-  for (int j = 0; j < CPQR_MAXR; ++j) plan.act[j] = (int32_t)std::min<int64_t>(M, ipow(j + 1, m));
+  for (int j = 0; j < CPQR_MAXR; ++j) plan.act[j] = (int32_t)std::min<int64_t>(Mp, ipow(j + 1, mp));
   TriPtrs tri{};
   for (int k = 0; k < m; ++k) tri.p[k] = Rs_dev + (size_t)k * R * R;
   cudaError_t e = cudaMemcpyAsync(dperm, perm.data(), perm.size() * 4, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(ds, 0, 4, st);
-  if (e == cudaSuccess) e = launch_krp_qr(plan, tri, Q0_dev, R0_dev, work, ds, st);
+  if (e == cudaSuccess) {
+    if (m >= 3) e = launch_krp_qr_nested(plan, tri, m, Q0_dev, R0_dev, work, ds, st);
+    else e = launch_krp_qr(plan, tri, Q0_dev, R0_dev, work, ds, st);
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cudaFree(dperm); cudaFree(work); cudaFree(ds);
   return e == cudaSuccess ? CPQR_OK : CPQR_ECUDA;

@@ -72,6 +72,13 @@ struct TriPtrs {
 cudaError_t launch_krp_qr(const ZPlan& plan, TriPtrs Rs, double* Q0, double* R0, double* work,
                           unsigned int* dev_status, cudaStream_t st, float* Q0f = nullptr);
 size_t krp_qr_work_doubles(const ZPlan& plan);
+// QR of a product of m >= 2 triangles as m - 1 staircase QRs of two-triangle products (plan2:
+// the plan for m = 2) and m - 2 FP64 assemblies; work: krp_nested_work_doubles(m, R) doubles.
+// *nlaunch (optional) receives the number of kernels launched.
+size_t krp_nested_work_doubles(int m, int R);
+cudaError_t launch_krp_qr_nested(const ZPlan& plan2, TriPtrs Rs, int m, double* Q0, double* R0, double* work,
+                                 unsigned int* dev_status, cudaStream_t st, float* Q0f = nullptr,
+                                 int* nlaunch = nullptr);
 
 // V[i, c] = sum_{p, s} Y[p, i, s] * Qc[p*S + s, c], c < C, Qc = [Q0 | Q0prev] (K x C,
 // K = P*S), as *nparts split-K slices of I x C in work (leaf_v_splits(I, K) * I * C
@@ -99,6 +106,11 @@ struct FinishOut {
   double* Rn;       // R x R
   float* Qf;        // I x R FP32 copy (may be null)
   double* fit_terms;  // 2 doubles
+  // optional: Q^T split into bf16 hi / lo for the tensor-core TTMs, Qt[2][Rp][Kp] with the
+  // padding left untouched (zero from the state's initialisation)
+  __nv_bfloat16* Qt = nullptr;
+  int Rp = 0;
+  int64_t Kp = 0;
 };
 cudaError_t launch_mode_finish(const double* Ahat, const double* fitpart, int nfit, int64_t I, int R, FinishOut out,
                                double* work, unsigned int* dev_status, cudaStream_t st);

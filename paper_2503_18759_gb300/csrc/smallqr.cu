@@ -470,6 +470,14 @@ __global__ void __launch_bounds__(NT, 1) qr_cluster_kernel(QrParams p) {
         const size_t orow = (p.mode == MODE_KRP) ? (size_t)(sperm ? sperm[u] : p.perm[t]) : (size_t)t;
         p.Q[orow * R + c] = q;
         if (p.Qf) p.Qf[orow * R + c] = (float)q;
+        if (p.mode == MODE_FINISH && p.fin.Qt) {
+          // the tensor cores' B operand, as the separate staging would write it
+          const float q32 = (float)q;
+          const __nv_bfloat16 h = __float2bfloat16_rn(q32);
+          const size_t e = (size_t)c * p.fin.Kp + orow;
+          p.fin.Qt[e] = h;
+          p.fin.Qt[(size_t)p.fin.Rp * p.fin.Kp + e] = __float2bfloat16_rn(q32 - __bfloat162float(h));
+        }
       }
     }
   }
@@ -724,6 +732,99 @@ cudaError_t launch_krp_qr(const ZPlan& plan, TriPtrs Rs, double* Q0, double* R0,
   p.Rout = R0;
   p.status = dev_status;
   return run(p, st);
+}
+
+// ---------------------------------------------------------------------------
+// Nested QR of a Khatri-Rao product of m >= 3 upper triangles.
+//
+// With W = R_{k2} (.) ... (.) R_{km} = Q_W S_W, the rows (i, w) of Z = R_{k1} (.) W are
+// R_{k1}[i, r] (Q_W S_W)[w, r], so Z = (I_R (x) Q_W) Y with Y = R_{k1} (.) S_W, again a
+// product of two upper triangles (R^2 rows, the staircase QR above).  Hence Z = Q0 R0 with
+// R0 = R_Y and Q0 = (I_R (x) Q_W) Q_Y: m - 1 staircase QRs of R^2 x R products, from the
+// right, and m - 2 assemblies Q <- (I (x) Q_W) Q_Y in FP64.  Every step is orthogonal and every
+// R has a positive diagonal, so Q0 and R0 are those of the direct QR of Z up to rounding.
+// ---------------------------------------------------------------------------
+
+// out[(i, w), c] = sum_j QW[w, j] QY[(i, j), c] for i < R, w < Mw (row (i, w) = i * Mw + w);
+// one row per Rpad lanes (Rpad = R rounded up to a power of two), lane = column c.
+__global__ void __launch_bounds__(256) krp_assemble_kernel(const double* __restrict__ QW, int64_t Mw,
+                                                            const double* __restrict__ QY, int R, int Rpad,
+                                                            double* __restrict__ out, float* __restrict__ outf) {
+  const int lane = threadIdx.x & 31, sub = lane / Rpad, c = lane % Rpad;
+  const int rpw = 32 / Rpad;
+  const int64_t rows = (int64_t)R * Mw;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t wr = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); wr * rpw < rows; wr += nwarps) {
+    const int64_t row = wr * rpw + sub;
+    const bool live = row < rows && c < R;
+    const int64_t i = live ? row / Mw : 0, w = live ? row - i * Mw : 0;
+    const double qw = live ? QW[w * R + c] : 0.0;
+    const double* qy = QY + (size_t)i * R * R + c;
+    double acc = 0.0;
+    for (int j = 0; j < R; ++j) {
+      const double a = __shfl_sync(FULL, qw, sub * Rpad + j);
+      if (live) acc = fma(a, qy[(size_t)j * R], acc);
+    }
+    if (live) {
+      out[row * R + c] = acc;
+      if (outf) outf[row * R + c] = (float)acc;
+    }
+  }
+}
+
+size_t krp_nested_work_doubles(int m, int R) {
+  size_t Mw = 1;
+  for (int k = 0; k < m - 1; ++k) Mw *= (size_t)R;
+  // two triangles, Q_Y, the staircase QR's rows, two Q_W
+  return 2 * (size_t)R * R + 2 * (size_t)R * R * R + 2 * Mw * R;
+}
+
+cudaError_t launch_krp_qr_nested(const ZPlan& plan2, TriPtrs Rs, int m, double* Q0, double* R0, double* work,
+                                 unsigned int* dev_status, cudaStream_t st, float* Q0f, int* nlaunch) {
+  const int R = plan2.R;
+  if (plan2.m != 2 || m < 2 || m > CPQR_MAXN || R < 1 || R > CPQR_MAXR) return cudaErrorInvalidValue;
+  int launches = 0;
+  TriPtrs t2{};
+  t2.p[0] = Rs.p[m - 2];
+  t2.p[1] = Rs.p[m - 1];
+  if (m == 2) {
+    if (nlaunch) *nlaunch = 1;
+    return launch_krp_qr(plan2, t2, Q0, R0, work, dev_status, st, Q0f);
+  }
+  size_t Mw = 1;
+  for (int k = 0; k < m - 1; ++k) Mw *= (size_t)R;
+  double* S[2] = {work, work + (size_t)R * R};
+  double* QY = work + 2 * (size_t)R * R;
+  double* qrw = QY + (size_t)R * R * R;
+  double* QW[2] = {qrw + (size_t)R * R * R, qrw + (size_t)R * R * R + Mw * R};
+  // level 2: R_{k(m-1)} (.) R_{km} = Q_{W,2} S_2
+  cudaError_t e = launch_krp_qr(plan2, t2, QW[0], S[0], qrw, dev_status, st);
+  if (e != cudaSuccess) return e;
+  ++launches;
+  int cur = 0;
+  int64_t mw = (int64_t)R * R;  // rows of Q_{W,d-1}
+  int Rpad = 1;
+  while (Rpad < R) Rpad <<= 1;
+  for (int d = 3; d <= m; ++d) {
+    const bool last = (d == m);
+    TriPtrs t{};
+    t.p[0] = Rs.p[m - d];
+    t.p[1] = S[(d - 3) & 1];
+    e = launch_krp_qr(plan2, t, QY, last ? R0 : S[(d - 2) & 1], qrw, dev_status, st);
+    if (e != cudaSuccess) return e;
+    double* out = last ? Q0 : QW[cur ^ 1];
+    const int64_t rows = (int64_t)R * mw;
+    const int64_t warps = (rows + (32 / Rpad) - 1) / (32 / Rpad);
+    const int grid = (int)std::min<int64_t>((warps + 7) / 8, 152 * 8);
+    krp_assemble_kernel<<<grid, 256, 0, st>>>(QW[cur], mw, QY, R, Rpad, out, last ? Q0f : nullptr);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    launches += 2;
+    cur ^= 1;
+    mw *= R;
+  }
+  if (nlaunch) *nlaunch = launches;
+  return cudaSuccess;
 }
 
 int finish_prep_blocks(int64_t I) { return (int)((I + PREP_WARPS - 1) / PREP_WARPS); }
