@@ -107,6 +107,15 @@ struct cpqr_ctx {
   cudaStream_t st2 = nullptr;      // side stream: Khatri-Rao QR overlapped with the TTM chain
   cudaEvent_t ev_ready = nullptr;  // main stream: triangles R_k of the previous update ready
   cudaEvent_t ev_z = nullptr;      // side stream: Q0, R0 of the upcoming update ready
+  // Lagged fit (split path, once nothing in the next sweep depends on the fit): the explicit
+  // residual of sweep k runs on st3 beside the first factor QR of sweep k + 1 and is read one
+  // sweep later.
+  cudaStream_t st3 = nullptr;
+  cudaEvent_t ev_prep = nullptr;   // main stream: a mode's finish is about to start
+  cudaEvent_t ev_fit = nullptr;    // st3: lagged residual read back
+  bool lag_ok = false;             // set by the sweep loops that need no fit before the next sweep
+  bool resid_pending = false;      // snapshot of the factors taken, residual not launched yet
+  bool resid_inflight = false;     // residual launched, fit not read yet
   bool z_pending = false;
   int z_mode = -1;
   const void* X = nullptr;
@@ -179,7 +188,11 @@ struct cpqr_ctx {
   ~cpqr_ctx() {
     if (st) cudaStreamSynchronize(st);
     if (st2) cudaStreamSynchronize(st2);
+    if (st3) cudaStreamSynchronize(st3);
     for (cudaEvent_t e : evpool) cudaEventDestroy(e);
+    if (ev_prep) cudaEventDestroy(ev_prep);
+    if (ev_fit) cudaEventDestroy(ev_fit);
+    if (st3) cudaStreamDestroy(st3);
     for (Checkpoint& c : ckpt)
       if (c.arena) cudaFree(c.arena);
     if (ev_ready) cudaEventDestroy(ev_ready);
@@ -514,6 +527,8 @@ cpqr_status launch_z(cpqr_ctx* ctx, int n) {
   return CPQR_OK;
 }
 
+cpqr_status launch_lagged_residual(cpqr_ctx* ctx);
+
 cpqr_status run_update(cpqr_ctx* ctx, int n, int leaf, double beta) {
   auto it = ctx->nodes.find(leaf);
   if (it == ctx->nodes.end()) return fail(ctx, CPQR_EINVAL);
@@ -558,11 +573,84 @@ cpqr_status run_update(cpqr_ctx* ctx, int n, int leaf, double beta) {
     else
       CK(launch_finish_prep<float>((const float*)ctx->v_work, nparts, I, C, R, ctx->R0, b, ctx->alpha, ctx->V,
                                    ctx->fitpart, ctx->dstatus, st));
+    if (ctx->resid_pending) {
+      // the previous sweep's residual runs beside this factor QR (one GPC busy, the rest idle)
+      CK(cudaEventRecord(ctx->ev_prep, st));
+      cpqr_status s = launch_lagged_residual(ctx);
+      if (s != CPQR_OK) return s;
+    }
     CK(launch_mode_finish(ctx->V, ctx->fitpart, finish_prep_blocks(I), I, R, fo, ctx->qr_work, ctx->dstatus, st));
   }
   std::swap(ctx->Q0, ctx->Q0prev[n]);
   std::swap(ctx->Q0f, ctx->Q0fprev[n]);
   ctx->has_prev[n] = true;
+  return CPQR_OK;
+}
+
+double fit_from_r2(const cpqr_ctx* ctx, double r2) {
+  return 1.0 - std::sqrt(std::max(r2, 0.0)) / std::sqrt(ctx->normX2);
+}
+
+// Whether the fit of the current sweep may be read one sweep late: split path with the tensor-
+// core residual, and a beta for the following sweeps that no longer depends on the fit.
+bool can_lag(const cpqr_ctx* ctx) {
+  if (!ctx->lag_ok || ctx->prec != CPQR_PREC_SPLIT_BF16 || ctx->x64) return false;
+  if (!residual_tc_supported(ctx->N, ctx->dims.data(), ctx->R, ctx->X)) return false;
+  if (ctx->extrap == CPQR_EXTRAP_LEARNED) return false;
+  if (ctx->extrap == CPQR_EXTRAP_PAPER && !ctx->activated) return false;
+  return true;
+}
+
+// The residual of the snapshot in res_work on st3, after ev_prep (recorded on st after the
+// snapshot), on the GPCs the factor QR leaves free; its value goes to h_pinned[4].
+cpqr_status launch_lagged_residual(cpqr_ctx* ctx) {
+  CK(cudaStreamWaitEvent(ctx->st3, ctx->ev_prep, 0));
+  {
+    Timed tm(ctx, CPQR_BUCKET_FIT, 1, ctx->st3);
+    const double* A[CPQR_MAXN];
+    for (int n = 0; n < ctx->N; ++n) A[n] = ctx->A[n];
+    CK(launch_residual2<float>((const float*)ctx->X, ctx->N, ctx->dims.data(), A, ctx->lambda, ctx->R,
+                               ctx->d_scalar + 1, ctx->res_work, ctx->dstatus, ctx->st3, RESIDUAL_EVALUATE,
+                               qr_cluster_sms()));
+  }
+  CK(cudaMemcpyAsync(ctx->h_pinned + 4, ctx->d_scalar + 1, sizeof(double), cudaMemcpyDeviceToHost, ctx->st3));
+  CK(cudaEventRecord(ctx->ev_fit, ctx->st3));
+  ctx->resid_pending = false;
+  ctx->resid_inflight = true;
+  return CPQR_OK;
+}
+
+void observe_fit(cpqr_ctx* ctx, double fit);
+
+// Reads the lagged fit once its residual has finished and records it.
+cpqr_status collect_lagged_fit(cpqr_ctx* ctx) {
+  if (!ctx->resid_inflight) return CPQR_OK;
+  CK(cudaEventSynchronize(ctx->ev_fit));
+  ctx->resid_inflight = false;
+  const double f = fit_from_r2(ctx, ctx->h_pinned[4]);
+  if (!std::isfinite(f)) return fail(ctx, CPQR_ENONFINITE);
+  observe_fit(ctx, f);
+  return CPQR_OK;
+}
+
+// Completes every lagged fit, checks the device status and collects the timing events.
+cpqr_status flush_lag(cpqr_ctx* ctx) {
+  if (!ctx->resid_pending && !ctx->resid_inflight) return CPQR_OK;
+  if (ctx->resid_pending) {
+    CK(cudaEventRecord(ctx->ev_prep, ctx->st));
+    cpqr_status s = launch_lagged_residual(ctx);
+    if (s != CPQR_OK) return s;
+  }
+  cpqr_status s = collect_lagged_fit(ctx);
+  if (s != CPQR_OK) return s;
+  CK(cudaMemcpyAsync(ctx->h_pinned + 2, ctx->dstatus, sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  CK(cudaStreamSynchronize(ctx->st2));
+  if (ctx->timing) collect_timing(ctx);
+  unsigned int ds;
+  std::memcpy(&ds, ctx->h_pinned + 2, sizeof(ds));
+  if (ds & CPQR_DEV_TIMEOUT) return fail(ctx, CPQR_ETIMEOUT);
+  if (ds & CPQR_DEV_SINGULAR) return fail(ctx, CPQR_ESINGULAR);
   return CPQR_OK;
 }
 
@@ -594,7 +682,7 @@ cpqr_status read_fit(cpqr_ctx* ctx, double* fit) {
   if (ds & CPQR_DEV_SINGULAR) return fail(ctx, CPQR_ESINGULAR);
   double in = ctx->h_pinned[0], nn = ctx->h_pinned[1];
   double r2 = explicit_fit ? ctx->h_pinned[3] : ctx->normX2 - 2.0 * in + nn;
-  double f = 1.0 - std::sqrt(std::max(r2, 0.0)) / std::sqrt(ctx->normX2);
+  double f = fit_from_r2(ctx, r2);
   if (!std::isfinite(f)) return fail(ctx, CPQR_ENONFINITE);
   *fit = f;
   return CPQR_OK;
@@ -620,6 +708,11 @@ void observe_fit(cpqr_ctx* ctx, double fit) {
 
 cpqr_status one_sweep(cpqr_ctx* ctx, double* fit_out, const double* forced_beta = nullptr) {
   const double beta = forced_beta ? *forced_beta : beta_for_sweep(ctx);
+  const bool lag = !forced_beta && can_lag(ctx);
+  if (!lag) {
+    cpqr_status s = flush_lag(ctx);
+    if (s != CPQR_OK) return s;
+  }
   ctx->ops.clear();
   try {
     ctx->sched->next_sweep(ctx->ops);
@@ -642,6 +735,26 @@ cpqr_status one_sweep(cpqr_ctx* ctx, double* fit_out, const double* forced_beta 
     else if (op.kind == OP_UPDATE) s = run_update(ctx, op.a, op.b, beta);
     else free_node(ctx, op.a);
     if (s != CPQR_OK) return s;
+  }
+  if (lag) {
+    // snapshot of this sweep's factors for its residual (launched during the next sweep); the
+    // previous residual reads the same buffer, so the snapshot waits for it
+    if (ctx->resid_inflight) CK(cudaStreamWaitEvent(ctx->st, ctx->ev_fit, 0));
+    {
+      Timed tm(ctx, CPQR_BUCKET_OTHER, 1);
+      const double* A[CPQR_MAXN];
+      for (int n = 0; n < ctx->N; ++n) A[n] = ctx->A[n];
+      CK(launch_residual2<float>((const float*)ctx->X, ctx->N, ctx->dims.data(), A, ctx->lambda, ctx->R,
+                                 ctx->d_scalar + 1, ctx->res_work, ctx->dstatus, ctx->st, RESIDUAL_SNAPSHOT));
+    }
+    ctx->last_beta = beta;
+    ++ctx->sweeps;
+    ctx->betas.push_back(beta);
+    cpqr_status s = collect_lagged_fit(ctx);  // the previous sweep's
+    if (s != CPQR_OK) return s;
+    ctx->resid_pending = true;
+    if (fit_out) *fit_out = NAN;
+    return CPQR_OK;
   }
   double fit = 0.0;
   cpqr_status s = read_fit(ctx, &fit);
@@ -807,7 +920,7 @@ cpqr_status cp_als_qr_init(cpqr_ctx** out, int32_t N, const int64_t* dims, int32
   const int64_t M0 = ipow(R, N - 1);
   int64_t Imax = 0;
   for (int n = 0; n < N; ++n) Imax = std::max(Imax, dims[n]);
-  CK(cudaMallocHost(&ctx->h_pinned, 4 * sizeof(double)));
+  CK(cudaMallocHost(&ctx->h_pinned, 8 * sizeof(double)));
   // Per-mode state lives in one arena so that a checkpoint is a single copy.
   const bool split = opt.prec == CPQR_PREC_SPLIT_BF16;
   ctx->Rp = ((R + 15) / 16) * 16;
@@ -866,7 +979,10 @@ cpqr_status cp_als_qr_init(cpqr_ctx** out, int32_t N, const int64_t* dims, int32
     int least = 0, greatest = 0;
     CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
     CK(cudaStreamCreateWithPriority(&ctx->st2, cudaStreamNonBlocking, greatest));
+    CK(cudaStreamCreateWithPriority(&ctx->st3, cudaStreamNonBlocking, least));
   }
+  CK(cudaEventCreateWithFlags(&ctx->ev_prep, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&ctx->ev_fit, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&ctx->ev_ready, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&ctx->ev_z, cudaEventDisableTiming));
   CK(ctx->alloc(&ctx->fit_terms, 2));
@@ -963,12 +1079,16 @@ cpqr_status cp_als_qr_sweep(cpqr_ctx* ctx, int32_t nsweeps, double* fits_host) {
   if (!ctx) return CPQR_EINVAL;
   if (ctx->err != CPQR_OK) return ctx->err;
   if (nsweeps < 0) return CPQR_EINVAL;
-  for (int i = 0; i < nsweeps; ++i) {
-    double f = 0.0;
-    cpqr_status s = next_sweep(ctx, &f);
-    if (s != CPQR_OK) return s;
-    if (fits_host) fits_host[i] = f;
-  }
+  // no decision between these sweeps needs a fit once beta is fixed: fits may come one sweep late
+  ctx->lag_ok = true;
+  cpqr_status s = CPQR_OK;
+  for (int i = 0; i < nsweeps && s == CPQR_OK; ++i) s = next_sweep(ctx, nullptr);
+  ctx->lag_ok = false;
+  if (s != CPQR_OK) return s;
+  s = flush_lag(ctx);
+  if (s != CPQR_OK) return s;
+  if (fits_host)
+    for (int i = 0; i < nsweeps; ++i) fits_host[i] = ctx->fits[ctx->fits.size() - nsweeps + i];
   return CPQR_OK;
 }
 
@@ -976,6 +1096,17 @@ cpqr_status cp_als_qr_fit(cpqr_ctx* ctx, double tol, int32_t max_sweeps, double*
   if (!ctx) return CPQR_EINVAL;
   if (ctx->err != CPQR_OK) return ctx->err;
   if (max_sweeps < 0) return CPQR_EINVAL;
+  if (!(tol > 0.0)) {  // no stopping test: every sweep runs, fits may come one sweep late
+    cpqr_status s = cp_als_qr_sweep(ctx, max_sweeps, nullptr);
+    if (s != CPQR_OK) return s;
+    if (final_fit) *final_fit = ctx->fits.empty() ? NAN : ctx->fits.back();
+    if (sweeps_done) *sweeps_done = max_sweeps;
+    return max_sweeps == 0 ? CPQR_OK : CPQR_ENOTCONV;
+  }
+  {
+    cpqr_status s = flush_lag(ctx);
+    if (s != CPQR_OK) return s;
+  }
   double prev = NAN, f = NAN;
   int done = 0;
   bool conv = false;

@@ -123,18 +123,22 @@ cudaError_t launch_norm2(const TX* X, int64_t n, double* out, double* work, cuda
 // device pointers; work: device scratch of residual2_work_bytes(N, d, R).  FP32 tensors whose
 // last dimension is a multiple of 4 go to the tensor-core kernel (residual_tc.cu), the rest to
 // a CUDA-core kernel.  dev_status collects CPQR_DEV_TIMEOUT of the tensor-core kernel.
+// parts: RESIDUAL_SNAPSHOT converts the factors (FP32, lambda folded) into work;
+// RESIDUAL_EVALUATE computes the residual from the snapshot in work (the two may run on
+// different streams, the snapshot first).  reserve_sms: SMs of one cluster QR to leave free.
 size_t residual2_work_bytes(int N, const int64_t* d, int R);
+constexpr int RESIDUAL_SNAPSHOT = 1, RESIDUAL_EVALUATE = 2;
 template <typename TX>
 cudaError_t launch_residual2(const TX* X, int N, const int64_t* d, const double* const* A,
                              const double* lambda, int R, double* out, double* work, unsigned int* dev_status,
-                             cudaStream_t st);
+                             cudaStream_t st, int parts = RESIDUAL_SNAPSHOT | RESIDUAL_EVALUATE, int reserve_sms = 0);
 
 // ----- tensor-core explicit residual (residual_tc.cu) -----
 // Af: host array of N device pointers to the FP32 factors (lambda folded into Af[0], Af[N-1]
 // stored transposed, R x I_last); accumulates ||X - K||^2 into *out (not cleared).
 bool residual_tc_supported(int N, const int64_t* d, int R, const void* X);
 cudaError_t launch_residual_tc(const float* X, int N, const int64_t* d, const float* const* Af, int R, double* out,
-                               unsigned int* dev_status, cudaStream_t st);
+                               unsigned int* dev_status, cudaStream_t st, int reserve_sms = 0);
 
 cudaError_t launch_to_f32(const double* a, float* b, int64_t n, cudaStream_t st);
 

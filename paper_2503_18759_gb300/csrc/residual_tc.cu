@@ -96,6 +96,7 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
   const int Il = p.d[p.N - 1];
   const int cg = blockIdx.x / p.cpg, kq = blockIdx.x % p.cpg;
   const int c0 = cg * p.gw;
+  if (c0 >= Il) return;  // padding CTA of a clustered launch: no column group
   const int width = min(p.gw, Il - c0);
   const int t0 = (int)((int64_t)p.rtiles * kq / p.cpg), t1 = (int)((int64_t)p.rtiles * (kq + 1) / p.cpg);
   const int ntl = t1 - t0;
@@ -341,7 +342,7 @@ size_t residual_tc_smem_bytes(int ncp) {
 }
 
 cudaError_t launch_residual_tc(const float* X, int N, const int64_t* d, const float* const* Af, int R, double* out,
-                               unsigned int* dev_status, cudaStream_t st) {
+                               unsigned int* dev_status, cudaStream_t st, int reserve_sms) {
   if (!residual_tc_supported(N, d, R, X)) return cudaErrorNotSupported;
   tc::EncodeTiledFn enc = tc::encode_tiled_fn();
   if (!enc) return cudaErrorNotSupported;
@@ -382,6 +383,36 @@ cudaError_t launch_residual_tc(const float* X, int N, const int64_t* d, const fl
                                          (int)residual_tc_smem_bytes(RT_MAXW));
     if (e != cudaSuccess) return e;
     smem_set = residual_tc_smem_bytes(RT_MAXW);
+  }
+  if (reserve_sms > 0) {
+    // Beside a cluster QR (reserve_sms CTAs in one GPC): clusters of the same size, one fewer than
+    // fit, leave a GPC free for it (the CTAs never synchronise as a cluster).  CTAs past
+    // ncg * cpg have no work and return at once.
+    const int cl = reserve_sms;
+    cudaError_t e = cudaFuncSetAttribute(residual_tc_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(RT_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3((unsigned)cl, 1, 1);
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, residual_tc_kernel, &cfg) == cudaSuccess && nclusters >= 2) {
+      const int ctas = (nclusters - 1) * cl;
+      p.cpg = std::max(1, std::min(p.rtiles, ctas / ncg));
+      cfg.gridDim = dim3((unsigned)ctas, 1, 1);
+      e = cudaLaunchKernelEx(&cfg, residual_tc_kernel, tm, p);
+      if (e == cudaSuccess) return cudaSuccess;
+    }
+    cudaGetLastError();
+    p.cpg = std::max(1, std::min(p.rtiles, (tc::num_sms() - reserve_sms) / ncg));
   }
   residual_tc_kernel<<<(unsigned)(ncg * p.cpg), RT_THREADS, smem, st>>>(tm, p);
   return cudaGetLastError();

@@ -644,7 +644,8 @@ size_t residual2_work_bytes(int N, const int64_t* d, int R) {
 
 template <typename TX>
 cudaError_t launch_residual2(const TX* X, int N, const int64_t* d, const double* const* A, const double* lambda,
-                             int R, double* out, double* work, unsigned int* dev_status, cudaStream_t st) {
+                             int R, double* out, double* work, unsigned int* dev_status, cudaStream_t st, int parts,
+                             int reserve_sms) {
   // work: >= sum_n d[n] * R floats + N pointers (device)
   ResParams rp{};
   rp.N = N;
@@ -664,14 +665,20 @@ cudaError_t launch_residual2(const TX* X, int N, const int64_t* d, const double*
     rp.A[n] = f32 + off;
     off += d[n] * R;
   }
-  cudaError_t e = cudaMemcpyAsync(ptrs, A, N * sizeof(double*), cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return e;
-  factors_to_f32_kernel<<<(int)std::min<int64_t>((total + 255) / 256, 512), 256, 0, st>>>(rp, ptrs, lambda, f32,
-                                                                                         (int)total);
+  cudaError_t e = cudaSuccess;
+  if (parts & RESIDUAL_SNAPSHOT) {
+    e = cudaMemcpyAsync(ptrs, A, N * sizeof(double*), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    factors_to_f32_kernel<<<(int)std::min<int64_t>((total + 255) / 256, 512), 256, 0, st>>>(rp, ptrs, lambda, f32,
+                                                                                           (int)total);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (!(parts & RESIDUAL_EVALUATE)) return cudaSuccess;
   e = cudaMemsetAsync(out, 0, sizeof(double), st);
   if (e != cudaSuccess) return e;
   if (std::is_same<TX, float>::value && residual_tc_supported(N, d, R, X)) {
-    e = launch_residual_tc(reinterpret_cast<const float*>(X), N, d, rp.A, R, out, dev_status, st);
+    e = launch_residual_tc(reinterpret_cast<const float*>(X), N, d, rp.A, R, out, dev_status, st, reserve_sms);
     if (e != cudaErrorNotSupported) return e;
   }
   // contiguous ranges of (row tile, column chunk) items, two CTAs per SM
@@ -681,9 +688,10 @@ cudaError_t launch_residual2(const TX* X, int N, const int64_t* d, const double*
   return cudaGetLastError();
 }
 template cudaError_t launch_residual2<float>(const float*, int, const int64_t*, const double* const*, const double*,
-                                             int, double*, double*, unsigned int*, cudaStream_t);
+                                             int, double*, double*, unsigned int*, cudaStream_t, int, int);
 template cudaError_t launch_residual2<double>(const double*, int, const int64_t*, const double* const*,
-                                              const double*, int, double*, double*, unsigned int*, cudaStream_t);
+                                              const double*, int, double*, double*, unsigned int*, cudaStream_t, int,
+                                              int);
 
 cudaError_t launch_to_f32(const double* a, float* b, int64_t n, cudaStream_t st) {
   to_f32_kernel<<<grid_for(n, 256 * 4), 256, 0, st>>>(a, b, n);

@@ -215,3 +215,28 @@ def test_fit_exact_tensor_core_residual(dims, R):
         fx = d.fit_exact()
     ref = o.fit_explicit(prob.X, lam, A)
     assert abs(fx - ref) <= 1e-8
+
+
+@pytest.mark.parametrize("extrap,beta", [(b.EXTRAP_PAPER, 0.0), (b.EXTRAP_FIXED, 0.01), (b.EXTRAP_NONE, 0.0)])
+def test_lagged_fit_equals_sweep_by_sweep_fit(extrap, beta):
+    """Split path: cp_als_qr_sweep reads the explicit-residual fit of a sweep one sweep late once
+    beta no longer depends on the fit (the residual runs beside the next sweep's first factor
+    QR).  Fits, betas and factors equal those of sweep-by-sweep reads (cp_als_qr_sweep(1) per
+    sweep), up to the summation order of the residual's CTA partials."""
+    prob = inputs.make_problem("lag", [48, 40, 56], 8, seed=9, c=0.6, eta=1e-3, dtype=np.float32)
+    X = _dev(prob.X)
+    opts = b.make_options(tree=b.TREE_RESTRUCTURED, prec=b.PREC_SPLIT_BF16, extrap=extrap, beta_fixed=beta)
+    with b.Decomposition(prob.dims, prob.R, X.data_ptr(), False, prob.A0, opts) as d:
+        f_many = d.sweep(12)
+        A1, lam1, _, _ = d.factors()
+        h1 = d.history()
+    with b.Decomposition(prob.dims, prob.R, X.data_ptr(), False, prob.A0, opts) as d:
+        f_one = np.array([d.sweep(1)[0] for _ in range(12)])
+        A2, lam2, _, _ = d.factors()
+        h2 = d.history()
+    assert np.all(np.isfinite(f_many))
+    assert np.allclose(f_many, f_one, rtol=0, atol=1e-12), (f_many, f_one)
+    assert np.array_equal(h1[1], h2[1])  # betas
+    for a1, a2 in zip(A1, A2):
+        assert np.array_equal(a1, a2)
+    assert np.array_equal(lam1, lam2)
