@@ -152,6 +152,7 @@ struct cpqr_ctx {
   double* fitpart = nullptr;           // per-block partial fit terms of the finish preparation
   double* qr_work = nullptr;
   double* zq_work = nullptr;
+  double* zg_work = nullptr;       // Gram-route Khatri-Rao QR workspace
   double* v_work = nullptr;
   double* res_work = nullptr;
   double* fit_terms = nullptr;
@@ -518,7 +519,9 @@ cpqr_status launch_z(cpqr_ctx* ctx, int n) {
                               &nl));
       ctx->launches += nl - 1;
     } else {
-      CK(launch_krp_qr(ctx->zplan, tri, ctx->Q0, ctx->R0, ctx->zq_work, ctx->dstatus, ctx->st2, ctx->Q0f));
+      CK(launch_krp_qr_gram(ctx->zplan, tri.p[0], tri.p[1], ctx->Q0, ctx->R0, ctx->zg_work, ctx->zq_work,
+                            ctx->dstatus, ctx->st2, ctx->Q0f));
+      ctx->launches += 4;
     }
   }
   CK(cudaEventRecord(ctx->ev_z, ctx->st2));
@@ -966,6 +969,7 @@ cpqr_status cp_als_qr_init(cpqr_ctx** out, int32_t N, const int64_t* dims, int32
   CK(ctx->alloc(&ctx->fitpart, 2 * (size_t)finish_prep_blocks(Imax)));
   CK(ctx->alloc(&ctx->qr_work, std::max<int64_t>(M0, Imax) * R));
   CK(ctx->alloc(&ctx->zq_work, std::max<size_t>((size_t)(M0 * R), krp_nested_work_doubles(N - 1, R))));
+  CK(ctx->alloc(&ctx->zg_work, krp_gram_work_doubles(R)));
   CK(ctx->alloc((char**)&ctx->res_work, residual2_work_bytes(N, dims, R)));
   {
     int64_t vw = 0;
@@ -1415,12 +1419,15 @@ cpqr_status cpqr_krp_qr(const double* Rs_dev, int32_t m, int32_t R, double* Q0_d
   for (int k = 0; k < m; ++k) tri.p[k] = Rs_dev + (size_t)k * R * R;
   cudaError_t e = cudaMemcpyAsync(dperm, perm.data(), perm.size() * 4, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(ds, 0, 4, st);
+  double* gwork = nullptr;
+  if (e == cudaSuccess && m == 2 && cudaMalloc(&gwork, krp_gram_work_doubles(R) * 8) != cudaSuccess) e = cudaErrorMemoryAllocation;
   if (e == cudaSuccess) {
     if (m >= 3) e = launch_krp_qr_nested(plan, tri, m, Q0_dev, R0_dev, work, ds, st);
+    else if (m == 2) e = launch_krp_qr_gram(plan, tri.p[0], tri.p[1], Q0_dev, R0_dev, gwork, work, ds, st);
     else e = launch_krp_qr(plan, tri, Q0_dev, R0_dev, work, ds, st);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  cudaFree(dperm); cudaFree(work); cudaFree(ds);
+  cudaFree(dperm); cudaFree(work); cudaFree(ds); cudaFree(gwork);
   return e == cudaSuccess ? CPQR_OK : CPQR_ECUDA;
 }
 

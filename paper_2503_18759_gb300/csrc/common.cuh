@@ -69,13 +69,23 @@ size_t house_qr_work_doubles(int64_t M, int R);
 struct TriPtrs {
   const double* p[CPQR_MAXN];
 };
+// run_if (optional device flag): the QR runs only if *run_if != 0.
 cudaError_t launch_krp_qr(const ZPlan& plan, TriPtrs Rs, double* Q0, double* R0, double* work,
-                          unsigned int* dev_status, cudaStream_t st, float* Q0f = nullptr);
+                          unsigned int* dev_status, cudaStream_t st, float* Q0f = nullptr,
+                          const int* run_if = nullptr);
 size_t krp_qr_work_doubles(const ZPlan& plan);
 // QR of a product of m >= 2 triangles as m - 1 staircase QRs of two-triangle products (plan2:
 // the plan for m = 2) and m - 2 FP64 assemblies; work: krp_nested_work_doubles(m, R) doubles.
 // *nlaunch (optional) receives the number of kernels launched.
 size_t krp_nested_work_doubles(int m, int R);
+// QR of Ra (.) Rb (plan2: the two-triangle plan) by the guarded Gram route (krp_gram.cu): Cholesky
+// of the Hadamard product of the triangles' Grams, one orthogonality correction, and the
+// Householder staircase QR as the fallback when the correction is not small.  gram_work:
+// krp_gram_work_doubles(R) doubles; qr_work: the staircase QR's scratch.
+size_t krp_gram_work_doubles(int R);
+cudaError_t launch_krp_qr_gram(const ZPlan& plan2, const double* Ra, const double* Rb, double* Q0, double* R0,
+                               double* gram_work, double* qr_work, unsigned int* dev_status, cudaStream_t st,
+                               float* Q0f = nullptr);
 cudaError_t launch_krp_qr_nested(const ZPlan& plan2, TriPtrs Rs, int m, double* Q0, double* R0, double* work,
                                  unsigned int* dev_status, cudaStream_t st, float* Q0f = nullptr,
                                  int* nlaunch = nullptr);

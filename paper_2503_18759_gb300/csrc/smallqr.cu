@@ -105,6 +105,7 @@ struct QrParams {
   float* Qf;  // FP32 copy of Q (may be null)
   double* Rout;
   unsigned int* status;
+  const int* run_if;  // when set: the QR runs only if *run_if != 0 (a guarded fallback)
 };
 
 struct SmemLayout {
@@ -220,6 +221,7 @@ __global__ void __launch_bounds__(NT, 1) qr_cluster_kernel(QrParams p) {
   double (*VT)[CPQR_MAXR] = reinterpret_cast<double (*)[CPQR_MAXR]>(&sm.big[RR]);
 
   QR_PHASE(0);
+  if (p.run_if && *(volatile const int*)p.run_if == 0) return;  // every CTA reads the same flag
   // mbarriers of the st.async exchanges, armed for their first phase before any peer can send
   if (tid == 0) {
     for (int b = 0; b < 3; ++b) tc::mbar_init(smem_u32(&sm.bar[b]), 1);
@@ -716,7 +718,7 @@ cudaError_t launch_house_qr(const double* A, int64_t M, int R, double* Q, double
 }
 
 cudaError_t launch_krp_qr(const ZPlan& plan, TriPtrs Rs, double* Q0, double* R0, double* work,
-                          unsigned int* dev_status, cudaStream_t st, float* Q0f) {
+                          unsigned int* dev_status, cudaStream_t st, float* Q0f, const int* run_if) {
   QrParams p{};
   p.mode = MODE_KRP;
   if (plan.M > (int64_t(1) << 30)) return cudaErrorInvalidValue;
@@ -731,6 +733,7 @@ cudaError_t launch_krp_qr(const ZPlan& plan, TriPtrs Rs, double* Q0, double* R0,
   p.Qf = Q0f;
   p.Rout = R0;
   p.status = dev_status;
+  p.run_if = run_if;
   return run(p, st);
 }
 

@@ -240,3 +240,33 @@ def test_lagged_fit_equals_sweep_by_sweep_fit(extrap, beta):
     for a1, a2 in zip(A1, A2):
         assert np.array_equal(a1, a2)
     assert np.array_equal(lam1, lam2)
+
+
+@pytest.mark.parametrize("delta", [1e-10, 0.0])
+def test_krp_qr_gram_route_falls_back_on_ill_conditioned_products(delta):
+    """The Khatri-Rao QR of two triangles goes through the Gram matrix (Cholesky of the Hadamard
+    product of the triangles' Grams, one orthogonality correction) and falls back to the
+    Householder QR when the correction is not small.  Columns 0 and 1 of both source matrices
+    nearly coincide here (kappa(Z) ~ 1e5, or a singular Gram at delta = 0): the result must still
+    be the Householder one, orthonormal and reproducing Z to rounding."""
+    R = 12
+    g = np.random.default_rng(77)
+    tri = []
+    for _ in range(2):
+        B = g.standard_normal((R + 6, R))
+        B[:, 1] = B[:, 0] + delta * g.standard_normal(R + 6)
+        Rk = o.householder_qr(B)[1]
+        tri.append(Rk)
+    Z = o.khatri_rao(tri)
+    Q0 = torch.empty(Z.shape, dtype=torch.float64, device=DEV)
+    R0 = torch.empty((R, R), dtype=torch.float64, device=DEV)
+    Rd = _dev(np.stack(tri))
+    b.cpqr_krp_qr(Rd.data_ptr(), 2, R, Q0.data_ptr(), R0.data_ptr())
+    torch.cuda.synchronize()
+    Qg, Rg = Q0.cpu().numpy(), R0.cpu().numpy()
+    assert np.abs(Qg.T @ Qg - np.eye(R)).max() < 1e-13
+    assert np.abs(Qg @ Rg - Z).max() < 1e-13 * np.abs(Z).max()
+    assert np.all(np.diag(Rg)[np.abs(np.diag(Rg)) > 1e-12] > 0)
+    if delta > 0:
+        Q0r, R0r = o.householder_qr(Z)
+        assert np.allclose(Rg, R0r, atol=1e-12 * np.abs(R0r).max())
