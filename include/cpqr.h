@@ -53,7 +53,10 @@ typedef enum {
 } cpqr_tree;
 
 /* Arithmetic of the TTM chains.  Z_n = Q0 R0, the R0^{-T} solve and the
- * factor QRs are FP64 in both modes. */
+ * factor QRs are FP64 in both modes.  Inside a sweep, the QR of a two-triangle Khatri-Rao
+ * product and each factor QR take a guarded Gram route (Cholesky of the Gram matrix, one
+ * orthogonality correction); a pivot that is not positive or a correction above 1e-8 hands
+ * that QR to the Householder QR, so the result is the Householder-quality QR either way. */
 typedef enum {
   CPQR_PREC_FP64 = 0,      /* every TTM in FP64 (X promoted exactly) */
   CPQR_PREC_SPLIT_BF16 = 1 /* TTMs at every tree level on tcgen05 tensor cores with the
@@ -72,11 +75,17 @@ typedef enum {
                              fallback and judges every proposal by the fit it reaches */
 } cpqr_extrap;
 
+/* How a sweep computes the QR of a two-triangle Khatri-Rao product and the factor QRs. */
+typedef enum {
+  CPQR_QR_GRAM = 0,       /* guarded Gram route (default; see cpqr_prec) */
+  CPQR_QR_HOUSEHOLDER = 1 /* Householder QR only */
+} cpqr_qr_route;
+
 typedef struct {
   int32_t tree;       /* cpqr_tree */
   int32_t prec;       /* cpqr_prec */
   int32_t extrap;     /* cpqr_extrap */
-  int32_t reserved0;
+  int32_t qr_route;   /* cpqr_qr_route */
   double alpha;       /* eq. 19 alpha; <= 0 selects 1/10 */
   double beta_fixed;  /* beta for CPQR_EXTRAP_FIXED */
   uint64_t seed;      /* seed of the N(0,1) starting factors when A0 is NULL */
@@ -109,12 +118,14 @@ typedef struct {
   int64_t launches;        /* kernels this context launched */
   double ms_bucket[CPQR_NBUCKETS];   /* device time per bucket (only while timing is on) */
   int64_t n_bucket[CPQR_NBUCKETS];   /* launches per bucket (only while timing is on) */
+  int64_t qr_fallbacks;    /* Gram-route QRs (Khatri-Rao and factor) whose guard handed them to
+                              the Householder QR; reading it synchronises the context's streams */
 } cpqr_stats;
 
 /* Turn per-launch CUDA-event timing on (1) or off (0); resets the bucket times. */
 cpqr_status cp_als_qr_set_timing(cpqr_ctx* ctx, int32_t on);
 
-/* Fill *opt with the defaults: restructured tree, FP64, paper extrapolation,
+/* Fill *opt with the defaults: restructured tree, FP64, paper extrapolation, Gram QR route,
  * alpha = 0.1, beta_fixed = 0, seed = 0, no learned model. */
 void cp_als_qr_default_options(cpqr_options* opt);
 
@@ -221,7 +232,8 @@ cpqr_status cpqr_house_qr_noalloc(const double* A_dev, int64_t M, int32_t R, dou
 /* QR of Z = R_1 (.) ... (.) R_m, the Khatri-Rao product of m upper-triangular R x R
  * matrices (Alg. 2 lines 3-4), rows (r_1, ..., r_m) with r_m fastest: Rs_dev holds the m
  * triangles back to back (device, FP64).  Q0_dev (R^m x R) and R0_dev (R x R) receive the
- * factors, diag(R0) > 0. */
+ * factors, diag(R0) > 0.  m = 2 takes the guarded Gram route (see cpqr_prec); m >= 3 the
+ * nested Householder staircase QRs. */
 cpqr_status cpqr_krp_qr(const double* Rs_dev, int32_t m, int32_t R, double* Q0_dev,
                         double* R0_dev, void* stream);
 

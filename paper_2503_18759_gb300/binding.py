@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libcpqr.so")
 TREE_NONE, TREE_STANDARD, TREE_RESTRUCTURED = 0, 1, 2
 PREC_FP64, PREC_SPLIT_BF16 = 0, 1
 EXTRAP_NONE, EXTRAP_PAPER, EXTRAP_FIXED, EXTRAP_LEARNED = 0, 1, 2, 3
+QR_GRAM, QR_HOUSEHOLDER = 0, 1
 TTM_F64, TTM_F32, TTM_F32_IN_F64, TTM_SPLIT_BF16 = 0, 1, 2, 3
 
 OK, ENOTCONV = 0, 7
@@ -31,7 +32,7 @@ class CpqrError(RuntimeError):
 
 
 class Options(C.Structure):
-    _fields_ = [("tree", C.c_int32), ("prec", C.c_int32), ("extrap", C.c_int32), ("reserved0", C.c_int32),
+    _fields_ = [("tree", C.c_int32), ("prec", C.c_int32), ("extrap", C.c_int32), ("qr_route", C.c_int32),
                 ("alpha", C.c_double), ("beta_fixed", C.c_double), ("seed", C.c_uint64),
                 ("mlp_weights", C.POINTER(C.c_float))]
 
@@ -44,7 +45,7 @@ class Stats(C.Structure):
     _fields_ = [("sweeps", C.c_int64), ("ttm_flops", C.c_int64), ("full_ttms", C.c_int64),
                 ("last_fit", C.c_double), ("beta", C.c_double), ("proposals", C.c_int64),
                 ("accepted", C.c_int64), ("launches", C.c_int64), ("ms_bucket", C.c_double * NBUCKETS),
-                ("n_bucket", C.c_int64 * NBUCKETS)]
+                ("n_bucket", C.c_int64 * NBUCKETS), ("qr_fallbacks", C.c_int64)]
 
 
 _lib = None
@@ -127,9 +128,9 @@ def cp_als_qr_default_options() -> Options:
 
 
 def make_options(tree=TREE_RESTRUCTURED, prec=PREC_FP64, extrap=EXTRAP_PAPER, alpha=0.1, beta_fixed=0.0,
-                 seed=0, mlp_weights: Optional[np.ndarray] = None) -> Options:
+                 seed=0, mlp_weights: Optional[np.ndarray] = None, qr_route=QR_GRAM) -> Options:
     o = cp_als_qr_default_options()
-    o.tree, o.prec, o.extrap = int(tree), int(prec), int(extrap)
+    o.tree, o.prec, o.extrap, o.qr_route = int(tree), int(prec), int(extrap), int(qr_route)
     o.alpha, o.beta_fixed, o.seed = float(alpha), float(beta_fixed), int(seed)
     if mlp_weights is not None:
         w = np.ascontiguousarray(mlp_weights, dtype=np.float32)

@@ -102,6 +102,7 @@ struct cpqr_ctx {
   int N = 0, R = 0;
   std::vector<int64_t> dims;
   int tree = 2, prec = 0, extrap = 1;
+  bool gram = true;  // Gram QR route (cpqr_qr_route)
   double alpha = kAlphaDefault, beta_fixed = 0.0;
   cudaStream_t st = nullptr;
   cudaStream_t st2 = nullptr;      // side stream: Khatri-Rao QR overlapped with the TTM chain
@@ -153,6 +154,14 @@ struct cpqr_ctx {
   double* qr_work = nullptr;
   double* zq_work = nullptr;
   double* zg_work = nullptr;       // Gram-route Khatri-Rao QR workspace
+  // per mode (state arena): equilibrated Gram of the factor (float-float, 32 x 32 upper) and
+  // its column norms, from which the Gram route's Khatri-Rao Cholesky is formed
+  float2* Gf[CPQR_MAXN] = {};
+  double* cn[CPQR_MAXN] = {};
+  int zchol_mode = -1;               // mode whose Khatri-Rao Cholesky is already issued on st2
+  cudaEvent_t ev_gram = nullptr;     // main stream: the last factor's Gram stored
+  double* fg_work = nullptr;       // Gram-route factor QR workspace
+  double* hpart = nullptr;         // per-block folded Gram partials of A^ (finish prep)
   double* v_work = nullptr;
   double* res_work = nullptr;
   double* fit_terms = nullptr;
@@ -173,6 +182,7 @@ struct cpqr_ctx {
   bool timing = false;
   std::vector<cudaEvent_t> evpool;
   std::vector<std::pair<int, int>> evused;  // (bucket, index of start event; end = +1)
+  int evnext = 0;                           // next free pair in evpool (groups may nest)
   double ms_bucket[CPQR_NBUCKETS] = {};
   int64_t n_bucket[CPQR_NBUCKETS] = {};
   int64_t launches = 0;
@@ -198,6 +208,7 @@ struct cpqr_ctx {
       if (c.arena) cudaFree(c.arena);
     if (ev_ready) cudaEventDestroy(ev_ready);
     if (ev_z) cudaEventDestroy(ev_z);
+    if (ev_gram) cudaEventDestroy(ev_gram);
     if (st2) cudaStreamDestroy(st2);
     pool.release();
     for (void* p : owned) cudaFree(p);
@@ -242,7 +253,8 @@ struct Timed {
     s = stream ? stream : ctx->st;
     ctx->launches += nlaunch;
     if (!ctx->timing) return;
-    idx = (int)ctx->evused.size() * 2;
+    idx = ctx->evnext;
+    ctx->evnext += 2;
     while ((int)ctx->evpool.size() < idx + 2) {
       cudaEvent_t e;
       if (cudaEventCreate(&e) != cudaSuccess) {
@@ -269,6 +281,7 @@ void collect_timing(cpqr_ctx* ctx) {
     }
   }
   ctx->evused.clear();
+  ctx->evnext = 0;
 }
 
 int64_t ipow(int64_t b, int e) {
@@ -482,6 +495,7 @@ cpqr_status checkpoint_restore(cpqr_ctx* ctx, int slot) {
   ctx->Q0 = c.Q0;
   ctx->Q0f = c.Q0f;
   ctx->z_pending = false;
+  ctx->zchol_mode = -1;
   return CPQR_OK;
 }
 
@@ -501,9 +515,17 @@ cpqr_status stage_q(cpqr_ctx* ctx, int n) {
   return CPQR_OK;
 }
 
+// The two modes other than n of an order-3 tensor (ascending, as the triangles of Z_n).
+void z_modes(const cpqr_ctx* ctx, int n, int* a, int* b) {
+  int m = 0;
+  for (int k = 0; k < ctx->N; ++k)
+    if (k != n) *(m++ == 0 ? a : b) = k;
+}
+
 // Alg. 3 lines 3-4 for mode n: QR of the Khatri-Rao product of the other triangles,
 // issued on the side stream as soon as the previous update has produced its R_k so
-// that it runs under the TTM chain of mode n.
+// that it runs under the TTM chain of mode n.  On the Gram route its Cholesky may already be
+// on the side stream (issued by the previous update once its factor's Gram existed).
 cpqr_status launch_z(cpqr_ctx* ctx, int n) {
   TriPtrs tri{};
   int m = 0;
@@ -518,10 +540,19 @@ cpqr_status launch_z(cpqr_ctx* ctx, int n) {
       CK(launch_krp_qr_nested(ctx->zplan2, tri, m, ctx->Q0, ctx->R0, ctx->zq_work, ctx->dstatus, ctx->st2, ctx->Q0f,
                               &nl));
       ctx->launches += nl - 1;
+    } else if (ctx->gram) {
+      if (ctx->zchol_mode != n) {
+        int a = -1, b = -1;
+        z_modes(ctx, n, &a, &b);
+        CK(launch_krp_chol(ctx->Gf[a], ctx->Gf[b], ctx->cn[a], ctx->cn[b], ctx->R, ctx->zg_work, ctx->st2));
+        ctx->launches += 1;
+      }
+      ctx->zchol_mode = -1;
+      CK(launch_krp_rows(ctx->zplan, tri.p[0], tri.p[1], ctx->Q0, ctx->R0, ctx->zg_work, ctx->zq_work, ctx->dstatus,
+                         ctx->st2, ctx->Q0f));
+      ctx->launches += 3;
     } else {
-      CK(launch_krp_qr_gram(ctx->zplan, tri.p[0], tri.p[1], ctx->Q0, ctx->R0, ctx->zg_work, ctx->zq_work,
-                            ctx->dstatus, ctx->st2, ctx->Q0f));
-      ctx->launches += 4;
+      CK(launch_krp_qr(ctx->zplan, tri, ctx->Q0, ctx->R0, ctx->zq_work, ctx->dstatus, ctx->st2, ctx->Q0f));
     }
   }
   CK(cudaEventRecord(ctx->ev_z, ctx->st2));
@@ -532,7 +563,7 @@ cpqr_status launch_z(cpqr_ctx* ctx, int n) {
 
 cpqr_status launch_lagged_residual(cpqr_ctx* ctx);
 
-cpqr_status run_update(cpqr_ctx* ctx, int n, int leaf, double beta) {
+cpqr_status run_update(cpqr_ctx* ctx, int n, int leaf, double beta, int next_mode) {
   auto it = ctx->nodes.find(leaf);
   if (it == ctx->nodes.end()) return fail(ctx, CPQR_EINVAL);
   const NodeBuf lb = it->second;
@@ -568,21 +599,40 @@ cpqr_status run_update(cpqr_ctx* ctx, int n, int leaf, double beta) {
     fo.Kp = ctx->Kp[n];
   }
   {
-    Timed tm(ctx, CPQR_BUCKET_QR, 2);
+    // finish prep, then the factor QR: by the guarded Gram route, 4 kernels and the Householder
+    // finish, which runs only when the guard trips; else the Householder finish alone
+    Timed tm(ctx, CPQR_BUCKET_QR, ctx->gram ? 6 : 2);
     const double b = ext ? beta : 0.0;
+    double* hpart = ctx->gram ? ctx->hpart : nullptr;
     if (fp64)
       CK(launch_finish_prep<double>(ctx->v_work, nparts, I, C, R, ctx->R0, b, ctx->alpha, ctx->V, ctx->fitpart,
-                                    ctx->dstatus, st));
+                                    hpart, ctx->dstatus, st));
     else
       CK(launch_finish_prep<float>((const float*)ctx->v_work, nparts, I, C, R, ctx->R0, b, ctx->alpha, ctx->V,
-                                   ctx->fitpart, ctx->dstatus, st));
+                                   ctx->fitpart, hpart, ctx->dstatus, st));
     if (ctx->resid_pending) {
       // the previous sweep's residual runs beside this factor QR (one GPC busy, the rest idle)
       CK(cudaEventRecord(ctx->ev_prep, st));
       cpqr_status s = launch_lagged_residual(ctx);
       if (s != CPQR_OK) return s;
     }
-    CK(launch_mode_finish(ctx->V, ctx->fitpart, finish_prep_blocks(I), I, R, fo, ctx->qr_work, ctx->dstatus, st));
+    if (ctx->gram) {
+      const int nblk = finish_prep_blocks(I);
+      CK(launch_finish_gram_chol(ctx->hpart, ctx->fitpart, nblk, I, R, fo, ctx->fg_work, ctx->Gf[n], ctx->cn[n], st));
+      if (ctx->N == 3 && next_mode >= 0 && next_mode != n && !ctx->z_pending) {
+        // the next mode's Khatri-Rao Cholesky needs only the factors' Grams: it runs on the
+        // side stream beside the rest of this factor QR
+        int a = -1, b = -1;
+        z_modes(ctx, next_mode, &a, &b);
+        CK(cudaEventRecord(ctx->ev_gram, st));
+        CK(cudaStreamWaitEvent(ctx->st2, ctx->ev_gram, 0));
+        Timed tz(ctx, CPQR_BUCKET_Q0, 1, ctx->st2);
+        CK(launch_krp_chol(ctx->Gf[a], ctx->Gf[b], ctx->cn[a], ctx->cn[b], R, ctx->zg_work, ctx->st2));
+        ctx->zchol_mode = next_mode;
+      }
+      CK(launch_finish_gram_rows(ctx->V, ctx->fitpart, nblk, I, R, fo, ctx->fg_work, ctx->qr_work, ctx->dstatus, st));
+    } else
+      CK(launch_mode_finish(ctx->V, ctx->fitpart, finish_prep_blocks(I), I, R, fo, ctx->qr_work, ctx->dstatus, st));
   }
   std::swap(ctx->Q0, ctx->Q0prev[n]);
   std::swap(ctx->Q0f, ctx->Q0fprev[n]);
@@ -735,7 +785,12 @@ cpqr_status one_sweep(cpqr_ctx* ctx, double* fit_out, const double* forced_beta 
       if (s != CPQR_OK) return s;
     }
     if (op.kind == OP_TTM) s = run_ttm(ctx, op);
-    else if (op.kind == OP_UPDATE) s = run_update(ctx, op.a, op.b, beta);
+    else if (op.kind == OP_UPDATE) {
+      int next_mode = -1;
+      for (size_t k = i + 1; k < ctx->ops.size() && next_mode < 0; ++k)
+        if (ctx->ops[k].kind == OP_UPDATE) next_mode = ctx->ops[k].a;
+      s = run_update(ctx, op.a, op.b, beta, next_mode);
+    }
     else free_node(ctx, op.a);
     if (s != CPQR_OK) return s;
   }
@@ -858,6 +913,7 @@ void cp_als_qr_default_options(cpqr_options* opt) {
   opt->tree = CPQR_TREE_RESTRUCTURED;
   opt->prec = CPQR_PREC_FP64;
   opt->extrap = CPQR_EXTRAP_PAPER;
+  opt->qr_route = CPQR_QR_GRAM;
   opt->alpha = kAlphaDefault;
   opt->beta_fixed = 0.0;
   opt->seed = 0;
@@ -888,7 +944,8 @@ cpqr_status cp_als_qr_init(cpqr_ctx** out, int32_t N, const int64_t* dims, int32
   cpqr_options opt;
   if (opt_in) opt = *opt_in;
   else cp_als_qr_default_options(&opt);
-  if (!valid_enum(opt.tree, 0, 2) || !valid_enum(opt.prec, 0, 1) || !valid_enum(opt.extrap, 0, 3))
+  if (!valid_enum(opt.tree, 0, 2) || !valid_enum(opt.prec, 0, 1) || !valid_enum(opt.extrap, 0, 3) ||
+      !valid_enum(opt.qr_route, 0, 1))
     return CPQR_EINVAL;
   int64_t nX = 1;
   for (int n = 0; n < N; ++n) {
@@ -912,6 +969,7 @@ cpqr_status cp_als_qr_init(cpqr_ctx** out, int32_t N, const int64_t* dims, int32
   ctx->tree = opt.tree;
   ctx->prec = opt.prec;
   ctx->extrap = opt.extrap;
+  ctx->gram = opt.qr_route == CPQR_QR_GRAM;
   ctx->alpha = opt.alpha > 0 ? opt.alpha : kAlphaDefault;
   ctx->beta_fixed = opt.beta_fixed;
   ctx->st = (cudaStream_t)stream;
@@ -935,6 +993,7 @@ cpqr_status cp_als_qr_init(cpqr_ctx** out, int32_t N, const int64_t* dims, int32
       return o;
     };
     size_t oA[CPQR_MAXN], oQ[CPQR_MAXN], oR[CPQR_MAXN], oQf[CPQR_MAXN], oP[CPQR_MAXN], oT[CPQR_MAXN], oPf[CPQR_MAXN];
+    size_t oG[CPQR_MAXN], oC[CPQR_MAXN];
     for (int n = 0; n < N; ++n) {
       ctx->Kp[n] = ((dims[n] + 63) / 64) * 64;
       oA[n] = take(dims[n] * R * 8);
@@ -944,6 +1003,8 @@ cpqr_status cp_als_qr_init(cpqr_ctx** out, int32_t N, const int64_t* dims, int32
       oP[n] = take(M0 * R * 8);
       oT[n] = split ? take((size_t)2 * ctx->Rp * ctx->Kp[n] * 2) : 0;
       oPf[n] = split ? take(M0 * R * 4) : 0;
+      oG[n] = take((size_t)CPQR_MAXR * CPQR_MAXR * sizeof(float2));
+      oC[n] = take((size_t)CPQR_MAXR * 8);
     }
     size_t oQ0 = take(M0 * R * 8), oL = take(R * 8), oQ0f = split ? take(M0 * R * 4) : 0;
     ctx->arena_bytes = off;
@@ -959,6 +1020,8 @@ cpqr_status cp_als_qr_init(cpqr_ctx** out, int32_t N, const int64_t* dims, int32
       ctx->Q0prev[n] = (double*)(a + oP[n]);
       if (split) ctx->Qt[n] = (__nv_bfloat16*)(a + oT[n]);
       if (split) ctx->Q0fprev[n] = (float*)(a + oPf[n]);
+      ctx->Gf[n] = (float2*)(a + oG[n]);
+      ctx->cn[n] = (double*)(a + oC[n]);
     }
     ctx->Q0 = (double*)(a + oQ0);
     if (split) ctx->Q0f = (float*)(a + oQ0f);
@@ -970,6 +1033,10 @@ cpqr_status cp_als_qr_init(cpqr_ctx** out, int32_t N, const int64_t* dims, int32
   CK(ctx->alloc(&ctx->qr_work, std::max<int64_t>(M0, Imax) * R));
   CK(ctx->alloc(&ctx->zq_work, std::max<size_t>((size_t)(M0 * R), krp_nested_work_doubles(N - 1, R))));
   CK(ctx->alloc(&ctx->zg_work, krp_gram_work_doubles(R)));
+  CK(ctx->alloc(&ctx->fg_work, factor_gram_work_doubles(Imax, R)));
+  CK(ctx->alloc(&ctx->hpart, (size_t)finish_prep_blocks(Imax) * 17 * 32));
+  CK(cudaMemsetAsync(ctx->zg_work, 0, krp_gram_work_doubles(R) * sizeof(double), st));
+  CK(cudaMemsetAsync(ctx->fg_work, 0, factor_gram_work_doubles(Imax, R) * sizeof(double), st));
   CK(ctx->alloc((char**)&ctx->res_work, residual2_work_bytes(N, dims, R)));
   {
     int64_t vw = 0;
@@ -989,6 +1056,7 @@ cpqr_status cp_als_qr_init(cpqr_ctx** out, int32_t N, const int64_t* dims, int32
   CK(cudaEventCreateWithFlags(&ctx->ev_fit, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&ctx->ev_ready, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&ctx->ev_z, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&ctx->ev_gram, cudaEventDisableTiming));
   CK(ctx->alloc(&ctx->fit_terms, 2));
   CK(ctx->alloc(&ctx->d_scalar, 2));
   CK(ctx->alloc(&ctx->dstatus, 1));
@@ -1034,6 +1102,7 @@ cpqr_status cp_als_qr_init(cpqr_ctx** out, int32_t N, const int64_t* dims, int32
     CK(cudaMemcpyAsync(ctx->A[n], host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, st));
     CK(launch_house_qr(ctx->A[n], dims[n], R, ctx->Q[n], ctx->Rf[n], ctx->qr_work, ctx->dstatus, st));
     CK(launch_to_f32(ctx->Q[n], ctx->Qf[n], dims[n] * R, st));
+    CK(launch_tri_gram(ctx->Rf[n], R, ctx->Gf[n], ctx->cn[n], st));
     CK(cudaStreamSynchronize(st));
   }
   // Split-precision staging.
@@ -1159,6 +1228,14 @@ cpqr_status cp_als_qr_stats(cpqr_ctx* ctx, cpqr_stats* out) {
     out->ms_bucket[b] = ctx->ms_bucket[b];
     out->n_bucket[b] = ctx->n_bucket[b];
   }
+  if (ctx->zg_work && ctx->fg_work) {
+    int cnt[2] = {0, 0};
+    if (cudaStreamSynchronize(ctx->st) != cudaSuccess || cudaStreamSynchronize(ctx->st2) != cudaSuccess ||
+        cudaMemcpy(&cnt[0], gram_fallback_counter(ctx->zg_work), sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(&cnt[1], gram_fallback_counter(ctx->fg_work), sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(ctx, CPQR_ECUDA);
+    out->qr_fallbacks = (int64_t)cnt[0] + cnt[1];
+  }
   return ctx->err;
 }
 
@@ -1167,6 +1244,7 @@ cpqr_status cp_als_qr_set_timing(cpqr_ctx* ctx, int32_t on) {
   if (ctx->err != CPQR_OK) return ctx->err;
   CK(cudaStreamSynchronize(ctx->st));
   ctx->evused.clear();
+  ctx->evnext = 0;
   ctx->timing = on != 0;
   for (int b = 0; b < CPQR_NBUCKETS; ++b) {
     ctx->ms_bucket[b] = 0.0;

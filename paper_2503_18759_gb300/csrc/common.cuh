@@ -14,6 +14,29 @@
 
 namespace cpqr {
 
+// Programmatic dependent launch: the kernel may be scheduled while the previous kernel of the
+// stream drains (its launch latency then overlaps that kernel's tail), so it must call
+// pdl_wait() before it reads anything an earlier launch wrote.  Only for kernels that are not
+// clusters (whose launch this does not shorten).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+// Waits until the grids this one depends on have completed and their writes are visible
+// (returns at once for a launch without the programmatic attribute).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Block size of the FP64 small-QR kernels.
 constexpr int kQrThreads = 256;
 
@@ -69,10 +92,9 @@ size_t house_qr_work_doubles(int64_t M, int R);
 struct TriPtrs {
   const double* p[CPQR_MAXN];
 };
-// run_if (optional device flag): the QR runs only if *run_if != 0.
+// run_if (optional device pair): the QR runs only if run_if[0] != 0, and then adds 1 to run_if[1].
 cudaError_t launch_krp_qr(const ZPlan& plan, TriPtrs Rs, double* Q0, double* R0, double* work,
-                          unsigned int* dev_status, cudaStream_t st, float* Q0f = nullptr,
-                          const int* run_if = nullptr);
+                          unsigned int* dev_status, cudaStream_t st, float* Q0f = nullptr, int* run_if = nullptr);
 size_t krp_qr_work_doubles(const ZPlan& plan);
 // QR of a product of m >= 2 triangles as m - 1 staircase QRs of two-triangle products (plan2:
 // the plan for m = 2) and m - 2 FP64 assemblies; work: krp_nested_work_doubles(m, R) doubles.
@@ -86,6 +108,14 @@ size_t krp_gram_work_doubles(int R);
 cudaError_t launch_krp_qr_gram(const ZPlan& plan2, const double* Ra, const double* Rb, double* Q0, double* R0,
                                double* gram_work, double* qr_work, unsigned int* dev_status, cudaStream_t st,
                                float* Q0f = nullptr);
+// The Khatri-Rao QR of the guarded Gram route in two phases: the Cholesky of D (Ga o Gb) D from
+// the two factors' stored Grams and norms (..._chol), then the rows of Q0, R0 and the guard
+// (..._rows, which needs the triangles).  Both use the same gram_work.
+cudaError_t launch_krp_chol(const float2* Ga, const float2* Gb, const double* sa, const double* sb, int R,
+                            double* gram_work, cudaStream_t st);
+cudaError_t launch_krp_rows(const ZPlan& plan2, const double* Ra, const double* Rb, double* Q0, double* R0,
+                            double* gram_work, double* qr_work, unsigned int* dev_status, cudaStream_t st,
+                            float* Q0f = nullptr);
 cudaError_t launch_krp_qr_nested(const ZPlan& plan2, TriPtrs Rs, int m, double* Q0, double* R0, double* work,
                                  unsigned int* dev_status, cudaStream_t st, float* Q0f = nullptr,
                                  int* nlaunch = nullptr);
@@ -100,12 +130,13 @@ cudaError_t launch_leaf_v(const TY* Y, int64_t P, int64_t I, int64_t S, const TQ
 
 // Mode update, Alg. 3 lines 5 and 7-8: adds the nparts slices of V = [V0 | V1] (I x C,
 // C = R or 2R), V^ = (1+beta) V0 - alpha beta V1 (eq. 19), A^ = V^ R0^{-T} into Ahat (I x R),
-// and per-block partials of <V0, V^>, ||V^||^2 into fitpart (finish_prep_blocks(I) x 2).
+// and per-block partials of <V0, V^>, ||V^||^2 into fitpart (finish_prep_blocks(I) x 2);
+// hpart (optional): per-block folded partials of A^T A^ (finish_prep_blocks(I) x 17 x 32).
 int finish_prep_blocks(int64_t I);
 template <typename TP>
 cudaError_t launch_finish_prep(const TP* parts, int nparts, int64_t I, int C, int R, const double* R0, double beta,
-                               double alpha, double* Ahat, double* fitpart, unsigned int* dev_status,
-                               cudaStream_t st);
+                               double alpha, double* Ahat, double* fitpart, double* hpart,
+                               unsigned int* dev_status, cudaStream_t st);
 
 // Finish of a mode update (Alg. 3 lines 9-10): lambda = column norms of A^, A = A^ / lambda,
 // A = Q_n R_n; the fit terms <V0, V^>, ||V^||^2 from the nfit block partials.
@@ -123,7 +154,29 @@ struct FinishOut {
   int64_t Kp = 0;
 };
 cudaError_t launch_mode_finish(const double* Ahat, const double* fitpart, int nfit, int64_t I, int R, FinishOut out,
-                               double* work, unsigned int* dev_status, cudaStream_t st);
+                               double* work, unsigned int* dev_status, cudaStream_t st, int* run_if = nullptr);
+// The same finish by the guarded Gram route (krp_gram.cu): Gram of A^ from the hpart block
+// partials of launch_finish_prep, lambda, Cholesky of the equilibrated Gram (..._chol, which can
+// also store the new factor's equilibrated Gram, float-float 32 x 32 upper, and its unit column
+// norms), row-parallel substitution and one orthogonality correction (..._rows); the Householder
+// finish runs instead (launched last, returning at once otherwise) when a pivot fails or the
+// correction is not small.  gram_work: factor_gram_work_doubles(Imax, R) doubles; qr_work: the
+// Householder finish's scratch.  launch_finish_gram = ..._chol without the Gram, then ..._rows.
+size_t factor_gram_work_doubles(int64_t Imax, int R);
+cudaError_t launch_finish_gram_chol(const double* hpart, const double* fitpart, int nblk, int64_t I, int R,
+                                    FinishOut out, double* gram_work, float2* gram_out, double* colnorm_out,
+                                    cudaStream_t st);
+cudaError_t launch_finish_gram_rows(const double* Ahat, const double* fitpart, int nblk, int64_t I, int R,
+                                    FinishOut out, double* gram_work, double* qr_work, unsigned int* dev_status,
+                                    cudaStream_t st);
+cudaError_t launch_finish_gram(const double* Ahat, const double* hpart, const double* fitpart, int nblk, int64_t I,
+                               int R, FinishOut out, double* gram_work, double* qr_work, unsigned int* dev_status,
+                               cudaStream_t st);
+// Equilibrated Gram (float-float, 32 x 32 upper) and column norms of the factor whose QR
+// triangle is T (R x R upper, device): for factors without a Gram from the finish.
+cudaError_t launch_tri_gram(const double* T, int R, float2* Gf, double* s, cudaStream_t st);
+// Runs of the Householder fallback recorded in a Gram-route workspace (device int counter).
+int* gram_fallback_counter(double* gram_work);
 
 // ||X||^2 in FP64 (partials into work, final into out[0]).
 template <typename TX>

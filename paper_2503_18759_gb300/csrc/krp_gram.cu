@@ -1,6 +1,8 @@
-// QR of the Khatri-Rao product of two upper triangles, Z = R_a (.) R_b (R^2 x R, Alg. 2
-// lines 3-4 for order-3 tensors and the building block of the nested QR for higher orders),
-// by the Gram route, guarded by the Householder QR.
+// QRs by the Gram route, guarded by the Householder QR:
+//  - the Khatri-Rao product of two upper triangles, Z = R_a (.) R_b (R^2 x R, Alg. 2 lines 3-4
+//    for order-3 tensors and the building block of the nested QR for higher orders);
+//  - the factor of a mode update, A = A^ / lambda (I x R, Alg. 2 lines 9-10), whose Gram
+//    comes from per-block partials written by the R0^{-T} solve that produces A^.
 //
 // Z's Gram matrix needs no pass over Z: Z^T Z = (R_a^T R_a) o (R_b^T R_b) (Hadamard product),
 // because row (i, k) of Z is R_a[i, :] o R_b[k, :].  Then
@@ -13,9 +15,14 @@
 // kappa(Z)^2 * 2^-53.  If a pivot of the Cholesky is not positive or max |E| > kEMax, a device flag
 // makes the Householder staircase QR (smallqr.cu), launched after these kernels, recompute Q0 and
 // R0; otherwise it returns at once.  The Householder QR's stability is thus kept for every Z,
-// while the common well-conditioned case costs one 32-step Cholesky (after a Gram spread over one
-// cluster) plus three row-parallel FP64 passes over all SMs instead of 32 cluster-wide
-// Householder steps.
+// while the common well-conditioned case costs one 32-step Cholesky plus three row-parallel FP64
+// passes over all SMs instead of 32 cluster-wide Householder steps.  For Z, the Gram is the
+// Hadamard product of the two factors' stored Grams (kg_chol_kernel); for A, it comes from the
+// solve's partials.  Either Gram is equilibrated (unit diagonal: G = D^-1 G D^-1, D = the column
+// norms, for A lambda) and its Cholesky runs in float-float (~2^-48): R1 serves only as the
+// preconditioner of Q1 = Z R1^{-1}, which is formed in FP64 against whatever R1 is, so its
+// precision moves E (|E| ~ kappa^2 2^-48, the guard thus trips near kappa ~ 1e3 instead of 1e4)
+// and not the accuracy of an accepted (Q0, R0).
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -33,143 +40,495 @@ constexpr int KG_LD = KG_MAXR + 1;
 // max |E| accepted: the neglected O(E^2) terms stay below 1e-16
 constexpr double kEMax = 1e-8;
 
-// Workspace layout (doubles): R1, S (R1 scaled for the substitution), F, rinv, Q1 (R^2 x R),
-// Q1^T (R x R^2), then the int flag.
+// Workspace layout (doubles, every section 128-byte aligned): the int pair {fallback flag,
+// fallback count} (at a fixed offset, so the count survives calls with different row counts),
+// R1, S (R1 scaled for the substitution), F, rinv, 1/lambda (the equilibration), two Grams in
+// float-float and their column norms (for a QR whose triangles come without stored Grams),
+// Q1 (M x R), Q1^T (R x M).
+constexpr size_t KG_HEAD = 16;
+size_t kg_round16(size_t n) { return (n + 15) / 16 * 16; }
 struct KgWork {
+  int* flag;
   double* R1;
   double* S;
   double* F;
   double* rinv;
+  double* il;
+  float2* ga;
+  float2* gb;
+  double* sa;
+  double* sb;
   double* Q1;
   double* Q1T;
-  int* flag;
 };
 
-KgWork kg_views(double* work, int R) {
+size_t kg_work_doubles(int64_t M, int R) {
+  return KG_HEAD + 5 * (size_t)KG_MAXR * KG_MAXR + 4 * KG_MAXR + 2 * kg_round16((size_t)M * R);
+}
+
+KgWork kg_views(double* work, int R, int64_t M) {
   KgWork w;
-  const size_t rr = (size_t)KG_MAXR * KG_MAXR, M = (size_t)R * R;
-  w.R1 = work;
+  const size_t rr = (size_t)KG_MAXR * KG_MAXR;
+  w.flag = reinterpret_cast<int*>(work);
+  w.R1 = work + KG_HEAD;
   w.S = w.R1 + rr;
   w.F = w.S + rr;
   w.rinv = w.F + rr;
-  w.Q1 = w.rinv + KG_MAXR;
-  w.Q1T = w.Q1 + M * R;
-  w.flag = reinterpret_cast<int*>(w.Q1T + M * R);
+  w.il = w.rinv + KG_MAXR;
+  w.ga = reinterpret_cast<float2*>(w.il + KG_MAXR);
+  w.gb = reinterpret_cast<float2*>(w.il + KG_MAXR + rr);
+  w.sa = w.il + KG_MAXR + 2 * rr;
+  w.sb = w.sa + KG_MAXR;
+  w.Q1 = w.sb + KG_MAXR;
+  w.Q1T = w.Q1 + kg_round16((size_t)M * R);
   return w;
 }
 
 // Gram (Hadamard of the two triangles' Grams) and its Cholesky factor on one 16-CTA cluster of
 // 256 threads: CTA r forms rows c = r, r + 16 of the Gram (FP64 on one SM is ~8 GFLOP/s, so the
 // two triangular products are spread) and stores them into CTA 0's shared memory; CTA 0 then
-// runs the Cholesky.  Right-looking: at step j warp 0 forms row j of R1 from the pivot
-// (rsqrt.approx.f64, measured to 53 bits, in the normal range), then all warps update the
-// trailing rows.
+// runs the Cholesky (chol_pipelined).
 constexpr int KG_CL = 16;
+constexpr int KG_GK = 17;  // folded Gram entries per lane in the finish-prep partials
 
 // named barriers of 256 threads (barrier 0 is __syncthreads)
 __device__ __forceinline__ void nb_arrive(int id) { asm volatile("bar.arrive %0, 256;" ::"r"(id) : "memory"); }
 __device__ __forceinline__ void nb_sync(int id) { asm volatile("bar.sync %0, 256;" ::"r"(id) : "memory"); }
 
-__global__ void __cluster_dims__(KG_CL, 1, 1) __launch_bounds__(256)
-    kg_chol_kernel(const double* __restrict__ Ra, const double* __restrict__ Rb, int R, KgWork w) {
-  namespace cg = cooperative_groups;
-  cg::cluster_group cluster = cg::this_cluster();
-  const int rank = (int)cluster.block_rank();
-  __shared__ double sa[KG_MAXR][KG_LD], sb[KG_MAXR][KG_LD], G[KG_MAXR][KG_LD], R1[KG_MAXR][KG_LD];
-  __shared__ int bad;
+// ---- float-float numbers: the unevaluated sum hi + lo of two FP32 values (~2^-48 relative) ----
+// GB300 issues one FP64 warp instruction per 64 cycles per SM sub-partition at a 64-cycle
+// latency, FP32 one per cycle at 4 cycles, so the serial Cholesky runs in float-float.  The
+// operations are the error-free transformations TwoSum (Knuth) and TwoProd by FMA, written with
+// the _rn intrinsics so that the compiler neither contracts nor reorders them.
+struct ffn {
+  float hi, lo;
+};
+__device__ __forceinline__ ffn ff_make(float hi, float lo) {
+  ffn r;
+  r.hi = hi;
+  r.lo = lo;
+  return r;
+}
+__device__ __forceinline__ ffn ff_ld(const float2& v) { return ff_make(v.x, v.y); }
+__device__ __forceinline__ float2 ff_st(ffn a) { return make_float2(a.hi, a.lo); }
+// FP32 -> FP64, exact for zero and normal numbers (subnormal inputs, below 1.2e-38, read as
+// zero), by moving the IEEE-754 fields on the integer pipe: exponent rebiased from 127 to 1023,
+// mantissa widened.  (A conversion instruction would occupy the slow FP64 pipe.)
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned int b = __float_as_uint(f);
+  const unsigned int e = (b >> 23) & 0xffu;
+  const unsigned int E = (e == 0u) ? 0u : ((e == 255u) ? 2047u : e + 896u);
+  const unsigned long long m = (e == 0u) ? 0ull : (unsigned long long)(b & 0x7fffffu) << 29;
+  return __longlong_as_double(
+      (long long)(((unsigned long long)(b & 0x80000000u) << 32) | ((unsigned long long)E << 52) | m));
+}
+// FP64 -> FP32 rounded toward zero (below the FP32 normal range: zero; above: infinity, which
+// fails the pivot test), by moving the fields.
+__device__ __forceinline__ float d2f_trunc(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned int hi = (unsigned int)(b >> 32);
+  const unsigned int sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu) - 896;
+  if (e <= 0) return __uint_as_float(sign);
+  if (e >= 255) return __uint_as_float(sign | 0x7f800000u);
+  return __uint_as_float(sign | ((unsigned int)e << 23) | (unsigned int)((b >> 29) & 0x7fffffull));
+}
+// x as hi + lo (both truncated: ~2^-48 relative; x - hi is exact in FP64), one FP64 subtraction
+__device__ __forceinline__ ffn ff_from_bits(double x) {
+  const float h = d2f_trunc(x);
+  return ff_make(h, d2f_trunc(x - f2d_bits(h)));
+}
+// hi + lo in FP64 with one FP64 addition
+__device__ __forceinline__ double ff_val(const float2& v) { return f2d_bits(v.x) + f2d_bits(v.y); }
+__device__ __forceinline__ double ff_val(ffn a) { return f2d_bits(a.hi) + f2d_bits(a.lo); }
+__device__ __forceinline__ ffn ff_shfl(ffn a, int src) {
+  return ff_make(__shfl_sync(FULL, a.hi, src), __shfl_sync(FULL, a.lo, src));
+}
+// a b
+__device__ __forceinline__ ffn ff_mul(ffn a, ffn b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  const float h = __fadd_rn(p, e);
+  return ff_make(h, __fsub_rn(e, __fsub_rn(h, p)));
+}
+// t - a b
+__device__ __forceinline__ ffn ff_fms(ffn t, ffn a, ffn b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float pe = __fmaf_rn(a.hi, b.hi, -p);
+  pe = __fmaf_rn(a.hi, b.lo, pe);
+  pe = __fmaf_rn(a.lo, b.hi, pe);
+  const float s = __fsub_rn(t.hi, p);  // TwoSum(t.hi, -p)
+  const float bb = __fsub_rn(s, t.hi);
+  float err = __fadd_rn(__fsub_rn(t.hi, __fsub_rn(s, bb)), __fsub_rn(-p, bb));
+  err = __fadd_rn(err, __fsub_rn(t.lo, pe));
+  const float h = __fadd_rn(s, err);
+  return ff_make(h, __fsub_rn(err, __fsub_rn(h, s)));
+}
+// 1 / d for a pivot d: rcp.approx.ftz.f32 (at most 1 ulp off) and one Newton-Raphson step
+// y <- y + y (1 - d y) with the residual formed in float-float (error ~2^-46).  A pivot outside
+// (1e-30, 1e30), or not a number, sets *bad and gives 0.  d is warp-uniform.
+__device__ __forceinline__ ffn ff_recip(ffn d, int* bad) {
+  if (!(d.hi > 1e-30f && d.hi < 1e30f)) {
+    *bad = 1;
+    return ff_make(0.0f, 0.0f);
+  }
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(d.hi));
+  const float p = __fmul_rn(d.hi, y);
+  float pe = __fmaf_rn(d.hi, y, -p);
+  pe = __fmaf_rn(d.lo, y, pe);
+  const float r = __fsub_rn(__fsub_rn(1.0f, p), pe);
+  const float c = __fmul_rn(y, r);
+  const float h = __fadd_rn(y, c);
+  return ff_make(h, __fsub_rn(c, __fsub_rn(h, y)));
+}
+
+// CTA 0 of a Cholesky kernel, G (FP64, R x R block, both triangles) complete: scale = sqrt(diag
+// G), il = 1 / scale (rsqrt.approx.f64, measured to 53 bits; 0 for a zero or non-finite column,
+// whose zero row then fails its pivot), the equilibrated Gram Gf = D^-1 G D^-1 in float-float
+// (unit diagonal, entries in [-1, 1]; upper triangle, entries visited as the folded pairs
+// (c, (c + k) % 32), k = 0..16, so that every FP64 warp instruction has 32 live lanes), U = V = 0.
+__device__ __forceinline__ void equilibrate_ff(double (*G)[KG_LD], float2 (*Gf)[KG_LD], float2 (*U)[KG_LD],
+                                               float2 (*V)[KG_LD], double* scale, double* il, float2* ilf, int R,
+                                               const KgWork& w) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  for (int e = tid; e < KG_MAXR * KG_MAXR; e += 256) {
-    const int i = e / KG_MAXR, c = e % KG_MAXR;
-    const bool in = i < R && c < R;
-    sa[i][c] = in ? Ra[i * R + c] : 0.0;
-    sb[i][c] = in ? Rb[i * R + c] : 0.0;
-    R1[i][c] = 0.0;
-  }
-  if (tid == 0) bad = 0;
-  __syncthreads();
-  // G[c][d] = (sum_i Ra[i][c] Ra[i][d]) (sum_i Rb[i][c] Rb[i][d]), i <= min(c, d), into CTA 0
-  {
-    const int c = rank + KG_CL * warp;
-    if (warp < (KG_MAXR + KG_CL - 1) / KG_CL && c < R) {
-      double ga = 0.0, gb = 0.0;
-      const int d = lane;
-      const int imax = min(c, d);
-      for (int i = 0; i <= imax && d < R; ++i) {
-        ga = fma(sa[i][c], sa[i][d], ga);
-        gb = fma(sb[i][c], sb[i][d], gb);
-      }
-      cluster.map_shared_rank(&G[0][0], 0)[c * KG_LD + d] = (d < R) ? ga * gb : 0.0;
-    }
-  }
-  cluster.sync();  // every row of G is in CTA 0; the other CTAs are done
-  if (rank != 0) return;
-  // Pipelined right-looking Cholesky.  Warp 0 produces the rows of R1: for row s + 1 it applies
-  // step s's update itself (look-ahead) and starts the next square root at once, while warps
-  // 1-7 apply step s to rows >= s + 2.  "Row k of R1 written": warp 0 arrives, warps 1-7 wait,
-  // on barrier 1 (k even) or 3 (k odd).  "Step s applied to rows >= s + 2": warps 1-7 arrive,
-  // warp 0 waits before its look-ahead on row s + 2, on barrier 2 (s even) or 4 (s odd).  Two
-  // barriers per role because either side may arrive one generation ahead: warp 0 posts row
-  // k + 1 before the others have taken row k, and a warp may post step s + 1 before warp 0
-  // has taken step s.  Row k + 2 is posted only after warp 0 has taken step k (so all of
-  // warps 1-7 took row k), and step s + 2 only after row s + 2, which follows warp 0's wait on
-  // step s: each barrier's previous generation is complete before its next use.
-  auto pivot_row = [&](int j) {  // warp 0: row j of R1 from the up-to-date row j of G
-    const double g = G[j][j];
-    const long long gbits = __double_as_longlong(g);
-    double y;
-    if (gbits > 0x05CD0B15A491EB84LL && gbits < 0x7A11A0FC668AAC70LL) {  // 1e-280 < g < 1e280
+  if (tid < 32) {
+    const double g = (lane < R) ? G[lane][lane] : 0.0;
+    const long long b = __double_as_longlong(g);
+    double y = 0.0;
+    if (b > 0x05CD0B15A491EB84LL && b < 0x7A11A0FC668AAC70LL) {  // 1e-280 < g < 1e280
       asm("rsqrt.approx.f64 %0, %1;" : "=d"(y) : "d"(g));
-    } else {
-      y = (g > 0.0) ? 1.0 / sqrt(g) : 0.0;
-      if (!(g > 0.0) && lane == 0) bad = 1;
+    } else if (g > 0.0 && g < 1e300) {
+      y = 1.0 / sqrt(g);
     }
-    const double r = (lane >= j && lane < R) ? G[j][lane] * y : 0.0;
-    if (lane >= j && lane < R) R1[j][lane] = r;
-    if (lane == j) w.rinv[j] = y;
-    return r;
-  };
+    scale[lane] = (y > 0.0) ? g * y : 0.0;
+    il[lane] = y;
+    ilf[lane] = ff_st(ff_from_bits(y));
+    w.il[lane] = y;
+  }
+  for (int e = tid; e < KG_MAXR * KG_MAXR; e += blockDim.x) {
+    U[e / KG_MAXR][e % KG_MAXR] = make_float2(0.0f, 0.0f);
+    V[e / KG_MAXR][e % KG_MAXR] = make_float2(0.0f, 0.0f);
+  }
+  __syncthreads();
+  for (int k = warp; k <= KG_MAXR / 2; k += (int)(blockDim.x >> 5)) {
+    const int c = lane, d = (lane + k) & 31;
+    const int i = min(c, d), j = max(c, d);
+    const ffn x = ff_from_bits(G[i][j]);
+    Gf[i][j] = (j < R) ? ff_st(ff_mul(ff_mul(x, ff_ld(ilf[i])), ff_ld(ilf[j]))) : make_float2(0.0f, 0.0f);
+  }
+  __syncthreads();
+}
+
+// Cholesky of the R x R leading block of G (256 threads; shared G, U, V in float-float, U and V
+// zero on entry, G overwritten) in square-root-free form: U[j] is row j of the Schur complement
+// after j steps (U[j][j] = d_j, the pivot) and V[j] = U[j] / d_j, so that step j subtracts
+// V[j][k] U[j][l] from G[k][l], and R1 = diag(d)^-1/2 U (chol_outputs).  The square roots are
+// thus off the serial chain, which per row is one fused multiply-subtract, one shuffle and one
+// reciprocal.
+//
+// Pipelining: warp 0 produces the rows: for row j it applies step j - 1 itself (look-ahead,
+// with z = U[j-1][j] U[j-1] formed while the reciprocal of d_{j-1} was in flight), while warps
+// 1-7 apply step j - 1 to rows >= j + 1.  "Row j of U, V written": warp 0 arrives, warps 1-7
+// wait, on barrier 1 (j even) or 3 (j odd).  "Step s applied to rows >= s + 2": warps 1-7
+// arrive, warp 0 waits before its look-ahead on row s + 2, on barrier 2 (s even) or 4 (s odd).
+// Two barriers per role because either side may arrive one generation ahead: warp 0 posts row
+// j + 1 before the others have taken row j, and a warp may post step s + 1 before warp 0 has
+// taken step s.  Row j + 2 is posted only after warp 0 has taken step j (so all of warps 1-7
+// took row j), and step s + 2 only after row s + 2, which follows warp 0's wait on step s:
+// each barrier's previous generation is complete before its next use.
+__device__ __forceinline__ void chol_pipelined(float2 (*G)[KG_LD], float2 (*U)[KG_LD], float2 (*V)[KG_LD], int R,
+                                               int* bad) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool in = lane < R;
+  const ffn zero = ff_make(0.0f, 0.0f);
   if (warp == 0) {
-    double r = pivot_row(0);
+    ffn u = in ? ff_ld(G[0][lane]) : zero;
+    ffn w = ff_recip(ff_shfl(u, 0), bad);
+    ffn z = ff_mul(ff_shfl(u, 1), u);  // U[0][1] U[0][l], for row 1
+    if (in) {
+      U[0][lane] = ff_st(u);
+      V[0][lane] = ff_st(ff_mul(u, w));
+    }
     __syncwarp();
     nb_arrive(1);  // row 0
-    for (int s = 0; s + 1 < R; ++s) {
-      if (s >= 1) nb_sync(2 + 2 * ((s - 1) & 1));  // step s - 1 reached row s + 1
-      const double rk = __shfl_sync(FULL, r, s + 1);  // R1[s][s + 1]
-      if (lane >= s + 1 && lane < R) G[s + 1][lane] = fma(-rk, r, G[s + 1][lane]);
+    for (int j = 1; j < R; ++j) {
+      if (j >= 2) nb_sync(2 + 2 * ((j - 2) & 1));  // step j - 2 reached row j
+      const bool live = in && lane >= j;
+      u = live ? ff_fms(ff_ld(G[j][lane]), w, z) : zero;  // step j - 1 on row j
+      w = ff_recip(ff_shfl(u, j), bad);
+      z = ff_mul(ff_shfl(u, (j + 1) & 31), u);
+      if (live) {
+        U[j][lane] = ff_st(u);
+        V[j][lane] = ff_st(ff_mul(u, w));
+      }
       __syncwarp();
-      r = pivot_row(s + 1);
-      __syncwarp();
-      nb_arrive(1 + 2 * ((s + 1) & 1));  // row s + 1
+      nb_arrive(1 + 2 * (j & 1));  // row j
     }
   } else {
     for (int s = 0; s + 1 < R; ++s) {
-      nb_sync(1 + 2 * (s & 1));                     // row s of R1 is there
-      for (int k = s + 1 + warp; k < R; k += 7) {   // rows s + 2, ...
-        const double rk = R1[s][k];
-        if (lane >= k && lane < R) G[k][lane] = fma(-rk, R1[s][lane], G[k][lane]);
+      nb_sync(1 + 2 * (s & 1));  // row s of U, V is there
+      const ffn us = in ? ff_ld(U[s][lane]) : zero;
+      // this warp's rows k = s + 1 + warp + 7 q (rows s + 2, ...; at most 5): every load first
+      constexpr int KQ = (KG_MAXR + 6) / 7;
+      ffn m[KQ], g[KQ];
+#pragma unroll
+      for (int q = 0; q < KQ; ++q) {
+        const int k = s + 1 + warp + 7 * q;
+        m[q] = (k < R) ? ff_ld(V[s][k]) : zero;
+        g[q] = (k < R && in && lane >= k) ? ff_ld(G[k][lane]) : zero;
       }
-      if (s + 2 < R) nb_arrive(2 + 2 * (s & 1));    // step s
+#pragma unroll
+      for (int q = 0; q < KQ; ++q) {
+        const int k = s + 1 + warp + 7 * q;
+        if (k < R && in && lane >= k) G[k][lane] = ff_st(ff_fms(g[q], m[q], us));
+      }
+      if (s + 2 < R) nb_arrive(2 + 2 * (s & 1));  // step s
     }
     nb_sync(1 + 2 * ((R - 1) & 1));  // the last row
   }
-  __syncthreads();
-  // outputs: R1, S[c][c'] = R1[c][c'] / R1[c][c] (c < c') for the substitution, the flag
-  for (int e = tid; e < KG_MAXR * KG_MAXR; e += 256) {
-    const int c = e / KG_MAXR, d = e % KG_MAXR;
-    w.R1[e] = R1[c][d];
-    w.S[e] = (c < R && d < R && d > c) ? R1[c][d] * w.rinv[c] : 0.0;
-  }
-  if (tid == 0) *w.flag = bad;
 }
 
-// Q1 = Z R1^{-1}: one row (i, k) of Z per warp, z[c] = Ra[i][c] Rb[k][c]; forward substitution
-// q R1 = z with lane = column (x[c'] -= x[c] S[c][c'] after column c, q[c] = x[c] / R1[c][c]).
-// Writes Q1 row-major and transposed.
+// After chol_pipelined (and a __syncthreads): rinv = d^-1/2 (FP64, rsqrt.approx.f64, measured
+// to 53 bits, in the normal range), R1 = diag(rinv) U diag(colscale) (colscale: the
+// equilibration scale to undo, or null; the products in float-float), S[c][c'] = V[c][c']
+// (c < c', for the substitution of the equilibrated rows) and the flag, to global.  The upper
+// triangle is visited as folded pairs (one FP64 addition per entry and output, all lanes
+// live).  rsf, csf: 32 float2 of shared scratch each.
+__device__ __forceinline__ void chol_outputs(float2 (*U)[KG_LD], float2 (*V)[KG_LD], float2* rsf, float2* csf,
+                                             const double* colscale, int R, const KgWork& w, int* bad) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid < 32) {
+    const double d = (lane < R) ? ff_val(U[lane][lane]) : 1.0;
+    const long long b = __double_as_longlong(d);
+    double y;
+    if (b > 0x05CD0B15A491EB84LL && b < 0x7A11A0FC668AAC70LL) {  // 1e-280 < d < 1e280
+      asm("rsqrt.approx.f64 %0, %1;" : "=d"(y) : "d"(d));
+    } else {
+      y = (d > 0.0) ? 1.0 / sqrt(d) : 0.0;
+      if (!(d > 0.0)) *bad = 1;
+    }
+    if (lane >= R) y = 0.0;
+    rsf[lane] = ff_st(ff_from_bits(y));
+    csf[lane] = ff_st(colscale ? ff_from_bits(colscale[lane]) : ff_make(1.0f, 0.0f));
+    w.rinv[lane] = y;
+  }
+  for (int e = tid; e < KG_MAXR * KG_MAXR; e += blockDim.x) {  // strict lower triangles
+    const int c = e / KG_MAXR, d = e % KG_MAXR;
+    if (d < c) {
+      w.R1[e] = 0.0;
+      w.S[e] = 0.0;
+    }
+  }
+  __syncthreads();
+  for (int k = warp; k <= KG_MAXR / 2; k += (int)(blockDim.x >> 5)) {
+    const int c = lane, d = (lane + k) & 31;
+    const int i = min(c, d), j = max(c, d);
+    const bool live = j < R;
+    const double r = live ? ff_val(ff_mul(ff_mul(ff_ld(U[i][j]), ff_ld(rsf[i])), ff_ld(csf[j]))) : 0.0;
+    const double sv = (live && j > i) ? ff_val(V[i][j]) : 0.0;
+    w.R1[i * KG_MAXR + j] = r;
+    w.S[i * KG_MAXR + j] = sv;
+  }
+  if (tid == 0) *w.flag = *bad;
+}
+
+// Equilibrated Gram of an upper triangle T (one CTA of 256 threads per triangle, FP64):
+// G = T^T T, s = sqrt(diag G) (the column norms of any A = Q T), Gf = D^-1 G D^-1 in float-float
+// (upper triangle, row stride 32), s to global.  For triangles that come without a stored Gram
+// (the starting factors, the stand-alone Khatri-Rao QR); not on the sweep's path.
+__global__ void __launch_bounds__(256) tri_gram_kernel(TriPtrs tri, int R, float2* __restrict__ Gf_out,
+                                                        double* __restrict__ s_out) {
+  __shared__ double sT[KG_MAXR][KG_LD], G[KG_MAXR][KG_LD], sil[KG_MAXR];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const double* T = tri.p[blockIdx.x];
+  for (int e = tid; e < KG_MAXR * KG_MAXR; e += 256) {
+    const int i = e / KG_MAXR, c = e % KG_MAXR;
+    sT[i][c] = (i < R && c < R) ? T[i * R + c] : 0.0;
+  }
+  __syncthreads();
+  for (int c = warp; c < KG_MAXR; c += 8) {
+    double g = 0.0;
+    const int imax = min(c, lane);
+    for (int i = 0; i <= imax; ++i) g = fma(sT[i][c], sT[i][lane], g);
+    G[c][lane] = g;
+  }
+  __syncthreads();
+  if (tid < 32) {
+    const double sc = (lane < R) ? sqrt(G[lane][lane]) : 0.0;
+    sil[lane] = (sc > 0.0 && sc < 1e300) ? 1.0 / sc : 0.0;
+    s_out[(size_t)blockIdx.x * KG_MAXR + lane] = sc;
+  }
+  __syncthreads();
+  for (int e = tid; e < KG_MAXR * KG_MAXR; e += 256) {
+    const int i = e / KG_MAXR, j = e % KG_MAXR;
+    Gf_out[(size_t)blockIdx.x * KG_MAXR * KG_MAXR + e] =
+        (i <= j && j < R) ? ff_st(ff_from_bits(G[i][j] * sil[i] * sil[j])) : make_float2(0.0f, 0.0f);
+  }
+}
+
+// Cholesky of the Khatri-Rao product's equilibrated Gram, one CTA of 256 threads.  Row (i, k)
+// of Z = R_a (.) R_b is R_a[i, :] o R_b[k, :], so Z^T Z = (R_a^T R_a) o (R_b^T R_b) =
+// (A_a^T A_a) o (A_b^T A_b) (up to the rounding of the factor QRs), and with the factors'
+// equilibrated Grams Ga, Gb (float-float) and column norms sa, sb:
+// Z^T Z = D (Ga o Gb) D, D = diag(sa sb).  The Gram thus costs one float-float Hadamard product
+// and no pass over the triangles, and this kernel needs only the two Grams: a sweep launches it
+// as soon as the previous factor's Gram exists, before that factor's QR has finished.
+__global__ void __launch_bounds__(256) kg_chol_kernel(const float2* __restrict__ Ga, const float2* __restrict__ Gb,
+                                                       const double* __restrict__ sa, const double* __restrict__ sb,
+                                                       int R, KgWork w) {
+  __shared__ __align__(16) float2 Gf[KG_MAXR][KG_LD], U[KG_MAXR][KG_LD], V[KG_MAXR][KG_LD];
+  __shared__ float2 rsf[KG_MAXR], csf[KG_MAXR];
+  __shared__ double scale[KG_MAXR];
+  __shared__ int bad;
+  const int tid = threadIdx.x, lane = tid & 31;
+  pdl_wait();
+  if (tid < 32) {
+    const double sc = (lane < R) ? sa[lane] * sb[lane] : 0.0;
+    scale[lane] = sc;
+    w.il[lane] = (sc > 0.0 && sc < 1e300) ? 1.0 / sc : 0.0;
+  }
+  if (tid == 0) bad = 0;
+  for (int e = tid; e < KG_MAXR * KG_MAXR; e += 256) {
+    const int i = e / KG_MAXR, j = e % KG_MAXR;
+    Gf[i][j] = (i <= j && j < R) ? ff_st(ff_mul(ff_ld(Ga[e]), ff_ld(Gb[e]))) : make_float2(0.0f, 0.0f);
+    U[i][j] = make_float2(0.0f, 0.0f);
+    V[i][j] = make_float2(0.0f, 0.0f);
+  }
+  __syncthreads();
+  chol_pipelined(Gf, U, V, R, &bad);
+  __syncthreads();
+  chol_outputs(U, V, rsf, csf, scale, R, w, &bad);
+}
+
+// Factor route, Gram and Cholesky on one 16-CTA cluster of 256 threads: CTA r adds up folded
+// row k = r (CTA 0 also k = 16) of the block partials hpart[blk][k][c] = sum a^_c a^_(c+k)%32
+// (warp w takes blocks w, w + 8, ...; fixed order) and stores G[c][(c+k)%32] and its mirror into
+// CTA 0.  CTA 0 then forms lambda = sqrt(diag G), G = D^-1 G D^-1 (also stored, with unit column
+// norms, as the new factor's Gram for the following Khatri-Rao QRs), the fit terms from the
+// finish-prep partials, and the Cholesky.
+__global__ void __cluster_dims__(KG_CL, 1, 1) __launch_bounds__(256)
+    fg_chol_kernel(const double* __restrict__ hpart, int nblk, int R, const double* __restrict__ fitpart,
+                   double* __restrict__ lambda, double* __restrict__ fit_terms, float2* __restrict__ gram_out,
+                   double* __restrict__ colnorm_out, KgWork w) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  __shared__ __align__(16) double G[KG_MAXR][KG_LD];
+  __shared__ __align__(16) float2 Gf[KG_MAXR][KG_LD], U[KG_MAXR][KG_LD], V[KG_MAXR][KG_LD];
+  __shared__ double red[8][32], scale[KG_MAXR], il[KG_MAXR];
+  __shared__ float2 ilf[KG_MAXR], rsf[KG_MAXR], csf[KG_MAXR];
+  __shared__ int bad;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) bad = 0;
+  for (int k = rank; k < KG_GK; k += KG_CL) {
+    const double* hp = hpart + (size_t)k * 32 + lane;
+    const size_t bs = (size_t)KG_GK * 32;
+    // 16 blocks per pass with every load issued before the adds (fixed order)
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    for (int b0 = warp; b0 < nblk; b0 += 128) {
+      double x[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int b = b0 + 8 * u;
+        x[u] = (b < nblk) ? hp[(size_t)b * bs] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 16; u += 4) {
+        a0 += x[u];
+        a1 += x[u + 1];
+        a2 += x[u + 2];
+        a3 += x[u + 3];
+      }
+    }
+    red[warp][lane] = (a0 + a1) + (a2 + a3);
+    __syncthreads();
+    if (warp == 0) {
+      const double g = ((red[0][lane] + red[1][lane]) + (red[2][lane] + red[3][lane])) +
+                       ((red[4][lane] + red[5][lane]) + (red[6][lane] + red[7][lane]));
+      const int c = lane, d = (lane + k) & 31;
+      double* G0 = cluster.map_shared_rank(&G[0][0], 0);
+      G0[c * KG_LD + d] = g;
+      G0[d * KG_LD + c] = g;
+    }
+    __syncthreads();
+  }
+  cluster.sync();  // all of G is in CTA 0; the other CTAs are done
+  if (rank != 0) return;
+  if (warp == 1) {
+    // <V0, V^> and ||V^||^2 from the finish-prep block partials (the Householder finish's order)
+    double a = 0.0, b = 0.0;
+    for (int k = lane; k < nblk; k += 32) {
+      a += fitpart[2 * k];
+      b += fitpart[2 * k + 1];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(FULL, a, o);
+      b += __shfl_xor_sync(FULL, b, o);
+    }
+    if (lane == 0) {
+      fit_terms[0] = a;
+      fit_terms[1] = b;
+    }
+  }
+  equilibrate_ff(G, Gf, U, V, scale, il, ilf, R, w);  // scale = lambda, il = 1 / lambda
+  if (tid < R) lambda[tid] = scale[tid];
+  // the Gram of A = A^ / lambda (unit columns) for the next Khatri-Rao QRs
+  if (gram_out) {
+    for (int e = tid; e < KG_MAXR * KG_MAXR; e += 256) {
+      const int i = e / KG_MAXR, j = e % KG_MAXR;
+      gram_out[e] = (i <= j) ? Gf[i][j] : make_float2(0.0f, 0.0f);
+    }
+    if (tid < 32) colnorm_out[tid] = (tid < R) ? 1.0 : 0.0;
+  }
+  chol_pipelined(Gf, U, V, R, &bad);
+  __syncthreads();
+  chol_outputs(U, V, rsf, csf, nullptr, R, w, &bad);
+}
+
+// Factor route, Q1 = A R1^{-1} with A = A^ / lambda: one row of A^ per warp (A also written
+// out), the forward substitution of kg_q1_kernel.
+__global__ void __launch_bounds__(128) fg_q1_kernel(const double* __restrict__ Ahat, int I, int R, KgWork w,
+                                                     double* __restrict__ Aout) {
+  const int lane = threadIdx.x & 31;
+  const int t = blockIdx.x * 4 + (threadIdx.x >> 5);
+  pdl_wait();
+  if (t >= I) return;
+  double scol[KG_MAXR];
+#pragma unroll
+  for (int c = 0; c < KG_MAXR; ++c) scol[c] = (c < R && lane > c && lane < R) ? w.S[c * KG_MAXR + lane] : 0.0;
+  const double ri = (lane < R) ? w.rinv[lane] : 0.0;
+  double x = 0.0;
+  if (lane < R) {
+    x = Ahat[(size_t)t * R + lane] * w.il[lane];
+    Aout[(size_t)t * R + lane] = x;
+  }
+#pragma unroll
+  for (int c = 0; c < KG_MAXR - 1; ++c) {
+    if (c + 1 < R) {
+      const double xc = __shfl_sync(FULL, x, c);
+      x = fma(-xc, scol[c], x);
+    }
+  }
+  if (lane < R) {
+    const double q = x * ri;
+    w.Q1[(size_t)t * R + lane] = q;
+    w.Q1T[(size_t)lane * I + t] = q;
+  }
+}
+
+// Q1 = Z R1^{-1} = (Z D^-1) R1e^{-1} (R1e: the equilibrated factor, D = diag(||Z e_c||)): one row
+// (i, k) of Z per warp, z[c] = Ra[i][c] Rb[k][c] / D[c]; forward substitution q R1e = z with
+// lane = column (x[c'] -= x[c] S[c][c'] after column c, q[c] = x[c] / R1e[c][c]).  Writes Q1
+// row-major and transposed.
 __global__ void __launch_bounds__(128) kg_q1_kernel(const double* __restrict__ Ra, const double* __restrict__ Rb,
                                                      int R, KgWork w) {
   const int lane = threadIdx.x & 31;
   const int M = R * R;
   const int t = blockIdx.x * 4 + (threadIdx.x >> 5);
+  pdl_wait();
   if (t >= M) return;
   // column `lane` of S in registers (every load issued up front)
   double scol[KG_MAXR];
@@ -177,7 +536,8 @@ __global__ void __launch_bounds__(128) kg_q1_kernel(const double* __restrict__ R
   for (int c = 0; c < KG_MAXR; ++c) scol[c] = (c < R && lane > c && lane < R) ? w.S[c * KG_MAXR + lane] : 0.0;
   const double ri = (lane < R) ? w.rinv[lane] : 0.0;
   const int i = t / R, k = t - i * R;
-  double x = (lane < R) ? Ra[i * R + lane] * Rb[k * R + lane] : 0.0;
+  // row (i, k) of Z, equilibrated like the Gram (column c times 1 / ||Z e_c||)
+  double x = (lane < R) ? Ra[i * R + lane] * Rb[k * R + lane] * w.il[lane] : 0.0;
 #pragma unroll
   for (int c = 0; c < KG_MAXR - 1; ++c) {
     if (c + 1 < R) {
@@ -194,11 +554,11 @@ __global__ void __launch_bounds__(128) kg_q1_kernel(const double* __restrict__ R
 
 // E = Q1^T Q1 - I and F = striu(E) + diag(E) / 2: one warp per upper entry (c, d), lanes over
 // the rows (coalesced through Q1^T); raises the fallback flag if |E[c][d]| > kEMax.
-__global__ void __launch_bounds__(128) kg_e_kernel(int R, KgWork w) {
+__global__ void __launch_bounds__(128) kg_e_kernel(int M, int R, KgWork w) {
   const int lane = threadIdx.x & 31;
-  const int M = R * R;
   const int npair = R * (R + 1) / 2;
   const int gw = blockIdx.x * 4 + (threadIdx.x >> 5);
+  pdl_wait();
   if (gw >= npair) return;
   int c = 0, rem = gw;
   while (rem >= R - c) {
@@ -208,18 +568,18 @@ __global__ void __launch_bounds__(128) kg_e_kernel(int R, KgWork w) {
   const int d = c + rem;
   const double* qc = w.Q1T + (size_t)c * M;
   const double* qd = w.Q1T + (size_t)d * M;
-  // eight rows per lane per pass, every load issued before the products
+  // 32 rows per lane per pass (1024 rows), every load issued before the products
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int t0 = 0; t0 < M; t0 += 256) {
-    double xc[8], xd[8];
+  for (int t0 = 0; t0 < M; t0 += 1024) {
+    double xc[32], xd[32];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < 32; ++u) {
       const int t = t0 + 32 * u + lane;
       xc[u] = (t < M) ? qc[t] : 0.0;
       xd[u] = (t < M) ? qd[t] : 0.0;
     }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) acc[u & 3] = fma(xc[u], xd[u], acc[u & 3]);
+    for (int u = 0; u < 32; ++u) acc[u & 3] = fma(xc[u], xd[u], acc[u & 3]);
   }
   double s = (acc[0] + acc[1]) + (acc[2] + acc[3]);
 #pragma unroll
@@ -232,12 +592,15 @@ __global__ void __launch_bounds__(128) kg_e_kernel(int R, KgWork w) {
 }
 
 // Q0 = Q1 (I - F) (one row per warp, lane = column: q0[c] = q1[c] - sum_{k <= c} q1[k] F[k][c]),
-// and, on the first R warps of the grid, row c of R0 = (I + F) R1.
-__global__ void __launch_bounds__(128) kg_q0_kernel(int R, KgWork w, double* __restrict__ Q0, float* __restrict__ Q0f,
-                                                     double* __restrict__ R0) {
+// and, on the first R warps of the grid, row c of R0 = (I + F) R1.  Optional copies: Q0f
+// (FP32) and Qt, Q0^T split into bf16 hi / lo for the tensor cores (Qt[2][Rp][Kp], the layout
+// the Householder finish writes).
+__global__ void __launch_bounds__(128) kg_q0_kernel(int M, int R, KgWork w, double* __restrict__ Q0,
+                                                     float* __restrict__ Q0f, double* __restrict__ R0,
+                                                     __nv_bfloat16* __restrict__ Qt, int Rp, int64_t Kp) {
   const int lane = threadIdx.x & 31;
-  const int M = R * R;
   const int t = blockIdx.x * 4 + (threadIdx.x >> 5);
+  pdl_wait();
   if (t >= M) return;
   double fcol[KG_MAXR];  // F[k][lane], k <= lane
 #pragma unroll
@@ -267,14 +630,69 @@ __global__ void __launch_bounds__(128) kg_q0_kernel(int R, KgWork w, double* __r
   if (lane < R) {
     Q0[(size_t)t * R + lane] = q;
     if (Q0f) Q0f[(size_t)t * R + lane] = (float)q;
+    if (Qt) {
+      const float q32 = (float)q;
+      const __nv_bfloat16 h = __float2bfloat16_rn(q32);
+      const size_t e = (size_t)lane * Kp + t;
+      Qt[e] = h;
+      Qt[(size_t)Rp * Kp + e] = __float2bfloat16_rn(q32 - __bfloat162float(h));
+    }
   }
+}
+
+// the 16-CTA cluster needs the non-portable size allowed, once per device
+cudaError_t kg_cluster_attributes() {
+  static bool done[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (done[dev]) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(fg_chol_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) return e;
+  done[dev] = true;
+  return cudaSuccess;
 }
 
 }  // namespace
 
-size_t krp_gram_work_doubles(int R) {
-  const size_t M = (size_t)R * R;
-  return 3 * (size_t)KG_MAXR * KG_MAXR + KG_MAXR + 2 * M * R + 1;
+size_t krp_gram_work_doubles(int R) { return kg_work_doubles((int64_t)R * R, R); }
+size_t factor_gram_work_doubles(int64_t Imax, int R) { return kg_work_doubles(Imax, R); }
+int* gram_fallback_counter(double* gram_work) { return reinterpret_cast<int*>(gram_work) + 1; }
+
+cudaError_t launch_tri_gram(const double* T, int R, float2* Gf, double* s, cudaStream_t st) {
+  if (R < 1 || R > KG_MAXR) return cudaErrorInvalidValue;
+  TriPtrs t{};
+  t.p[0] = T;
+  tri_gram_kernel<<<1, 256, 0, st>>>(t, R, Gf, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_krp_chol(const float2* Ga, const float2* Gb, const double* sa, const double* sb, int R,
+                            double* gram_work, cudaStream_t st) {
+  if (R < 1 || R > KG_MAXR) return cudaErrorInvalidValue;
+  const KgWork w = kg_views(gram_work, R, (int64_t)R * R);
+  return launch_pdl(kg_chol_kernel, dim3(1), dim3(256), 0, st, Ga, Gb, sa, sb, R, w);
+}
+
+cudaError_t launch_krp_rows(const ZPlan& plan2, const double* Ra, const double* Rb, double* Q0, double* R0,
+                            double* gram_work, double* qr_work, unsigned int* dev_status, cudaStream_t st,
+                            float* Q0f) {
+  const int R = plan2.R;
+  if (plan2.m != 2 || R < 1 || R > KG_MAXR || plan2.M != (int64_t)R * R) return cudaErrorInvalidValue;
+  const int M = R * R;
+  const KgWork w = kg_views(gram_work, R, M);
+  cudaError_t e = launch_pdl(kg_q1_kernel, dim3((M + 3) / 4), dim3(128), 0, st, Ra, Rb, R, w);
+  if (e != cudaSuccess) return e;
+  const int npair = R * (R + 1) / 2;
+  e = launch_pdl(kg_e_kernel, dim3((npair + 3) / 4), dim3(128), 0, st, M, R, w);
+  if (e != cudaSuccess) return e;
+  e = launch_pdl(kg_q0_kernel, dim3((M + 3) / 4), dim3(128), 0, st, M, R, w, Q0, Q0f, R0, (__nv_bfloat16*)nullptr, 0,
+                 (int64_t)0);
+  if (e != cudaSuccess) return e;
+  // the Householder staircase QR, which returns at once unless the flag was raised
+  TriPtrs t2{};
+  t2.p[0] = Ra;
+  t2.p[1] = Rb;
+  return launch_krp_qr(plan2, t2, Q0, R0, qr_work, dev_status, st, Q0f, w.flag);
 }
 
 cudaError_t launch_krp_qr_gram(const ZPlan& plan2, const double* Ra, const double* Rb, double* Q0, double* R0,
@@ -282,34 +700,54 @@ cudaError_t launch_krp_qr_gram(const ZPlan& plan2, const double* Ra, const doubl
                                float* Q0f) {
   const int R = plan2.R;
   if (plan2.m != 2 || R < 1 || R > KG_MAXR || plan2.M != (int64_t)R * R) return cudaErrorInvalidValue;
-  const KgWork w = kg_views(gram_work, R);
-  const int M = R * R;
-  static bool attr_done[64] = {};  // per device
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-  if (!attr_done[dev]) {
-    cudaError_t ea = cudaFuncSetAttribute(kg_chol_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (ea != cudaSuccess) return ea;
-    attr_done[dev] = true;
-  }
-  kg_chol_kernel<<<KG_CL, 256, 0, st>>>(Ra, Rb, R, w);
+  const KgWork w = kg_views(gram_work, R, (int64_t)R * R);
+  TriPtrs t{};
+  t.p[0] = Ra;
+  t.p[1] = Rb;
+  tri_gram_kernel<<<2, 256, 0, st>>>(t, R, w.ga, w.sa);  // ga, gb and sa, sb are adjacent
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  kg_q1_kernel<<<(M + 3) / 4, 128, 0, st>>>(Ra, Rb, R, w);
-  e = cudaGetLastError();
+  e = launch_krp_chol(w.ga, w.gb, w.sa, w.sb, R, gram_work, st);
+  if (e != cudaSuccess) return e;
+  return launch_krp_rows(plan2, Ra, Rb, Q0, R0, gram_work, qr_work, dev_status, st, Q0f);
+}
+
+cudaError_t launch_finish_gram_chol(const double* hpart, const double* fitpart, int nblk, int64_t I, int R,
+                                    FinishOut out, double* gram_work, float2* gram_out, double* colnorm_out,
+                                    cudaStream_t st) {
+  if (I < 1 || I > (int64_t(1) << 30) || R < 1 || R > KG_MAXR || nblk < 1) return cudaErrorInvalidValue;
+  if ((gram_out == nullptr) != (colnorm_out == nullptr)) return cudaErrorInvalidValue;
+  const KgWork w = kg_views(gram_work, R, I);
+  cudaError_t e = kg_cluster_attributes();
+  if (e != cudaSuccess) return e;
+  fg_chol_kernel<<<KG_CL, 256, 0, st>>>(hpart, nblk, R, fitpart, out.lambda, out.fit_terms, gram_out, colnorm_out, w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finish_gram_rows(const double* Ahat, const double* fitpart, int nblk, int64_t I, int R,
+                                    FinishOut out, double* gram_work, double* qr_work, unsigned int* dev_status,
+                                    cudaStream_t st) {
+  if (I < 1 || I > (int64_t(1) << 30) || R < 1 || R > KG_MAXR || nblk < 1) return cudaErrorInvalidValue;
+  const int M = (int)I;
+  const KgWork w = kg_views(gram_work, R, M);
+  cudaError_t e = launch_pdl(fg_q1_kernel, dim3((M + 3) / 4), dim3(128), 0, st, Ahat, M, R, w, out.A);
   if (e != cudaSuccess) return e;
   const int npair = R * (R + 1) / 2;
-  kg_e_kernel<<<(npair + 3) / 4, 128, 0, st>>>(R, w);
-  e = cudaGetLastError();
+  e = launch_pdl(kg_e_kernel, dim3((npair + 3) / 4), dim3(128), 0, st, M, R, w);
   if (e != cudaSuccess) return e;
-  kg_q0_kernel<<<(M + 3) / 4, 128, 0, st>>>(R, w, Q0, Q0f, R0);
-  e = cudaGetLastError();
+  e = launch_pdl(kg_q0_kernel, dim3((M + 3) / 4), dim3(128), 0, st, M, R, w, out.Q, out.Qf, out.Rn, out.Qt, out.Rp,
+                 out.Kp);
   if (e != cudaSuccess) return e;
-  // the Householder staircase QR, which returns at once unless the flag was raised
-  TriPtrs t2{};
-  t2.p[0] = Ra;
-  t2.p[1] = Rb;
-  return launch_krp_qr(plan2, t2, Q0, R0, qr_work, dev_status, st, Q0f, w.flag);
+  // the Householder finish, which returns at once unless the flag was raised
+  return launch_mode_finish(Ahat, fitpart, nblk, I, R, out, qr_work, dev_status, st, w.flag);
+}
+
+cudaError_t launch_finish_gram(const double* Ahat, const double* hpart, const double* fitpart, int nblk, int64_t I,
+                               int R, FinishOut out, double* gram_work, double* qr_work, unsigned int* dev_status,
+                               cudaStream_t st) {
+  cudaError_t e = launch_finish_gram_chol(hpart, fitpart, nblk, I, R, out, gram_work, nullptr, nullptr, st);
+  if (e != cudaSuccess) return e;
+  return launch_finish_gram_rows(Ahat, fitpart, nblk, I, R, out, gram_work, qr_work, dev_status, st);
 }
 
 }  // namespace cpqr

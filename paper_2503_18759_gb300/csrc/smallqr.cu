@@ -105,7 +105,8 @@ struct QrParams {
   float* Qf;  // FP32 copy of Q (may be null)
   double* Rout;
   unsigned int* status;
-  const int* run_if;  // when set: the QR runs only if *run_if != 0 (a guarded fallback)
+  int* run_if;  // when set: the QR runs only if run_if[0] != 0 (a guarded fallback) and counts
+                // its runs in run_if[1]
 };
 
 struct SmemLayout {
@@ -221,7 +222,10 @@ __global__ void __launch_bounds__(NT, 1) qr_cluster_kernel(QrParams p) {
   double (*VT)[CPQR_MAXR] = reinterpret_cast<double (*)[CPQR_MAXR]>(&sm.big[RR]);
 
   QR_PHASE(0);
-  if (p.run_if && *(volatile const int*)p.run_if == 0) return;  // every CTA reads the same flag
+  if (p.run_if) {
+    if (*(volatile const int*)p.run_if == 0) return;  // every CTA reads the same flag
+    if (rank == 0 && tid == 0) atomicAdd(p.run_if + 1, 1);
+  }
   // mbarriers of the st.async exchanges, armed for their first phase before any peer can send
   if (tid == 0) {
     for (int b = 0; b < 3; ++b) tc::mbar_init(smem_u32(&sm.bar[b]), 1);
@@ -509,19 +513,25 @@ __global__ void __launch_bounds__(NT, 1) qr_cluster_kernel(QrParams p) {
 // are added in a fixed order (FP32 slices in FP32: the split path's V carries the split TTMs'
 // ~2^-16 relative error), V^ = (1 + beta) V0 - alpha beta V1, and A^ R0^T = V^ is solved by
 // back substitution with lane = column.  Each block also adds up <V0, V^> and ||V^||^2 over
-// its rows; the finish kernel adds the block partials.
+// its rows; the finish kernel adds the block partials.  With hpart set, each block also writes
+// its rows' share of the Gram A^T A^ folded into 17 x 32 entries: hpart[blk][k][c] =
+// sum_i a^_ic a^_i,(c+k)%32 for k = 0..16 (every unordered pair once, k = 16 twice).
 constexpr int PREP_WARPS = 4;
+constexpr int PREP_GK = 17;  // folded Gram entries per lane
 
 template <typename TP>
 __global__ void __launch_bounds__(PREP_WARPS * 32) finish_prep_kernel(const TP* __restrict__ part, int nparts, int I,
                                                                       int C, int R, const double* __restrict__ R0,
                                                                       double c0, double c1, double* __restrict__ Ahat,
                                                                       double* __restrict__ fitpart,
+                                                                      double* __restrict__ hpart,
                                                                       unsigned int* status) {
   __shared__ double sM[CPQR_MAXR][CPQR_MAXR + 1];  // sM[l][c] = R0[l][c] / R0[c][c], l < c
   __shared__ double rdiag[CPQR_MAXR];
   __shared__ double red[PREP_WARPS][2];
+  __shared__ double hred[PREP_WARPS][PREP_GK][32];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  pdl_wait();
   if (tid < R) {
     const double d = R0[tid * R + tid];
     rdiag[tid] = (d != 0.0) ? 1.0 / d : 0.0;
@@ -533,6 +543,9 @@ __global__ void __launch_bounds__(PREP_WARPS * 32) finish_prep_kernel(const TP* 
   const bool ext = (C == 2 * R);
   const size_t n = (size_t)I * C;
   double f_in = 0.0, f_nn = 0.0;
+  double h[PREP_GK];
+#pragma unroll
+  for (int k = 0; k < PREP_GK; ++k) h[k] = 0.0;
   const int i = blockIdx.x * PREP_WARPS + warp;
   if (i < I) {
     double v0 = 0.0, v1 = 0.0;
@@ -569,6 +582,14 @@ __global__ void __launch_bounds__(PREP_WARPS * 32) finish_prep_kernel(const TP* 
       if (lane < c) res = fma(-sM[lane][c], x, res);
     }
     if (lane < R) Ahat[(size_t)i * R + lane] = ahat;
+    if (hpart) {
+#pragma unroll
+      for (int k = 0; k < PREP_GK; ++k) h[k] = ahat * __shfl_sync(FULL, ahat, (lane + k) & 31);
+    }
+  }
+  if (hpart) {
+#pragma unroll
+    for (int k = 0; k < PREP_GK; ++k) hred[warp][k][lane] = h[k];
   }
   for (int o = 16; o > 0; o >>= 1) {
     f_in += __shfl_xor_sync(FULL, f_in, o);
@@ -587,6 +608,15 @@ __global__ void __launch_bounds__(PREP_WARPS * 32) finish_prep_kernel(const TP* 
     }
     fitpart[2 * blockIdx.x] = a;
     fitpart[2 * blockIdx.x + 1] = b;
+  }
+  if (hpart) {
+    for (int e = tid; e < PREP_GK * 32; e += PREP_WARPS * 32) {
+      const int k = e >> 5, c = e & 31;
+      double a = 0.0;
+#pragma unroll
+      for (int w = 0; w < PREP_WARPS; ++w) a += hred[w][k][c];
+      hpart[(size_t)blockIdx.x * PREP_GK * 32 + e] = a;
+    }
   }
 }
 
@@ -718,7 +748,7 @@ cudaError_t launch_house_qr(const double* A, int64_t M, int R, double* Q, double
 }
 
 cudaError_t launch_krp_qr(const ZPlan& plan, TriPtrs Rs, double* Q0, double* R0, double* work,
-                          unsigned int* dev_status, cudaStream_t st, float* Q0f, const int* run_if) {
+                          unsigned int* dev_status, cudaStream_t st, float* Q0f, int* run_if) {
   QrParams p{};
   p.mode = MODE_KRP;
   if (plan.M > (int64_t(1) << 30)) return cudaErrorInvalidValue;
@@ -834,22 +864,21 @@ int finish_prep_blocks(int64_t I) { return (int)((I + PREP_WARPS - 1) / PREP_WAR
 
 template <typename TP>
 cudaError_t launch_finish_prep(const TP* parts, int nparts, int64_t I, int C, int R, const double* R0, double beta,
-                               double alpha, double* Ahat, double* fitpart, unsigned int* dev_status,
-                               cudaStream_t st) {
+                               double alpha, double* Ahat, double* fitpart, double* hpart,
+                               unsigned int* dev_status, cudaStream_t st) {
   if (I < 1 || I > (int64_t(1) << 30) || R < 1 || R > CPQR_MAXR || (C != R && C != 2 * R) || nparts < 1)
     return cudaErrorInvalidValue;
   const double c0 = 1.0 + beta, c1 = -alpha * beta;
-  finish_prep_kernel<TP><<<finish_prep_blocks(I), PREP_WARPS * 32, 0, st>>>(parts, nparts, (int)I, C, R, R0, c0, c1,
-                                                                          Ahat, fitpart, dev_status);
-  return cudaGetLastError();
+  return launch_pdl(finish_prep_kernel<TP>, dim3(finish_prep_blocks(I)), dim3(PREP_WARPS * 32), 0, st, parts, nparts,
+                    (int)I, C, R, R0, c0, c1, Ahat, fitpart, hpart, dev_status);
 }
 template cudaError_t launch_finish_prep<double>(const double*, int, int64_t, int, int, const double*, double, double,
-                                                double*, double*, unsigned int*, cudaStream_t);
+                                                double*, double*, double*, unsigned int*, cudaStream_t);
 template cudaError_t launch_finish_prep<float>(const float*, int, int64_t, int, int, const double*, double, double,
-                                               double*, double*, unsigned int*, cudaStream_t);
+                                               double*, double*, double*, unsigned int*, cudaStream_t);
 
 cudaError_t launch_mode_finish(const double* Ahat, const double* fitpart, int nfit, int64_t I, int R, FinishOut out,
-                               double* work, unsigned int* dev_status, cudaStream_t st) {
+                               double* work, unsigned int* dev_status, cudaStream_t st, int* run_if) {
   QrParams p{};
   p.mode = MODE_FINISH;
   if (I > (int64_t(1) << 30)) return cudaErrorInvalidValue;
@@ -865,6 +894,7 @@ cudaError_t launch_mode_finish(const double* Ahat, const double* fitpart, int nf
   p.Qf = out.Qf;
   p.Rout = out.Rn;
   p.status = dev_status;
+  p.run_if = run_if;
   return run(p, st);
 }
 

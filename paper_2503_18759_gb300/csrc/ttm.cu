@@ -260,6 +260,7 @@ __global__ void __launch_bounds__(256) leaf_v_kernel(const TY* __restrict__ Y, i
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc[a][b] = TA(0);
+  pdl_wait();
   // the next chunk's operands are loaded into registers while the current one is multiplied
   TY ybuf[NLY];
   TQ qbuf[NLQ];
@@ -616,9 +617,9 @@ cudaError_t launch_leaf_v(const TY* Y, int64_t P, int64_t I, int64_t S, const TQ
   const int64_t ktiles = (K + kchunk - 1) / kchunk;  // <= splits: fits the work slices
   dim3 grid((unsigned)itiles, (unsigned)ktiles);
   using TA = typename std::conditional<std::is_same<TY, double>::value, double, float>::type;
-  leaf_v_kernel<TY, TA, TQ><<<grid, 256, 0, st>>>(Y, (int)P, (int)I, (int)S, Q0, Q0prev, R, C, (int)kchunk, work);
   *nparts = (int)ktiles;
-  return cudaGetLastError();
+  return launch_pdl(leaf_v_kernel<TY, TA, TQ>, grid, dim3(256), 0, st, Y, (int)P, (int)I, (int)S, Q0, Q0prev, R, C,
+                    (int)kchunk, work);
 }
 
 template cudaError_t launch_leaf_v<double, double>(const double*, int64_t, int64_t, int64_t, const double*,

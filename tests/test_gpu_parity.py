@@ -103,10 +103,10 @@ def test_krp_qr(m, R):
     assert np.allclose(Q0.cpu().numpy(), Q0r, atol=1e-11)
 
 
-def _run_gpu(prob, tree, extrap, beta_fixed, sweeps, prec=b.PREC_FP64):
+def _run_gpu(prob, tree, extrap, beta_fixed, sweeps, prec=b.PREC_FP64, route=b.QR_GRAM):
     x64 = prob.X.dtype == np.float64
     X = _dev(prob.X)
-    opts = b.make_options(tree=tree, prec=prec, extrap=extrap, beta_fixed=beta_fixed)
+    opts = b.make_options(tree=tree, prec=prec, extrap=extrap, beta_fixed=beta_fixed, qr_route=route)
     with b.Decomposition(prob.dims, prob.R, X.data_ptr(), x64, prob.A0, opts) as d:
         fits = d.sweep(sweeps)
         A, lam, Q, Rn = d.factors()
@@ -137,18 +137,56 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("route", [b.QR_GRAM, b.QR_HOUSEHOLDER], ids=["gram", "householder"])
 @pytest.mark.parametrize("name,cfg,tree,extrap,beta,sweeps", CASES, ids=[c[0] for c in CASES])
-def test_fp64_solver_matches_oracle(name, cfg, tree, extrap, beta, sweeps):
+def test_fp64_solver_matches_oracle(name, cfg, tree, extrap, beta, sweeps, route):
+    """Both QR routes of a sweep against the oracle (Householder QRs throughout); on these
+    well-conditioned problems the Gram route's guard never hands a QR to the Householder QR."""
     cfg = dict(cfg)
     prob = inputs.make_problem(name, cfg.pop("dims"), cfg.pop("R"), seed=3, **cfg)
-    fits, A, lam, Q, Rn, st = _run_gpu(prob, tree, extrap, beta, sweeps)
+    fits, A, lam, Q, Rn, st = _run_gpu(prob, tree, extrap, beta, sweeps, route=route)
     ref = _run_oracle(prob, tree, extrap, beta, sweeps)
     assert np.max(np.abs(fits - np.array(ref.fits))) <= 1e-10, (fits, ref.fits)
     for n in range(len(prob.dims)):
         assert o.subspace_sine(A[n], ref.A[n]) <= 1e-10
         assert np.allclose(A[n], ref.A[n], atol=1e-8)
+        assert np.abs(Q[n].T @ Q[n] - np.eye(prob.R)).max() < 1e-13
+        assert np.allclose(Q[n] @ Rn[n], A[n], atol=1e-13)
+        assert np.all(np.diag(Rn[n]) > 0)
     assert np.allclose(lam, ref.lam, rtol=1e-8)
     assert st.ttm_flops == ref.flops
+    assert st.qr_fallbacks == 0
+
+
+@pytest.mark.parametrize("route", [b.QR_GRAM, b.QR_HOUSEHOLDER], ids=["gram", "householder"])
+def test_factor_qr_guard_hands_collinear_factor_to_householder(route):
+    """Mode 0's true factor has two columns 1e-7 apart (kappa(A_0) ~ 1e7, so the Gram route's
+    orthogonality correction would be ~1e-2): its factor QR must go to the Householder QR, while
+    the other modes' (well-conditioned) QRs stay on the Gram route.  Both routes track the
+    oracle; the least-squares problems themselves stay well-conditioned (the Khatri-Rao Grams
+    of the other modes are), so the fit and every normalised factor agree to rounding."""
+    dims, R, seed = [30, 28, 26], 5, 11
+    B = inputs.gaussian_factors(dims, R, seed)
+    g = np.random.default_rng(seed)
+    B[0][:, 1] = B[0][:, 0] + 1e-7 * g.standard_normal(dims[0])
+    X = inputs.add_noise(inputs.cp_dense(B), 1e-6, seed)
+    prob = inputs.Problem("collinear_mode0", dims, R, np.ascontiguousarray(X), inputs.init_factors(dims, R, seed),
+                          B, 1e-6, seed)
+    sweeps = 4
+    fits, A, lam, Q, Rn, st = _run_gpu(prob, b.TREE_RESTRUCTURED, b.EXTRAP_NONE, 0.0, sweeps, route=route)
+    ref = _run_oracle(prob, b.TREE_RESTRUCTURED, b.EXTRAP_NONE, 0.0, sweeps)
+    assert np.linalg.cond(A[0]) > 1e6
+    assert np.max(np.abs(fits - np.array(ref.fits))) <= 1e-10, (fits, ref.fits)
+    for n in range(3):
+        assert np.allclose(A[n], ref.A[n], atol=1e-8), (n, np.abs(A[n] - ref.A[n]).max())
+        assert np.abs(Q[n].T @ Q[n] - np.eye(R)).max() < 1e-13
+        assert np.allclose(Q[n] @ Rn[n], A[n], atol=1e-13)
+    if route == b.QR_GRAM:
+        # mode 0's factor QR every sweep; another factor may come close to kappa ~ 1e4 on the way
+        # (the guard's 1e-8 on kappa^2 2^-53) and be handed over too
+        assert st.qr_fallbacks >= sweeps
+    else:
+        assert st.qr_fallbacks == 0
 
 
 def test_cube60_fifty_sweeps_parity():
