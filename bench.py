@@ -37,7 +37,6 @@ WORKLOAD = "cube400_r32_c09"
 # kernel changed after its capture
 TTM_TC_TRAFFIC = 270.5e6    # ttm_tc_kernel<0>, 1 x 400 x 160000 -> R = 32 (256.1 MB read + 14.4 MB written)
 TTM_DEEP_TRAFFIC = 20.6e6   # ttm_tc_kernel<1>, 12800 x 400 x 1 -> R = 32 (20.6 MB read, output left in L2)
-QR_TRAFFIC = 168.2e3        # qr_cluster_kernel<16>, 400 x 32 plain QR (168 KB read, output left in L2)
 # whole-GPU FP64 DFMA rate measured by a probe on the GB300s (TFLOP/s)
 FP64_PEAK_TFLOPS = 1.20
 
@@ -230,28 +229,26 @@ def run_ours(args, rank, world, local_rank):
                              "unit": "TFLOP/s", "kernel": "ttm_kernel<float,double,double> (first-level TTM, FP64)",
                              "peak_kind": "FP64 DFMA rate measured by a probe", "alg_flops_per_launch": flops})
             roof_ttm["frac"] = roof_ttm["achieved"] / roof_ttm["peak"]
-        # the factor-QR finish kernel (Alg. 3 lines 8-10 on one 16-CTA cluster): FP64, latency bound
+        # the mode update after V (Alg. 3 lines 8-10: eq. 19, the R0^{-T} solve, normalisation and the
+        # factor QR by the guarded Gram route): FP64 and float-float, bound by the latency of its
+        # serial parts (the 32-step back substitution, the 32-step Cholesky), not by a roof
         n_qr = st.n_bucket[4]
         qr_ms = st.ms_bucket[4] / max(n_qr, 1)
         I, R = prob.dims[0], prob.R
-        qr_flops = 5 * I * R * R - (2 * R ** 3) // 3
+        # solve I R^2, Gram I R^2, Cholesky R^3 / 3, substitution I R^2, E I R^2, correction I R^2
+        qr_flops = 5 * I * R * R + R ** 3 // 3
         roof_qr = {"bound": "alu", "achieved": qr_flops / (qr_ms * 1e-3) / 1e12 if n_qr else None,
-                   "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "traffic": QR_TRAFFIC,
-                   "kernel": "finish_prep_kernel + qr_cluster_kernel<16> (eq. 19, R0^{-T} solve, normalise, "
-                             "Householder QR, Q)",
-                   "peak_kind": "FP64 DFMA rate of the whole GPU measured by a probe; the QR runs on one "
-                                "16-SM cluster and is bound by the latency of its 32 serial Householder columns",
-                   "alg_flops_per_launch": qr_flops, "avg_launch_ms": qr_ms, "launches": int(n_qr),
-                   "cluster_peak_tflops": FP64_PEAK_TFLOPS * 16 / 152,
-                   "traffic_note": "ncu capture of the same cluster kernel on the 400 x 32 plain QR"}
-        if n_qr:
-            roof_qr["frac"] = roof_qr["achieved"] / roof_qr["peak"]
-            roof_qr["frac_of_cluster_peak"] = roof_qr["achieved"] / roof_qr["cluster_peak_tflops"]
-        else:
-            roof_qr["frac"] = None
-        # dominant kernel by device time per sweep
-        qr_share = st.ms_bucket[4] + st.ms_bucket[2]
-        roof = roof_qr if (prec == b.PREC_SPLIT_BF16 and qr_share > st.ms_bucket[0]) else roof_ttm
+                   "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "traffic": None,
+                   "kernel": "finish_prep_kernel, fg_chol_kernel, fg_q1_kernel, kg_e_kernel, kg_q0_kernel "
+                             "(eq. 19, R0^{-T} solve, normalise, Gram-route factor QR; the Householder finish "
+                             "launched after them returns at once unless the guard trips)",
+                   "peak_kind": "FP64 DFMA rate of the whole GPU measured by a probe; the chain is bound by the "
+                                "latency of its serial 32-step solve and Cholesky",
+                   "alg_flops_per_launch": qr_flops, "avg_launch_ms": qr_ms, "launches": int(n_qr)}
+        roof_qr["frac"] = roof_qr["achieved"] / roof_qr["peak"] if n_qr else None
+        # the dominant kernel by device time: the first-level TTM (one launch per sweep reads all of X)
+        roof = roof_ttm
+        roof["share_of_sweep"] = (st.ms_bucket[0] / max(args.steps, 1)) / ms if ms > 0 else None
         out = {"metric": METRIC, "value": ms * 1e-3 / world, "unit": "s/sweep", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
                "vs_baseline": None,
@@ -262,8 +259,8 @@ def run_ours(args, rank, world, local_rank):
                           "l2": "no flush; inputs larger than L2 (256 MB tensor, 512 MB bf16 split)",
                           "replicas": world},
                "roofline": roof,
-               "roofline_ttm_full": roof_ttm,
                "roofline_ttm_deep": roof_deep,
+               "roofline_factor_qr": roof_qr,
                "buckets_ms_per_sweep": buckets,
                "gpu_launches": int(launches),
                "fit_last": float(fits[-1]) if len(fits) else None}

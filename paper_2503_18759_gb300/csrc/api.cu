@@ -385,9 +385,12 @@ cpqr_status run_ttm(cpqr_ctx* ctx, const Op& op) {
         shi = h;
         slo = l;
       }
-      // a Khatri-Rao QR running on the side stream holds one cluster of SMs: the persistent
-      // grid leaves those free so that the two overlap instead of queueing behind each other
-      const int reserve = ctx->z_pending ? qr_cluster_sms() : 0;
+      // a Householder Khatri-Rao QR running on the side stream holds one 16-CTA cluster: the
+      // persistent grid then leaves a GPC free so that the two overlap instead of queueing behind
+      // each other.  That costs the TTM a third of the SMs (one 16-CTA cluster per GPC), so the
+      // Gram route, whose side-stream work is row kernels plus a fallback that returns at once,
+      // gives the TTM the whole GPU.
+      const int reserve = (ctx->z_pending && !ctx->gram) ? qr_cluster_sms() : 0;
       CK(launch_ttm_tc(shi, slo, ctx->Qt[k], ctx->Rp, ctx->Kp[k], of, P, K, S, R, ctx->dstatus, st, reserve, ohi,
                        olo));
     } else {
@@ -611,7 +614,8 @@ cpqr_status run_update(cpqr_ctx* ctx, int n, int leaf, double beta, int next_mod
       CK(launch_finish_prep<float>((const float*)ctx->v_work, nparts, I, C, R, ctx->R0, b, ctx->alpha, ctx->V,
                                    ctx->fitpart, hpart, ctx->dstatus, st));
     if (ctx->resid_pending) {
-      // the previous sweep's residual runs beside this factor QR (one GPC busy, the rest idle)
+      // the previous sweep's residual runs beside this factor QR (one GPC busy with its Cholesky,
+      // the rest mostly idle)
       CK(cudaEventRecord(ctx->ev_prep, st));
       cpqr_status s = launch_lagged_residual(ctx);
       if (s != CPQR_OK) return s;
