@@ -43,8 +43,8 @@ constexpr double kEMax = 1e-8;
 // Workspace layout (doubles, every section 128-byte aligned): the int pair {fallback flag,
 // fallback count} (at a fixed offset, so the count survives calls with different row counts),
 // R1, S (R1 scaled for the substitution), F, rinv, 1/lambda (the equilibration), two Grams in
-// float-float and their column norms (for a QR whose triangles come without stored Grams),
-// Q1 (M x R), Q1^T (R x M).
+// float-float and their column norms (for a QR whose triangles come without stored Grams), F in
+// float-float, Q1 (M x R), Q1^T (R x M).
 constexpr size_t KG_HEAD = 16;
 size_t kg_round16(size_t n) { return (n + 15) / 16 * 16; }
 struct KgWork {
@@ -58,12 +58,13 @@ struct KgWork {
   float2* gb;
   double* sa;
   double* sb;
+  float2* Ff;
   double* Q1;
   double* Q1T;
 };
 
 size_t kg_work_doubles(int64_t M, int R) {
-  return KG_HEAD + 5 * (size_t)KG_MAXR * KG_MAXR + 4 * KG_MAXR + 2 * kg_round16((size_t)M * R);
+  return KG_HEAD + 6 * (size_t)KG_MAXR * KG_MAXR + 4 * KG_MAXR + 2 * kg_round16((size_t)M * R);
 }
 
 KgWork kg_views(double* work, int R, int64_t M) {
@@ -79,7 +80,8 @@ KgWork kg_views(double* work, int R, int64_t M) {
   w.gb = reinterpret_cast<float2*>(w.il + KG_MAXR + rr);
   w.sa = w.il + KG_MAXR + 2 * rr;
   w.sb = w.sa + KG_MAXR;
-  w.Q1 = w.sb + KG_MAXR;
+  w.Ff = reinterpret_cast<float2*>(w.sb + KG_MAXR);
+  w.Q1 = w.sb + KG_MAXR + rr;
   w.Q1T = w.Q1 + kg_round16((size_t)M * R);
   return w;
 }
@@ -166,6 +168,16 @@ __device__ __forceinline__ ffn ff_fms(ffn t, ffn a, ffn b) {
   const float h = __fadd_rn(s, err);
   return ff_make(h, __fsub_rn(err, __fsub_rn(h, s)));
 }
+// a + b
+__device__ __forceinline__ ffn ff_add(ffn a, ffn b) {
+  const float s = __fadd_rn(a.hi, b.hi);  // TwoSum(a.hi, b.hi)
+  const float bb = __fsub_rn(s, a.hi);
+  float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  err = __fadd_rn(err, __fadd_rn(a.lo, b.lo));
+  const float h = __fadd_rn(s, err);
+  return ff_make(h, __fsub_rn(err, __fsub_rn(h, s)));
+}
+__device__ __forceinline__ ffn ff_neg(ffn a) { return ff_make(-a.hi, -a.lo); }
 // 1 / d for a pivot d: rcp.approx.ftz.f32 (at most 1 ulp off) and one Newton-Raphson step
 // y <- y + y (1 - d y) with the residual formed in float-float (error ~2^-46).  A pivot outside
 // (1e-30, 1e30), or not a number, sets *bad and gives 0.  d is warp-uniform.
@@ -292,12 +304,14 @@ __device__ __forceinline__ void chol_pipelined(float2 (*G)[KG_LD], float2 (*U)[K
 }
 
 // After chol_pipelined (and a __syncthreads): rinv = d^-1/2 (FP64, rsqrt.approx.f64, measured
-// to 53 bits, in the normal range), R1 = diag(rinv) U diag(colscale) (colscale: the
-// equilibration scale to undo, or null; the products in float-float), S[c][c'] = V[c][c']
-// (c < c', for the substitution of the equilibrated rows) and the flag, to global.  The upper
-// triangle is visited as folded pairs (one FP64 addition per entry and output, all lanes
-// live).  rsf, csf: 32 float2 of shared scratch each.
-__device__ __forceinline__ void chol_outputs(float2 (*U)[KG_LD], float2 (*V)[KG_LD], float2* rsf, float2* csf,
+// to 53 bits, in the normal range), S[c][c'] = V[c][c'] (c < c', for the substitution of the
+// equilibrated rows) and R1 diag(colscale) (colscale: the equilibration scale to undo, or null),
+// with R1 taken as the triangle the substitution implies: R1[c][c] = r_c = d_c rinv_c (= 1 /
+// rinv_c to FP64 rounding) and R1[c][c'] = S[c][c'] r_c.  So Q1 R1 = Z holds to FP64 rounding
+// whatever the float-float rounding of U and V was, which the accuracy of Q0 R0 relies on.
+// Upper-triangle entries are visited as folded pairs (all lanes live); the flag last.  rsd, csd:
+// 32 doubles of shared scratch each.
+__device__ __forceinline__ void chol_outputs(float2 (*U)[KG_LD], float2 (*V)[KG_LD], double* rsd, double* csd,
                                              const double* colscale, int R, const KgWork& w, int* bad) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid < 32) {
@@ -311,8 +325,8 @@ __device__ __forceinline__ void chol_outputs(float2 (*U)[KG_LD], float2 (*V)[KG_
       if (!(d > 0.0)) *bad = 1;
     }
     if (lane >= R) y = 0.0;
-    rsf[lane] = ff_st(ff_from_bits(y));
-    csf[lane] = ff_st(colscale ? ff_from_bits(colscale[lane]) : ff_make(1.0f, 0.0f));
+    rsd[lane] = d * y;
+    csd[lane] = colscale ? colscale[lane] : 1.0;
     w.rinv[lane] = y;
   }
   for (int e = tid; e < KG_MAXR * KG_MAXR; e += blockDim.x) {  // strict lower triangles
@@ -327,8 +341,8 @@ __device__ __forceinline__ void chol_outputs(float2 (*U)[KG_LD], float2 (*V)[KG_
     const int c = lane, d = (lane + k) & 31;
     const int i = min(c, d), j = max(c, d);
     const bool live = j < R;
-    const double r = live ? ff_val(ff_mul(ff_mul(ff_ld(U[i][j]), ff_ld(rsf[i])), ff_ld(csf[j]))) : 0.0;
     const double sv = (live && j > i) ? ff_val(V[i][j]) : 0.0;
+    const double r = live ? ((j == i) ? rsd[i] : sv * rsd[i]) * csd[j] : 0.0;
     w.R1[i * KG_MAXR + j] = r;
     w.S[i * KG_MAXR + j] = sv;
   }
@@ -380,8 +394,7 @@ __global__ void __launch_bounds__(256) kg_chol_kernel(const float2* __restrict__
                                                        const double* __restrict__ sa, const double* __restrict__ sb,
                                                        int R, KgWork w) {
   __shared__ __align__(16) float2 Gf[KG_MAXR][KG_LD], U[KG_MAXR][KG_LD], V[KG_MAXR][KG_LD];
-  __shared__ float2 rsf[KG_MAXR], csf[KG_MAXR];
-  __shared__ double scale[KG_MAXR];
+  __shared__ double scale[KG_MAXR], rsd[KG_MAXR], csd[KG_MAXR];
   __shared__ int bad;
   const int tid = threadIdx.x, lane = tid & 31;
   pdl_wait();
@@ -400,7 +413,7 @@ __global__ void __launch_bounds__(256) kg_chol_kernel(const float2* __restrict__
   __syncthreads();
   chol_pipelined(Gf, U, V, R, &bad);
   __syncthreads();
-  chol_outputs(U, V, rsf, csf, scale, R, w, &bad);
+  chol_outputs(U, V, rsd, csd, scale, R, w, &bad);
 }
 
 // Factor route, Gram and Cholesky on one 16-CTA cluster of 256 threads: CTA r adds up folded
@@ -419,7 +432,8 @@ __global__ void __cluster_dims__(KG_CL, 1, 1) __launch_bounds__(256)
   __shared__ __align__(16) double G[KG_MAXR][KG_LD];
   __shared__ __align__(16) float2 Gf[KG_MAXR][KG_LD], U[KG_MAXR][KG_LD], V[KG_MAXR][KG_LD];
   __shared__ double red[8][32], scale[KG_MAXR], il[KG_MAXR];
-  __shared__ float2 ilf[KG_MAXR], rsf[KG_MAXR], csf[KG_MAXR];
+  __shared__ float2 ilf[KG_MAXR];
+  __shared__ double rsd[KG_MAXR], csd[KG_MAXR];
   __shared__ int bad;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) bad = 0;
@@ -485,7 +499,7 @@ __global__ void __cluster_dims__(KG_CL, 1, 1) __launch_bounds__(256)
   }
   chol_pipelined(Gf, U, V, R, &bad);
   __syncthreads();
-  chol_outputs(U, V, rsf, csf, nullptr, R, w, &bad);
+  chol_outputs(U, V, rsd, csd, nullptr, R, w, &bad);
 }
 
 // Factor route, Q1 = A R1^{-1} with A = A^ / lambda: one row of A^ per warp (A also written
@@ -586,7 +600,9 @@ __global__ void __launch_bounds__(128) kg_e_kernel(int M, int R, KgWork w) {
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
   if (lane == 0) {
     const double e = (c == d) ? s - 1.0 : s;
-    w.F[c * KG_MAXR + d] = (c == d) ? 0.5 * e : e;
+    const double f = (c == d) ? 0.5 * e : e;
+    w.F[c * KG_MAXR + d] = f;
+    w.Ff[c * KG_MAXR + d] = ff_st(ff_from_bits(f));
     if (!(fabs(e) <= kEMax)) atomicOr(w.flag, 1);  // also catches NaN
   }
 }
@@ -594,7 +610,9 @@ __global__ void __launch_bounds__(128) kg_e_kernel(int M, int R, KgWork w) {
 // Q0 = Q1 (I - F) (one row per warp, lane = column: q0[c] = q1[c] - sum_{k <= c} q1[k] F[k][c]),
 // and, on the first R warps of the grid, row c of R0 = (I + F) R1.  Optional copies: Q0f
 // (FP32) and Qt, Q0^T split into bf16 hi / lo for the tensor cores (Qt[2][Rp][Kp], the layout
-// the Householder finish writes).
+// the Householder finish writes).  The correction sum runs in float-float on the FP32 pipe:
+// every |F[k][c]| <= 1e-8 once the guard accepts, so the sum is below 3.2e-7 and its ~2^-46
+// relative error below 1e-20, far under the FP64 rounding of q1; only q1 - sum is FP64.
 __global__ void __launch_bounds__(128) kg_q0_kernel(int M, int R, KgWork w, double* __restrict__ Q0,
                                                      float* __restrict__ Q0f, double* __restrict__ R0,
                                                      __nv_bfloat16* __restrict__ Qt, int Rp, int64_t Kp) {
@@ -602,9 +620,10 @@ __global__ void __launch_bounds__(128) kg_q0_kernel(int M, int R, KgWork w, doub
   const int t = blockIdx.x * 4 + (threadIdx.x >> 5);
   pdl_wait();
   if (t >= M) return;
-  double fcol[KG_MAXR];  // F[k][lane], k <= lane
+  ffn fcol[KG_MAXR];  // F[k][lane], k <= lane
 #pragma unroll
-  for (int k = 0; k < KG_MAXR; ++k) fcol[k] = (k < R && lane >= k && lane < R) ? w.F[k * KG_MAXR + lane] : 0.0;
+  for (int k = 0; k < KG_MAXR; ++k)
+    fcol[k] = (k < R && lane >= k && lane < R) ? ff_ld(w.Ff[k * KG_MAXR + lane]) : ff_make(0.0f, 0.0f);
   if (t < R) {
     // R0[t][d] = R1[t][d] + sum_{t <= k <= d} F[t][k] R1[k][d], d = lane
     double r = (lane < R) ? w.R1[t * KG_MAXR + lane] : 0.0;
@@ -619,14 +638,15 @@ __global__ void __launch_bounds__(128) kg_q0_kernel(int M, int R, KgWork w, doub
     if (lane < R) R0[t * R + lane] = (lane >= t) ? r : 0.0;
   }
   const double q1 = (lane < R) ? w.Q1[(size_t)t * R + lane] : 0.0;
-  double q = q1;
+  const ffn q1f = ff_from_bits(q1);
+  ffn acc[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) acc[u] = ff_make(0.0f, 0.0f);
 #pragma unroll
   for (int k = 0; k < KG_MAXR; ++k) {
-    if (k < R) {
-      const double qk = __shfl_sync(FULL, q1, k);
-      q = fma(-qk, fcol[k], q);
-    }
+    if (k < R) acc[k & 3] = ff_fms(acc[k & 3], ff_neg(ff_shfl(q1f, k)), fcol[k]);
   }
+  const double q = q1 - ff_val(ff_add(ff_add(acc[0], acc[1]), ff_add(acc[2], acc[3])));
   if (lane < R) {
     Q0[(size_t)t * R + lane] = q;
     if (Q0f) Q0f[(size_t)t * R + lane] = (float)q;

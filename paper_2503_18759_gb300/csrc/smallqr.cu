@@ -574,13 +574,15 @@ __global__ void __launch_bounds__(PREP_WARPS * 32) finish_prep_kernel(const TP* 
     f_in = v0 * vh;
     f_nn = vh * vh;
     // column c of the back substitution: a^_c = res_c / R0[c][c], res_l -= R0[l][c] a^_c (l < c);
-    // with the scaled R0 the serial chain is one shuffle and one FMA per column
-    double res = vh, ahat = 0.0;
+    // with the scaled R0 the serial chain is one shuffle and one FMA per column, and lane c keeps
+    // its res_c (a move, not an FP64 instruction) for one scaling after the loop
+    double res = vh, xk = 0.0;
     for (int c = R - 1; c >= 0; --c) {
       const double x = __shfl_sync(FULL, res, c);
-      if (lane == c) ahat = x * rdiag[c];
+      if (lane == c) xk = x;
       if (lane < c) res = fma(-sM[lane][c], x, res);
     }
+    const double ahat = (lane < R) ? xk * rdiag[lane] : 0.0;
     if (lane < R) Ahat[(size_t)i * R + lane] = ahat;
     if (hpart) {
 #pragma unroll
