@@ -29,11 +29,13 @@
 
 #include "common.cuh"
 #include "tc_common.cuh"
+#include "ff.cuh"
 
 namespace cpqr {
 
 namespace {
 
+using namespace ffa;
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int KG_MAXR = CPQR_MAXR;
 constexpr int KG_LD = KG_MAXR + 1;
@@ -97,106 +99,6 @@ constexpr int KG_GK = 17;  // folded Gram entries per lane in the finish-prep pa
 __device__ __forceinline__ void nb_arrive(int id) { asm volatile("bar.arrive %0, 256;" ::"r"(id) : "memory"); }
 __device__ __forceinline__ void nb_sync(int id) { asm volatile("bar.sync %0, 256;" ::"r"(id) : "memory"); }
 
-// ---- float-float numbers: the unevaluated sum hi + lo of two FP32 values (~2^-48 relative) ----
-// GB300 issues one FP64 warp instruction per 64 cycles per SM sub-partition at a 64-cycle
-// latency, FP32 one per cycle at 4 cycles, so the serial Cholesky runs in float-float.  The
-// operations are the error-free transformations TwoSum (Knuth) and TwoProd by FMA, written with
-// the _rn intrinsics so that the compiler neither contracts nor reorders them.
-struct ffn {
-  float hi, lo;
-};
-__device__ __forceinline__ ffn ff_make(float hi, float lo) {
-  ffn r;
-  r.hi = hi;
-  r.lo = lo;
-  return r;
-}
-__device__ __forceinline__ ffn ff_ld(const float2& v) { return ff_make(v.x, v.y); }
-__device__ __forceinline__ float2 ff_st(ffn a) { return make_float2(a.hi, a.lo); }
-// FP32 -> FP64, exact for zero and normal numbers (subnormal inputs, below 1.2e-38, read as
-// zero), by moving the IEEE-754 fields on the integer pipe: exponent rebiased from 127 to 1023,
-// mantissa widened.  (A conversion instruction would occupy the slow FP64 pipe.)
-__device__ __forceinline__ double f2d_bits(float f) {
-  const unsigned int b = __float_as_uint(f);
-  const unsigned int e = (b >> 23) & 0xffu;
-  const unsigned int E = (e == 0u) ? 0u : ((e == 255u) ? 2047u : e + 896u);
-  const unsigned long long m = (e == 0u) ? 0ull : (unsigned long long)(b & 0x7fffffu) << 29;
-  return __longlong_as_double(
-      (long long)(((unsigned long long)(b & 0x80000000u) << 32) | ((unsigned long long)E << 52) | m));
-}
-// FP64 -> FP32 rounded toward zero (below the FP32 normal range: zero; above: infinity, which
-// fails the pivot test), by moving the fields.
-__device__ __forceinline__ float d2f_trunc(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned int hi = (unsigned int)(b >> 32);
-  const unsigned int sign = hi & 0x80000000u;
-  const int e = (int)((hi >> 20) & 0x7ffu) - 896;
-  if (e <= 0) return __uint_as_float(sign);
-  if (e >= 255) return __uint_as_float(sign | 0x7f800000u);
-  return __uint_as_float(sign | ((unsigned int)e << 23) | (unsigned int)((b >> 29) & 0x7fffffull));
-}
-// x as hi + lo (both truncated: ~2^-48 relative; x - hi is exact in FP64), one FP64 subtraction
-__device__ __forceinline__ ffn ff_from_bits(double x) {
-  const float h = d2f_trunc(x);
-  return ff_make(h, d2f_trunc(x - f2d_bits(h)));
-}
-// hi + lo in FP64 with one FP64 addition
-__device__ __forceinline__ double ff_val(const float2& v) { return f2d_bits(v.x) + f2d_bits(v.y); }
-__device__ __forceinline__ double ff_val(ffn a) { return f2d_bits(a.hi) + f2d_bits(a.lo); }
-__device__ __forceinline__ ffn ff_shfl(ffn a, int src) {
-  return ff_make(__shfl_sync(FULL, a.hi, src), __shfl_sync(FULL, a.lo, src));
-}
-// a b
-__device__ __forceinline__ ffn ff_mul(ffn a, ffn b) {
-  const float p = __fmul_rn(a.hi, b.hi);
-  float e = __fmaf_rn(a.hi, b.hi, -p);
-  e = __fmaf_rn(a.hi, b.lo, e);
-  e = __fmaf_rn(a.lo, b.hi, e);
-  const float h = __fadd_rn(p, e);
-  return ff_make(h, __fsub_rn(e, __fsub_rn(h, p)));
-}
-// t - a b
-__device__ __forceinline__ ffn ff_fms(ffn t, ffn a, ffn b) {
-  const float p = __fmul_rn(a.hi, b.hi);
-  float pe = __fmaf_rn(a.hi, b.hi, -p);
-  pe = __fmaf_rn(a.hi, b.lo, pe);
-  pe = __fmaf_rn(a.lo, b.hi, pe);
-  const float s = __fsub_rn(t.hi, p);  // TwoSum(t.hi, -p)
-  const float bb = __fsub_rn(s, t.hi);
-  float err = __fadd_rn(__fsub_rn(t.hi, __fsub_rn(s, bb)), __fsub_rn(-p, bb));
-  err = __fadd_rn(err, __fsub_rn(t.lo, pe));
-  const float h = __fadd_rn(s, err);
-  return ff_make(h, __fsub_rn(err, __fsub_rn(h, s)));
-}
-// a + b
-__device__ __forceinline__ ffn ff_add(ffn a, ffn b) {
-  const float s = __fadd_rn(a.hi, b.hi);  // TwoSum(a.hi, b.hi)
-  const float bb = __fsub_rn(s, a.hi);
-  float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
-  err = __fadd_rn(err, __fadd_rn(a.lo, b.lo));
-  const float h = __fadd_rn(s, err);
-  return ff_make(h, __fsub_rn(err, __fsub_rn(h, s)));
-}
-__device__ __forceinline__ ffn ff_neg(ffn a) { return ff_make(-a.hi, -a.lo); }
-// 1 / d for a pivot d: rcp.approx.ftz.f32 (at most 1 ulp off) and one Newton-Raphson step
-// y <- y + y (1 - d y) with the residual formed in float-float (error ~2^-46).  A pivot outside
-// (1e-30, 1e30), or not a number, sets *bad and gives 0.  d is warp-uniform.
-__device__ __forceinline__ ffn ff_recip(ffn d, int* bad) {
-  if (!(d.hi > 1e-30f && d.hi < 1e30f)) {
-    *bad = 1;
-    return ff_make(0.0f, 0.0f);
-  }
-  float y;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(d.hi));
-  const float p = __fmul_rn(d.hi, y);
-  float pe = __fmaf_rn(d.hi, y, -p);
-  pe = __fmaf_rn(d.lo, y, pe);
-  const float r = __fsub_rn(__fsub_rn(1.0f, p), pe);
-  const float c = __fmul_rn(y, r);
-  const float h = __fadd_rn(y, c);
-  return ff_make(h, __fsub_rn(c, __fsub_rn(h, y)));
-}
-
 // CTA 0 of a Cholesky kernel, G (FP64, R x R block, both triangles) complete: scale = sqrt(diag
 // G), il = 1 / scale (rsqrt.approx.f64, measured to 53 bits; 0 for a zero or non-finite column,
 // whose zero row then fails its pivot), the equilibrated Gram Gf = D^-1 G D^-1 in float-float
@@ -241,25 +143,31 @@ __device__ __forceinline__ void equilibrate_ff(double (*G)[KG_LD], float2 (*Gf)[
 // thus off the serial chain, which per row is one fused multiply-subtract, one shuffle and one
 // reciprocal.
 //
-// Pipelining: warp 0 produces the rows: for row j it applies step j - 1 itself (look-ahead,
-// with z = U[j-1][j] U[j-1] formed while the reciprocal of d_{j-1} was in flight), while warps
-// 1-7 apply step j - 1 to rows >= j + 1.  "Row j of U, V written": warp 0 arrives, warps 1-7
-// wait, on barrier 1 (j even) or 3 (j odd).  "Step s applied to rows >= s + 2": warps 1-7
-// arrive, warp 0 waits before its look-ahead on row s + 2, on barrier 2 (s even) or 4 (s odd).
-// Two barriers per role because either side may arrive one generation ahead: warp 0 posts row
-// j + 1 before the others have taken row j, and a warp may post step s + 1 before warp 0 has
-// taken step s.  Row j + 2 is posted only after warp 0 has taken step j (so all of warps 1-7
-// took row j), and step s + 2 only after row s + 2, which follows warp 0's wait on step s:
-// each barrier's previous generation is complete before its next use.
+// Pipelining: warp 0 produces the rows and keeps the next one in registers.  At iteration j it
+// finishes row j by applying step j - 1 to the copy it prepared (with z = U[j-1][j] U[j-1]
+// formed while the reciprocal of d_{j-1} was in flight), and meanwhile prepares row j + 1:
+// it loads it once warps 1-7 have applied the steps up to j - 2, then applies step j - 1 itself.
+// So warps 1-7 apply step s to rows >= s + 3, and no shared-memory load sits on the chain.
+// "Row j of U, V written": warp 0 arrives, warps 1-7 wait, on barrier 1 (j even) or 3 (j odd).
+// "Step s applied": warps 1-7 arrive, warp 0 waits at iteration s + 2 before loading row s + 3,
+// on barrier 2 (s even) or 4 (s odd).  Two barriers per role because either side may arrive
+// one generation ahead: warp 0 posts row j + 1 before the others have taken row j, and a warp may
+// post step s + 1 before warp 0 has taken step s.  Row j + 2 is posted only after warp 0 has
+// taken step j (so all of warps 1-7 took row j), and step s + 2 only after row s + 2, which
+// follows warp 0's wait on step s: each barrier's previous generation is complete before its
+// next use.
 __device__ __forceinline__ void chol_pipelined(float2 (*G)[KG_LD], float2 (*U)[KG_LD], float2 (*V)[KG_LD], int R,
                                                int* bad) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool in = lane < R;
   const ffn zero = ff_make(0.0f, 0.0f);
   if (warp == 0) {
+    // row 0; the prepared copy of row 1 needs no step yet
     ffn u = in ? ff_ld(G[0][lane]) : zero;
+    ffn nxt = (in && lane >= 1 && R > 1) ? ff_ld(G[1][lane]) : zero;
     ffn w = ff_recip(ff_shfl(u, 0), bad);
-    ffn z = ff_mul(ff_shfl(u, 1), u);  // U[0][1] U[0][l], for row 1
+    ffn z = ff_mul(ff_shfl(u, 1), u);         // U[0][1] U[0][l]: step 0 on row 1
+    ffn z2 = ff_mul(ff_shfl(u, 2 & 31), u);  // U[0][2] U[0][l]: step 0 on row 2
     if (in) {
       U[0][lane] = ff_st(u);
       V[0][lane] = ff_st(ff_mul(u, w));
@@ -267,11 +175,18 @@ __device__ __forceinline__ void chol_pipelined(float2 (*G)[KG_LD], float2 (*U)[K
     __syncwarp();
     nb_arrive(1);  // row 0
     for (int j = 1; j < R; ++j) {
-      if (j >= 2) nb_sync(2 + 2 * ((j - 2) & 1));  // step j - 2 reached row j
       const bool live = in && lane >= j;
-      u = live ? ff_fms(ff_ld(G[j][lane]), w, z) : zero;  // step j - 1 on row j
+      u = live ? ff_fms(nxt, w, z) : zero;  // step j - 1 on row j
+      // row j + 1 after steps up to j - 2 from warps 1-7 (j >= 2): its load is issued before the
+      // reciprocal's dependent chain, which then hides its latency
+      if (j >= 2) nb_sync(2 + 2 * ((j - 2) & 1));
+      const bool live1 = in && lane >= j + 1;
+      const ffn t = live1 ? ff_ld(G[j + 1][lane]) : zero;
+      const ffn w1 = w, z21 = z2;
       w = ff_recip(ff_shfl(u, j), bad);
-      z = ff_mul(ff_shfl(u, (j + 1) & 31), u);
+      z = ff_mul(ff_shfl(u, (j + 1) & 31), u);   // step j on row j + 1
+      z2 = ff_mul(ff_shfl(u, (j + 2) & 31), u);  // step j on row j + 2
+      nxt = live1 ? ff_fms(t, w1, z21) : zero;   // step j - 1 on row j + 1
       if (live) {
         U[j][lane] = ff_st(u);
         V[j][lane] = ff_st(ff_mul(u, w));
@@ -283,18 +198,18 @@ __device__ __forceinline__ void chol_pipelined(float2 (*G)[KG_LD], float2 (*U)[K
     for (int s = 0; s + 1 < R; ++s) {
       nb_sync(1 + 2 * (s & 1));  // row s of U, V is there
       const ffn us = in ? ff_ld(U[s][lane]) : zero;
-      // this warp's rows k = s + 1 + warp + 7 q (rows s + 2, ...; at most 5): every load first
+      // this warp's rows k = s + 2 + warp + 7 q (rows s + 3, ...; at most 5): every load first
       constexpr int KQ = (KG_MAXR + 6) / 7;
       ffn m[KQ], g[KQ];
 #pragma unroll
       for (int q = 0; q < KQ; ++q) {
-        const int k = s + 1 + warp + 7 * q;
+        const int k = s + 2 + warp + 7 * q;
         m[q] = (k < R) ? ff_ld(V[s][k]) : zero;
         g[q] = (k < R && in && lane >= k) ? ff_ld(G[k][lane]) : zero;
       }
 #pragma unroll
       for (int q = 0; q < KQ; ++q) {
-        const int k = s + 1 + warp + 7 * q;
+        const int k = s + 2 + warp + 7 * q;
         if (k < R && in && lane >= k) G[k][lane] = ff_st(ff_fms(g[q], m[q], us));
       }
       if (s + 2 < R) nb_arrive(2 + 2 * (s & 1));  // step s
@@ -438,26 +353,45 @@ __global__ void __cluster_dims__(KG_CL, 1, 1) __launch_bounds__(256)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) bad = 0;
   for (int k = rank; k < KG_GK; k += KG_CL) {
-    const double* hp = hpart + (size_t)k * 32 + lane;
     const size_t bs = (size_t)KG_GK * 32;
-    // 16 blocks per pass with every load issued before the adds (fixed order)
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-    for (int b0 = warp; b0 < nblk; b0 += 128) {
-      double x[16];
+    // 16 blocks per pass with every load issued before the adds (fixed order); the diagonal row
+    // (k = 0) in FP64, the others in float-float as the finish prep wrote them
+    if (k == 0) {
+      const double* hp = hpart + lane;
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      for (int b0 = warp; b0 < nblk; b0 += 128) {
+        double x[16];
 #pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const int b = b0 + 8 * u;
-        x[u] = (b < nblk) ? hp[(size_t)b * bs] : 0.0;
-      }
+        for (int u = 0; u < 16; ++u) {
+          const int b = b0 + 8 * u;
+          x[u] = (b < nblk) ? hp[(size_t)b * bs] : 0.0;
+        }
 #pragma unroll
-      for (int u = 0; u < 16; u += 4) {
-        a0 += x[u];
-        a1 += x[u + 1];
-        a2 += x[u + 2];
-        a3 += x[u + 3];
+        for (int u = 0; u < 16; u += 4) {
+          a0 += x[u];
+          a1 += x[u + 1];
+          a2 += x[u + 2];
+          a3 += x[u + 3];
+        }
       }
+      red[warp][lane] = (a0 + a1) + (a2 + a3);
+    } else {
+      const float2* hp = reinterpret_cast<const float2*>(hpart) + (size_t)k * 32 + lane;
+      ffn a[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) a[u] = ff_make(0.0f, 0.0f);
+      for (int b0 = warp; b0 < nblk; b0 += 128) {
+        float2 x[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const int b = b0 + 8 * u;
+          x[u] = (b < nblk) ? hp[(size_t)b * bs] : make_float2(0.0f, 0.0f);
+        }
+#pragma unroll
+        for (int u = 0; u < 16; ++u) a[u & 3] = ff_add(a[u & 3], ff_ld(x[u]));
+      }
+      red[warp][lane] = ff_val(ff_add(ff_add(a[0], a[1]), ff_add(a[2], a[3])));
     }
-    red[warp][lane] = (a0 + a1) + (a2 + a3);
     __syncthreads();
     if (warp == 0) {
       const double g = ((red[0][lane] + red[1][lane]) + (red[2][lane] + red[3][lane])) +

@@ -35,6 +35,7 @@
 #include <cstdlib>
 
 #include "common.cuh"
+#include "ff.cuh"
 #include "tc_common.cuh"
 
 namespace cg = cooperative_groups;
@@ -514,8 +515,10 @@ __global__ void __launch_bounds__(NT, 1) qr_cluster_kernel(QrParams p) {
 // ~2^-16 relative error), V^ = (1 + beta) V0 - alpha beta V1, and A^ R0^T = V^ is solved by
 // back substitution with lane = column.  Each block also adds up <V0, V^> and ||V^||^2 over
 // its rows; the finish kernel adds the block partials.  With hpart set, each block also writes
-// its rows' share of the Gram A^T A^ folded into 17 x 32 entries: hpart[blk][k][c] =
-// sum_i a^_ic a^_i,(c+k)%32 for k = 0..16 (every unordered pair once, k = 16 twice).
+// its rows' share of the Gram A^T A^ folded into 17 x 32 entries of 8 bytes: hpart[blk][k][c] =
+// sum_i a^_ic a^_i,(c+k)%32 for k = 0..16 (every unordered pair once, k = 16 twice); the
+// diagonal (k = 0, which gives lambda) as FP64, the rest as float-float (float2), which is all
+// the Gram-route Cholesky uses them for, off the slow FP64 pipe.
 constexpr int PREP_WARPS = 4;
 constexpr int PREP_GK = 17;  // folded Gram entries per lane
 
@@ -529,7 +532,8 @@ __global__ void __launch_bounds__(PREP_WARPS * 32) finish_prep_kernel(const TP* 
   __shared__ double sM[CPQR_MAXR][CPQR_MAXR + 1];  // sM[l][c] = R0[l][c] / R0[c][c], l < c
   __shared__ double rdiag[CPQR_MAXR];
   __shared__ double red[PREP_WARPS][2];
-  __shared__ double hred[PREP_WARPS][PREP_GK][32];
+  __shared__ double hred0[PREP_WARPS][32];
+  __shared__ float2 hredf[PREP_WARPS][PREP_GK - 1][32];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   pdl_wait();
   if (tid < R) {
@@ -543,9 +547,10 @@ __global__ void __launch_bounds__(PREP_WARPS * 32) finish_prep_kernel(const TP* 
   const bool ext = (C == 2 * R);
   const size_t n = (size_t)I * C;
   double f_in = 0.0, f_nn = 0.0;
-  double h[PREP_GK];
+  double h0 = 0.0;
+  ffa::ffn hf[PREP_GK - 1];
 #pragma unroll
-  for (int k = 0; k < PREP_GK; ++k) h[k] = 0.0;
+  for (int k = 0; k < PREP_GK - 1; ++k) hf[k] = ffa::ff_make(0.0f, 0.0f);
   const int i = blockIdx.x * PREP_WARPS + warp;
   if (i < I) {
     double v0 = 0.0, v1 = 0.0;
@@ -585,13 +590,16 @@ __global__ void __launch_bounds__(PREP_WARPS * 32) finish_prep_kernel(const TP* 
     const double ahat = (lane < R) ? xk * rdiag[lane] : 0.0;
     if (lane < R) Ahat[(size_t)i * R + lane] = ahat;
     if (hpart) {
+      h0 = ahat * ahat;
+      const ffa::ffn af = ffa::ff_from_bits(ahat);
 #pragma unroll
-      for (int k = 0; k < PREP_GK; ++k) h[k] = ahat * __shfl_sync(FULL, ahat, (lane + k) & 31);
+      for (int k = 1; k < PREP_GK; ++k) hf[k - 1] = ffa::ff_mul(af, ffa::ff_shfl(af, (lane + k) & 31));
     }
   }
   if (hpart) {
+    hred0[warp][lane] = h0;
 #pragma unroll
-    for (int k = 0; k < PREP_GK; ++k) hred[warp][k][lane] = h[k];
+    for (int k = 1; k < PREP_GK; ++k) hredf[warp][k - 1][lane] = ffa::ff_st(hf[k - 1]);
   }
   for (int o = 16; o > 0; o >>= 1) {
     f_in += __shfl_xor_sync(FULL, f_in, o);
@@ -612,12 +620,20 @@ __global__ void __launch_bounds__(PREP_WARPS * 32) finish_prep_kernel(const TP* 
     fitpart[2 * blockIdx.x + 1] = b;
   }
   if (hpart) {
-    for (int e = tid; e < PREP_GK * 32; e += PREP_WARPS * 32) {
+    for (int e = tid; e < PREP_GK * 32; e += PREP_WARPS * 32) {  // warp-uniform k
       const int k = e >> 5, c = e & 31;
-      double a = 0.0;
+      const size_t o = (size_t)blockIdx.x * PREP_GK * 32 + e;
+      if (k == 0) {
+        double a = 0.0;
 #pragma unroll
-      for (int w = 0; w < PREP_WARPS; ++w) a += hred[w][k][c];
-      hpart[(size_t)blockIdx.x * PREP_GK * 32 + e] = a;
+        for (int w = 0; w < PREP_WARPS; ++w) a += hred0[w][c];
+        hpart[o] = a;
+      } else {
+        ffa::ffn a = ffa::ff_ld(hredf[0][k - 1][c]);
+#pragma unroll
+        for (int w = 1; w < PREP_WARPS; ++w) a = ffa::ff_add(a, ffa::ff_ld(hredf[w][k - 1][c]));
+        reinterpret_cast<float2*>(hpart)[o] = ffa::ff_st(a);
+      }
     }
   }
 }

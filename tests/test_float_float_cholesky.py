@@ -59,8 +59,10 @@ def _val(a):
 
 
 def chol_float_float(G):
-    """Square-root-free Cholesky in the kernel's order: warp 0 applies step j-1 to row j with
-    z = U[j-1][j] U[j-1]; the other warps apply step s to rows >= s + 2."""
+    """Square-root-free Cholesky in the kernel's order: warp 0 finishes row j by applying step
+    j - 1 to the copy of row j it prepared one iteration earlier (that copy got step j - 2 from
+    warp 0 and the steps before from the other warps), z = U[j-1][j] U[j-1]; the other warps
+    apply step s to rows >= s + 3."""
     R = G.shape[0]
     zero = (f32(0), f32(0))
     T = [[_split(G[i, j]) for j in range(R)] for i in range(R)]
@@ -68,21 +70,29 @@ def chol_float_float(G):
     V = [[zero] * R for _ in range(R)]
 
     def trailing(s):
-        for k in range(s + 2, R):
+        for k in range(s + 3, R):
             for l in range(k, R):
                 T[k][l] = _fms(T[k][l], V[s][k], U[s][l])
 
+    def pick(row, l):
+        return row[l] if l < R else zero
+
     u = [T[0][l] for l in range(R)]
+    nxt = [T[1][l] if (R > 1 and l >= 1) else zero for l in range(R)]
     w = _recip(u[0])
-    z = [_mul(u[1] if R > 1 else zero, u[l]) for l in range(R)]
+    z = [_mul(pick(u, 1), u[l]) for l in range(R)]
+    z2 = [_mul(pick(u, 2), u[l]) for l in range(R)]
     U[0], V[0] = u[:], [_mul(u[l], w) for l in range(R)]
     for j in range(1, R):
+        u = [_fms(nxt[l], w, z[l]) if l >= j else zero for l in range(R)]
         if j >= 2:
             trailing(j - 2)
-        u = [_fms(T[j][l], w, z[l]) if l >= j else zero for l in range(R)]
+        t = [T[j + 1][l] if (j + 1 < R and l >= j + 1) else zero for l in range(R)]
+        w1, z21 = w, z2
         w = _recip(u[j])
-        zz = u[j + 1] if j + 1 < R else zero
-        z = [_mul(zz, u[l]) for l in range(R)]
+        z = [_mul(pick(u, j + 1), u[l]) for l in range(R)]
+        z2 = [_mul(pick(u, j + 2), u[l]) for l in range(R)]
+        nxt = [_fms(t[l], w1, z21[l]) if (j + 1 < R and l >= j + 1) else zero for l in range(R)]
         U[j], V[j] = u[:], [_mul(u[l], w) if l >= j else zero for l in range(R)]
     Ud = np.array([[_val(U[i][j]) for j in range(R)] for i in range(R)])
     return np.triu(Ud / np.sqrt(np.diag(Ud))[:, None])
