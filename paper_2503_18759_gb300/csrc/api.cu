@@ -109,10 +109,10 @@ struct cpqr_ctx {
   cudaEvent_t ev_ready = nullptr;  // main stream: triangles R_k of the previous update ready
   cudaEvent_t ev_z = nullptr;      // side stream: Q0, R0 of the upcoming update ready
   // Lagged fit (split path, once nothing in the next sweep depends on the fit): the explicit
-  // residual of sweep k runs on st3 beside the first factor QR of sweep k + 1 and is read one
-  // sweep later.
+  // residual of sweep k runs on st3 after the first factor QR of sweep k + 1, beside that sweep's
+  // next TTM chain, and is read one sweep later.
   cudaStream_t st3 = nullptr;
-  cudaEvent_t ev_prep = nullptr;   // main stream: a mode's finish is about to start
+  cudaEvent_t ev_prep = nullptr;   // main stream: the point after which the lagged residual runs
   cudaEvent_t ev_fit = nullptr;    // st3: lagged residual read back
   bool lag_ok = false;             // set by the sweep loops that need no fit before the next sweep
   bool resid_pending = false;      // snapshot of the factors taken, residual not launched yet
@@ -613,13 +613,6 @@ cpqr_status run_update(cpqr_ctx* ctx, int n, int leaf, double beta, int next_mod
     else
       CK(launch_finish_prep<float>((const float*)ctx->v_work, nparts, I, C, R, ctx->R0, b, ctx->alpha, ctx->V,
                                    ctx->fitpart, hpart, ctx->dstatus, st));
-    if (ctx->resid_pending) {
-      // the previous sweep's residual runs beside this factor QR (one GPC busy with its Cholesky,
-      // the rest mostly idle)
-      CK(cudaEventRecord(ctx->ev_prep, st));
-      cpqr_status s = launch_lagged_residual(ctx);
-      if (s != CPQR_OK) return s;
-    }
     if (ctx->gram) {
       const int nblk = finish_prep_blocks(I);
       CK(launch_finish_gram_chol(ctx->hpart, ctx->fitpart, nblk, I, R, fo, ctx->fg_work, ctx->Gf[n], ctx->cn[n], st));
@@ -637,6 +630,14 @@ cpqr_status run_update(cpqr_ctx* ctx, int n, int leaf, double beta, int next_mod
       CK(launch_finish_gram_rows(ctx->V, ctx->fitpart, nblk, I, R, fo, ctx->fg_work, ctx->qr_work, ctx->dstatus, st));
     } else
       CK(launch_mode_finish(ctx->V, ctx->fitpart, finish_prep_blocks(I), I, R, fo, ctx->qr_work, ctx->dstatus, st));
+  }
+  if (ctx->resid_pending) {
+    // the previous sweep's residual runs after this factor QR, beside the next mode's TTM chain
+    // and Khatri-Rao QR: launched beside the factor QR, it raced the factor Cholesky's cluster for
+    // a free GPC and sometimes held it back for the whole residual
+    CK(cudaEventRecord(ctx->ev_prep, st));
+    cpqr_status s = launch_lagged_residual(ctx);
+    if (s != CPQR_OK) return s;
   }
   std::swap(ctx->Q0, ctx->Q0prev[n]);
   std::swap(ctx->Q0f, ctx->Q0fprev[n]);
@@ -659,7 +660,8 @@ bool can_lag(const cpqr_ctx* ctx) {
 }
 
 // The residual of the snapshot in res_work on st3, after ev_prep (recorded on st after the
-// snapshot), on the GPCs the factor QR leaves free; its value goes to h_pinned[4].
+// snapshot), leaving one GPC free for the cluster kernels of the chain; its value goes to
+// h_pinned[4].
 cpqr_status launch_lagged_residual(cpqr_ctx* ctx) {
   CK(cudaStreamWaitEvent(ctx->st3, ctx->ev_prep, 0));
   {
