@@ -330,6 +330,21 @@ def extras(args, prob, X, dev, b):
         v["seconds_to_common_target"] = k * v["s_per_sweep"] if k else None
     res["common_fit_target"] = target
     res["time_to_tol_1e-6"] = ttf
+    # the same split-precision sweeps with every QR on the Householder route (the paper's plain
+    # form; cpqr_options.qr_route), against the default guarded Gram route
+    routes = {}
+    for name, route in (("gram", b.QR_GRAM), ("householder", b.QR_HOUSEHOLDER)):
+        o = b.make_options(tree=b.TREE_RESTRUCTURED, prec=b.PREC_SPLIT_BF16, extrap=b.EXTRAP_PAPER, qr_route=route)
+        with b.Decomposition(prob.dims, prob.R, X.data_ptr(), False, prob.A0, o) as d:
+            d.sweep(5)
+            torch.cuda.synchronize()
+            e0.record()
+            f = d.sweep(20)
+            e1.record()
+            torch.cuda.synchronize()
+            routes[name] = {"ms_per_sweep": e0.elapsed_time(e1) / 20, "fit_after_25": float(f[-1]) if len(f) else None,
+                            "qr_fallbacks": int(d.stats().qr_fallbacks)}
+    res["qr_routes"] = routes
     return res
 
 

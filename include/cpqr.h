@@ -53,10 +53,10 @@ typedef enum {
 } cpqr_tree;
 
 /* Arithmetic of the TTM chains.  Z_n = Q0 R0, the R0^{-T} solve and the
- * factor QRs are FP64 in both modes.  Inside a sweep, the QR of a two-triangle Khatri-Rao
- * product and each factor QR take a guarded Gram route (Cholesky of the Gram matrix, one
- * orthogonality correction); a pivot that is not positive or a correction above 1e-8 hands
- * that QR to the Householder QR, so the result is the Householder-quality QR either way. */
+ * factor QRs are FP64 in both modes.  Inside a sweep, the Khatri-Rao QR and each factor QR take
+ * a guarded Gram route (Cholesky of the Gram matrix, one orthogonality correction); a pivot that
+ * is not positive or a correction above 1e-8 hands that QR to the Householder QR, so the result is
+ * the Householder-quality QR either way. */
 typedef enum {
   CPQR_PREC_FP64 = 0,      /* every TTM in FP64 (X promoted exactly) */
   CPQR_PREC_SPLIT_BF16 = 1 /* TTMs at every tree level on tcgen05 tensor cores with the
@@ -232,8 +232,8 @@ cpqr_status cpqr_house_qr_noalloc(const double* A_dev, int64_t M, int32_t R, dou
 /* QR of Z = R_1 (.) ... (.) R_m, the Khatri-Rao product of m upper-triangular R x R
  * matrices (Alg. 2 lines 3-4), rows (r_1, ..., r_m) with r_m fastest: Rs_dev holds the m
  * triangles back to back (device, FP64).  Q0_dev (R^m x R) and R0_dev (R x R) receive the
- * factors, diag(R0) > 0.  m = 2 takes the guarded Gram route (see cpqr_prec); m >= 3 the
- * nested Householder staircase QRs. */
+ * factors, diag(R0) > 0, by the guarded Gram route (see cpqr_prec) for m >= 2, whose fallback is
+ * the Householder staircase QR (nested for m >= 3). */
 cpqr_status cpqr_krp_qr(const double* Rs_dev, int32_t m, int32_t R, double* Q0_dev,
                         double* R0_dev, void* stream);
 

@@ -518,11 +518,30 @@ cpqr_status stage_q(cpqr_ctx* ctx, int n) {
   return CPQR_OK;
 }
 
-// The two modes other than n of an order-3 tensor (ascending, as the triangles of Z_n).
-void z_modes(const cpqr_ctx* ctx, int n, int* a, int* b) {
+// The stored Grams and column norms of the modes other than n (ascending, as the triangles of Z_n).
+GramPtrs z_grams(const cpqr_ctx* ctx, int n) {
+  GramPtrs gp{};
   int m = 0;
   for (int k = 0; k < ctx->N; ++k)
-    if (k != n) *(m++ == 0 ? a : b) = k;
+    if (k != n) {
+      gp.g[m] = ctx->Gf[k];
+      gp.s[m] = ctx->cn[k];
+      ++m;
+    }
+  return gp;
+}
+
+// The Grams of the first Cholesky of Z_n's Gram-route QR: the last two triangles (level 2 of the
+// nested QR; all of Z_n for an order-3 tensor).
+GramPtrs z_grams_level2(const cpqr_ctx* ctx, int n) {
+  const GramPtrs all = z_grams(ctx, n);
+  const int m = ctx->N - 1;
+  GramPtrs g2{};
+  g2.g[0] = all.g[m - 2];
+  g2.s[0] = all.s[m - 2];
+  g2.g[1] = all.g[m - 1];
+  g2.s[1] = all.s[m - 1];
+  return g2;
 }
 
 // Alg. 3 lines 3-4 for mode n: QR of the Khatri-Rao product of the other triangles,
@@ -538,22 +557,21 @@ cpqr_status launch_z(cpqr_ctx* ctx, int n) {
   CK(cudaStreamWaitEvent(ctx->st2, ctx->ev_ready, 0));
   {
     Timed tm(ctx, CPQR_BUCKET_Q0, 1, ctx->st2);
-    if (m >= 3) {
+    if (ctx->gram) {
+      if (ctx->zchol_mode != n) {
+        CK(launch_krp_chol(z_grams_level2(ctx, n), 2, ctx->R, ctx->zg_work, ctx->st2));
+        ctx->launches += 1;
+      }
+      ctx->zchol_mode = -1;
+      int nl = 0;
+      CK(launch_krp_rows(ctx->zplan2, tri, m, z_grams(ctx, n), ctx->Q0, ctx->R0, ctx->zg_work, ctx->zq_work,
+                         ctx->dstatus, ctx->st2, ctx->Q0f, &nl));
+      ctx->launches += nl - 1;
+    } else if (m >= 3) {
       int nl = 0;
       CK(launch_krp_qr_nested(ctx->zplan2, tri, m, ctx->Q0, ctx->R0, ctx->zq_work, ctx->dstatus, ctx->st2, ctx->Q0f,
                               &nl));
       ctx->launches += nl - 1;
-    } else if (ctx->gram) {
-      if (ctx->zchol_mode != n) {
-        int a = -1, b = -1;
-        z_modes(ctx, n, &a, &b);
-        CK(launch_krp_chol(ctx->Gf[a], ctx->Gf[b], ctx->cn[a], ctx->cn[b], ctx->R, ctx->zg_work, ctx->st2));
-        ctx->launches += 1;
-      }
-      ctx->zchol_mode = -1;
-      CK(launch_krp_rows(ctx->zplan, tri.p[0], tri.p[1], ctx->Q0, ctx->R0, ctx->zg_work, ctx->zq_work, ctx->dstatus,
-                         ctx->st2, ctx->Q0f));
-      ctx->launches += 3;
     } else {
       CK(launch_krp_qr(ctx->zplan, tri, ctx->Q0, ctx->R0, ctx->zq_work, ctx->dstatus, ctx->st2, ctx->Q0f));
     }
@@ -616,15 +634,13 @@ cpqr_status run_update(cpqr_ctx* ctx, int n, int leaf, double beta, int next_mod
     if (ctx->gram) {
       const int nblk = finish_prep_blocks(I);
       CK(launch_finish_gram_chol(ctx->hpart, ctx->fitpart, nblk, I, R, fo, ctx->fg_work, ctx->Gf[n], ctx->cn[n], st));
-      if (ctx->N == 3 && next_mode >= 0 && next_mode != n && !ctx->z_pending) {
+      if (next_mode >= 0 && next_mode != n && !ctx->z_pending) {
         // the next mode's Khatri-Rao Cholesky needs only the factors' Grams: it runs on the
         // side stream beside the rest of this factor QR
-        int a = -1, b = -1;
-        z_modes(ctx, next_mode, &a, &b);
         CK(cudaEventRecord(ctx->ev_gram, st));
         CK(cudaStreamWaitEvent(ctx->st2, ctx->ev_gram, 0));
         Timed tz(ctx, CPQR_BUCKET_Q0, 1, ctx->st2);
-        CK(launch_krp_chol(ctx->Gf[a], ctx->Gf[b], ctx->cn[a], ctx->cn[b], R, ctx->zg_work, ctx->st2));
+        CK(launch_krp_chol(z_grams_level2(ctx, next_mode), 2, R, ctx->zg_work, ctx->st2));
         ctx->zchol_mode = next_mode;
       }
       CK(launch_finish_gram_rows(ctx->V, ctx->fitpart, nblk, I, R, fo, ctx->fg_work, ctx->qr_work, ctx->dstatus, st));
@@ -1504,10 +1520,12 @@ cpqr_status cpqr_krp_qr(const double* Rs_dev, int32_t m, int32_t R, double* Q0_d
   cudaError_t e = cudaMemcpyAsync(dperm, perm.data(), perm.size() * 4, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(ds, 0, 4, st);
   double* gwork = nullptr;
-  if (e == cudaSuccess && m == 2 && cudaMalloc(&gwork, krp_gram_work_doubles(R) * 8) != cudaSuccess) e = cudaErrorMemoryAllocation;
+  if (e == cudaSuccess && m >= 2 && cudaMalloc(&gwork, krp_gram_work_doubles(R) * 8) != cudaSuccess)
+    e = cudaErrorMemoryAllocation;
+  // the workspace's guard flag and fallback count start at zero
+  if (e == cudaSuccess && gwork) e = cudaMemsetAsync(gwork, 0, krp_gram_work_doubles(R) * 8, st);
   if (e == cudaSuccess) {
-    if (m >= 3) e = launch_krp_qr_nested(plan, tri, m, Q0_dev, R0_dev, work, ds, st);
-    else if (m == 2) e = launch_krp_qr_gram(plan, tri.p[0], tri.p[1], Q0_dev, R0_dev, gwork, work, ds, st);
+    if (m >= 2) e = launch_krp_qr_gram(plan, tri, m, Q0_dev, R0_dev, gwork, work, ds, st);
     else e = launch_krp_qr(plan, tri, Q0_dev, R0_dev, work, ds, st);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);

@@ -100,25 +100,47 @@ size_t krp_qr_work_doubles(const ZPlan& plan);
 // the plan for m = 2) and m - 2 FP64 assemblies; work: krp_nested_work_doubles(m, R) doubles.
 // *nlaunch (optional) receives the number of kernels launched.
 size_t krp_nested_work_doubles(int m, int R);
-// QR of Ra (.) Rb (plan2: the two-triangle plan) by the guarded Gram route (krp_gram.cu): Cholesky
-// of the Hadamard product of the triangles' Grams, one orthogonality correction, and the
-// Householder staircase QR as the fallback when the correction is not small.  gram_work:
-// krp_gram_work_doubles(R) doubles; qr_work: the staircase QR's scratch.
-size_t krp_gram_work_doubles(int R);
-cudaError_t launch_krp_qr_gram(const ZPlan& plan2, const double* Ra, const double* Rb, double* Q0, double* R0,
-                               double* gram_work, double* qr_work, unsigned int* dev_status, cudaStream_t st,
-                               float* Q0f = nullptr);
-// The Khatri-Rao QR of the guarded Gram route in two phases: the Cholesky of D (Ga o Gb) D from
-// the two factors' stored Grams and norms (..._chol), then the rows of Q0, R0 and the guard
-// (..._rows, which needs the triangles).  Both use the same gram_work.
-cudaError_t launch_krp_chol(const float2* Ga, const float2* Gb, const double* sa, const double* sb, int R,
-                            double* gram_work, cudaStream_t st);
-cudaError_t launch_krp_rows(const ZPlan& plan2, const double* Ra, const double* Rb, double* Q0, double* R0,
-                            double* gram_work, double* qr_work, unsigned int* dev_status, cudaStream_t st,
-                            float* Q0f = nullptr);
+// out[(i, w), c] = sum_j QW[w, j] QY[(i, j), c] (i < R, w < mw): the assembly step of the nested QR.
+cudaError_t launch_krp_assemble(const double* QW, int64_t mw, const double* QY, int R, double* out, float* outf,
+                                cudaStream_t st);
+// Buffers of the nested QR inside its work (krp_nested_work_doubles(m, R) doubles): the two level
+// triangles S, Q_Y, the staircase QR's scratch and the two Q_W.
+struct NestedBufs {
+  double* S[2];
+  double* QY;
+  double* qrw;
+  double* QW[2];
+};
+NestedBufs nested_views(double* work, int m, int R);
+// run_if (optional): every launch returns at once unless run_if[0] != 0 (the guarded fallback of
+// the Gram route; each staircase QR that runs adds 1 to run_if[1]).
 cudaError_t launch_krp_qr_nested(const ZPlan& plan2, TriPtrs Rs, int m, double* Q0, double* R0, double* work,
                                  unsigned int* dev_status, cudaStream_t st, float* Q0f = nullptr,
-                                 int* nlaunch = nullptr);
+                                 int* nlaunch = nullptr, int* run_if = nullptr);
+// QR of Z = R_1 (.) ... (.) R_m (m >= 2; plan2: the two-triangle plan) by the guarded Gram route
+// (krp_gram.cu): for m = 2, Cholesky of the Hadamard product of the triangles' equilibrated Grams,
+// FP64 rows over the R^2 rows of Z, one orthogonality correction; for m >= 3 the same for every
+// two-triangle level of the nested QR (level d's Gram is the Hadamard product of the last d
+// Grams) with the nested assembly between levels.  The Householder QR (the staircase QR, nested
+// for m >= 3) is the fallback when a pivot fails or a correction is not small.  gram_work:
+// krp_gram_work_doubles(R) doubles; qr_work: krp_nested_work_doubles(m, R) doubles (m >= 3; the
+// staircase QR's scratch for m = 2).
+size_t krp_gram_work_doubles(int R);
+cudaError_t launch_krp_qr_gram(const ZPlan& plan2, TriPtrs tri, int m, double* Q0, double* R0, double* gram_work,
+                               double* qr_work, unsigned int* dev_status, cudaStream_t st, float* Q0f = nullptr);
+// The same in two phases.  ..._chol: a Cholesky from stored Grams (float-float, 32 x 32 upper) and
+// column norms: for the QR, the last two triangles' (level 2; the whole product for m = 2); acc = 1
+// keeps the guard of earlier levels.  ..._rows: everything after, with the Grams of all m
+// triangles (gp, in the order of tri) for the later levels.  *nlaunch (optional): kernels
+// launched by ..._rows.
+struct GramPtrs {
+  const float2* g[CPQR_MAXN - 1];
+  const double* s[CPQR_MAXN - 1];
+};
+cudaError_t launch_krp_chol(const GramPtrs& gp, int m, int R, double* gram_work, cudaStream_t st, int acc = 0);
+cudaError_t launch_krp_rows(const ZPlan& plan2, TriPtrs tri, int m, const GramPtrs& gp, double* Q0, double* R0,
+                            double* gram_work, double* qr_work, unsigned int* dev_status, cudaStream_t st,
+                            float* Q0f = nullptr, int* nlaunch = nullptr);
 
 // V[i, c] = sum_{p, s} Y[p, i, s] * Qc[p*S + s, c], c < C, Qc = [Q0 | Q0prev] (K x C,
 // K = P*S), as *nparts split-K slices of I x C in work (leaf_v_splits(I, K) * I * C

@@ -44,10 +44,12 @@ constexpr double kEMax = 1e-8;
 
 // Workspace layout (doubles, every section 128-byte aligned): the int pair {fallback flag,
 // fallback count} (at a fixed offset, so the count survives calls with different row counts),
-// R1, S (R1 scaled for the substitution), F, rinv, 1/lambda (the equilibration), two Grams in
+// R1, S (R1 scaled for the substitution), F, rinv, 1/lambda (the equilibration), KG_MAXM Grams in
 // float-float and their column norms (for a QR whose triangles come without stored Grams), F in
-// float-float, Q1 (M x R), Q1^T (R x M).
+// float-float, the block partials of E for many rows (KG_EBLK x 17 x 32), Q1 (M x R), Q1^T (R x M).
 constexpr size_t KG_HEAD = 16;
+constexpr int KG_MAXM = CPQR_MAXN - 1;  // triangles of a Khatri-Rao product
+constexpr int KG_EBLK = 152;            // blocks of the many-row E pass
 size_t kg_round16(size_t n) { return (n + 15) / 16 * 16; }
 struct KgWork {
   int* flag;
@@ -56,17 +58,17 @@ struct KgWork {
   double* F;
   double* rinv;
   double* il;
-  float2* ga;
-  float2* gb;
-  double* sa;
-  double* sb;
+  float2* g[KG_MAXM];
+  double* s[KG_MAXM];
   float2* Ff;
+  double* epart;
   double* Q1;
   double* Q1T;
 };
 
 size_t kg_work_doubles(int64_t M, int R) {
-  return KG_HEAD + 6 * (size_t)KG_MAXR * KG_MAXR + 4 * KG_MAXR + 2 * kg_round16((size_t)M * R);
+  return KG_HEAD + (5 + KG_MAXM) * (size_t)KG_MAXR * KG_MAXR + (2 + KG_MAXM) * KG_MAXR +
+         kg_round16((size_t)KG_EBLK * 17 * 32) + 2 * kg_round16((size_t)M * R);
 }
 
 KgWork kg_views(double* work, int R, int64_t M) {
@@ -78,12 +80,12 @@ KgWork kg_views(double* work, int R, int64_t M) {
   w.F = w.S + rr;
   w.rinv = w.F + rr;
   w.il = w.rinv + KG_MAXR;
-  w.ga = reinterpret_cast<float2*>(w.il + KG_MAXR);
-  w.gb = reinterpret_cast<float2*>(w.il + KG_MAXR + rr);
-  w.sa = w.il + KG_MAXR + 2 * rr;
-  w.sb = w.sa + KG_MAXR;
-  w.Ff = reinterpret_cast<float2*>(w.sb + KG_MAXR);
-  w.Q1 = w.sb + KG_MAXR + rr;
+  double* p = w.il + KG_MAXR;
+  for (int k = 0; k < KG_MAXM; ++k, p += rr) w.g[k] = reinterpret_cast<float2*>(p);
+  for (int k = 0; k < KG_MAXM; ++k, p += KG_MAXR) w.s[k] = p;
+  w.Ff = reinterpret_cast<float2*>(p);
+  w.epart = p + rr;
+  w.Q1 = w.epart + kg_round16((size_t)KG_EBLK * 17 * 32);
   w.Q1T = w.Q1 + kg_round16((size_t)M * R);
   return w;
 }
@@ -227,7 +229,8 @@ __device__ __forceinline__ void chol_pipelined(float2 (*G)[KG_LD], float2 (*U)[K
 // Upper-triangle entries are visited as folded pairs (all lanes live); the flag last.  rsd, csd:
 // 32 doubles of shared scratch each.
 __device__ __forceinline__ void chol_outputs(float2 (*U)[KG_LD], float2 (*V)[KG_LD], double* rsd, double* csd,
-                                             const double* colscale, int R, const KgWork& w, int* bad) {
+                                             const double* colscale, int R, const KgWork& w, int* bad,
+                                             int acc = 0) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid < 32) {
     const double d = (lane < R) ? ff_val(U[lane][lane]) : 1.0;
@@ -261,7 +264,7 @@ __device__ __forceinline__ void chol_outputs(float2 (*U)[KG_LD], float2 (*V)[KG_
     w.R1[i * KG_MAXR + j] = r;
     w.S[i * KG_MAXR + j] = sv;
   }
-  if (tid == 0) *w.flag = *bad;
+  if (tid == 0) *w.flag = acc ? (*w.flag | *bad) : *bad;  // acc: a later level of one nested QR
 }
 
 // Equilibrated Gram of an upper triangle T (one CTA of 256 threads per triangle, FP64):
@@ -298,37 +301,42 @@ __global__ void __launch_bounds__(256) tri_gram_kernel(TriPtrs tri, int R, float
   }
 }
 
-// Cholesky of the Khatri-Rao product's equilibrated Gram, one CTA of 256 threads.  Row (i, k)
-// of Z = R_a (.) R_b is R_a[i, :] o R_b[k, :], so Z^T Z = (R_a^T R_a) o (R_b^T R_b) =
-// (A_a^T A_a) o (A_b^T A_b) (up to the rounding of the factor QRs), and with the factors'
-// equilibrated Grams Ga, Gb (float-float) and column norms sa, sb:
-// Z^T Z = D (Ga o Gb) D, D = diag(sa sb).  The Gram thus costs one float-float Hadamard product
-// and no pass over the triangles, and this kernel needs only the two Grams: a sweep launches it
-// as soon as the previous factor's Gram exists, before that factor's QR has finished.
-__global__ void __launch_bounds__(256) kg_chol_kernel(const float2* __restrict__ Ga, const float2* __restrict__ Gb,
-                                                       const double* __restrict__ sa, const double* __restrict__ sb,
-                                                       int R, KgWork w) {
+// Cholesky of the Khatri-Rao product's equilibrated Gram, one CTA of 256 threads.  A row of
+// Z = R_1 (.) ... (.) R_m is the Hadamard product of one row of each triangle, so
+// Z^T Z = (R_1^T R_1) o ... o (R_m^T R_m) = (A_1^T A_1) o ... o (A_m^T A_m) (up to the rounding
+// of the factor QRs), and with the factors' equilibrated Grams G_k (float-float) and column norms
+// s_k: Z^T Z = D (G_1 o ... o G_m) D, D = diag(s_1 ... s_m).  The Gram thus costs float-float
+// Hadamard products and no pass over the triangles, and this kernel needs only the Grams: a sweep
+// launches it as soon as the previous factor's Gram exists, before that factor's QR has finished.
+__global__ void __launch_bounds__(256) kg_chol_kernel(GramPtrs gp, int m, int R, int acc, KgWork w) {
   __shared__ __align__(16) float2 Gf[KG_MAXR][KG_LD], U[KG_MAXR][KG_LD], V[KG_MAXR][KG_LD];
   __shared__ double scale[KG_MAXR], rsd[KG_MAXR], csd[KG_MAXR];
   __shared__ int bad;
   const int tid = threadIdx.x, lane = tid & 31;
   pdl_wait();
   if (tid < 32) {
-    const double sc = (lane < R) ? sa[lane] * sb[lane] : 0.0;
+    double sc = (lane < R) ? 1.0 : 0.0;
+    for (int k = 0; k < m; ++k) sc *= (lane < R) ? gp.s[k][lane] : 0.0;
     scale[lane] = sc;
     w.il[lane] = (sc > 0.0 && sc < 1e300) ? 1.0 / sc : 0.0;
   }
   if (tid == 0) bad = 0;
   for (int e = tid; e < KG_MAXR * KG_MAXR; e += 256) {
     const int i = e / KG_MAXR, j = e % KG_MAXR;
-    Gf[i][j] = (i <= j && j < R) ? ff_st(ff_mul(ff_ld(Ga[e]), ff_ld(Gb[e]))) : make_float2(0.0f, 0.0f);
+    float2 g = make_float2(0.0f, 0.0f);
+    if (i <= j && j < R) {
+      ffn h = ff_ld(gp.g[0][e]);
+      for (int k = 1; k < m; ++k) h = ff_mul(h, ff_ld(gp.g[k][e]));
+      g = ff_st(h);
+    }
+    Gf[i][j] = g;
     U[i][j] = make_float2(0.0f, 0.0f);
     V[i][j] = make_float2(0.0f, 0.0f);
   }
   __syncthreads();
   chol_pipelined(Gf, U, V, R, &bad);
   __syncthreads();
-  chol_outputs(U, V, rsd, csd, scale, R, w, &bad);
+  chol_outputs(U, V, rsd, csd, scale, R, w, &bad, acc);
 }
 
 // Factor route, Gram and Cholesky on one 16-CTA cluster of 256 threads: CTA r adds up folded
@@ -468,13 +476,11 @@ __global__ void __launch_bounds__(128) fg_q1_kernel(const double* __restrict__ A
 }
 
 // Q1 = Z R1^{-1} = (Z D^-1) R1e^{-1} (R1e: the equilibrated factor, D = diag(||Z e_c||)): one row
-// (i, k) of Z per warp, z[c] = Ra[i][c] Rb[k][c] / D[c]; forward substitution q R1e = z with
+// (i_1, ..., i_m) of Z per warp, z[c] = prod_k R_k[i_k][c] / D[c]; forward substitution q R1e = z with
 // lane = column (x[c'] -= x[c] S[c][c'] after column c, q[c] = x[c] / R1e[c][c]).  Writes Q1
 // row-major and transposed.
-__global__ void __launch_bounds__(128) kg_q1_kernel(const double* __restrict__ Ra, const double* __restrict__ Rb,
-                                                     int R, KgWork w) {
+__global__ void __launch_bounds__(128) kg_q1_kernel(TriPtrs tri, int m, int M, int R, KgWork w) {
   const int lane = threadIdx.x & 31;
-  const int M = R * R;
   const int t = blockIdx.x * 4 + (threadIdx.x >> 5);
   pdl_wait();
   if (t >= M) return;
@@ -483,9 +489,18 @@ __global__ void __launch_bounds__(128) kg_q1_kernel(const double* __restrict__ R
 #pragma unroll
   for (int c = 0; c < KG_MAXR; ++c) scol[c] = (c < R && lane > c && lane < R) ? w.S[c * KG_MAXR + lane] : 0.0;
   const double ri = (lane < R) ? w.rinv[lane] : 0.0;
-  const int i = t / R, k = t - i * R;
-  // row (i, k) of Z, equilibrated like the Gram (column c times 1 / ||Z e_c||)
-  double x = (lane < R) ? Ra[i * R + lane] * Rb[k * R + lane] * w.il[lane] : 0.0;
+  // row t = (i_1, ..., i_m) of Z (i_m fastest), equilibrated like the Gram (column c times
+  // 1 / ||Z e_c||)
+  double x = 0.0;
+  if (lane < R) {
+    x = w.il[lane];
+    int rest = t;
+    for (int k = m - 1; k >= 0; --k) {
+      const int ik = rest % R;
+      rest /= R;
+      x *= tri.p[k][ik * R + lane];
+    }
+  }
 #pragma unroll
   for (int c = 0; c < KG_MAXR - 1; ++c) {
     if (c + 1 < R) {
@@ -539,6 +554,86 @@ __global__ void __launch_bounds__(128) kg_e_kernel(int M, int R, KgWork w) {
     w.Ff[c * KG_MAXR + d] = ff_st(ff_from_bits(f));
     if (!(fabs(e) <= kEMax)) atomicOr(w.flag, 1);  // also catches NaN
   }
+}
+
+// E for many rows (M > 1024, where one warp per entry would stream all rows): pass 1, KG_EBLK
+// blocks of 4 warps, each warp adding the folded products q[c] q[(c+k)%32] (k = 0..16) of rows
+// gw, gw + 4 KG_EBLK, ... (four rows loaded ahead); the block's sums to epart[blk][k][c].
+__global__ void __launch_bounds__(128) kg_epart_kernel(int M, int R, KgWork w) {
+  __shared__ double red[4][17][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * 4 + warp, nw = gridDim.x * 4;
+  pdl_wait();
+  double h[17];
+#pragma unroll
+  for (int k = 0; k < 17; ++k) h[k] = 0.0;
+  for (int t0 = gw; t0 < M; t0 += 4 * nw) {
+    double q[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int t = t0 + u * nw;
+      q[u] = (t < M && lane < R) ? w.Q1[(size_t)t * R + lane] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+#pragma unroll
+      for (int k = 0; k < 17; ++k) h[k] = fma(q[u], __shfl_sync(FULL, q[u], (lane + k) & 31), h[k]);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 17; ++k) red[warp][k][lane] = h[k];
+  __syncthreads();
+  for (int e = threadIdx.x; e < 17 * 32; e += 128) {
+    const int k = e >> 5, c = e & 31;
+    w.epart[(size_t)blockIdx.x * 17 * 32 + e] = (red[0][k][c] + red[1][k][c]) + (red[2][k][c] + red[3][k][c]);
+  }
+}
+
+// Pass 2: block k adds folded row k of the partials over the pass-1 blocks (fixed order) and
+// writes F, the float-float F and the guard, as kg_e_kernel does.
+__global__ void __launch_bounds__(128) kg_ered_kernel(int nblk, int R, KgWork w) {
+  __shared__ double red[4][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int k = blockIdx.x;
+  pdl_wait();
+  double a[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int b0 = warp; b0 < nblk; b0 += 64) {
+    double x[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int b = b0 + 4 * u;
+      x[u] = (b < nblk) ? w.epart[(size_t)b * 17 * 32 + k * 32 + lane] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 16; ++u) a[u & 3] += x[u];
+  }
+  red[warp][lane] = (a[0] + a[1]) + (a[2] + a[3]);
+  __syncthreads();
+  if (warp == 0) {
+    const double sum = (red[0][lane] + red[1][lane]) + (red[2][lane] + red[3][lane]);
+    const int c = lane, d = (lane + k) & 31, i = min(c, d), j = max(c, d);
+    if (j < R) {
+      const double e = (i == j) ? sum - 1.0 : sum;
+      const double f = (i == j) ? 0.5 * e : e;
+      w.F[i * KG_MAXR + j] = f;
+      w.Ff[i * KG_MAXR + j] = ff_st(ff_from_bits(f));
+      if (!(fabs(e) <= kEMax)) atomicOr(w.flag, 1);  // also catches NaN
+    }
+  }
+}
+
+// E, F and the guard for M rows: the one-warp-per-entry kernel up to 1024 rows, the two passes
+// above beyond.  *n: kernels launched.
+cudaError_t launch_e(int M, int R, const KgWork& w, cudaStream_t st, int* n) {
+  if (M <= 1024) {
+    *n = 1;
+    const int npair = R * (R + 1) / 2;
+    return launch_pdl(kg_e_kernel, dim3((npair + 3) / 4), dim3(128), 0, st, M, R, w);
+  }
+  *n = 2;
+  cudaError_t e = launch_pdl(kg_epart_kernel, dim3(KG_EBLK), dim3(128), 0, st, M, R, w);
+  if (e != cudaSuccess) return e;
+  return launch_pdl(kg_ered_kernel, dim3(17), dim3(128), 0, st, (int)KG_EBLK, R, w);
 }
 
 // Q0 = Q1 (I - F) (one row per warp, lane = column: q0[c] = q1[c] - sum_{k <= c} q1[k] F[k][c]),
@@ -608,7 +703,6 @@ cudaError_t kg_cluster_attributes() {
 
 }  // namespace
 
-size_t krp_gram_work_doubles(int R) { return kg_work_doubles((int64_t)R * R, R); }
 size_t factor_gram_work_doubles(int64_t Imax, int R) { return kg_work_doubles(Imax, R); }
 int* gram_fallback_counter(double* gram_work) { return reinterpret_cast<int*>(gram_work) + 1; }
 
@@ -620,50 +714,102 @@ cudaError_t launch_tri_gram(const double* T, int R, float2* Gf, double* s, cudaS
   return cudaGetLastError();
 }
 
-cudaError_t launch_krp_chol(const float2* Ga, const float2* Gb, const double* sa, const double* sb, int R,
-                            double* gram_work, cudaStream_t st) {
-  if (R < 1 || R > KG_MAXR) return cudaErrorInvalidValue;
+size_t krp_gram_work_doubles(int R) { return kg_work_doubles((int64_t)R * R, R); }
+
+cudaError_t launch_krp_chol(const GramPtrs& gp, int m, int R, double* gram_work, cudaStream_t st, int acc) {
+  if (R < 1 || R > KG_MAXR || m < 2 || m > KG_MAXM) return cudaErrorInvalidValue;
   const KgWork w = kg_views(gram_work, R, (int64_t)R * R);
-  return launch_pdl(kg_chol_kernel, dim3(1), dim3(256), 0, st, Ga, Gb, sa, sb, R, w);
+  return launch_pdl(kg_chol_kernel, dim3(1), dim3(256), 0, st, gp, m, R, acc, w);
 }
 
-cudaError_t launch_krp_rows(const ZPlan& plan2, const double* Ra, const double* Rb, double* Q0, double* R0,
-                            double* gram_work, double* qr_work, unsigned int* dev_status, cudaStream_t st,
-                            float* Q0f) {
-  const int R = plan2.R;
-  if (plan2.m != 2 || R < 1 || R > KG_MAXR || plan2.M != (int64_t)R * R) return cudaErrorInvalidValue;
+// The rows of a Gram-route QR of a two-triangle product (R^2 rows) after its Cholesky: Q1, E and
+// the guard, then Q (and Qf) and the triangle Rt.  *n: kernels launched.
+static cudaError_t krp_rows_only(const double* Ra, const double* Rb, int R, const KgWork& w, double* Q, float* Qf,
+                                 double* Rt, cudaStream_t st, int* n) {
   const int M = R * R;
-  const KgWork w = kg_views(gram_work, R, M);
-  cudaError_t e = launch_pdl(kg_q1_kernel, dim3((M + 3) / 4), dim3(128), 0, st, Ra, Rb, R, w);
-  if (e != cudaSuccess) return e;
-  const int npair = R * (R + 1) / 2;
-  e = launch_pdl(kg_e_kernel, dim3((npair + 3) / 4), dim3(128), 0, st, M, R, w);
-  if (e != cudaSuccess) return e;
-  e = launch_pdl(kg_q0_kernel, dim3((M + 3) / 4), dim3(128), 0, st, M, R, w, Q0, Q0f, R0, (__nv_bfloat16*)nullptr, 0,
-                 (int64_t)0);
-  if (e != cudaSuccess) return e;
-  // the Householder staircase QR, which returns at once unless the flag was raised
-  TriPtrs t2{};
-  t2.p[0] = Ra;
-  t2.p[1] = Rb;
-  return launch_krp_qr(plan2, t2, Q0, R0, qr_work, dev_status, st, Q0f, w.flag);
-}
-
-cudaError_t launch_krp_qr_gram(const ZPlan& plan2, const double* Ra, const double* Rb, double* Q0, double* R0,
-                               double* gram_work, double* qr_work, unsigned int* dev_status, cudaStream_t st,
-                               float* Q0f) {
-  const int R = plan2.R;
-  if (plan2.m != 2 || R < 1 || R > KG_MAXR || plan2.M != (int64_t)R * R) return cudaErrorInvalidValue;
-  const KgWork w = kg_views(gram_work, R, (int64_t)R * R);
   TriPtrs t{};
   t.p[0] = Ra;
   t.p[1] = Rb;
-  tri_gram_kernel<<<2, 256, 0, st>>>(t, R, w.ga, w.sa);  // ga, gb and sa, sb are adjacent
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = launch_pdl(kg_q1_kernel, dim3((M + 3) / 4), dim3(128), 0, st, t, 2, M, R, w);
   if (e != cudaSuccess) return e;
-  e = launch_krp_chol(w.ga, w.gb, w.sa, w.sb, R, gram_work, st);
+  int ne = 0;
+  e = launch_e(M, R, w, st, &ne);
   if (e != cudaSuccess) return e;
-  return launch_krp_rows(plan2, Ra, Rb, Q0, R0, gram_work, qr_work, dev_status, st, Q0f);
+  *n = 2 + ne;
+  return launch_pdl(kg_q0_kernel, dim3((M + 3) / 4), dim3(128), 0, st, M, R, w, Q, Qf, Rt, (__nv_bfloat16*)nullptr, 0,
+                    (int64_t)0);
+}
+
+cudaError_t launch_krp_rows(const ZPlan& plan2, TriPtrs tri, int m, const GramPtrs& gp, double* Q0, double* R0,
+                            double* gram_work, double* qr_work, unsigned int* dev_status, cudaStream_t st,
+                            float* Q0f, int* nlaunch) {
+  const int R = plan2.R;
+  if (plan2.m != 2 || R < 1 || R > KG_MAXR || m < 2 || m > KG_MAXM) return cudaErrorInvalidValue;
+  const KgWork w = kg_views(gram_work, R, (int64_t)R * R);
+  int launches = 0, n = 0;
+  cudaError_t e;
+  if (m == 2) {
+    e = krp_rows_only(tri.p[0], tri.p[1], R, w, Q0, Q0f, R0, st, &n);
+    if (e != cudaSuccess) return e;
+    launches += n;
+    // the Householder staircase QR, which returns at once unless the flag was raised
+    e = launch_krp_qr(plan2, tri, Q0, R0, qr_work, dev_status, st, Q0f, w.flag);
+    if (nlaunch) *nlaunch = launches + 1;
+    return e;
+  }
+  // nested: level 2, R_{m-1} (.) R_m = Q_W S (its Cholesky issued by the caller); level d = 3..m,
+  // R_{m-d} (.) S = Q_Y S' with the Gram of S the Hadamard product of the later triangles' Grams
+  // (S^T S is the previous level's Gram), and Q_W <- (I (x) Q_W) Q_Y; the guard accumulates over
+  // the levels, and the nested Householder QR recomputes everything if it tripped
+  const NestedBufs nb = nested_views(qr_work, m, R);
+  e = krp_rows_only(tri.p[m - 2], tri.p[m - 1], R, w, nb.QW[0], nullptr, nb.S[0], st, &n);
+  if (e != cudaSuccess) return e;
+  launches += n;
+  int cur = 0;
+  int64_t mw = (int64_t)R * R;
+  for (int d = 3; d <= m; ++d) {
+    const bool last = (d == m);
+    GramPtrs gd{};
+    for (int k = 0; k < d; ++k) {
+      gd.g[k] = gp.g[m - d + k];
+      gd.s[k] = gp.s[m - d + k];
+    }
+    e = launch_krp_chol(gd, d, R, gram_work, st, 1);
+    if (e != cudaSuccess) return e;
+    e = krp_rows_only(tri.p[m - d], nb.S[(d - 3) & 1], R, w, nb.QY, nullptr, last ? R0 : nb.S[(d - 2) & 1], st, &n);
+    if (e != cudaSuccess) return e;
+    e = launch_krp_assemble(nb.QW[cur], mw, nb.QY, R, last ? Q0 : nb.QW[cur ^ 1], last ? Q0f : nullptr, st);
+    if (e != cudaSuccess) return e;
+    launches += n + 2;
+    cur ^= 1;
+    mw *= R;
+  }
+  int nf = 0;
+  e = launch_krp_qr_nested(plan2, tri, m, Q0, R0, qr_work, dev_status, st, Q0f, &nf, w.flag);
+  if (nlaunch) *nlaunch = launches + nf;
+  return e;
+}
+
+cudaError_t launch_krp_qr_gram(const ZPlan& plan2, TriPtrs tri, int m, double* Q0, double* R0, double* gram_work,
+                               double* qr_work, unsigned int* dev_status, cudaStream_t st, float* Q0f) {
+  const int R = plan2.R;
+  if (plan2.m != 2 || R < 1 || R > KG_MAXR || m < 2 || m > KG_MAXM) return cudaErrorInvalidValue;
+  const KgWork w = kg_views(gram_work, R, (int64_t)R * R);
+  GramPtrs gp{};
+  for (int k = 0; k < m; ++k) {
+    cudaError_t e = launch_tri_gram(tri.p[k], R, w.g[k], w.s[k], st);
+    if (e != cudaSuccess) return e;
+    gp.g[k] = w.g[k];
+    gp.s[k] = w.s[k];
+  }
+  GramPtrs g2{};  // level 2 (or the whole product for m = 2): the last two triangles
+  g2.g[0] = gp.g[m - 2];
+  g2.s[0] = gp.s[m - 2];
+  g2.g[1] = gp.g[m - 1];
+  g2.s[1] = gp.s[m - 1];
+  cudaError_t e = launch_krp_chol(g2, 2, R, gram_work, st, 0);
+  if (e != cudaSuccess) return e;
+  return launch_krp_rows(plan2, tri, m, gp, Q0, R0, gram_work, qr_work, dev_status, st, Q0f, nullptr);
 }
 
 cudaError_t launch_finish_gram_chol(const double* hpart, const double* fitpart, int nblk, int64_t I, int R,
@@ -686,8 +832,8 @@ cudaError_t launch_finish_gram_rows(const double* Ahat, const double* fitpart, i
   const KgWork w = kg_views(gram_work, R, M);
   cudaError_t e = launch_pdl(fg_q1_kernel, dim3((M + 3) / 4), dim3(128), 0, st, Ahat, M, R, w, out.A);
   if (e != cudaSuccess) return e;
-  const int npair = R * (R + 1) / 2;
-  e = launch_pdl(kg_e_kernel, dim3((npair + 3) / 4), dim3(128), 0, st, M, R, w);
+  int ne = 0;
+  e = launch_e(M, R, w, st, &ne);
   if (e != cudaSuccess) return e;
   e = launch_pdl(kg_q0_kernel, dim3((M + 3) / 4), dim3(128), 0, st, M, R, w, out.Q, out.Qf, out.Rn, out.Qt, out.Rp,
                  out.Kp);

@@ -797,10 +797,13 @@ cudaError_t launch_krp_qr(const ZPlan& plan, TriPtrs Rs, double* Q0, double* R0,
 // ---------------------------------------------------------------------------
 
 // out[(i, w), c] = sum_j QW[w, j] QY[(i, j), c] for i < R, w < Mw (row (i, w) = i * Mw + w);
-// one row per Rpad lanes (Rpad = R rounded up to a power of two), lane = column c.
+// one row per Rpad lanes (Rpad = R rounded up to a power of two), lane = column c.  run_if (a
+// guarded fallback): returns at once unless *run_if != 0.
 __global__ void __launch_bounds__(256) krp_assemble_kernel(const double* __restrict__ QW, int64_t Mw,
                                                             const double* __restrict__ QY, int R, int Rpad,
-                                                            double* __restrict__ out, float* __restrict__ outf) {
+                                                            double* __restrict__ out, float* __restrict__ outf,
+                                                            const int* run_if) {
+  if (run_if && *(volatile const int*)run_if == 0) return;
   const int lane = threadIdx.x & 31, sub = lane / Rpad, c = lane % Rpad;
   const int rpw = 32 / Rpad;
   const int64_t rows = (int64_t)R * Mw;
@@ -823,6 +826,30 @@ __global__ void __launch_bounds__(256) krp_assemble_kernel(const double* __restr
   }
 }
 
+cudaError_t launch_krp_assemble(const double* QW, int64_t mw, const double* QY, int R, double* out, float* outf,
+                                cudaStream_t st) {
+  int Rpad = 1;
+  while (Rpad < R) Rpad <<= 1;
+  const int64_t rows = (int64_t)R * mw;
+  const int64_t warps = (rows + (32 / Rpad) - 1) / (32 / Rpad);
+  const int grid = (int)std::min<int64_t>((warps + 7) / 8, 152 * 8);
+  krp_assemble_kernel<<<grid, 256, 0, st>>>(QW, mw, QY, R, Rpad, out, outf, nullptr);
+  return cudaGetLastError();
+}
+
+NestedBufs nested_views(double* work, int m, int R) {
+  size_t Mw = 1;
+  for (int k = 0; k < m - 1; ++k) Mw *= (size_t)R;
+  NestedBufs b;
+  b.S[0] = work;
+  b.S[1] = work + (size_t)R * R;
+  b.QY = work + 2 * (size_t)R * R;
+  b.qrw = b.QY + (size_t)R * R * R;
+  b.QW[0] = b.qrw + (size_t)R * R * R;
+  b.QW[1] = b.QW[0] + Mw * R;
+  return b;
+}
+
 size_t krp_nested_work_doubles(int m, int R) {
   size_t Mw = 1;
   for (int k = 0; k < m - 1; ++k) Mw *= (size_t)R;
@@ -831,7 +858,7 @@ size_t krp_nested_work_doubles(int m, int R) {
 }
 
 cudaError_t launch_krp_qr_nested(const ZPlan& plan2, TriPtrs Rs, int m, double* Q0, double* R0, double* work,
-                                 unsigned int* dev_status, cudaStream_t st, float* Q0f, int* nlaunch) {
+                                 unsigned int* dev_status, cudaStream_t st, float* Q0f, int* nlaunch, int* run_if) {
   const int R = plan2.R;
   if (plan2.m != 2 || m < 2 || m > CPQR_MAXN || R < 1 || R > CPQR_MAXR) return cudaErrorInvalidValue;
   int launches = 0;
@@ -840,16 +867,15 @@ cudaError_t launch_krp_qr_nested(const ZPlan& plan2, TriPtrs Rs, int m, double* 
   t2.p[1] = Rs.p[m - 1];
   if (m == 2) {
     if (nlaunch) *nlaunch = 1;
-    return launch_krp_qr(plan2, t2, Q0, R0, work, dev_status, st, Q0f);
+    return launch_krp_qr(plan2, t2, Q0, R0, work, dev_status, st, Q0f, run_if);
   }
-  size_t Mw = 1;
-  for (int k = 0; k < m - 1; ++k) Mw *= (size_t)R;
-  double* S[2] = {work, work + (size_t)R * R};
-  double* QY = work + 2 * (size_t)R * R;
-  double* qrw = QY + (size_t)R * R * R;
-  double* QW[2] = {qrw + (size_t)R * R * R, qrw + (size_t)R * R * R + Mw * R};
+  const NestedBufs nb = nested_views(work, m, R);
+  double* const* S = nb.S;
+  double* QY = nb.QY;
+  double* qrw = nb.qrw;
+  double* const* QW = nb.QW;
   // level 2: R_{k(m-1)} (.) R_{km} = Q_{W,2} S_2
-  cudaError_t e = launch_krp_qr(plan2, t2, QW[0], S[0], qrw, dev_status, st);
+  cudaError_t e = launch_krp_qr(plan2, t2, QW[0], S[0], qrw, dev_status, st, nullptr, run_if);
   if (e != cudaSuccess) return e;
   ++launches;
   int cur = 0;
@@ -861,13 +887,13 @@ cudaError_t launch_krp_qr_nested(const ZPlan& plan2, TriPtrs Rs, int m, double* 
     TriPtrs t{};
     t.p[0] = Rs.p[m - d];
     t.p[1] = S[(d - 3) & 1];
-    e = launch_krp_qr(plan2, t, QY, last ? R0 : S[(d - 2) & 1], qrw, dev_status, st);
+    e = launch_krp_qr(plan2, t, QY, last ? R0 : S[(d - 2) & 1], qrw, dev_status, st, nullptr, run_if);
     if (e != cudaSuccess) return e;
     double* out = last ? Q0 : QW[cur ^ 1];
     const int64_t rows = (int64_t)R * mw;
     const int64_t warps = (rows + (32 / Rpad) - 1) / (32 / Rpad);
     const int grid = (int)std::min<int64_t>((warps + 7) / 8, 152 * 8);
-    krp_assemble_kernel<<<grid, 256, 0, st>>>(QW[cur], mw, QY, R, Rpad, out, last ? Q0f : nullptr);
+    krp_assemble_kernel<<<grid, 256, 0, st>>>(QW[cur], mw, QY, R, Rpad, out, last ? Q0f : nullptr, run_if);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     launches += 2;
