@@ -120,6 +120,9 @@ typedef struct {
   int64_t n_bucket[CPQR_NBUCKETS];   /* launches per bucket (only while timing is on) */
   int64_t qr_fallbacks;    /* Gram-route QRs (Khatri-Rao and factor) whose guard handed them to
                               the Householder QR; reading it synchronises the context's streams */
+  int64_t krp_split;       /* Khatri-Rao QRs (order >= 4, Gram route) that took the split route:
+                              the QR of the other triangles formed one update ahead, only the level
+                              with the last-updated triangle after that update */
 } cpqr_stats;
 
 /* Turn per-launch CUDA-event timing on (1) or off (0); resets the bucket times. */

@@ -159,6 +159,20 @@ struct cpqr_ctx {
   float2* Gf[CPQR_MAXN] = {};
   double* cn[CPQR_MAXN] = {};
   int zchol_mode = -1;               // mode whose Khatri-Rao Cholesky is already issued on st2
+  bool zchol_split = false;          // ... and it is the split route's (all m Grams, W's guard)
+  // Split Khatri-Rao QR (Gram route, N - 1 >= 3 triangles): right behind the QR for mode n, st2
+  // forms the QR of W, the product of the triangles of every mode but n and the update after n
+  // (they are final by then); that next update's QR then waits for its last level only, the one
+  // with R_n.  Stream order on st2 keeps W's buffers apart from their previous reader.
+  double* wg_work = nullptr;
+  double* wq_work = nullptr;
+  double* WQ = nullptr;  // Q_W, R^(N-2) x R
+  double* WS = nullptr;  // S_W, R x R
+  bool w_ok = false;     // the buffers above exist (N - 1 >= 3)
+  int wpf_mode = -1;     // the update whose W is formed; -1: none
+  int wpf_excl = -1;     // the update before it, left out of W
+  int last_updated = -1;  // mode of the last update enqueued
+  int64_t n_split = 0;    // Khatri-Rao QRs issued on the split route
   cudaEvent_t ev_gram = nullptr;     // main stream: the last factor's Gram stored
   double* fg_work = nullptr;       // Gram-route factor QR workspace
   double* hpart = nullptr;         // per-block folded Gram partials of A^ (finish prep)
@@ -499,6 +513,8 @@ cpqr_status checkpoint_restore(cpqr_ctx* ctx, int slot) {
   ctx->Q0f = c.Q0f;
   ctx->z_pending = false;
   ctx->zchol_mode = -1;
+  ctx->wpf_mode = -1;
+  ctx->last_updated = -1;
   return CPQR_OK;
 }
 
@@ -544,25 +560,79 @@ GramPtrs z_grams_level2(const cpqr_ctx* ctx, int n) {
   return g2;
 }
 
+// The QR of W for the update `after` (the one that follows n): the triangles of every mode but n
+// and `after`, final once the update before n has run.  On st2 behind the QR for mode n: beside
+// it on a stream of its own, W's kernels shared the SMs with the TTM chain's persistent grid and
+// held it back by about what they saved (48^5, R = 16: 1.945 against 1.928 ms per sweep).
+cpqr_status launch_w(cpqr_ctx* ctx, int n, int after) {
+  TriPtrs tw{};
+  GramPtrs gw{};
+  int mw = 0;
+  for (int k = 0; k < ctx->N; ++k)
+    if (k != n && k != after) {
+      tw.p[mw] = ctx->Rf[k];
+      gw.g[mw] = ctx->Gf[k];
+      gw.s[mw] = ctx->cn[k];
+      ++mw;
+    }
+  GramPtrs g2{};
+  g2.g[0] = gw.g[mw - 2];
+  g2.s[0] = gw.s[mw - 2];
+  g2.g[1] = gw.g[mw - 1];
+  g2.s[1] = gw.s[mw - 1];
+  {
+    Timed tm(ctx, CPQR_BUCKET_Q0, 1, ctx->st2);
+    CK(launch_krp_chol(g2, 2, ctx->R, ctx->wg_work, ctx->st2));
+    int nl = 0;
+    CK(launch_krp_rows(ctx->zplan2, tw, mw, gw, ctx->WQ, ctx->WS, ctx->wg_work, ctx->wq_work, ctx->dstatus, ctx->st2,
+                       nullptr, &nl, false));
+    ctx->launches += nl;
+  }
+  ctx->wpf_mode = after;
+  ctx->wpf_excl = n;
+  return CPQR_OK;
+}
+
+// Whether the split route serves the QR for mode n: W formed for n, leaving out the last update.
+bool split_ready(const cpqr_ctx* ctx, int n) {
+  return ctx->gram && ctx->w_ok && ctx->wpf_mode == n && ctx->last_updated >= 0 &&
+         ctx->wpf_excl == ctx->last_updated && ctx->last_updated != n;
+}
+
 // Alg. 3 lines 3-4 for mode n: QR of the Khatri-Rao product of the other triangles,
 // issued on the side stream as soon as the previous update has produced its R_k so
 // that it runs under the TTM chain of mode n.  On the Gram route its Cholesky may already be
-// on the side stream (issued by the previous update once its factor's Gram existed).
-cpqr_status launch_z(cpqr_ctx* ctx, int n) {
+// on the side stream (issued by the previous update once its factor's Gram existed); with a W
+// formed for n, only the level with the last update's triangle is left (split route), and the W
+// of the update after n (`after`, -1 if none in this sweep) is started.
+cpqr_status launch_z(cpqr_ctx* ctx, int n, int after) {
   TriPtrs tri{};
-  int m = 0;
+  int m = 0, s = -1;
   for (int k = 0; k < ctx->N; ++k)
-    if (k != n) tri.p[m++] = ctx->Rf[k];
+    if (k != n) {
+      if (k == ctx->last_updated) s = m;
+      tri.p[m++] = ctx->Rf[k];
+    }
+  const bool split = split_ready(ctx, n) && s >= 0;
   CK(cudaEventRecord(ctx->ev_ready, ctx->st));
   CK(cudaStreamWaitEvent(ctx->st2, ctx->ev_ready, 0));
   {
     Timed tm(ctx, CPQR_BUCKET_Q0, 1, ctx->st2);
-    if (ctx->gram) {
-      if (ctx->zchol_mode != n) {
+    if (split) {
+      if (!(ctx->zchol_mode == n && ctx->zchol_split)) {
+        CK(launch_krp_chol(z_grams(ctx, n), m, ctx->R, ctx->zg_work, ctx->st2, 0, gram_flag(ctx->wg_work)));
+        ctx->launches += 1;
+      }
+      int nl = 0;
+      CK(launch_krp_rows_split(ctx->zplan2, tri, m, s, ctx->WQ, ctx->WS, ctx->Q0, ctx->R0, ctx->zg_work, ctx->zq_work,
+                               ctx->dstatus, ctx->st2, ctx->Q0f, &nl));
+      ctx->launches += nl - 1;
+      ctx->n_split += 1;
+    } else if (ctx->gram) {
+      if (!(ctx->zchol_mode == n && !ctx->zchol_split)) {
         CK(launch_krp_chol(z_grams_level2(ctx, n), 2, ctx->R, ctx->zg_work, ctx->st2));
         ctx->launches += 1;
       }
-      ctx->zchol_mode = -1;
       int nl = 0;
       CK(launch_krp_rows(ctx->zplan2, tri, m, z_grams(ctx, n), ctx->Q0, ctx->R0, ctx->zg_work, ctx->zq_work,
                          ctx->dstatus, ctx->st2, ctx->Q0f, &nl));
@@ -576,9 +646,15 @@ cpqr_status launch_z(cpqr_ctx* ctx, int n) {
       CK(launch_krp_qr(ctx->zplan, tri, ctx->Q0, ctx->R0, ctx->zq_work, ctx->dstatus, ctx->st2, ctx->Q0f));
     }
   }
+  ctx->zchol_mode = -1;
+  ctx->wpf_mode = -1;
   CK(cudaEventRecord(ctx->ev_z, ctx->st2));
   ctx->z_pending = true;
   ctx->z_mode = n;
+  if (ctx->gram && ctx->w_ok && m >= 3 && after >= 0 && after != n) {
+    cpqr_status st = launch_w(ctx, n, after);
+    if (st != CPQR_OK) return st;
+  }
   return CPQR_OK;
 }
 
@@ -591,7 +667,7 @@ cpqr_status run_update(cpqr_ctx* ctx, int n, int leaf, double beta, int next_mod
   const int N = ctx->N, R = ctx->R;
   cudaStream_t st = ctx->st;
   if (!ctx->z_pending || ctx->z_mode != n) {
-    cpqr_status s = launch_z(ctx, n);
+    cpqr_status s = launch_z(ctx, n, next_mode);
     if (s != CPQR_OK) return s;
   }
   CK(cudaStreamWaitEvent(st, ctx->ev_z, 0));
@@ -636,12 +712,18 @@ cpqr_status run_update(cpqr_ctx* ctx, int n, int leaf, double beta, int next_mod
       CK(launch_finish_gram_chol(ctx->hpart, ctx->fitpart, nblk, I, R, fo, ctx->fg_work, ctx->Gf[n], ctx->cn[n], st));
       if (next_mode >= 0 && next_mode != n && !ctx->z_pending) {
         // the next mode's Khatri-Rao Cholesky needs only the factors' Grams: it runs on the
-        // side stream beside the rest of this factor QR
+        // side stream beside the rest of this factor QR (on the split route, the Cholesky of its
+        // last level, which also takes W's guard)
+        const bool split = ctx->gram && ctx->w_ok && ctx->wpf_mode == next_mode && ctx->wpf_excl == n;
         CK(cudaEventRecord(ctx->ev_gram, st));
         CK(cudaStreamWaitEvent(ctx->st2, ctx->ev_gram, 0));
         Timed tz(ctx, CPQR_BUCKET_Q0, 1, ctx->st2);
-        CK(launch_krp_chol(z_grams_level2(ctx, next_mode), 2, R, ctx->zg_work, ctx->st2));
+        if (split)
+          CK(launch_krp_chol(z_grams(ctx, next_mode), N - 1, R, ctx->zg_work, ctx->st2, 0, gram_flag(ctx->wg_work)));
+        else
+          CK(launch_krp_chol(z_grams_level2(ctx, next_mode), 2, R, ctx->zg_work, ctx->st2));
         ctx->zchol_mode = next_mode;
+        ctx->zchol_split = split;
       }
       CK(launch_finish_gram_rows(ctx->V, ctx->fitpart, nblk, I, R, fo, ctx->fg_work, ctx->qr_work, ctx->dstatus, st));
     } else
@@ -658,6 +740,7 @@ cpqr_status run_update(cpqr_ctx* ctx, int n, int leaf, double beta, int next_mod
   std::swap(ctx->Q0, ctx->Q0prev[n]);
   std::swap(ctx->Q0f, ctx->Q0fprev[n]);
   ctx->has_prev[n] = true;
+  ctx->last_updated = n;
   return CPQR_OK;
 }
 
@@ -789,6 +872,7 @@ cpqr_status one_sweep(cpqr_ctx* ctx, double* fit_out, const double* forced_beta 
     if (s != CPQR_OK) return s;
   }
   ctx->ops.clear();
+  ctx->wpf_mode = -1;  // a W never outlives the sweep that formed it
   try {
     ctx->sched->next_sweep(ctx->ops);
   } catch (const std::exception&) {
@@ -801,7 +885,10 @@ cpqr_status one_sweep(cpqr_ctx* ctx, double* fit_out, const double* forced_beta 
       // first TTM of the next mode's chain: start its Khatri-Rao QR alongside
       for (size_t k = i + 1; k < ctx->ops.size(); ++k)
         if (ctx->ops[k].kind == OP_UPDATE) {
-          s = launch_z(ctx, ctx->ops[k].a);
+          int after = -1;
+          for (size_t q = k + 1; q < ctx->ops.size() && after < 0; ++q)
+            if (ctx->ops[q].kind == OP_UPDATE) after = ctx->ops[q].a;
+          s = launch_z(ctx, ctx->ops[k].a, after);
           break;
         }
       if (s != CPQR_OK) return s;
@@ -1074,6 +1161,17 @@ cpqr_status cp_als_qr_init(cpqr_ctx** out, int32_t N, const int64_t* dims, int32
     CK(cudaStreamCreateWithPriority(&ctx->st2, cudaStreamNonBlocking, greatest));
     CK(cudaStreamCreateWithPriority(&ctx->st3, cudaStreamNonBlocking, least));
   }
+  if (N - 1 >= 3) {
+    // the split Khatri-Rao QR's W (a few hundred KB at most)
+    size_t mwq = (size_t)R;
+    for (int k = 0; k < N - 2; ++k) mwq *= (size_t)R;
+    CK(ctx->alloc(&ctx->wg_work, krp_gram_work_doubles(R)));
+    CK(cudaMemsetAsync(ctx->wg_work, 0, krp_gram_work_doubles(R) * sizeof(double), st));
+    CK(ctx->alloc(&ctx->wq_work, std::max<size_t>(krp_nested_work_doubles(N - 2, R), 1)));
+    CK(ctx->alloc(&ctx->WQ, mwq));
+    CK(ctx->alloc(&ctx->WS, (size_t)R * R));
+    ctx->w_ok = true;
+  }
   CK(cudaEventCreateWithFlags(&ctx->ev_prep, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&ctx->ev_fit, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&ctx->ev_ready, cudaEventDisableTiming));
@@ -1246,6 +1344,7 @@ cpqr_status cp_als_qr_stats(cpqr_ctx* ctx, cpqr_stats* out) {
   out->proposals = ctx->proposals;
   out->accepted = ctx->accepted;
   out->launches = ctx->launches;
+  out->krp_split = ctx->n_split;
   for (int b = 0; b < CPQR_NBUCKETS; ++b) {
     out->ms_bucket[b] = ctx->ms_bucket[b];
     out->n_bucket[b] = ctx->n_bucket[b];

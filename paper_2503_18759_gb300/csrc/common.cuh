@@ -100,9 +100,14 @@ size_t krp_qr_work_doubles(const ZPlan& plan);
 // the plan for m = 2) and m - 2 FP64 assemblies; work: krp_nested_work_doubles(m, R) doubles.
 // *nlaunch (optional) receives the number of kernels launched.
 size_t krp_nested_work_doubles(int m, int R);
-// out[(i, w), c] = sum_j QW[w, j] QY[(i, j), c] (i < R, w < mw): the assembly step of the nested QR.
+// out[(i, w), c] = sum_j QW[w, j] QY[(i, j), c] (i < R, w < mw): the assembly step of the nested QR,
+// for a QY whose row (i, j) is zero left of column max(i, j) (the Gram route's; the Householder
+// route assembles with a dense kernel).
 cudaError_t launch_krp_assemble(const double* QW, int64_t mw, const double* QY, int R, double* out, float* outf,
                                 cudaStream_t st);
+// The same with rows (l, i, t) = (l * R + i) * T + t and w = l * T + t (l < L, t < T).
+cudaError_t launch_krp_assemble_tri(const double* QW, int64_t L, int64_t T, const double* QY, int R, double* out,
+                                    float* outf, cudaStream_t st);
 // Buffers of the nested QR inside its work (krp_nested_work_doubles(m, R) doubles): the two level
 // triangles S, Q_Y, the staircase QR's scratch and the two Q_W.
 struct NestedBufs {
@@ -137,10 +142,26 @@ struct GramPtrs {
   const float2* g[CPQR_MAXN - 1];
   const double* s[CPQR_MAXN - 1];
 };
-cudaError_t launch_krp_chol(const GramPtrs& gp, int m, int R, double* gram_work, cudaStream_t st, int acc = 0);
+// flag_in (optional, device): a guard raised elsewhere (the split route's W) that the Cholesky
+// carries into its own.  fallback = false leaves out the Householder fallback (the split route's
+// W, whose guard the final level carries).
+cudaError_t launch_krp_chol(const GramPtrs& gp, int m, int R, double* gram_work, cudaStream_t st, int acc = 0,
+                            const int* flag_in = nullptr);
 cudaError_t launch_krp_rows(const ZPlan& plan2, TriPtrs tri, int m, const GramPtrs& gp, double* Q0, double* R0,
                             double* gram_work, double* qr_work, unsigned int* dev_status, cudaStream_t st,
-                            float* Q0f = nullptr, int* nlaunch = nullptr);
+                            float* Q0f = nullptr, int* nlaunch = nullptr, bool fallback = true);
+// Split route of the same QR (m >= 3), for a product whose triangle at position s (tri.p[s]) is the
+// only one that changed since the QR of the others, W = Q_W S_W (rows w = (l, t) over the triangles
+// before and after s; QW: R^(m-1) x R, SW: R x R), was formed: Y = R_s (.) S_W by the Gram route
+// (its Cholesky, the Hadamard product of all m Grams, issued first by launch_krp_chol with W's
+// guard as flag_in), Q0[(l, i, t)] = sum_j QW[(l, t), j] Q_Y[(i, j)], R0 = R_Y, and the nested
+// Householder QR of tri as the fallback.  gram_work, qr_work: as for launch_krp_rows with m.
+cudaError_t launch_krp_rows_split(const ZPlan& plan2, TriPtrs tri, int m, int s, const double* QW, const double* SW,
+                                  double* Q0, double* R0, double* gram_work, double* qr_work,
+                                  unsigned int* dev_status, cudaStream_t st, float* Q0f = nullptr,
+                                  int* nlaunch = nullptr);
+// The guard word of a Gram-route workspace (device int: nonzero = fall back).
+int* gram_flag(double* gram_work);
 
 // V[i, c] = sum_{p, s} Y[p, i, s] * Qc[p*S + s, c], c < C, Qc = [Q0 | Q0prev] (K x C,
 // K = P*S), as *nparts split-K slices of I x C in work (leaf_v_splits(I, K) * I * C

@@ -308,7 +308,8 @@ __global__ void __launch_bounds__(256) tri_gram_kernel(TriPtrs tri, int R, float
 // s_k: Z^T Z = D (G_1 o ... o G_m) D, D = diag(s_1 ... s_m).  The Gram thus costs float-float
 // Hadamard products and no pass over the triangles, and this kernel needs only the Grams: a sweep
 // launches it as soon as the previous factor's Gram exists, before that factor's QR has finished.
-__global__ void __launch_bounds__(256) kg_chol_kernel(GramPtrs gp, int m, int R, int acc, KgWork w) {
+__global__ void __launch_bounds__(256) kg_chol_kernel(GramPtrs gp, int m, int R, int acc, const int* flag_in,
+                                                       KgWork w) {
   __shared__ __align__(16) float2 Gf[KG_MAXR][KG_LD], U[KG_MAXR][KG_LD], V[KG_MAXR][KG_LD];
   __shared__ double scale[KG_MAXR], rsd[KG_MAXR], csd[KG_MAXR];
   __shared__ int bad;
@@ -336,6 +337,7 @@ __global__ void __launch_bounds__(256) kg_chol_kernel(GramPtrs gp, int m, int R,
   __syncthreads();
   chol_pipelined(Gf, U, V, R, &bad);
   __syncthreads();
+  if (tid == 0 && flag_in && *(volatile const int*)flag_in) bad = 1;
   chol_outputs(U, V, rsd, csd, scale, R, w, &bad, acc);
 }
 
@@ -716,11 +718,14 @@ cudaError_t launch_tri_gram(const double* T, int R, float2* Gf, double* s, cudaS
 
 size_t krp_gram_work_doubles(int R) { return kg_work_doubles((int64_t)R * R, R); }
 
-cudaError_t launch_krp_chol(const GramPtrs& gp, int m, int R, double* gram_work, cudaStream_t st, int acc) {
+cudaError_t launch_krp_chol(const GramPtrs& gp, int m, int R, double* gram_work, cudaStream_t st, int acc,
+                            const int* flag_in) {
   if (R < 1 || R > KG_MAXR || m < 2 || m > KG_MAXM) return cudaErrorInvalidValue;
   const KgWork w = kg_views(gram_work, R, (int64_t)R * R);
-  return launch_pdl(kg_chol_kernel, dim3(1), dim3(256), 0, st, gp, m, R, acc, w);
+  return launch_pdl(kg_chol_kernel, dim3(1), dim3(256), 0, st, gp, m, R, acc, flag_in, w);
 }
+
+int* gram_flag(double* gram_work) { return reinterpret_cast<int*>(gram_work); }
 
 // The rows of a Gram-route QR of a two-triangle product (R^2 rows) after its Cholesky: Q1, E and
 // the guard, then Q (and Qf) and the triangle Rt.  *n: kernels launched.
@@ -742,7 +747,7 @@ static cudaError_t krp_rows_only(const double* Ra, const double* Rb, int R, cons
 
 cudaError_t launch_krp_rows(const ZPlan& plan2, TriPtrs tri, int m, const GramPtrs& gp, double* Q0, double* R0,
                             double* gram_work, double* qr_work, unsigned int* dev_status, cudaStream_t st,
-                            float* Q0f, int* nlaunch) {
+                            float* Q0f, int* nlaunch, bool fallback) {
   const int R = plan2.R;
   if (plan2.m != 2 || R < 1 || R > KG_MAXR || m < 2 || m > KG_MAXM) return cudaErrorInvalidValue;
   const KgWork w = kg_views(gram_work, R, (int64_t)R * R);
@@ -752,6 +757,10 @@ cudaError_t launch_krp_rows(const ZPlan& plan2, TriPtrs tri, int m, const GramPt
     e = krp_rows_only(tri.p[0], tri.p[1], R, w, Q0, Q0f, R0, st, &n);
     if (e != cudaSuccess) return e;
     launches += n;
+    if (!fallback) {
+      if (nlaunch) *nlaunch = launches;
+      return cudaSuccess;
+    }
     // the Householder staircase QR, which returns at once unless the flag was raised
     e = launch_krp_qr(plan2, tri, Q0, R0, qr_work, dev_status, st, Q0f, w.flag);
     if (nlaunch) *nlaunch = launches + 1;
@@ -784,9 +793,39 @@ cudaError_t launch_krp_rows(const ZPlan& plan2, TriPtrs tri, int m, const GramPt
     cur ^= 1;
     mw *= R;
   }
+  if (!fallback) {
+    if (nlaunch) *nlaunch = launches;
+    return cudaSuccess;
+  }
   int nf = 0;
   e = launch_krp_qr_nested(plan2, tri, m, Q0, R0, qr_work, dev_status, st, Q0f, &nf, w.flag);
   if (nlaunch) *nlaunch = launches + nf;
+  return e;
+}
+
+// Z = R_1 (.) ... (.) R_m with rows (l, i, t): l over the triangles before s, i over R_s, t over
+// those after.  With W = R_1 (.) .. R_(s-1) (.) R_(s+1) .. (.) R_m = Q_W S_W (rows w = (l, t)),
+// Z[(l, i, t), c] = R_s[i, c] W[(l, t), c] = sum_j Q_W[(l, t), j] R_s[i, c] S_W[j, c], so with
+// Y = R_s (.) S_W = Q_Y R_Y (rows (i, j)), Z = P (I_R (x) Q_W) Q_Y R_Y for the row permutation P
+// of (i, (l, t)) to (l, i, t): Q0 = P (I (x) Q_W) Q_Y, orthonormal, and R0 = R_Y, positive diagonal.
+cudaError_t launch_krp_rows_split(const ZPlan& plan2, TriPtrs tri, int m, int s, const double* QW, const double* SW,
+                                  double* Q0, double* R0, double* gram_work, double* qr_work,
+                                  unsigned int* dev_status, cudaStream_t st, float* Q0f, int* nlaunch) {
+  const int R = plan2.R;
+  if (plan2.m != 2 || R < 1 || R > KG_MAXR || m < 3 || m > KG_MAXM || s < 0 || s >= m) return cudaErrorInvalidValue;
+  const KgWork w = kg_views(gram_work, R, (int64_t)R * R);
+  const NestedBufs nb = nested_views(qr_work, m, R);
+  int n = 0;
+  cudaError_t e = krp_rows_only(tri.p[s], SW, R, w, nb.QY, nullptr, R0, st, &n);
+  if (e != cudaSuccess) return e;
+  int64_t L = 1, T = 1;
+  for (int k = 0; k < s; ++k) L *= R;
+  for (int k = s + 1; k < m; ++k) T *= R;
+  e = launch_krp_assemble_tri(QW, L, T, nb.QY, R, Q0, Q0f, st);
+  if (e != cudaSuccess) return e;
+  int nf = 0;
+  e = launch_krp_qr_nested(plan2, tri, m, Q0, R0, qr_work, dev_status, st, Q0f, &nf, w.flag);
+  if (nlaunch) *nlaunch = n + 1 + nf;
   return e;
 }
 

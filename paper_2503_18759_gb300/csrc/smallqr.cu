@@ -826,14 +826,79 @@ __global__ void __launch_bounds__(256) krp_assemble_kernel(const double* __restr
   }
 }
 
+// The same assembly when QY comes from the Gram route's rows kernels: row (i, j) of QY is the row
+// R_a[i, :] * S[j, :] of two upper triangles times upper-triangular factors, so it is exactly zero
+// left of column max(i, j), and only the terms j <= c of the columns c >= i can be nonzero (about
+// a third of the dense multiply-adds, the part that bounds the dense kernel on GB300's FP64 pipe).
+// The kept terms are summed in the dense kernel's order, so the results agree up to the sign of
+// zero.  Rows (l, i, t) = (l * R + i) * T + t with w = l * T + t: T = mw, L = 1 is the assembly
+// above.  One output row per thread and 32 consecutive w per warp; a warp takes the rows i and
+// R - 1 - i, whose costs add up to about the mean, and of each the part `part` of P column
+// ranges of equal cost, so every warp does about the same work, i (hence every QY address) is
+// the same across the warp, and P brings small assemblies up to a few warps per SM quarter.
+template <int RP>
+__global__ void __launch_bounds__(128) krp_assemble_tri_kernel(const double* __restrict__ QW, int64_t LT, int64_t T,
+                                                                const double* __restrict__ QY, int R, int P,
+                                                                double* __restrict__ out, float* __restrict__ outf) {
+  const int lane = threadIdx.x & 31;
+  const int ng = (R + 1) / 2;
+  const int64_t gw = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5);
+  const int part = (int)(gw % P);
+  const int64_t rest = gw / P;
+  const int64_t chunk = rest / ng;
+  const int grp = (int)(rest - chunk * ng);
+  if (chunk * 32 >= LT) return;
+  const int64_t w = chunk * 32 + lane;
+  const bool live = w < LT;
+  double qw[RP];
+#pragma unroll
+  for (int j = 0; j < RP; ++j) qw[j] = (live && j < R) ? QW[w * R + j] : 0.0;
+  const int64_t l = live ? w / T : 0, t = live ? w - l * T : 0;
+  for (int h = 0; h < 2; ++h) {
+    const int i = h ? R - 1 - grp : grp;
+    if (h && i == grp) break;
+    // column c >= i costs c + 1 and starts at cost (c (c + 1) - i (i + 1)) / 2 of the row's total;
+    // it belongs to part min(P - 1, floor(start * P / total)), the zero columns c < i to part 0
+    const int total = (R * (R + 1) - i * (i + 1)) / 2;
+    const double* qy = QY + (size_t)i * R * R;
+    const int64_t o = ((l * R + i) * T + t) * R;
+#pragma unroll
+    for (int c = 0; c < RP; ++c) {
+      const int sp = (c * (c + 1) - i * (i + 1)) / 2 * P;
+      const bool mine = (c < i) ? (part == 0) : (sp >= part * total && (part == P - 1 || sp < (part + 1) * total));
+      if (c < R && mine) {
+        double v = 0.0;
+        if (c >= i) {
+#pragma unroll
+          for (int j = 0; j <= c; ++j) v = fma(qw[j], qy[j * R + c], v);
+        }
+        if (live) {
+          out[o + c] = v;
+          if (outf) outf[o + c] = (float)v;
+        }
+      }
+    }
+  }
+}
+
 cudaError_t launch_krp_assemble(const double* QW, int64_t mw, const double* QY, int R, double* out, float* outf,
                                 cudaStream_t st) {
-  int Rpad = 1;
-  while (Rpad < R) Rpad <<= 1;
-  const int64_t rows = (int64_t)R * mw;
-  const int64_t warps = (rows + (32 / Rpad) - 1) / (32 / Rpad);
-  const int grid = (int)std::min<int64_t>((warps + 7) / 8, 152 * 8);
-  krp_assemble_kernel<<<grid, 256, 0, st>>>(QW, mw, QY, R, Rpad, out, outf, nullptr);
+  return launch_krp_assemble_tri(QW, 1, mw, QY, R, out, outf, st);
+}
+
+cudaError_t launch_krp_assemble_tri(const double* QW, int64_t L, int64_t T, const double* QY, int R, double* out,
+                                    float* outf, cudaStream_t st) {
+  if (R < 1 || R > CPQR_MAXR || L < 1 || T < 1) return cudaErrorInvalidValue;
+  const int64_t LT = L * T;
+  const int64_t base = (LT + 31) / 32 * ((R + 1) / 2);
+  // column parts for small assemblies: about 1024 warps (measured: 65536 rows of R = 16 ran in
+  // 22.7 us as 1024 warps and 26 us as 3072; 4096 rows in 17.4 us as 64 warps, 8.5 us as 512)
+  const int P = (int)std::max<int64_t>(1, std::min<int64_t>((1024 + base - 1) / base, std::max(1, R / 2)));
+  const int64_t grid = (base * P + 3) / 4;
+  if (grid > 0x7fffffff) return cudaErrorInvalidValue;
+  if (R <= 8) krp_assemble_tri_kernel<8><<<(unsigned)grid, 128, 0, st>>>(QW, LT, T, QY, R, P, out, outf);
+  else if (R <= 16) krp_assemble_tri_kernel<16><<<(unsigned)grid, 128, 0, st>>>(QW, LT, T, QY, R, P, out, outf);
+  else krp_assemble_tri_kernel<32><<<(unsigned)grid, 128, 0, st>>>(QW, LT, T, QY, R, P, out, outf);
   return cudaGetLastError();
 }
 

@@ -250,7 +250,12 @@ __global__ void __launch_bounds__(256) leaf_v_kernel(const TY* __restrict__ Y, i
   __shared__ __align__(16) TA sQ[VK][VC];
   constexpr int NLY = (VK * VI) / 256, NLQ = (VK * VC) / 256;
   const int tid = threadIdx.x;
-  const int ty = tid >> 4, tx = tid & 15;  // rows ty*4 .. +3, columns tx*4 .. +3
+  // rows ty*4 .. +3, columns tx*4 .. +3.  For C <= 32 a warp holds two column groups, so the
+  // warps whose columns all lie at or past C skip the multiply; wider C keeps two row groups per
+  // warp (one shared-memory broadcast of the rows instead of one of the columns)
+  const bool narrow = C <= 32;
+  const int tx = narrow ? tid >> 4 : tid & 15, ty = narrow ? tid & 15 : tid >> 4;
+  const bool busy = !narrow || (tid >> 5) * 8 < C;
   const int i0 = blockIdx.x * VI;
   const int K = P * S;
   const int kbeg = blockIdx.y * kchunk;
@@ -302,7 +307,7 @@ __global__ void __launch_bounds__(256) leaf_v_kernel(const TY* __restrict__ Y, i
     __syncthreads();
     if (k0 + VK < kend) fetch(k0 + VK);
 #pragma unroll 4
-    for (int kk = 0; kk < VK; ++kk) {
+    for (int kk = 0; kk < (busy ? VK : 0); ++kk) {
       TA y[4], qv[4];
 #pragma unroll
       for (int a = 0; a < 4; ++a) {

@@ -88,7 +88,7 @@ def test_house_qr(M, R):
     assert np.allclose(Q.cpu().numpy(), Qr, atol=1e-12)
 
 
-@pytest.mark.parametrize("m,R", [(2, 5), (2, 32), (3, 24), (4, 16), (2, 1), (3, 7), (4, 5)])
+@pytest.mark.parametrize("m,R", [(2, 5), (2, 32), (3, 24), (4, 16), (2, 1), (3, 7), (4, 5), (3, 32), (4, 17)])
 def test_krp_qr(m, R):
     g = np.random.default_rng(m * 100 + R)
     Rs = [o.householder_qr(g.standard_normal((R + 4, R)))[1] for _ in range(m)]
@@ -160,6 +160,11 @@ def test_fp64_solver_matches_oracle(name, cfg, tree, extrap, beta, sweeps, route
     assert np.allclose(lam, ref.lam, rtol=1e-8)
     assert st.ttm_flops == ref.flops
     assert st.qr_fallbacks == 0
+    if route == b.QR_GRAM and len(prob.dims) >= 4:
+        # every update of a sweep but the first takes the split Khatri-Rao QR
+        assert st.krp_split == (len(prob.dims) - 1) * sweeps
+    else:
+        assert st.krp_split == 0
 
 
 @pytest.mark.parametrize("route", [b.QR_GRAM, b.QR_HOUSEHOLDER], ids=["gram", "householder"])
@@ -191,6 +196,36 @@ def test_factor_qr_guard_hands_collinear_factor_to_householder(route):
         assert st.qr_fallbacks >= sweeps
     else:
         assert st.qr_fallbacks == 0
+
+
+@pytest.mark.parametrize("order", [4, 5])
+def test_split_krp_qr_carries_the_guard_of_its_prefetched_half(order):
+    """The starting factors of modes 2 .. N-1 have columns 0 and 1 1e-7 apart, so the Khatri-Rao
+    product of their triangles has kappa ~ 1e7 (the other modes keep every product that also
+    holds one of them well-conditioned).  In the first sweep the QR for mode 1 takes the split
+    route: W, the product of the triangles of modes 2 .. N-1, was formed from those starting
+    factors one update ahead; its guard must reach the final level so that the whole QR goes to
+    the nested Householder QR, like mode 0's QR on the nested route (its first level is the
+    same product).  The factors and fits then track the oracle to rounding."""
+    dims = [14, 13, 12, 11] if order == 4 else [9, 8, 7, 6, 7]
+    R, seed, sweeps = 4, 5, 4
+    B = inputs.gaussian_factors(dims, R, seed)
+    X = inputs.add_noise(inputs.cp_dense(B), 1e-4, seed)
+    A0 = inputs.init_factors(dims, R, seed)
+    g = np.random.default_rng(seed)
+    for n in range(2, order):
+        A0[n][:, 1] = A0[n][:, 0] + 1e-7 * g.standard_normal(dims[n])
+    prob = inputs.Problem(f"collinear_start_order{order}", dims, R, np.ascontiguousarray(X), A0, B, 1e-4, seed)
+    fits, A, lam, Q, Rn, st = _run_gpu(prob, b.TREE_RESTRUCTURED, b.EXTRAP_NONE, 0.0, sweeps)
+    ref = _run_oracle(prob, b.TREE_RESTRUCTURED, b.EXTRAP_NONE, 0.0, sweeps)
+    assert np.max(np.abs(fits - np.array(ref.fits))) <= 1e-10, (fits, ref.fits)
+    for n in range(len(dims)):
+        assert o.subspace_sine(A[n], ref.A[n]) <= 1e-10
+        assert np.allclose(A[n], ref.A[n], atol=1e-8), (n, np.abs(A[n] - ref.A[n]).max())
+        assert np.abs(Q[n].T @ Q[n] - np.eye(R)).max() < 1e-13
+    assert st.krp_split == (len(dims) - 1) * sweeps
+    # mode 0's nested QR and mode 1's split QR of the first sweep (the starting QRs are Householder)
+    assert st.qr_fallbacks >= 2, st.qr_fallbacks
 
 
 def test_cube60_fifty_sweeps_parity():
