@@ -172,7 +172,14 @@ struct cpqr_ctx {
   int wpf_mode = -1;     // the update whose W is formed; -1: none
   int wpf_excl = -1;     // the update before it, left out of W
   int last_updated = -1;  // mode of the last update enqueued
+  int next_first = -1;    // first update of the sweep after the current one (-1: unknown)
   int64_t n_split = 0;    // Khatri-Rao QRs issued on the split route
+  // The restructured tree updates the last mode of a sweep again first in the next one: nothing
+  // but that mode changed in between, so its Khatri-Rao QR is the one just computed, bit for bit
+  // (every reduction has a fixed order).  zq_mode: the mode whose Q0 (now in Q0prev[zq_mode])
+  // and R0 are still those of its inputs; -1 once another mode's factor changed.
+  int zq_mode = -1;
+  int64_t n_reused = 0;   // Khatri-Rao QRs taken over from the previous update of the same mode
   cudaEvent_t ev_gram = nullptr;     // main stream: the last factor's Gram stored
   double* fg_work = nullptr;       // Gram-route factor QR workspace
   double* hpart = nullptr;         // per-block folded Gram partials of A^ (finish prep)
@@ -515,6 +522,7 @@ cpqr_status checkpoint_restore(cpqr_ctx* ctx, int slot) {
   ctx->zchol_mode = -1;
   ctx->wpf_mode = -1;
   ctx->last_updated = -1;
+  ctx->zq_mode = -1;
   return CPQR_OK;
 }
 
@@ -613,12 +621,22 @@ cpqr_status launch_z(cpqr_ctx* ctx, int n, int after) {
       if (k == ctx->last_updated) s = m;
       tri.p[m++] = ctx->Rf[k];
     }
-  const bool split = split_ready(ctx, n) && s >= 0;
+  const bool reuse = ctx->zq_mode == n && ctx->last_updated == n && ctx->has_prev[n];
+  const bool split = !reuse && split_ready(ctx, n) && s >= 0;
   CK(cudaEventRecord(ctx->ev_ready, ctx->st));
   CK(cudaStreamWaitEvent(ctx->st2, ctx->ev_ready, 0));
   {
-    Timed tm(ctx, CPQR_BUCKET_Q0, 1, ctx->st2);
-    if (split) {
+    Timed tm(ctx, CPQR_BUCKET_Q0, reuse ? 0 : 1, ctx->st2);
+    if (reuse) {
+      // the previous update of n used this very Q0 (swapped into Q0prev[n]); R0 is untouched
+      const size_t M0 = (size_t)ipow(ctx->R, m);
+      CK(cudaMemcpyAsync(ctx->Q0, ctx->Q0prev[n], M0 * ctx->R * sizeof(double), cudaMemcpyDeviceToDevice,
+                         ctx->st2));
+      if (ctx->Q0f)
+        CK(cudaMemcpyAsync(ctx->Q0f, ctx->Q0fprev[n], M0 * ctx->R * sizeof(float), cudaMemcpyDeviceToDevice,
+                           ctx->st2));
+      ctx->n_reused += 1;
+    } else if (split) {
       if (!(ctx->zchol_mode == n && ctx->zchol_split)) {
         CK(launch_krp_chol(z_grams(ctx, n), m, ctx->R, ctx->zg_work, ctx->st2, 0, gram_flag(ctx->wg_work)));
         ctx->launches += 1;
@@ -651,6 +669,7 @@ cpqr_status launch_z(cpqr_ctx* ctx, int n, int after) {
   CK(cudaEventRecord(ctx->ev_z, ctx->st2));
   ctx->z_pending = true;
   ctx->z_mode = n;
+  ctx->zq_mode = n;
   if (ctx->gram && ctx->w_ok && m >= 3 && after >= 0 && after != n) {
     cpqr_status st = launch_w(ctx, n, after);
     if (st != CPQR_OK) return st;
@@ -741,6 +760,7 @@ cpqr_status run_update(cpqr_ctx* ctx, int n, int leaf, double beta, int next_mod
   std::swap(ctx->Q0f, ctx->Q0fprev[n]);
   ctx->has_prev[n] = true;
   ctx->last_updated = n;
+  if (ctx->zq_mode != n) ctx->zq_mode = -1;
   return CPQR_OK;
 }
 
@@ -833,7 +853,10 @@ cpqr_status read_fit(cpqr_ctx* ctx, double* fit) {
     CK(cudaMemcpyAsync(ctx->h_pinned + 2, ctx->dstatus, sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->st));
   }
   CK(cudaStreamSynchronize(ctx->st));
-  if (ctx->timing) collect_timing(ctx);
+  if (ctx->timing) {
+    CK(cudaStreamSynchronize(ctx->st2));  // the next sweep's W may still be running there
+    collect_timing(ctx);
+  }
   unsigned int ds;
   std::memcpy(&ds, ctx->h_pinned + 2, sizeof(ds));
   if (ds & CPQR_DEV_TIMEOUT) return fail(ctx, CPQR_ETIMEOUT);
@@ -872,12 +895,34 @@ cpqr_status one_sweep(cpqr_ctx* ctx, double* fit_out, const double* forced_beta 
     if (s != CPQR_OK) return s;
   }
   ctx->ops.clear();
-  ctx->wpf_mode = -1;  // a W never outlives the sweep that formed it
   try {
     ctx->sched->next_sweep(ctx->ops);
   } catch (const std::exception&) {
     return fail(ctx, CPQR_EINVAL);
   }
+  // The schedule is deterministic, so a copy tells the first update of the following sweep: the
+  // last update of this one forms the W of that update.  Between sweeps only a rollback changes the
+  // factors, and it drops that W (wpf_mode); a W is otherwise used only for the update and the
+  // last-updated mode it was formed for.
+  ctx->next_first = -1;
+  try {
+    Schedule peek(*ctx->sched);
+    std::vector<Op> nxt;
+    peek.next_sweep(nxt);
+    for (const Op& q : nxt)
+      if (q.kind == OP_UPDATE) {
+        ctx->next_first = q.a;
+        break;
+      }
+  } catch (const std::exception&) {
+    ctx->next_first = -1;
+  }
+  // the update after ops[k]: the next one in this sweep, else the first of the next sweep
+  auto update_after = [ctx](size_t k) {
+    for (size_t q = k + 1; q < ctx->ops.size(); ++q)
+      if (ctx->ops[q].kind == OP_UPDATE) return ctx->ops[q].a;
+    return ctx->next_first;
+  };
   for (size_t i = 0; i < ctx->ops.size(); ++i) {
     const Op& op = ctx->ops[i];
     cpqr_status s = CPQR_OK;
@@ -885,20 +930,14 @@ cpqr_status one_sweep(cpqr_ctx* ctx, double* fit_out, const double* forced_beta 
       // first TTM of the next mode's chain: start its Khatri-Rao QR alongside
       for (size_t k = i + 1; k < ctx->ops.size(); ++k)
         if (ctx->ops[k].kind == OP_UPDATE) {
-          int after = -1;
-          for (size_t q = k + 1; q < ctx->ops.size() && after < 0; ++q)
-            if (ctx->ops[q].kind == OP_UPDATE) after = ctx->ops[q].a;
-          s = launch_z(ctx, ctx->ops[k].a, after);
+          s = launch_z(ctx, ctx->ops[k].a, update_after(k));
           break;
         }
       if (s != CPQR_OK) return s;
     }
     if (op.kind == OP_TTM) s = run_ttm(ctx, op);
     else if (op.kind == OP_UPDATE) {
-      int next_mode = -1;
-      for (size_t k = i + 1; k < ctx->ops.size() && next_mode < 0; ++k)
-        if (ctx->ops[k].kind == OP_UPDATE) next_mode = ctx->ops[k].a;
-      s = run_update(ctx, op.a, op.b, beta, next_mode);
+      s = run_update(ctx, op.a, op.b, beta, update_after(i));
     }
     else free_node(ctx, op.a);
     if (s != CPQR_OK) return s;
@@ -1345,6 +1384,7 @@ cpqr_status cp_als_qr_stats(cpqr_ctx* ctx, cpqr_stats* out) {
   out->accepted = ctx->accepted;
   out->launches = ctx->launches;
   out->krp_split = ctx->n_split;
+  out->krp_reused = ctx->n_reused;
   for (int b = 0; b < CPQR_NBUCKETS; ++b) {
     out->ms_bucket[b] = ctx->ms_bucket[b];
     out->n_bucket[b] = ctx->n_bucket[b];

@@ -139,6 +139,16 @@ CASES = [
 ]
 
 
+def _krp_routes(dims, R, tree, sweeps):
+    """Expected Khatri-Rao QR routes from the schedule's update order: an update of the same mode
+    as the one before reuses that QR (the other triangles did not change); any other update
+    after the first takes the split route on the Gram route at order >= 4."""
+    ops, _ = b.cp_als_qr_schedule(dims, R, tree, sweeps)
+    ups = [int(o[1]) for o in ops if int(o[0]) == 1]
+    reused = sum(1 for j in range(1, len(ups)) if ups[j] == ups[j - 1])
+    return reused, len(ups) - 1 - reused
+
+
 @pytest.mark.parametrize("route", [b.QR_GRAM, b.QR_HOUSEHOLDER], ids=["gram", "householder"])
 @pytest.mark.parametrize("name,cfg,tree,extrap,beta,sweeps", CASES, ids=[c[0] for c in CASES])
 def test_fp64_solver_matches_oracle(name, cfg, tree, extrap, beta, sweeps, route):
@@ -160,11 +170,9 @@ def test_fp64_solver_matches_oracle(name, cfg, tree, extrap, beta, sweeps, route
     assert np.allclose(lam, ref.lam, rtol=1e-8)
     assert st.ttm_flops == ref.flops
     assert st.qr_fallbacks == 0
-    if route == b.QR_GRAM and len(prob.dims) >= 4:
-        # every update of a sweep but the first takes the split Khatri-Rao QR
-        assert st.krp_split == (len(prob.dims) - 1) * sweeps
-    else:
-        assert st.krp_split == 0
+    reused, split = _krp_routes(prob.dims, prob.R, tree, sweeps)
+    assert st.krp_reused == reused
+    assert st.krp_split == (split if route == b.QR_GRAM and len(prob.dims) >= 4 else 0)
 
 
 @pytest.mark.parametrize("route", [b.QR_GRAM, b.QR_HOUSEHOLDER], ids=["gram", "householder"])
@@ -223,7 +231,8 @@ def test_split_krp_qr_carries_the_guard_of_its_prefetched_half(order):
         assert o.subspace_sine(A[n], ref.A[n]) <= 1e-10
         assert np.allclose(A[n], ref.A[n], atol=1e-8), (n, np.abs(A[n] - ref.A[n]).max())
         assert np.abs(Q[n].T @ Q[n] - np.eye(R)).max() < 1e-13
-    assert st.krp_split == (len(dims) - 1) * sweeps
+    reused, split = _krp_routes(dims, R, b.TREE_RESTRUCTURED, sweeps)
+    assert (st.krp_split, st.krp_reused) == (split, reused)
     # mode 0's nested QR and mode 1's split QR of the first sweep (the starting QRs are Householder)
     assert st.qr_fallbacks >= 2, st.qr_fallbacks
 
