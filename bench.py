@@ -209,8 +209,8 @@ def run_ours(args, rank, world, local_rank):
                     "traffic": TTM_TC_TRAFFIC if prec == b.PREC_SPLIT_BF16 else None,
                     "kernel": "ttm_tc_kernel (first-level TTM, full tensor)",
                     "peak_kind": f"{peak_kind} copy bandwidth (burst)",
-                    "note": "runs as 16-CTA clusters on all GPCs but one, beside the Khatri-Rao QR cluster; "
-                            "alone the same launch takes ~54 us (profiles/ttm_tc_cube400_r32.md)",
+                    "note": "persistent grid on all SMs; the previous sweep's lagged explicit residual streams X "
+                            "beside it; alone the same launch takes ~54 us (profiles/ttm_tc_cube400_r32.md)",
                     "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": full_ms, "launches": int(n_full)}
         # deeper TTMs (every one on this workload contracts a 400 x 400 x 32 node to 400 x 32 x 32):
         # node read once (4 B per element: FP32, or bf16 hi + lo) + result written once (4 B per element)
