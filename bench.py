@@ -348,6 +348,61 @@ def extras(args, prob, X, dev, b):
     return res
 
 
+def run_kernel(args):
+    """One library kernel on a seeded case, timed with CUDA events (also the command the ncu
+    summaries capture):
+      --kernel ttm_tc   --shape P K S R   split-bf16 tensor-core TTM of the middle mode of P x K x S
+      --kernel ttm_f32  --shape P K S R   FP32 CUDA-core TTM
+      --kernel house_qr --shape M R       FP64 cluster Householder QR
+      --kernel krp_qr   --shape m R       QR of the Khatri-Rao product of m triangles"""
+    import torch
+    from paper_2503_18759_gb300 import binding as b
+    from paper_2503_18759_gb300 import build
+    build.build()
+    b.lib()
+    g = np.random.default_rng(0)
+    dev = "cuda"
+    kind, shp = args.kernel, [int(v) for v in args.shape]
+    alg = None
+    if kind in ("ttm_tc", "ttm_f32"):
+        P, K, S, R = shp
+        X = torch.from_numpy(g.standard_normal((P, K, S)).astype(np.float32)).to(dev)
+        Qn = np.linalg.qr(g.standard_normal((K, R)))[0]
+        Q = torch.from_numpy(Qn if kind == "ttm_tc" else Qn.astype(np.float32)).to(dev)
+        out = torch.empty((P, R, S), dtype=torch.float32, device=dev)
+        dt = b.TTM_SPLIT_BF16 if kind == "ttm_tc" else b.TTM_F32
+        run = lambda: b.cpqr_ttm(X.data_ptr(), [P, K, S], 1, Q.data_ptr(), R, out.data_ptr(), dt)
+        alg = {"bytes": 4 * P * K * S + 4 * P * R * S, "note": "the entry point also splits X and Q first"}
+    elif kind == "house_qr":
+        M, R = shp
+        A = torch.from_numpy(g.standard_normal((M, R))).to(dev)
+        Q = torch.empty((M, R), dtype=torch.float64, device=dev)
+        Rm = torch.empty((R, R), dtype=torch.float64, device=dev)
+        run = lambda: b.cpqr_house_qr(A.data_ptr(), M, R, Q.data_ptr(), Rm.data_ptr())
+    elif kind == "krp_qr":
+        m, R = shp
+        tri = [np.linalg.qr(g.standard_normal((R + 8, R)))[1] for _ in range(m)]
+        tri = [t * np.sign(np.diag(t))[:, None] for t in tri]
+        Rs = torch.from_numpy(np.stack(tri)).to(dev)
+        Q0 = torch.empty((R ** m, R), dtype=torch.float64, device=dev)
+        R0 = torch.empty((R, R), dtype=torch.float64, device=dev)
+        run = lambda: b.cpqr_krp_qr(Rs.data_ptr(), m, R, Q0.data_ptr(), R0.data_ptr())
+    else:
+        raise SystemExit(run_kernel.__doc__)
+    for _ in range(max(args.warmup, 1)):
+        run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        run()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    return {"kernel": kind, "shape": shp, "ms_per_call": ms, "calls": args.steps, "algorithmic": alg,
+            "note": "CUDA events around whole entry-point calls (their own allocations and copies included)"}
+
+
 def cpu_baseline(prob):
     from oracle import cpqr_oracle as o
     t = oracle_sweep_times(prob, o.TREE_RESTRUCTURED, 4)
@@ -367,7 +422,12 @@ def main():
                     "line's); others print timing and buckets only")
     ap.add_argument("--tree", default="restructured", choices=["restructured", "standard", "none"],
                     help="dimension tree of the extra workloads (the bench line is always restructured)")
+    ap.add_argument("--kernel", default=None, help="time one library kernel instead (see run_kernel)")
+    ap.add_argument("--shape", nargs="*", default=[], help="sizes of the --kernel case")
     args = ap.parse_args()
+    if args.kernel:
+        print(json.dumps(run_kernel(args)))
+        return
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

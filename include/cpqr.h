@@ -123,9 +123,6 @@ typedef struct {
   int64_t krp_split;       /* Khatri-Rao QRs (order >= 4, Gram route) that took the split route:
                               the QR of the other triangles formed one update ahead, only the level
                               with the last-updated triangle after that update */
-  int64_t krp_reused;      /* Khatri-Rao QRs taken over from the previous update of the same mode
-                              (the restructured tree updates a sweep's last mode first in the next;
-                              the other triangles are unchanged, so the QR is the same) */
 } cpqr_stats;
 
 /* Turn per-launch CUDA-event timing on (1) or off (0); resets the bucket times. */

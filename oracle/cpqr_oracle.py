@@ -35,11 +35,18 @@ design notes of the repository):
   activates when |fit_k - fit_{k-1}| < 0.03 with beta = 1/20000 (fit > 0.95),
   1/2000 (0.90 < fit <= 0.95), 1/500 (0.70 < fit <= 0.90), else 1/250; alpha =
   1/10; beta then stays fixed and applies from sweep k+1.
-* Restructured tree: sweep 1 is the standard tree; for order 4, sweeps 2 and
-  3 follow the structure that Table 5 counts; every other sweep (and every
-  sweep after the first for order 3 and order >= 5) picks, among the modes not
-  yet updated, the cheapest valid cached source (ties: lowest mode), and
+* Restructured tree: sweep 1 is the standard tree.  Order 3 then alternates
+  the two sweeps Section 3.1 describes: sweep 2 starts from the unused
+  Y(1,3) (A1) and forms Y(2,3) from X (A2, A3); sweep 3 proceeds from Y(2,3)
+  (A2) and forms Y(1,3) from X (A1, A3); sweeps 4, 5, ... repeat them.  For
+  order 4, sweeps 2 and 3 follow the structure that Table 5 counts.  Every
+  other sweep picks, among the modes not yet updated in the sweep and whose
+  update would not be a no-op (an update is a no-op when no other factor
+  changed since that mode's last update: same leaf, same Khatri-Rao QR, same
+  result), the cheapest valid cached source (ties: lowest mode), and
   contracts first the modes already updated in this sweep, then ascending.
+  Every update thus follows a change of another factor (the alternating
+  updates of Section 3.1).
 """
 from __future__ import annotations
 
@@ -217,6 +224,16 @@ class _Node:
     ver: Dict[int, int]            # contracted mode -> version of Q_k used
 
 
+# Order-3 restructured tree, sweeps 2 and 3 (repeated with period 2 after
+# that): (mode, free set of the source, contraction chain), 0-based modes.
+# Sweep 2: A1 from Y(1,3) x3, then Y(2,3) = X x1 -> A2 (x3), A3 (x2).
+# Sweep 3: A2 from Y(2,3) x3, then Y(1,3) = X x2 -> A1 (x3), A3 (x1).
+# With the standard first sweep this reproduces the item counts of Table 2.
+_ORDER3_SWEEPS = [
+    [(0, (0, 2), [2]), (1, (0, 1, 2), [0, 2]), (2, (1, 2), [1])],
+    [(1, (1, 2), [2]), (0, (0, 1, 2), [1, 2]), (2, (0, 2), [0])],
+]
+
 # Order-4 restructured tree, sweeps 2 and 3: (mode, free set of the source,
 # contraction chain), 0-based modes.  Reproduces the item counts of Table 5
 # together with the standard first sweep.
@@ -242,6 +259,8 @@ class Schedule:
         self.R = int(R)
         self.tree = int(tree)
         self.ver = [0] * self.N
+        # per mode: the versions of the other factors its last update saw
+        self.seen: Dict[int, Tuple[int, ...]] = {}
         self.nodes: Dict[int, _Node] = {0: _Node(tuple(range(self.N)), {})}
         self.next_id = 1
         self.sweep_index = 0
@@ -257,6 +276,13 @@ class Schedule:
 
     def _valid(self, node: _Node) -> bool:
         return all(self.ver[k] == v for k, v in node.ver.items())
+
+    def _others(self, n: int) -> Tuple[int, ...]:
+        return tuple(v for k, v in enumerate(self.ver) if k != n)
+
+    def is_noop(self, n: int) -> bool:
+        """An update of mode n now would repeat its last one: no other factor changed since."""
+        return self.seen.get(n) == self._others(n)
 
     def _ttm(self, src: int, k: int) -> int:
         node = self.nodes[src]
@@ -274,6 +300,7 @@ class Schedule:
         assert self.nodes[leaf].free == (n,)
         assert self._valid(self.nodes[leaf])
         self.ops.append((OP_UPDATE, n, leaf, 0))
+        self.seen[n] = self._others(n)
         self.ver[n] += 1
         self._free(leaf)
         for i in sorted(self.nodes):
@@ -321,7 +348,7 @@ class Schedule:
     def _greedy_step(self, done: set) -> Tuple[int, int, List[int]]:
         best = None
         for n in range(self.N):
-            if n in done:
+            if n in done or self.is_noop(n):
                 continue
             for i in sorted(self.nodes):
                 node = self.nodes[i]
@@ -357,6 +384,9 @@ class Schedule:
             self._standard(0, self.N, True)
             if self.tree == TREE_STANDARD:
                 self._free_all()
+        elif self.N == 3:
+            for n, free, chain in _ORDER3_SWEEPS[(s - 1) % 2]:
+                self._chain(self._find(free), n, chain)
         elif self.N == 4 and s in (1, 2):
             for n, free, chain in _ORDER4_SWEEPS[s - 1]:
                 self._chain(self._find(free), n, chain)

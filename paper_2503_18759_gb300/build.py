@@ -38,18 +38,10 @@ def _deps_mtime() -> float:
     return m
 
 
-def build(force: bool = False, verbose: bool = False, variant: str = "") -> str:
-    """Build libcpqr.so.  variant="phases" builds _build/phases/libcpqr.so with per-phase
-    %globaltimer stamps in the cluster QR kernel (for kernel_bench --phases)."""
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Build libcpqr.so (skipped when it is newer than every source and header)."""
     lib = LIB
     bdir = BUILD
-    extra = []
-    if variant == "phases":
-        bdir = os.path.join(BUILD, "phases")
-        lib = os.path.join(bdir, "libcpqr.so")
-        extra = ["-DCPQR_QR_PHASES"]
-    elif variant:
-        raise ValueError(variant)
     if not force and os.path.exists(lib) and os.path.getmtime(lib) >= _deps_mtime():
         return lib
     os.makedirs(bdir, exist_ok=True)
@@ -57,9 +49,9 @@ def build(force: bool = False, verbose: bool = False, variant: str = "") -> str:
 
     def compile_one(src: str) -> str:
         obj = os.path.join(bdir, src + ".o")
-        cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
         if src.endswith(".cpp"):
-            cmd = [nvcc, *NVCC_FLAGS, *extra, "-x", "cu", *ARCH, "-c", os.path.join(CSRC, src), "-o", obj]
+            cmd = [nvcc, *NVCC_FLAGS, "-x", "cu", *ARCH, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
@@ -79,5 +71,4 @@ def build(force: bool = False, verbose: bool = False, variant: str = "") -> str:
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
-                variant="phases" if "--phases" in sys.argv else ""))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))

@@ -174,12 +174,6 @@ struct cpqr_ctx {
   int last_updated = -1;  // mode of the last update enqueued
   int next_first = -1;    // first update of the sweep after the current one (-1: unknown)
   int64_t n_split = 0;    // Khatri-Rao QRs issued on the split route
-  // The restructured tree updates the last mode of a sweep again first in the next one: nothing
-  // but that mode changed in between, so its Khatri-Rao QR is the one just computed, bit for bit
-  // (every reduction has a fixed order).  zq_mode: the mode whose Q0 (now in Q0prev[zq_mode])
-  // and R0 are still those of its inputs; -1 once another mode's factor changed.
-  int zq_mode = -1;
-  int64_t n_reused = 0;   // Khatri-Rao QRs taken over from the previous update of the same mode
   cudaEvent_t ev_gram = nullptr;     // main stream: the last factor's Gram stored
   double* fg_work = nullptr;       // Gram-route factor QR workspace
   double* hpart = nullptr;         // per-block folded Gram partials of A^ (finish prep)
@@ -522,7 +516,6 @@ cpqr_status checkpoint_restore(cpqr_ctx* ctx, int slot) {
   ctx->zchol_mode = -1;
   ctx->wpf_mode = -1;
   ctx->last_updated = -1;
-  ctx->zq_mode = -1;
   return CPQR_OK;
 }
 
@@ -621,22 +614,12 @@ cpqr_status launch_z(cpqr_ctx* ctx, int n, int after) {
       if (k == ctx->last_updated) s = m;
       tri.p[m++] = ctx->Rf[k];
     }
-  const bool reuse = ctx->zq_mode == n && ctx->last_updated == n && ctx->has_prev[n];
-  const bool split = !reuse && split_ready(ctx, n) && s >= 0;
+  const bool split = split_ready(ctx, n) && s >= 0;
   CK(cudaEventRecord(ctx->ev_ready, ctx->st));
   CK(cudaStreamWaitEvent(ctx->st2, ctx->ev_ready, 0));
   {
-    Timed tm(ctx, CPQR_BUCKET_Q0, reuse ? 0 : 1, ctx->st2);
-    if (reuse) {
-      // the previous update of n used this very Q0 (swapped into Q0prev[n]); R0 is untouched
-      const size_t M0 = (size_t)ipow(ctx->R, m);
-      CK(cudaMemcpyAsync(ctx->Q0, ctx->Q0prev[n], M0 * ctx->R * sizeof(double), cudaMemcpyDeviceToDevice,
-                         ctx->st2));
-      if (ctx->Q0f)
-        CK(cudaMemcpyAsync(ctx->Q0f, ctx->Q0fprev[n], M0 * ctx->R * sizeof(float), cudaMemcpyDeviceToDevice,
-                           ctx->st2));
-      ctx->n_reused += 1;
-    } else if (split) {
+    Timed tm(ctx, CPQR_BUCKET_Q0, 1, ctx->st2);
+    if (split) {
       if (!(ctx->zchol_mode == n && ctx->zchol_split)) {
         CK(launch_krp_chol(z_grams(ctx, n), m, ctx->R, ctx->zg_work, ctx->st2, 0, gram_flag(ctx->wg_work)));
         ctx->launches += 1;
@@ -669,7 +652,6 @@ cpqr_status launch_z(cpqr_ctx* ctx, int n, int after) {
   CK(cudaEventRecord(ctx->ev_z, ctx->st2));
   ctx->z_pending = true;
   ctx->z_mode = n;
-  ctx->zq_mode = n;
   if (ctx->gram && ctx->w_ok && m >= 3 && after >= 0 && after != n) {
     cpqr_status st = launch_w(ctx, n, after);
     if (st != CPQR_OK) return st;
@@ -760,7 +742,6 @@ cpqr_status run_update(cpqr_ctx* ctx, int n, int leaf, double beta, int next_mod
   std::swap(ctx->Q0f, ctx->Q0fprev[n]);
   ctx->has_prev[n] = true;
   ctx->last_updated = n;
-  if (ctx->zq_mode != n) ctx->zq_mode = -1;
   return CPQR_OK;
 }
 
@@ -1384,7 +1365,6 @@ cpqr_status cp_als_qr_stats(cpqr_ctx* ctx, cpqr_stats* out) {
   out->accepted = ctx->accepted;
   out->launches = ctx->launches;
   out->krp_split = ctx->n_split;
-  out->krp_reused = ctx->n_reused;
   for (int b = 0; b < CPQR_NBUCKETS; ++b) {
     out->ms_bucket[b] = ctx->ms_bucket[b];
     out->n_bucket[b] = ctx->n_bucket[b];

@@ -6,13 +6,16 @@
 //   m-1 through contractions of modes 0..m-2 - ascending at the top level of
 //   an order >= 4 tree, descending otherwise.  Each sweep restarts from X.
 // * Restructured tree: the first sweep is the standard tree and every node
-//   stays cached while all Q_k it contracted are current.  Order 4 sweeps 2 and
-//   3 follow the structure counted in Table 5 (reusing Y(3,4), Y(2,3,4),
-//   Y(1,3,4), Y(1,4)); every other sweep repeatedly picks, among the modes not
-//   yet updated in the sweep, the cached source whose contraction chain is
-//   cheapest (ties: lower mode, then the lexicographically smaller free set,
-//   then the older node); the chain contracts the modes already updated in
-//   the sweep first, then ascending.
+//   stays cached while all Q_k it contracted are current.  Order 3 alternates
+//   the two sweeps of Section 3.1 (A1 from the unused Y(1,3), then Y(2,3) from
+//   X for A2 and A3; A2 from Y(2,3), then Y(1,3) from X for A1 and A3).  Order
+//   4 sweeps 2 and 3 follow the structure counted in Table 5 (reusing Y(3,4),
+//   Y(2,3,4), Y(1,3,4), Y(1,4)).  Every other sweep repeatedly picks, among the
+//   modes not yet updated in the sweep whose update is not a no-op (a mode is a
+//   no-op while no other factor changed since its last update), the cached
+//   source whose contraction chain is cheapest (ties: lower mode, then the
+//   lexicographically smaller free set, then the older node); the chain
+//   contracts the modes already updated in the sweep first, then ascending.
 // * No tree (Tables 3 and 6): each mode contracts X directly; order 3 uses the
 //   cyclic predecessors, higher orders contract the last modes first for the
 //   lower half of the modes and the first modes first for the upper half.
@@ -30,6 +33,14 @@ struct Step {
   uint32_t src_mask;
   std::vector<int> chain;
 };
+// Order-3 restructured sweeps 2 and 3, repeated with period 2 (0-based modes).
+const std::vector<std::vector<Step>>& order3_steps() {
+  static const std::vector<std::vector<Step>> s = {
+      {{0, 0b101u, {2}}, {1, 0b111u, {0, 2}}, {2, 0b110u, {1}}},
+      {{1, 0b110u, {2}}, {0, 0b111u, {1, 2}}, {2, 0b101u, {0}}},
+  };
+  return s;
+}
 // Order-4 restructured sweeps 2 and 3 (0-based modes).
 const std::vector<std::vector<Step>>& order4_steps() {
   static const std::vector<std::vector<Step>> s = {
@@ -41,7 +52,7 @@ const std::vector<std::vector<Step>>& order4_steps() {
 }  // namespace
 
 Schedule::Schedule(const std::vector<int64_t>& dims, int R, int tree)
-    : dims_(dims), N_((int)dims.size()), R_(R), tree_(tree), ver_(dims.size(), 0) {
+    : dims_(dims), N_((int)dims.size()), R_(R), tree_(tree), ver_(dims.size(), 0), seen_(dims.size()) {
   Node x;
   x.free_mask = (1u << N_) - 1u;
   x.ver.assign(N_, -1);
@@ -66,6 +77,15 @@ int64_t Schedule::ttm_cost(uint32_t mask) const {
   for (int64_t v : node_dims(mask)) p *= v;
   return p;
 }
+
+std::vector<int64_t> Schedule::others(int n) const {
+  std::vector<int64_t> v;
+  for (int k = 0; k < N_; ++k)
+    if (k != n) v.push_back(ver_[k]);
+  return v;
+}
+
+bool Schedule::is_noop(int n) const { return !seen_[n].empty() && seen_[n] == others(n); }
 
 bool Schedule::valid(const Node& nd) const {
   for (int k = 0; k < N_; ++k)
@@ -104,6 +124,7 @@ void Schedule::update(int n, int leaf, std::vector<Op>& out) {
   const Node& l = nodes_.at(leaf);
   if (l.free_mask != (1u << n) || !valid(l)) throw std::logic_error("invalid leaf");
   out.push_back({OP_UPDATE, n, leaf, 0});
+  seen_[n] = others(n);
   ++ver_[n];
   release(leaf, out);
   std::vector<int> stale;
@@ -152,7 +173,7 @@ void Schedule::standard(int src, int m, bool top, std::vector<Op>& out) {
 int Schedule::find_valid(uint32_t mask) const {
   for (auto& kv : nodes_)
     if (kv.second.free_mask == mask && valid(kv.second)) return kv.first;
-  throw std::logic_error("no valid cached node for the order-4 step");
+  throw std::logic_error("no valid cached node for a tabulated step");
 }
 
 void Schedule::next_sweep(std::vector<Op>& out) {
@@ -169,6 +190,10 @@ void Schedule::next_sweep(std::vector<Op>& out) {
     if (tree_ == 1) release_all(out);
     return;
   }
+  if (N_ == 3) {
+    for (const Step& st : order3_steps()[(s - 1) % 2]) chain(find_valid(st.src_mask), st.n, st.chain, out);
+    return;
+  }
   if (N_ == 4 && (s == 1 || s == 2)) {
     for (const Step& st : order4_steps()[s - 1]) chain(find_valid(st.src_mask), st.n, st.chain, out);
     return;
@@ -180,7 +205,7 @@ void Schedule::next_sweep(std::vector<Op>& out) {
     int best_n = 0, best_id = 0;
     std::vector<int> best_free, best_chain;
     for (int n = 0; n < N_; ++n) {
-      if (done & (1u << n)) continue;
+      if ((done & (1u << n)) || is_noop(n)) continue;
       for (auto& kv : nodes_) {
         const Node& nd = kv.second;
         if (!(nd.free_mask & (1u << n)) || !valid(nd)) continue;

@@ -33,6 +33,8 @@ class Schedule {
   std::vector<int64_t> node_dims(uint32_t mask) const;
   int64_t ttm_cost(uint32_t mask) const;
   bool valid(const Node& nd) const;
+  std::vector<int64_t> others(int n) const;  // versions of every Q_k but Q_n
+  bool is_noop(int n) const;                 // no other factor changed since n's last update
   int ttm(int src, int k, std::vector<Op>& out);
   void update(int n, int leaf, std::vector<Op>& out);
   void release(int id, std::vector<Op>& out);
@@ -45,6 +47,7 @@ class Schedule {
   std::vector<int64_t> dims_;
   int N_, R_, tree_;
   std::vector<int64_t> ver_;
+  std::vector<std::vector<int64_t>> seen_;  // per mode: others(n) at its last update
   std::map<int, Node> nodes_;
   int next_id_ = 1;
   int sweep_ = 0;

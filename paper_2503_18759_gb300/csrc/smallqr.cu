@@ -40,31 +40,6 @@
 
 namespace cg = cooperative_groups;
 
-#ifdef CPQR_QR_PHASES
-__device__ unsigned long long g_qr_phase[8];
-__device__ long long g_qr_col[2][8];  // per-column sub-phase cycles (clock64) summed over columns, ranks 0 and CL-1
-#define QR_PHASE(i)                                                              \
-  do {                                                                           \
-    if (threadIdx.x == 0 && cluster.block_rank() == 0) {                         \
-      unsigned long long t_;                                                     \
-      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_));                     \
-      g_qr_phase[i] = t_;                                                        \
-    }                                                                            \
-  } while (0)
-#define QR_COL(k)                   \
-  do {                              \
-    const long long t_ = clock64(); \
-    col_acc[k] += t_ - col_prev;    \
-    col_prev = t_;                  \
-  } while (0)
-#else
-#define QR_PHASE(i) \
-  do {              \
-  } while (0)
-#define QR_COL(k) \
-  do {            \
-  } while (0)
-#endif
 
 namespace cpqr {
 
@@ -222,7 +197,6 @@ __global__ void __launch_bounds__(NT, 1) qr_cluster_kernel(QrParams p) {
   double (*ST)[CPQR_MAXR] = reinterpret_cast<double (*)[CPQR_MAXR]>(&sm.big[0]);
   double (*VT)[CPQR_MAXR] = reinterpret_cast<double (*)[CPQR_MAXR]>(&sm.big[RR]);
 
-  QR_PHASE(0);
   if (p.run_if) {
     if (*(volatile const int*)p.run_if == 0) return;  // every CTA reads the same flag
     if (rank == 0 && tid == 0) atomicAdd(p.run_if + 1, 1);
@@ -299,17 +273,11 @@ __global__ void __launch_bounds__(NT, 1) qr_cluster_kernel(QrParams p) {
     }
   }
   __syncthreads();
-  QR_PHASE(1);
 
   // ---------------- Householder columns: one st.async exchange per column ----------------
   // Step j applies reflector j-1 to the rows it touches and, in the same pass, accumulates
   // x_j^T a_c (x_j = column j after that update) over the rows [j, act[j]) for every c.
-#ifdef CPQR_QR_PHASES
-  long long col_acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  long long col_prev = clock64();
-#endif
   for (int j = 0; j < R; ++j) {
-    QR_COL(0);
     const int buf = j & 1;
     const int pj = j - 1;
     const bool upd = (j > 0);
@@ -340,10 +308,8 @@ __global__ void __launch_bounds__(NT, 1) qr_cluster_kernel(QrParams p) {
         if (t == j) sm.pivloc[lane] = a;
       }
     }
-    QR_COL(1);
     sm.red[warp][lane] = acc;
     __syncthreads();
-    QR_COL(2);
     if (warp < 4) {
       // CTA sums of 8 columns per warp, stored into every CTA of the cluster
       const int slot = 8 * warp + (lane & 7), g = lane >> 3;
@@ -363,10 +329,8 @@ __global__ void __launch_bounds__(NT, 1) qr_cluster_kernel(QrParams p) {
       const uint32_t bar = smem_u32(&sm.bar[buf]);
       for (int r = lane >> 4; r < CL; r += 2) tc::st_async_v2(tc::mapa(src, r), lo, hi, tc::mapa(bar, r));
     }
-    QR_COL(3);
     if (warp < 4) {
       tc::mbar_wait_cluster(smem_u32(&sm.bar[buf]), (uint32_t)((j >> 1) & 1), &sm.abort_flag, p.status);
-      QR_COL(4);
       // re-arm this buffer for column j + 2: its bytes can only come after this CTA's column j + 1
       // sums, which it sends after every read of this buffer
       if (tid == 0 && j + 2 < R) tc::mbar_expect_tx(smem_u32(&sm.bar[buf]), kColBytes);
@@ -379,7 +343,6 @@ __global__ void __launch_bounds__(NT, 1) qr_cluster_kernel(QrParams p) {
       v += __shfl_xor_sync(FULL, v, 16);
       if (g == 0) sm.dvec[slot] = v;
       sync_warps0to3();
-      QR_COL(5);
       if (warp == 0) {
         const double s = sm.dvec[j], xj = sm.pbox[buf][j];
         double alpha, tau;
@@ -397,16 +360,9 @@ __global__ void __launch_bounds__(NT, 1) qr_cluster_kernel(QrParams p) {
           if (rank == 0 && tau == 0.0) atomicOr(p.status, CPQR_DEV_SINGULAR);
         }
       }
-      QR_COL(6);
     }
     __syncthreads();
-    QR_COL(7);
   }
-#ifdef CPQR_QR_PHASES
-  if (tid == 0 && (rank == 0 || rank == CL - 1))
-    for (int k = 0; k < 8; ++k) g_qr_col[rank == 0 ? 0 : 1][k] = col_acc[k];
-#endif
-  QR_PHASE(2);
 
   // ---------------- R factor (positive diagonal) ----------------
   for (int u = warp; u < L; u += NW) {
@@ -418,7 +374,6 @@ __global__ void __launch_bounds__(NT, 1) qr_cluster_kernel(QrParams p) {
       p.Rout[t * R + lane] = sg * v;
     }
   }
-  QR_PHASE(3);
 
   // ---------------- W2 = T V_top^T: column cc by warp cc / CL of CTA cc % CL ----------------
   // Tinv W2 = V_top^T with Tinv = striu(S) + diag(S)/2 upper triangular and diag(S)/2 = 1/tau;
@@ -440,9 +395,7 @@ __global__ void __launch_bounds__(NT, 1) qr_cluster_kernel(QrParams p) {
       for (int r = lane >> 4; r < CL; r += 2) tc::st_async_v2(tc::mapa(src, r), lo, hi, tc::mapa(bar, r));
     }
   }
-  QR_PHASE(4);
   tc::mbar_wait_cluster(smem_u32(&sm.bar[2]), 0u, &sm.abort_flag, p.status);
-  QR_PHASE(5);
 
   // ---------------- Q rows: Q[t, c] = sign_c (delta_tc - sum_a v_a[t] W2[a][c]) ----------------
   // Khatri-Rao mode: the output row of each local row, staged once (V^T V and V_top are dead:
@@ -488,7 +441,6 @@ __global__ void __launch_bounds__(NT, 1) qr_cluster_kernel(QrParams p) {
       }
     }
   }
-  QR_PHASE(6);
   if (p.mode == MODE_FINISH && rank == 0 && warp == 0) {
     // <V0, V^> and ||V^||^2: per-block partials of finish_prep_kernel, added in a fixed order
     double a = 0.0, b = 0.0;
@@ -733,17 +685,6 @@ cudaError_t run(QrParams& p, cudaStream_t st) {
 
 int qr_cluster_sms() { return cluster_size(); }
 
-#ifdef CPQR_QR_PHASES
-// Profiling build only: %globaltimer stamps of the last cluster-QR launch (rank 0).
-extern "C" void cpqr_debug_qr_phases(unsigned long long* out) {
-  cudaMemcpyFromSymbol(out, g_qr_phase, sizeof(g_qr_phase));
-}
-// Profiling build only: clock64 cycles per sub-phase of the Householder columns, summed over
-// columns, for cluster ranks 0 and CL-1 (2 x 8 values).
-extern "C" void cpqr_debug_qr_columns(long long* out) {
-  cudaMemcpyFromSymbol(out, g_qr_col, sizeof(g_qr_col));
-}
-#endif
 
 size_t house_qr_work_doubles(int64_t M, int R) { return (size_t)M * R; }
 size_t krp_qr_work_doubles(const ZPlan& plan) { return (size_t)plan.M * plan.R; }

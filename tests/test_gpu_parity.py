@@ -139,14 +139,14 @@ CASES = [
 ]
 
 
-def _krp_routes(dims, R, tree, sweeps):
-    """Expected Khatri-Rao QR routes from the schedule's update order: an update of the same mode
-    as the one before reuses that QR (the other triangles did not change); any other update
-    after the first takes the split route on the Gram route at order >= 4."""
+def _krp_split_count(dims, R, tree, sweeps):
+    """Expected split-route Khatri-Rao QRs on the Gram route at order >= 4: every update after the
+    first (no update repeats the mode of the one before it, so each has a W formed one update
+    ahead)."""
     ops, _ = b.cp_als_qr_schedule(dims, R, tree, sweeps)
     ups = [int(o[1]) for o in ops if int(o[0]) == 1]
-    reused = sum(1 for j in range(1, len(ups)) if ups[j] == ups[j - 1])
-    return reused, len(ups) - 1 - reused
+    assert all(ups[j] != ups[j - 1] for j in range(1, len(ups)))
+    return len(ups) - 1
 
 
 @pytest.mark.parametrize("route", [b.QR_GRAM, b.QR_HOUSEHOLDER], ids=["gram", "householder"])
@@ -170,8 +170,7 @@ def test_fp64_solver_matches_oracle(name, cfg, tree, extrap, beta, sweeps, route
     assert np.allclose(lam, ref.lam, rtol=1e-8)
     assert st.ttm_flops == ref.flops
     assert st.qr_fallbacks == 0
-    reused, split = _krp_routes(prob.dims, prob.R, tree, sweeps)
-    assert st.krp_reused == reused
+    split = _krp_split_count(prob.dims, prob.R, tree, sweeps)
     assert st.krp_split == (split if route == b.QR_GRAM and len(prob.dims) >= 4 else 0)
 
 
@@ -231,8 +230,7 @@ def test_split_krp_qr_carries_the_guard_of_its_prefetched_half(order):
         assert o.subspace_sine(A[n], ref.A[n]) <= 1e-10
         assert np.allclose(A[n], ref.A[n], atol=1e-8), (n, np.abs(A[n] - ref.A[n]).max())
         assert np.abs(Q[n].T @ Q[n] - np.eye(R)).max() < 1e-13
-    reused, split = _krp_routes(dims, R, b.TREE_RESTRUCTURED, sweeps)
-    assert (st.krp_split, st.krp_reused) == (split, reused)
+    assert st.krp_split == _krp_split_count(dims, R, b.TREE_RESTRUCTURED, sweeps)
     # mode 0's nested QR and mode 1's split QR of the first sweep (the starting QRs are Householder)
     assert st.qr_fallbacks >= 2, st.qr_fallbacks
 
