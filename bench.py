@@ -33,8 +33,8 @@ sys.path.insert(0, ROOT)
 METRIC = "sec/CP-ALS-QR sweep & time-to-fit 1e-6 (mixed+learned vs FP64 GPU); TTM %peak"
 WORKLOAD = "cube400_r32_c09"
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture of the current kernels
-# on this workload (profiles/ttm_tc_cube400_r32.md, profiles/qr_cluster_cube400_r32.md); None where a
-# kernel changed after its capture
+# on this workload (the same launch shapes through bench.py --kernel); None where a kernel changed
+# after its capture
 TTM_TC_TRAFFIC = 270.5e6    # ttm_tc_kernel<0>, 1 x 400 x 160000 -> R = 32 (256.1 MB read + 14.4 MB written)
 TTM_DEEP_TRAFFIC = 20.6e6   # ttm_tc_kernel<1>, 12800 x 400 x 1 -> R = 32 (20.6 MB read, output left in L2)
 # whole-GPU FP64 DFMA rate measured by a probe on the GB300s (TFLOP/s)
@@ -210,7 +210,7 @@ def run_ours(args, rank, world, local_rank):
                     "kernel": "ttm_tc_kernel (first-level TTM, full tensor)",
                     "peak_kind": f"{peak_kind} copy bandwidth (burst)",
                     "note": "persistent grid on all SMs; the previous sweep's lagged explicit residual streams X "
-                            "beside it; alone the same launch takes ~54 us (profiles/ttm_tc_cube400_r32.md)",
+                            "beside it; alone the same launch takes ~54 us (ncu)",
                     "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": full_ms, "launches": int(n_full)}
         # deeper TTMs (every one on this workload contracts a 400 x 400 x 32 node to 400 x 32 x 32):
         # node read once (4 B per element: FP32, or bf16 hi + lo) + result written once (4 B per element)
@@ -275,8 +275,47 @@ def run_ours(args, rank, world, local_rank):
     return out
 
 
+def _run_to_target(b, prob, X, opts, target, max_sweeps, chunk=25):
+    """Sweeps in chunks (fits may come one sweep late inside a chunk) until the fit reaches
+    target or max_sweeps; returns the history, the wall time per chunk and the final exact fit."""
+    import torch
+    with b.Decomposition(prob.dims, prob.R, X.data_ptr(), False, prob.A0, opts) as d:
+        fits, walls = [], []
+        torch.cuda.synchronize()
+        while len(fits) < max_sweeps:
+            n = min(chunk, max_sweeps - len(fits))
+            t0 = time.perf_counter()
+            f = d.sweep(n)
+            torch.cuda.synchronize()
+            walls.append((n, time.perf_counter() - t0))
+            fits.extend(float(v) for v in f)
+            if target is not None and max(fits) >= target:
+                break
+        st = d.stats()
+        return np.array(fits), walls, d.fit_exact(), st
+
+
+def _seconds_to(fits, walls, target):
+    """First sweep whose fit reaches target, and the wall time up to it (within-chunk time
+    prorated by sweeps)."""
+    hit = np.nonzero(fits >= target)[0]
+    if not len(hit):
+        return None, None
+    k = int(hit[0]) + 1
+    t, done = 0.0, 0
+    for n, w in walls:
+        if done + n >= k:
+            return k, t + w * (k - done) / n
+        t += w
+        done += n
+    return k, t
+
+
 def extras(args, prob, X, dev, b):
-    """e2e through the host-buffer entry point, the FP64 GPU path, and time to the 1e-6 fit tolerance."""
+    """e2e through the host-buffer entry point; time to the fit target f* - 1e-6 (f*: the FP64 path,
+    standard tree, no extrapolation, run to |delta fit| < 1e-12 or 2000 sweeps) and to the 1e-6
+    stopping test for plain FP64 CP-ALS-QR, ALS-QR-BRE on both paths (rule, learned proposer) and the
+    extrapolation ablation; the QR routes."""
     import torch
     res = {}
     # e2e: pinned host tensor -> device -> init -> sweeps -> factors back, one C call
@@ -295,41 +334,47 @@ def extras(args, prob, X, dev, b):
     res["e2e"] = {"value": e2e_ms * 1e-3 / ns, "unit": "s/sweep", "h2d_bytes_per_step": prob.X.nbytes / ns,
                   "d2h_bytes_per_step": fbytes / ns + 24, "sweeps_per_call": ns,
                   "note": "one cp_als_qr_run_host call (H2D of X from pinned memory, init, sweeps, factors D2H) / sweeps"}
-    # time to |delta fit| < 1e-6 from the same start: plain FP64 CP-ALS-QR (Alg. 2: no tree,
-    # no extrapolation) and ALS-QR-BRE on both paths, with the rule and with the learned proposer
+    # f*: the least-squares fit the method converges to, from the FP64 path
+    o64 = b.make_options(tree=b.TREE_STANDARD, prec=b.PREC_FP64, extrap=b.EXTRAP_NONE)
+    t0 = time.perf_counter()
+    with b.Decomposition(prob.dims, prob.R, X.data_ptr(), False, prob.A0, o64) as d:
+        conv, fstar_red, ns_star = d.fit(1e-12, 2000)
+        fstar = d.fit_exact()
+    res["fstar"] = {"value": fstar, "reduced_form": fstar_red, "sweeps": ns_star, "converged_1e-12": conv,
+                    "seconds": time.perf_counter() - t0,
+                    "how": "FP64 path, standard tree, no extrapolation, |delta fit| < 1e-12 or 2000 sweeps; "
+                           "explicit residual of its final factors"}
+    target = fstar - 1e-6
     from paper_2503_18759_gb300 import learn
     w = learn.load_weights()
-    ttf = {}
-    variants = [("fp64_plain_cpalsqr", b.PREC_FP64, b.TREE_NONE, b.EXTRAP_NONE, None),
-                ("fp64_bre_rule", b.PREC_FP64, b.TREE_RESTRUCTURED, b.EXTRAP_PAPER, None),
-                ("split_bre_rule", b.PREC_SPLIT_BF16, b.TREE_RESTRUCTURED, b.EXTRAP_PAPER, None),
-                ("split_bre_learned", b.PREC_SPLIT_BF16, b.TREE_RESTRUCTURED, b.EXTRAP_LEARNED, w),
-                ("split_br_none", b.PREC_SPLIT_BF16, b.TREE_RESTRUCTURED, b.EXTRAP_NONE, None)]
-    for name, prec, tree, ex, wt in variants:
-        o = b.make_options(tree=tree, prec=prec, extrap=ex, mlp_weights=wt)
-        with b.Decomposition(prob.dims, prob.R, X.data_ptr(), False, prob.A0, o) as d:
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            conv, f, ns = d.fit(1e-6, 300)
-            torch.cuda.synchronize()
-            wall = time.perf_counter() - t0
-            fx = d.fit_exact()
-            st = d.stats()
-            hist = d.history()[0]
-            ttf[name] = {"seconds": wall, "sweeps": ns, "converged": conv, "fit_reported": f, "fit_exact": fx,
-                         "s_per_sweep": wall / max(ns, 1), "proposals": st.proposals, "accepted": st.accepted,
-                         "_hist": hist}
-    # the variants stop at different fits (the tree changes the mode order, hence the
-    # trajectory): also time each to the lowest final fit any of them reached
-    target = min(v["fit_exact"] for v in ttf.values()) - 1e-6
-    for v in ttf.values():
-        h = v.pop("_hist")
-        hit = np.nonzero(h >= target)[0]
-        k = int(hit[0]) + 1 if len(hit) else None
-        v["sweeps_to_common_target"] = k
-        v["seconds_to_common_target"] = k * v["s_per_sweep"] if k else None
-    res["common_fit_target"] = target
-    res["time_to_tol_1e-6"] = ttf
+    variants = [("fp64_plain_cpalsqr", b.PREC_FP64, b.TREE_NONE, b.EXTRAP_NONE, 0.0, 0.1, None, 600),
+                ("fp64_bre_rule", b.PREC_FP64, b.TREE_RESTRUCTURED, b.EXTRAP_PAPER, 0.0, 0.1, None, 600),
+                ("split_bre_rule", b.PREC_SPLIT_BF16, b.TREE_RESTRUCTURED, b.EXTRAP_PAPER, 0.0, 0.1, None, 2000),
+                ("split_bre_learned", b.PREC_SPLIT_BF16, b.TREE_RESTRUCTURED, b.EXTRAP_LEARNED, 0.0, 0.1, w, 2000),
+                ("split_br_none", b.PREC_SPLIT_BF16, b.TREE_RESTRUCTURED, b.EXTRAP_NONE, 0.0, 0.1, None, 2000),
+                # extrapolation ablation (eq. 18 is alpha = 1; a fixed beta against the rule)
+                ("split_bre_fixed_5e-4", b.PREC_SPLIT_BF16, b.TREE_RESTRUCTURED, b.EXTRAP_FIXED, 5e-4, 0.1, None, 2000),
+                ("split_eq18_fixed_5e-4", b.PREC_SPLIT_BF16, b.TREE_RESTRUCTURED, b.EXTRAP_FIXED, 5e-4, 1.0, None, 2000)]
+    to_fstar, to_tol = {}, {}
+    for name, prec, tree, ex, beta, alpha, wt, cap in variants:
+        o = b.make_options(tree=tree, prec=prec, extrap=ex, beta_fixed=beta, alpha=alpha, mlp_weights=wt)
+        fits, walls, fx, st = _run_to_target(b, prob, X, o, target, cap)
+        k, sec = _seconds_to(fits, walls, target)
+        wall = sum(t for _, t in walls)
+        to_fstar[name] = {"reached": k is not None, "sweeps": k, "seconds": sec, "sweeps_run": len(fits),
+                          "s_per_sweep": wall / max(len(fits), 1), "best_fit": float(np.max(fits)),
+                          "final_fit_exact": fx, "gap_to_fstar": fstar - float(np.max(fits)),
+                          "proposals": int(st.proposals), "accepted": int(st.accepted)}
+        if name in ("fp64_plain_cpalsqr", "fp64_bre_rule", "split_bre_rule", "split_bre_learned", "split_br_none"):
+            with b.Decomposition(prob.dims, prob.R, X.data_ptr(), False, prob.A0, o) as d:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                conv, f, ns = d.fit(1e-6, cap)
+                torch.cuda.synchronize()
+                to_tol[name] = {"seconds": time.perf_counter() - t0, "sweeps": ns, "converged": conv, "fit": f,
+                                "fit_exact": d.fit_exact()}
+    res["time_to_fit"] = {"target": "f*-1e-6", "f*": fstar, "variants": to_fstar}
+    res["time_to_tol_1e-6"] = to_tol
     # the same split-precision sweeps with every QR on the Householder route (the paper's plain
     # form; cpqr_options.qr_route), against the default guarded Gram route
     routes = {}
@@ -345,7 +390,53 @@ def extras(args, prob, X, dev, b):
             routes[name] = {"ms_per_sweep": e0.elapsed_time(e1) / 20, "fit_after_25": float(f[-1]) if len(f) else None,
                             "qr_fallbacks": int(d.stats().qr_fallbacks)}
     res["qr_routes"] = routes
+    res["other_workloads"] = other_workloads(b, dev)
     return res
+
+
+def other_workloads(b, dev):
+    """ms per sweep of the other named workloads (after warm-up sweeps, CUDA events), and the
+    restructured / standard TTM flop ratio over the first three sweeps and over 50."""
+    import torch
+    from paper_2503_18759_gb300 import inputs
+    out = {}
+    plans = [("cube60_r5_f64", b.PREC_FP64, b.TREE_STANDARD, b.EXTRAP_NONE, 50),
+             ("hyper128_r24_c08", b.PREC_SPLIT_BF16, b.TREE_RESTRUCTURED, b.EXTRAP_PAPER, 30),
+             ("order5_48_r16", b.PREC_SPLIT_BF16, b.TREE_RESTRUCTURED, b.EXTRAP_PAPER, 30),
+             ("order5_48_r16", b.PREC_SPLIT_BF16, b.TREE_STANDARD, b.EXTRAP_PAPER, 30)]
+    for name, prec, tree, ex, sweeps in plans:
+        cfg = dict(inputs.WORKLOADS[name])
+        if cfg.get("dtype") == np.float64:
+            prob = inputs.workload(name, seed=0)
+            X = torch.from_numpy(prob.X).to(dev)
+            x64 = True
+        else:
+            prob = inputs.make_problem_device(name, cfg.pop("dims"), cfg.pop("R"), seed=0, c=cfg.get("c"),
+                                              eta=cfg.get("eta", 0.0), device=str(dev))
+            X, x64 = prob.X, False
+        o = b.make_options(tree=tree, prec=prec, extrap=ex)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with b.Decomposition(prob.dims, prob.R, X.data_ptr(), x64, prob.A0, o) as d:
+            d.sweep(5)
+            torch.cuda.synchronize()
+            e0.record()
+            f = d.sweep(sweeps)
+            e1.record()
+            torch.cuda.synchronize()
+            st = d.stats()
+        tname = {b.TREE_STANDARD: "standard", b.TREE_RESTRUCTURED: "restructured"}[tree]
+        key = f"{name}_{tname}"
+        out[key] = {"ms_per_sweep": e0.elapsed_time(e1) / sweeps, "sweeps_timed": sweeps,
+                    "precision": "fp64" if prec == b.PREC_FP64 else "split", "fit_last": float(f[-1]),
+                    "ttm_flops_per_sweep_avg": st.ttm_flops / (5 + sweeps)}
+        del X
+    for name in ("order5_48_r16", "hyper128_r24_c08"):
+        dims = inputs.WORKLOADS[name]["dims"]
+        R = inputs.WORKLOADS[name]["R"]
+        fl = {t: [b.cp_als_qr_schedule(dims, R, t, k)[1] for k in (3, 50)] for t in (b.TREE_STANDARD, b.TREE_RESTRUCTURED)}
+        out[f"{name}_ttm_flop_ratio"] = {"first_3_sweeps": fl[b.TREE_RESTRUCTURED][0] / fl[b.TREE_STANDARD][0],
+                                         "first_50_sweeps": fl[b.TREE_RESTRUCTURED][1] / fl[b.TREE_STANDARD][1]}
+    return out
 
 
 def run_kernel(args):
@@ -403,11 +494,43 @@ def run_kernel(args):
             "note": "CUDA events around whole entry-point calls (their own allocations and copies included)"}
 
 
+_ORACLE_SWEEP = """
+import json, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+from oracle import cpqr_oracle as o
+from paper_2503_18759_gb300 import inputs
+prob = inputs.workload({w!r}, seed=0)
+stamps = [time.perf_counter()]
+o.cp_als_qr(prob.X, prob.R, prob.A0, tree=o.TREE_RESTRUCTURED, extrapolate=True, max_sweeps={n},
+            on_sweep=lambda k, f: stamps.append(time.perf_counter()))
+print(json.dumps(list(np.diff(stamps))))
+"""
+
+
+def _oracle_sweeps_subprocess(threads, sweeps):
+    """Oracle sweep times in a fresh process whose BLAS uses `threads` threads."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[k] = str(threads)
+    code = _ORACLE_SWEEP.format(root=ROOT, w=WORKLOAD, n=sweeps)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        return None
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
 def cpu_baseline(prob):
+    """The oracle as it stands on the host cores: all cores (BLAS threads) and one core."""
+    cores = os.cpu_count()
     from oracle import cpqr_oracle as o
-    t = oracle_sweep_times(prob, o.TREE_RESTRUCTURED, 4)
-    return {"value": float(np.mean(t[1:])), "unit": "s/sweep", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": "3 full-size FP64 oracle sweeps (400^3, R=32) after its first sweep, numpy/BLAS on all host cores"}
+    t_all = oracle_sweep_times(prob, o.TREE_RESTRUCTURED, 4)
+    t_one = _oracle_sweeps_subprocess(1, 2)
+    one = {"value": float(np.mean(t_one[1:])), "unit": "s/sweep", "cores": 1} if t_one else None
+    return {"value": float(np.mean(t_all[1:])), "unit": "s/sweep", "cores": cores, "kind": "oracle",
+            "sample": "3 full-size FP64 oracle sweeps (400^3, R=32) after its first sweep, numpy/BLAS on all host "
+                      "cores; one_core: 1 sweep after the first with every BLAS limited to one thread",
+            "one_core": one}
 
 
 def main():

@@ -137,7 +137,8 @@ void cp_als_qr_default_options(cpqr_options* opt);
  * N host pointers to I_n x R FP64 row-major; NULL draws N(0,1) from opt->seed), their QRs
  * with positive diagonal, ||X||^2, and, for CPQR_PREC_SPLIT_BF16, the bf16 hi/lo split of X
  * (one pass over X).  opt NULL = defaults.  stream: cudaStream_t or NULL.
- * On failure *out is NULL and nothing is leaked. */
+ * A non-finite entry in A0 or in X returns CPQR_ENONFINITE, a zero column of A0 (no QR)
+ * CPQR_ESINGULAR, X = 0 CPQR_EINVAL.  On failure *out is NULL and nothing is leaked. */
 cpqr_status cp_als_qr_init(cpqr_ctx** out, int32_t N, const int64_t* dims, int32_t R,
                            const void* X_dev, int32_t x_is_fp64, const double* const* A0_host,
                            const cpqr_options* opt, void* stream);
@@ -212,7 +213,10 @@ cpqr_status cpqr_ttm(const void* T_dev, int32_t nd, const int64_t* tdims, int32_
                      const void* Q_dev, int32_t R, void* out_dev, int32_t dtype, void* stream);
 
 /* Compact QR of an M x R FP64 matrix (row-major, device) by Householder reflections with
- * diag(R) > 0 (Alg. 2 line 10): Q_dev (M x R) and R_dev (R x R) receive the factors. */
+ * diag(R) > 0 (Alg. 2 line 10): Q_dev (M x R) and R_dev (R x R) receive the factors.  Returns
+ * CPQR_ESINGULAR for a zero column (exactly zero Householder norm) and CPQR_ETIMEOUT if a bounded
+ * wait of the cluster kernel gave up; Q and R then hold partial results.  Synchronises the
+ * stream. */
 cpqr_status cpqr_house_qr(const double* A_dev, int64_t M, int32_t R, double* Q_dev,
                           double* R_dev, void* stream);
 
@@ -224,7 +228,11 @@ cpqr_status cpqr_house_qr(const double* A_dev, int64_t M, int32_t R, double* Q_d
  * doubles (8 MiB) that every GPU loading the library holds until the process exits.
  * - M * R must not exceed CPQR_NOALLOC_QR_MAX_ELEMS; larger problems return CPQR_EINVAL.
  * - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
- *   that device current; make that first call before any stream capture.
+ *   that device current; make that first call before any stream capture.  The address is kept
+ *   per device together with the context it belongs to: after cudaDeviceReset the next call
+ *   (in the new context) looks it up again, so make that call before any capture too.
+ * - Returns CPQR_ETIMEOUT if a bounded wait of the cluster kernel gave up and CPQR_ESINGULAR if
+ *   a column became zero (Q and R then hold partial results).
  * - All calls share the one array and it keeps the last call's contents: calls whose GPU work
  *   overlaps (other streams, other host threads) race and must be serialised by the caller.
  * Synchronises the stream before returning. */
@@ -236,7 +244,8 @@ cpqr_status cpqr_house_qr_noalloc(const double* A_dev, int64_t M, int32_t R, dou
  * matrices (Alg. 2 lines 3-4), rows (r_1, ..., r_m) with r_m fastest: Rs_dev holds the m
  * triangles back to back (device, FP64).  Q0_dev (R^m x R) and R0_dev (R x R) receive the
  * factors, diag(R0) > 0, by the guarded Gram route (see cpqr_prec) for m >= 2, whose fallback is
- * the Householder staircase QR (nested for m >= 3). */
+ * the Householder staircase QR (nested for m >= 3).  CPQR_ESINGULAR / CPQR_ETIMEOUT as for
+ * cpqr_house_qr.  Synchronises the stream. */
 cpqr_status cpqr_krp_qr(const double* Rs_dev, int32_t m, int32_t R, double* Q0_dev,
                         double* R0_dev, void* stream);
 
@@ -286,6 +295,14 @@ cpqr_status cp_als_qr_checkpoint(cpqr_ctx* ctx);
 cpqr_status cp_als_qr_rollback(cpqr_ctx* ctx);
 cpqr_status cp_als_qr_commit(cpqr_ctx* ctx);
 cpqr_status cp_als_qr_sweep_beta(cpqr_ctx* ctx, double beta, double* fit_host);
+
+/* Failure-detection test hook (no counterpart in the paper).  The next tensor-core TTM of a
+ * split-precision context issues no tile loads and its pipeline waits give up after limit_ns
+ * nanoseconds: the kernel raises CPQR_DEV_TIMEOUT, every warp leaves its loop, nothing is left
+ * in flight and tensor memory is freed, so the GPU context stays usable.  The sweep that ran it
+ * returns CPQR_ETIMEOUT, which is sticky: every later call on the context returns it, and
+ * cp_als_qr_destroy still releases everything.  CPQR_EUNSUPPORTED for an FP64 context. */
+cpqr_status cp_als_qr_test_wait_timeout(cpqr_ctx* ctx, uint64_t limit_ns);
 
 /* Fit and beta history of a context: up to cap sweeps into fits_host / betas_host (either may
  * be NULL); *n = sweeps done.  rule_beta / activated (may be NULL): the Section 4.2 rule state. */

@@ -22,7 +22,7 @@ EXTRAP_NONE, EXTRAP_PAPER, EXTRAP_FIXED, EXTRAP_LEARNED = 0, 1, 2, 3
 QR_GRAM, QR_HOUSEHOLDER = 0, 1
 TTM_F64, TTM_F32, TTM_F32_IN_F64, TTM_SPLIT_BF16 = 0, 1, 2, 3
 
-OK, ENOTCONV = 0, 7
+OK, EINVAL, ENOMEM, ECUDA, ESINGULAR, ENONFINITE, ETIMEOUT, ENOTCONV, EUNSUPPORTED = 0, 1, 2, 3, 4, 5, 6, 7, 8
 
 
 class CpqrError(RuntimeError):
@@ -91,6 +91,7 @@ def lib() -> C.CDLL:
     L.cp_als_qr_rollback.argtypes = [vp]
     L.cp_als_qr_commit.argtypes = [vp]
     L.cp_als_qr_sweep_beta.argtypes = [vp, dbl, P(dbl)]
+    L.cp_als_qr_test_wait_timeout.argtypes = [vp, C.c_uint64]
     L.cp_als_qr_history.argtypes = [vp, P(dbl), P(dbl), i32, P(i32), P(dbl), P(i32)]
     L.cpqr_house_qr.argtypes = [vp, i64, i32, vp, vp, vp]
     L.cpqr_krp_qr.argtypes = [vp, i32, i32, vp, vp, vp]
@@ -98,7 +99,7 @@ def lib() -> C.CDLL:
     for name in ("cp_als_qr_init", "cp_als_qr_sweep", "cp_als_qr_fit", "cp_als_qr_get", "cp_als_qr_stats",
                  "cp_als_qr_fit_exact", "cp_als_qr_set_timing", "cp_als_qr_schedule", "cp_als_qr_run_host",
                  "cpqr_mlp_features", "cpqr_mlp_forward", "cpqr_mlp_grad", "cpqr_mlp_adam", "cp_als_qr_checkpoint",
-                 "cp_als_qr_rollback", "cp_als_qr_commit", "cp_als_qr_sweep_beta", "cp_als_qr_history", "cpqr_ttm", "cpqr_house_qr", "cpqr_krp_qr", "cpqr_house_qr_noalloc"):
+                 "cp_als_qr_rollback", "cp_als_qr_commit", "cp_als_qr_sweep_beta", "cp_als_qr_test_wait_timeout", "cp_als_qr_history", "cpqr_ttm", "cpqr_house_qr", "cpqr_krp_qr", "cpqr_house_qr_noalloc"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -276,6 +277,10 @@ def cp_als_qr_sweep_beta(ctx, beta: float) -> float:
     f = C.c_double()
     _check(lib().cp_als_qr_sweep_beta(ctx, float(beta), C.byref(f)), "cp_als_qr_sweep_beta")
     return f.value
+
+
+def cp_als_qr_test_wait_timeout(ctx, limit_ns: int) -> None:
+    _check(lib().cp_als_qr_test_wait_timeout(ctx, int(limit_ns)), "cp_als_qr_test_wait_timeout")
 
 
 def cp_als_qr_history(ctx, cap: int = 100000):

@@ -210,6 +210,10 @@ struct cpqr_ctx {
   double last_beta = 0.0;
   int64_t sweeps = 0;
   int64_t proposals = 0, accepted = 0;
+  // failure-detection test hook (cp_als_qr_test_wait_timeout): the next tensor-core TTM issues no
+  // tile loads and its pipeline waits give up after test_wait_ns
+  bool test_skip_next_ttm = false;
+  unsigned long long test_wait_ns = 0;
 
   ~cpqr_ctx() {
     if (st) cudaStreamSynchronize(st);
@@ -406,8 +410,10 @@ cpqr_status run_ttm(cpqr_ctx* ctx, const Op& op) {
       // Gram route, whose side-stream work is row kernels plus a fallback that returns at once,
       // gives the TTM the whole GPU.
       const int reserve = (ctx->z_pending && !ctx->gram) ? qr_cluster_sms() : 0;
+      const bool skip = ctx->test_skip_next_ttm;
+      ctx->test_skip_next_ttm = false;
       CK(launch_ttm_tc(shi, slo, ctx->Qt[k], ctx->Rp, ctx->Kp[k], of, P, K, S, R, ctx->dstatus, st, reserve, ohi,
-                       olo));
+                       olo, skip ? ctx->test_wait_ns : 0, skip ? 1 : 0));
     } else {
       if (!sb.has_f32) return fail(ctx, CPQR_EINVAL);  // not produced for a CUDA-core consumer
       float* o32 = of;
@@ -1232,6 +1238,8 @@ cpqr_status cp_als_qr_init(cpqr_ctx** out, int32_t N, const int64_t* dims, int32
     host.resize(dims[n] * R);
     if (A0_host && A0_host[n]) {
       std::memcpy(host.data(), A0_host[n], host.size() * sizeof(double));
+      for (double v : host)
+        if (!std::isfinite(v)) return CPQR_ENONFINITE;
     } else {
       for (size_t i = 0; i < host.size(); ++i) {  // Box-Muller on SplitMix64
         double u1 = ((splitmix64(seed) >> 11) + 0.5) * (1.0 / 9007199254740992.0);
@@ -1267,7 +1275,8 @@ cpqr_status cp_als_qr_init(cpqr_ctx** out, int32_t N, const int64_t* dims, int32
     std::memcpy(&ds, ctx->h_pinned + 2, sizeof(ds));
     if (ds & CPQR_DEV_SINGULAR) return CPQR_ESINGULAR;
   }
-  if (!(ctx->normX2 > 0.0) || !std::isfinite(ctx->normX2)) return CPQR_EINVAL;
+  if (!std::isfinite(ctx->normX2)) return CPQR_ENONFINITE;
+  if (!(ctx->normX2 > 0.0)) return CPQR_EINVAL;
 
   if (ctx->extrap == CPQR_EXTRAP_LEARNED && opt.mlp_weights) {
     CK(ctx->alloc(&ctx->mlp_params, CPQR_MLP_NPARAMS));
@@ -1436,6 +1445,15 @@ cpqr_status cp_als_qr_commit(cpqr_ctx* ctx) {
   return CPQR_OK;
 }
 
+cpqr_status cp_als_qr_test_wait_timeout(cpqr_ctx* ctx, uint64_t limit_ns) {
+  if (!ctx || limit_ns == 0) return CPQR_EINVAL;
+  if (ctx->err != CPQR_OK) return ctx->err;
+  if (ctx->prec != CPQR_PREC_SPLIT_BF16) return CPQR_EUNSUPPORTED;
+  ctx->test_skip_next_ttm = true;
+  ctx->test_wait_ns = limit_ns;
+  return CPQR_OK;
+}
+
 cpqr_status cp_als_qr_sweep_beta(cpqr_ctx* ctx, double beta, double* fit_host) {
   if (!ctx || !(beta >= 0.0) || !std::isfinite(beta)) return CPQR_EINVAL;
   if (ctx->err != CPQR_OK) return ctx->err;
@@ -1586,7 +1604,7 @@ cpqr_status cpqr_ttm(const void* T_dev, int32_t nd, const int64_t* tdims, int32_
       if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, ds, 4, cudaMemcpyDeviceToHost, st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(st);
       cudaFree(xh); cudaFree(xl); cudaFree(qt); cudaFree(ds);
-      if (e == cudaSuccess && (hs & CPQR_DEV_TIMEOUT)) return CPQR_ETIMEOUT;
+      if (e == cudaSuccess && hs) return status_of_device_word(hs);
       break;
     }
     default: return CPQR_EINVAL;
@@ -1605,10 +1623,12 @@ cpqr_status cpqr_house_qr(const double* A_dev, int64_t M, int32_t R, double* Q_d
   }
   cudaError_t e = cudaMemsetAsync(ds, 0, 4, st);
   if (e == cudaSuccess) e = launch_house_qr(A_dev, M, R, Q_dev, R_dev, work, ds, st);
+  unsigned int hs = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, ds, 4, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cudaFree(work);
   cudaFree(ds);
-  return e == cudaSuccess ? CPQR_OK : CPQR_ECUDA;
+  return e == cudaSuccess ? status_of_device_word(hs) : CPQR_ECUDA;
 }
 
 cpqr_status cpqr_krp_qr(const double* Rs_dev, int32_t m, int32_t R, double* Q0_dev, double* R0_dev, void* stream) {
@@ -1647,9 +1667,11 @@ cpqr_status cpqr_krp_qr(const double* Rs_dev, int32_t m, int32_t R, double* Q0_d
     if (m >= 2) e = launch_krp_qr_gram(plan, tri, m, Q0_dev, R0_dev, gwork, work, ds, st);
     else e = launch_krp_qr(plan, tri, Q0_dev, R0_dev, work, ds, st);
   }
+  unsigned int hs = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, ds, 4, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cudaFree(dperm); cudaFree(work); cudaFree(ds); cudaFree(gwork);
-  return e == cudaSuccess ? CPQR_OK : CPQR_ECUDA;
+  return e == cudaSuccess ? status_of_device_word(hs) : CPQR_ECUDA;
 }
 
 }  // extern "C"

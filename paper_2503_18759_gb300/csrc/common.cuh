@@ -4,6 +4,8 @@
 #include <cuda_bf16.h>
 #include <cstdint>
 
+#include "cpqr.h"
+
 #define CPQR_MAXR 32
 #define CPQR_MAXN 5
 
@@ -13,6 +15,15 @@
 #define CPQR_DEV_TIMEOUT 4u
 
 namespace cpqr {
+
+// Library status of a device status word: a timed-out wait first (its results are partial), then
+// a zero pivot or norm, then a non-finite value.
+inline cpqr_status status_of_device_word(unsigned int w) {
+  if (w & CPQR_DEV_TIMEOUT) return CPQR_ETIMEOUT;
+  if (w & CPQR_DEV_SINGULAR) return CPQR_ESINGULAR;
+  if (w & CPQR_DEV_NONFINITE) return CPQR_ENONFINITE;
+  return CPQR_OK;
+}
 
 // Programmatic dependent launch: the kernel may be scheduled while the previous kernel of the
 // stream drains (its launch latency then overlaps that kernel's tail), so it must call
@@ -68,7 +79,8 @@ cudaError_t launch_split_x(const float* X, __nv_bfloat16* Xhi, __nv_bfloat16* Xl
 cudaError_t launch_ttm_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo, const __nv_bfloat16* Qt,
                           int Rp, int64_t Kp, float* out, int64_t P, int64_t K, int64_t S, int R,
                           unsigned int* dev_status, cudaStream_t st, int reserve_sms = 0,
-                          __nv_bfloat16* out_hi = nullptr, __nv_bfloat16* out_lo = nullptr);
+                          __nv_bfloat16* out_hi = nullptr, __nv_bfloat16* out_lo = nullptr,
+                          unsigned long long wait_ns = 0, int skip_x_loads = 0);
 bool ttm_tc_supported(int64_t P, int64_t K, int64_t S, int R);
 
 // ----- small FP64 kernels (smallqr.cu) -----

@@ -22,20 +22,44 @@ static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
+// Per device: the array's device address and the context it was looked up in.  A device reset
+// (cudaDeviceReset) destroys that context and unloads the module; the next call, made in the new
+// context, then looks the address up again instead of using a stale one.
 double* g_scratch_addr[kMaxDevices] = {};
+void* g_scratch_ctx[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device, looked up once per device.
+typedef int (*cu_ctx_get_current_fn)(void**);  // CUresult cuCtxGetCurrent(CUcontext*)
+
+// The current context's handle through the driver entry point (no link-time driver dependency).
+void* current_context() {
+  static cu_ctx_get_current_fn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<cu_ctx_get_current_fn>(f);
+  }();
+  void* c = nullptr;
+  if (!fn || fn(&c) != 0) return nullptr;
+  return c;
+}
+
+// Device address of the scratch array on the current device, looked up once per device and
+// context.  The lookup loads the library's module into the context if it is not loaded yet.
 cudaError_t scratch_for_current_device(double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  void* ctx = current_context();  // null before the runtime has made a context current
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_addr[dev]) {
+  if (!g_scratch_addr[dev] || !ctx || ctx != g_scratch_ctx[dev]) {
     void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);  // makes the primary context current if needed
     if (e != cudaSuccess) return e;
     g_scratch_addr[dev] = static_cast<double*>(p);
+    g_scratch_ctx[dev] = current_context();
   }
   *out = g_scratch_addr[dev];
   return cudaSuccess;
@@ -55,5 +79,9 @@ extern "C" cpqr_status cpqr_house_qr_noalloc(const double* A_dev, int64_t M, int
   // the status word must start at zero; the rows are fully written by the kernel before use
   if (cudaMemsetAsync(status, 0, sizeof(unsigned int), st) != cudaSuccess) return CPQR_ECUDA;
   if (cpqr::launch_house_qr(A_dev, M, R, Q_dev, R_dev, work, status, st) != cudaSuccess) return CPQR_ECUDA;
-  return cudaStreamSynchronize(st) == cudaSuccess ? CPQR_OK : CPQR_ECUDA;
+  // the kernel's status word: a timed-out cluster wait or a zero column (partial results)
+  unsigned int hs = 0;
+  if (cudaMemcpyAsync(&hs, status, sizeof(hs), cudaMemcpyDeviceToHost, st) != cudaSuccess) return CPQR_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return CPQR_ECUDA;
+  return cpqr::status_of_device_word(hs);
 }

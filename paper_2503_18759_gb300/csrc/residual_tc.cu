@@ -5,9 +5,8 @@
 // tile of 128 rows is K = W A_last^T with the Khatri-Rao weights W[row, r] =
 // prod_{n<N-1} A_n[i_n, r] (lambda folded into A_0), a 128 x R by R x I_last product.  It runs
 // as tcgen05 kind::tf32 MMAs with FP32 accumulation in tensor memory, each operand split into a
-// TF32 high part (the FP32 value with its 13 low mantissa bits cleared) and the FP32 remainder
-// (rounded to TF32 by the MMA): W A^T ~ Wh Ah^T + Wh Al^T + Wl Ah^T, relative error ~2^-20 per
-// product against ~1e-3 residuals.  The residual (x - k)^2 is summed in FP32 per 32 columns
+// TF32 high part and a TF32 remainder, both rounded to nearest: W A^T ~ Wh Ah^T + Wh Al^T +
+// Wl Ah^T, relative error ~2^-21 per product, of either sign, against ~1e-3 residuals.  The residual (x - k)^2 is summed in FP32 per 32 columns
 // and in FP64 across them.
 //
 // CTA roles (320 threads, one CTA per SM): warp 0 streams X tiles (128 rows x 32 columns,
@@ -68,9 +67,19 @@ __device__ __forceinline__ uint32_t sw128(int row, int q) {
   return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((q ^ (row & 7)) << 4));
 }
 
+__device__ __forceinline__ float tf32_rna(float v) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+  return __uint_as_float(r);
+}
+
+// Both parts rounded to the nearest TF32 value: the remainder v - hi - lo and the dropped lo * lo
+// term then take either sign.  Clearing the low bits instead (and letting the MMA truncate the
+// remainder) makes every split product low by a few 2^-22, which a fit taken away from a
+// least-squares optimum (eq. 19's scaled fixed point) sees to first order.
 __device__ __forceinline__ void split_tf32(float v, float& hi, float& lo) {
-  hi = __uint_as_float(__float_as_uint(v) & 0xffffe000u);
-  lo = v - hi;  // exact
+  hi = tf32_rna(v);
+  lo = tf32_rna(v - hi);  // v - hi is exact
 }
 
 // Lane 0 waits, the warp learns the outcome (keeps .sync.aligned instructions convergent).
@@ -181,13 +190,20 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
         fence_after();
         const uint32_t d = tmem + (uint32_t)(b * RT_MAXW);
         const uint32_t wh = sW + (uint32_t)(2 * b) * RT_WBYTES, wl = wh + RT_WBYTES;
+        // K = 32 as four steps of 8 TF32 (32 bytes).  The small correction products go first: the
+        // accumulator truncates each sum toward zero relative to its current size, so only the four
+        // hi * hi steps at the end truncate at the full size of the model entry
 #pragma unroll
-        for (int ks = 0; ks < 4; ++ks) {  // K = 32 as four steps of 8 TF32 (32 bytes)
+        for (int ks = 0; ks < 4; ++ks) {
           const uint64_t ah = smem_desc(wh + ks * 32, 16, 1024), al = smem_desc(wl + ks * 32, 16, 1024);
           const uint64_t bh = smem_desc(sB + ks * 32, 16, 1024), bl = smem_desc(sB + bbytes + ks * 32, 16, 1024);
-          mma_tf32(d, ah, bh, idesc, ks > 0 ? 1u : 0u);
-          mma_tf32(d, ah, bl, idesc, 1u);
+          mma_tf32(d, ah, bl, idesc, ks > 0 ? 1u : 0u);
           mma_tf32(d, al, bh, idesc, 1u);
+        }
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks) {
+          const uint64_t ah = smem_desc(wh + ks * 32, 16, 1024), bh = smem_desc(sB + ks * 32, 16, 1024);
+          mma_tf32(d, ah, bh, idesc, 1u);
         }
         mma_commit(smem_u32(&tail->mdone[b]));
       }

@@ -51,7 +51,7 @@ static __device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
 // Bounded wait for the phase with the given parity: false on timeout (which also raises the
 // abort flag) or, with honor_abort, as soon as another role has raised the abort flag.
 static __device__ bool mbar_wait(uint32_t a, uint32_t parity, int* abort_flag, unsigned int* status,
-                                 bool honor_abort = true) {
+                                 bool honor_abort = true, unsigned long long limit_ns = kTimeoutNs) {
   unsigned long long t0 = 0;
   for (int it = 0;; ++it) {
     if (mbar_try(a, parity)) return true;
@@ -60,7 +60,7 @@ static __device__ bool mbar_wait(uint32_t a, uint32_t parity, int* abort_flag, u
       const unsigned long long now = gtimer();
       if (t0 == 0) {
         t0 = now;
-      } else if (now - t0 > kTimeoutNs) {
+      } else if (now - t0 > limit_ns) {
         atomicOr(status, CPQR_DEV_TIMEOUT);
         *(volatile int*)abort_flag = 1;
         return false;

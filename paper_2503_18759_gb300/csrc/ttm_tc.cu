@@ -92,9 +92,10 @@ cudaError_t launch_split_q(const double* Q, int64_t K, int R, __nv_bfloat16* Qt,
 // Rows beyond S or P are zero-filled by TMA and masked in the epilogue.  Q^T
 // (bf16 hi/lo, K-major, zero padded to Rp x Kp) stays resident in shared
 // memory.  Per 16-deep K step four MMAs accumulate hi*hi + hi*lo + lo*hi + lo*lo
-// into an FP32 accumulator in tensor memory (M = 128, N = Rp): the products are
-// exact, so the error is that of the operands' two-term bf16 representations
-// (~2^-17 each); the tensor pipe is far from busy at these ranks.  The epilogue writes
+// into FP32 accumulators in tensor memory (M = 128, N = Rp; hi*hi of even and odd K
+// blocks and the corrections apart, see TC_NACC): the products are exact, so the
+// error is that of the operands' two-term bf16 representations (~2^-17 each) plus
+// the accumulators' truncation; the tensor pipe is far from busy at these ranks.  The epilogue writes
 // the FP32 result and, when asked, its own bf16 hi/lo split for the next TTM.
 //
 // Warp roles (192 threads): warps 0-3 epilogue (tensor-memory lanes 32w..32w+31),
@@ -112,7 +113,15 @@ constexpr int TC_NST = 4;                   // A pipeline stages
 constexpr int TC_HALF_BYTES = 64 * 64 * 2;  // one 64 x 64 bf16 box
 constexpr int TC_STAGE_BYTES = 4 * TC_HALF_BYTES;  // hi h0, hi h1, lo h0, lo h1
 constexpr int TC_MAX_KB = 8;                // K <= 512
-constexpr int TC_TMEM_COLS = 64;            // two accumulators of up to 32 columns
+// Tensor-core FP32 accumulation truncates toward zero: every MMA into an accumulator lowers it by
+// ~2^-26 relative on average (measured on GB300: mean relative error -1.3e-6 at K = 400 with one
+// accumulator for all four products).  So each tile has three accumulators of 32 columns: hi*hi of
+// the even and of the odd 64-deep K blocks, and the three small correction products; the epilogue
+// adds them in FP32 with rounding to nearest.  A main accumulator then takes an eighth of the MMAs,
+// and the corrections' truncation is relative to their own ~2^-8 smaller size.
+constexpr int TC_NACC = 3;
+constexpr int TC_ACC_COLS = TC_NACC * 32;   // per tile buffer
+constexpr int TC_TMEM_COLS = 256;           // two tile buffers (192 columns), rounded to a power of 2
 
 struct TcParams {
   int64_t P, K, S;
@@ -124,6 +133,8 @@ struct TcParams {
   __nv_bfloat16* out_hi;  // optional split copy of out (hi + lo = out to ~2^-16)
   __nv_bfloat16* out_lo;
   unsigned int* status;
+  unsigned long long wait_ns;  // limit of the pipeline waits (drain waits keep kTimeoutNs)
+  int skip_x_loads;            // failure-detection test: issue no tile loads, so the MMA wait runs out
 };
 
 struct TcSmemTail {
@@ -222,9 +233,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           }
         }
         for (int kb = 0; kb < p.nkb; ++kb) {
-          if (!mbar_wait(smem_u32(&tail->empty[stage]), phase ^ 1u, &tail->abort_flag, p.status)) {
+          if (!mbar_wait(smem_u32(&tail->empty[stage]), phase ^ 1u, &tail->abort_flag, p.status, true, p.wait_ns)) {
             ok = false;
             break;
+          }
+          if (p.skip_x_loads) {  // nothing arrives on full[stage]: the MMA issuer's wait runs out
+            if (++stage == TC_NST) {
+              stage = 0;
+              phase ^= 1u;
+            }
+            continue;
           }
           const uint32_t fb = smem_u32(&tail->full[stage]);
           const uint32_t dst = sA + stage * TC_STAGE_BYTES;
@@ -253,18 +271,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       // F32 accumulate, bf16 A and B, B K-major, A MN-major (bit 15) or K-major
       const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (KM ? 0u : (1u << 15)) |
                              ((uint32_t)(p.Rp >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-      bool ok = mbar_wait(smem_u32(&tail->bfull), 0, &tail->abort_flag, p.status);
+      bool ok = mbar_wait(smem_u32(&tail->bfull), 0, &tail->abort_flag, p.status, true, p.wait_ns);
       fence_after();
       int stage = 0;
       uint32_t phase = 0;
       for (int64_t lt = 0; lt < ntile_local && ok; ++lt) {
         const int acc = (int)(lt & 1);
         const uint32_t use = (uint32_t)(lt >> 1);
-        if (!mbar_wait(smem_u32(&tail->tempty[acc]), (use & 1u) ^ 1u, &tail->abort_flag, p.status)) break;
+        if (!mbar_wait(smem_u32(&tail->tempty[acc]), (use & 1u) ^ 1u, &tail->abort_flag, p.status, true, p.wait_ns))
+          break;
         fence_after();
-        const uint32_t d = tmem + (uint32_t)(acc * 32);
+        const uint32_t d0 = tmem + (uint32_t)(acc * TC_ACC_COLS);
+        const uint32_t dc = d0 + 64;  // correction products
         for (int kb = 0; kb < p.nkb; ++kb) {
-          if (!mbar_wait(smem_u32(&tail->full[stage]), phase, &tail->abort_flag, p.status)) {
+          const uint32_t dm = d0 + (uint32_t)((kb & 1) * 32);  // hi * hi of even / odd K blocks
+          if (!mbar_wait(smem_u32(&tail->full[stage]), phase, &tail->abort_flag, p.status, true, p.wait_ns)) {
             ok = false;
             break;
           }
@@ -281,10 +302,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const uint64_t al = KM ? smem_desc(a_lo + ks * 32, 16, 1024) : smem_desc(a_lo + ks * 2048, TC_HALF_BYTES, 1024);
             const uint64_t bh = smem_desc(b_hi + ks * 32, 16, 1024);
             const uint64_t bl = smem_desc(b_lo + ks * 32, 16, 1024);
-            mma_bf16(d, ah, bh, idesc, (kb | ks) != 0 ? 1u : 0u);
-            mma_bf16(d, ah, bl, idesc, 1u);
-            mma_bf16(d, al, bh, idesc, 1u);
-            mma_bf16(d, al, bl, idesc, 1u);
+            mma_bf16(dm, ah, bh, idesc, (kb >= 2 || ks != 0) ? 1u : 0u);
+            mma_bf16(dc, ah, bl, idesc, (kb | ks) != 0 ? 1u : 0u);
+            mma_bf16(dc, al, bh, idesc, 1u);
+            mma_bf16(dc, al, bl, idesc, 1u);
           }
           mma_commit(smem_u32(&tail->empty[stage]));
           if (++stage == TC_NST) {
@@ -305,12 +326,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     for (int64_t lt = 0; lt < ntile_local; ++lt) {
       const int acc = (int)(lt & 1);
       const uint32_t use = (uint32_t)(lt >> 1);
-      if (!mbar_wait(smem_u32(&tail->tfull[acc]), use & 1u, &tail->abort_flag, p.status)) break;
+      if (!mbar_wait(smem_u32(&tail->tfull[acc]), use & 1u, &tail->abort_flag, p.status, true, p.wait_ns)) break;
       fence_after();
-      float v[32];
-      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc * 32);
+      float v[32], w[32];
+#pragma unroll
+      for (int r = 0; r < 32; ++r) v[r] = w[r] = 0.f;  // columns past Rp = 16 stay zero
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc * TC_ACC_COLS);
+      // (even + odd) + corrections, each add rounded to nearest; a K of one block has no odd part
       if (p.Rp == 32) tmem_ld32(taddr, v);
       else tmem_ld16(taddr, v);
+      if (p.nkb > 1) {
+        if (p.Rp == 32) tmem_ld32(taddr + 32, w);
+        else tmem_ld16(taddr + 32, w);
+#pragma unroll
+        for (int r = 0; r < 32; ++r) v[r] += w[r];
+      }
+      if (p.Rp == 32) tmem_ld32(taddr + 64, w);
+      else tmem_ld16(taddr + 64, w);
+#pragma unroll
+      for (int r = 0; r < 32; ++r) v[r] += w[r];
       fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&tail->tempty[acc]));
@@ -375,7 +409,8 @@ bool ttm_tc_supported(int64_t P, int64_t K, int64_t S, int R) {
 
 cudaError_t launch_ttm_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo, const __nv_bfloat16* Qt, int Rp,
                           int64_t Kp, float* out, int64_t P, int64_t K, int64_t S, int R, unsigned int* dev_status,
-                          cudaStream_t st, int reserve_sms, __nv_bfloat16* out_hi, __nv_bfloat16* out_lo) {
+                          cudaStream_t st, int reserve_sms, __nv_bfloat16* out_hi, __nv_bfloat16* out_lo,
+                          unsigned long long wait_ns, int skip_x_loads) {
   if (!ttm_tc_supported(P, K, S, R) || (Rp != 16 && Rp != 32) || Rp < R || Kp < K || (Kp % 64) != 0)
     return cudaErrorNotSupported;
   if (((uintptr_t)Xhi & 15) || ((uintptr_t)Xlo & 15) || ((uintptr_t)Qt & 15)) return cudaErrorMisalignedAddress;
@@ -435,6 +470,8 @@ cudaError_t launch_ttm_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo, co
   prm.out_hi = out_hi;
   prm.out_lo = out_lo;
   prm.status = dev_status;
+  prm.wait_ns = wait_ns ? wait_ns : tc::kTimeoutNs;
+  prm.skip_x_loads = skip_x_loads;
   if (prm.nkb * 64 > Kp) return cudaErrorInvalidValue;
   const size_t smem = 1024 + (size_t)TC_NST * TC_STAGE_BYTES + (size_t)prm.nkb * 2 * Rp * 128 +
                       ((sizeof(TcSmemTail) + 15) / 16) * 16 + (km ? 4 * 32 * 33 * sizeof(float) : 0);

@@ -354,3 +354,112 @@ def test_krp_qr_gram_route_falls_back_on_ill_conditioned_products(delta):
     if delta > 0:
         Q0r, R0r = o.householder_qr(Z)
         assert np.allclose(Rg, R0r, atol=1e-12 * np.abs(R0r).max())
+
+
+CONVERGED_MIXED = [
+    ("br_c03", dict(c=0.3), b.EXTRAP_NONE, 0.0, 60),
+    ("bre_fixed_c05", dict(c=0.5), b.EXTRAP_FIXED, 0.01, 90),
+]
+
+
+@pytest.mark.parametrize("name,cfg,extrap,beta,sweeps", CONVERGED_MIXED, ids=[c[0] for c in CONVERGED_MIXED])
+def test_split_precision_final_fit_within_1e6_of_oracle(name, cfg, extrap, beta, sweeps):
+    """Mixed precision at its stated tolerance: on 96^3, R = 16 (FP32 tensor, noise 1e-3) both the
+    split path and the FP64 oracle run the restructured tree from the same start for enough
+    sweeps to converge (the oracle's last fit change is checked below 1e-10); the final fits,
+    each from an explicit residual of its own factors, agree to 1e-6 relative.  At a least-squares
+    optimum (beta = 0) the fit is stationary in the factors, so the split operands' ~2^-17 random
+    error enters it only to second order.  At eq. 19's scaled fixed point (beta > 0) a relative
+    scale error of the model moves the fit to first order: this case holds only because neither
+    the split TTMs nor the residual pass are biased (see the bias tests)."""
+    prob = inputs.make_problem(name, [96, 96, 96], 16, seed=7, eta=1e-3, dtype=np.float32, **cfg)
+    X = _dev(prob.X)
+    opts = b.make_options(tree=b.TREE_RESTRUCTURED, prec=b.PREC_SPLIT_BF16, extrap=extrap, beta_fixed=beta)
+    with b.Decomposition(prob.dims, prob.R, X.data_ptr(), False, prob.A0, opts) as d:
+        fits = d.sweep(sweeps)
+        fx = d.fit_exact()
+    kw = dict(extrapolate=False) if extrap == b.EXTRAP_NONE else dict(extrapolate=True, beta_fixed=beta)
+    ref = o.cp_als_qr(prob.X, prob.R, prob.A0, tree=o.TREE_RESTRUCTURED, max_sweeps=sweeps, **kw)
+    assert abs(ref.fits[-1] - ref.fits[-2]) < 1e-10
+    f_ref = o.fit_explicit(prob.X, ref.lam, ref.A)
+    assert abs(fx - f_ref) / f_ref <= 1e-6, (fx, f_ref)
+    assert abs(fits[-1] - f_ref) / f_ref <= 1e-6, (fits[-1], f_ref)
+    assert np.max(np.abs(fits - np.array(ref.fits))) <= 1e-4
+
+
+def test_eq18_plain_extrapolation_alpha_one_matches_oracle():
+    """alpha = 1 turns eq. 19 into eq. 18 (Q0^ = Q0 + beta (Q0 - Q0^{k-1})): FP64 path against the
+    oracle with the same alpha, fits and factor subspaces within 1e-10."""
+    prob = inputs.make_problem("eq18", [21, 19, 23], 5, seed=8, c=0.6, eta=1e-3, dtype=np.float64)
+    X = _dev(prob.X)
+    opts = b.make_options(tree=b.TREE_RESTRUCTURED, prec=b.PREC_FP64, extrap=b.EXTRAP_FIXED, beta_fixed=0.05,
+                          alpha=1.0)
+    with b.Decomposition(prob.dims, prob.R, X.data_ptr(), True, prob.A0, opts) as d:
+        fits = d.sweep(8)
+        A, lam, _, _ = d.factors()
+    ref = o.cp_als_qr(prob.X, prob.R, prob.A0, tree=o.TREE_RESTRUCTURED, extrapolate=True, beta_fixed=0.05,
+                      alpha=1.0, max_sweeps=8)
+    other = o.cp_als_qr(prob.X, prob.R, prob.A0, tree=o.TREE_RESTRUCTURED, extrapolate=True, beta_fixed=0.05,
+                        max_sweeps=8)
+    assert np.max(np.abs(fits - np.array(ref.fits))) <= 1e-10
+    assert np.max(np.abs(np.array(other.fits) - np.array(ref.fits))) > 1e-6  # alpha matters here
+    for n in range(3):
+        assert o.subspace_sine(A[n], ref.A[n]) <= 1e-10
+
+
+@pytest.mark.parametrize("prec", [b.PREC_FP64, b.PREC_SPLIT_BF16], ids=["fp64", "split"])
+def test_bre_with_beta_zero_is_br_bit_for_bit(prec):
+    """beta = 0 in eq. 19 leaves Q0 as it is: ALS-QR-BRE with a fixed beta of 0 runs the same
+    kernels on the same data as ALS-QR-BR, so fits and factors agree bit for bit."""
+    prob = inputs.make_problem("br0", [32, 24, 40], 6, seed=9, c=0.4, eta=1e-3, dtype=np.float32)
+    X = _dev(prob.X)
+    out = []
+    for ex in (b.EXTRAP_NONE, b.EXTRAP_FIXED):
+        opts = b.make_options(tree=b.TREE_RESTRUCTURED, prec=prec, extrap=ex, beta_fixed=0.0)
+        with b.Decomposition(prob.dims, prob.R, X.data_ptr(), False, prob.A0, opts) as d:
+            fits = np.array([d.sweep(1)[0] for _ in range(6)])
+            A, lam, _, _ = d.factors()
+        out.append((fits, A, lam))
+    assert np.array_equal(out[0][0], out[1][0])
+    for a0, a1 in zip(out[0][1], out[1][1]):
+        assert np.array_equal(a0, a1)
+
+
+def test_paper_rule_and_fixed_beta_follow_the_oracle():
+    """The Section 4.2 rule (beta switched on by the fit change, banded by the fit) against a
+    fixed beta from the second sweep, FP64 path, both against the oracle to 1e-10: the rule's
+    activation sweep and band match the oracle's, and the two controllers give different runs."""
+    prob = inputs.make_problem("rule", [26, 22, 24], 6, seed=10, c=0.7, eta=1e-3, dtype=np.float64)
+    X = _dev(prob.X)
+    res = {}
+    for name, ex, beta in (("rule", b.EXTRAP_PAPER, 0.0), ("fixed", b.EXTRAP_FIXED, 0.002)):
+        opts = b.make_options(tree=b.TREE_RESTRUCTURED, prec=b.PREC_FP64, extrap=ex, beta_fixed=beta)
+        with b.Decomposition(prob.dims, prob.R, X.data_ptr(), True, prob.A0, opts) as d:
+            fits = d.sweep(12)
+            hist = d.history()
+        kw = dict(extrapolate=True) if ex == b.EXTRAP_PAPER else dict(extrapolate=True, beta_fixed=beta)
+        ref = o.cp_als_qr(prob.X, prob.R, prob.A0, tree=o.TREE_RESTRUCTURED, max_sweeps=12, **kw)
+        assert np.max(np.abs(fits - np.array(ref.fits))) <= 1e-10, name
+        assert np.array_equal(hist[1], np.array(ref.betas)), name
+        res[name] = ref
+    assert any(bb > 0 for bb in res["rule"].betas)  # the rule activates within these sweeps
+    assert res["rule"].betas != res["fixed"].betas
+
+
+def test_fit_exact_at_an_extrapolated_fixed_point():
+    """At eq. 19's fixed point the model is the least-squares model scaled by 1 + beta (1 - alpha),
+    so the residual is no longer orthogonal to it and a relative scale error e of the residual
+    pass's model entries moves the fit by about e (at a least-squares optimum it would not move it
+    at all).  The FP64 path (factors equal to the oracle's to 1e-15) after 90 sweeps with a fixed
+    beta of 0.01: cp_als_qr_fit_exact against the oracle's dense residual of the same factors to
+    1.5e-7 (truncating TF32 splits gave 5.6e-7)."""
+    prob = inputs.make_problem("fx_bre", [96, 96, 96], 16, seed=7, c=0.5, eta=1e-3, dtype=np.float32)
+    X = _dev(prob.X)
+    opts = b.make_options(tree=b.TREE_RESTRUCTURED, prec=b.PREC_FP64, extrap=b.EXTRAP_FIXED, beta_fixed=0.01)
+    with b.Decomposition(prob.dims, prob.R, X.data_ptr(), False, prob.A0, opts) as d:
+        fits = d.sweep(90)
+        A, lam, _, _ = d.factors()
+        fx = d.fit_exact()
+    ref = o.fit_explicit(prob.X, lam, A)
+    assert abs(fx - ref) <= 1.5e-7, (fx, ref)
+    assert abs(fits[-1] - ref) <= 1e-9  # the reduced form is exact here

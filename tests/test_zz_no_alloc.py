@@ -1,9 +1,11 @@
 """cpqr_house_qr_noalloc — the QR entry point for callers that may not allocate device
 memory (their scratch lives in one static device array) — against cpqr_house_qr, which
-allocates its scratch per call.  Collected last on purpose."""
+allocates its scratch per call, and against the oracle's Householder QR.  Collected last on
+purpose."""
 import numpy as np
 import pytest
 
+from oracle import cpqr_oracle as o
 from paper_2503_18759_gb300 import binding as b
 
 torch = pytest.importorskip("torch")
@@ -40,6 +42,25 @@ def test_noalloc_qr_matches_allocating_qr_on_two_calls_in_a_row(M, R):
         assert np.allclose(Rn, Ra, rtol=0, atol=1e-12 * np.linalg.norm(A)), call
         assert np.allclose(Qn, Qa, rtol=0, atol=1e-12), call
         assert np.allclose(Qn @ Rn, A, atol=1e-11 * np.linalg.norm(A))
+        Qo, Ro = o.householder_qr(A)
+        assert np.allclose(Rn, Ro, rtol=0, atol=1e-12 * np.linalg.norm(A)), call
+        assert np.allclose(Qn, Qo, rtol=0, atol=1e-12), call
+
+
+@pytest.mark.parametrize("fn", ["cpqr_house_qr_noalloc", "cpqr_house_qr"])
+def test_zero_column_reports_singular(fn):
+    """A zero column has no Householder reflector (zero norm): the device flags it and the entry
+    point returns CPQR_ESINGULAR instead of a silent success; the next call is unaffected."""
+    g = np.random.default_rng(5)
+    A = g.standard_normal((300, 8))
+    A[:, 3] = 0.0
+    with pytest.raises(b.CpqrError) as e:
+        _qr(getattr(b, fn), A)
+    assert e.value.status == b.ESINGULAR
+    A[:, 3] = g.standard_normal(300)
+    Q, Rm = _qr(getattr(b, fn), A)
+    Qo, Ro = o.householder_qr(A)
+    assert np.allclose(Rm, Ro, atol=1e-12 * np.linalg.norm(A))
 
 
 def test_noalloc_qr_rejects_sizes_beyond_its_scratch():
