@@ -71,8 +71,13 @@ typedef enum {
   CPQR_EXTRAP_PAPER = 1,  /* Section 4.2 rule: alpha = 1/10, beta chosen by fit level once
                              |fit_k - fit_{k-1}| < 0.03, then fixed */
   CPQR_EXTRAP_FIXED = 2,  /* beta = beta_fixed from the second sweep on */
-  CPQR_EXTRAP_LEARNED = 3 /* beta proposed by the learned model; the Section 4.2 rule is the
-                             fallback and judges every proposal by the fit it reaches */
+  CPQR_EXTRAP_LEARNED = 3 /* beta proposed by the learned model after every sweep (features and
+                             network on the device).  A proposal other than the Section 4.2
+                             rule's beta (beta = 0 included) is judged: from one checkpoint both
+                             the proposal's and the rule's sweep run and the proposal is kept only
+                             if its fit is higher; the rule is the fallback.  A winning proposal
+                             stays approved for 1, 2, 4, ... 32 further sweeps (doubling on
+                             consecutive wins) while the fit does not drop */
 } cpqr_extrap;
 
 /* How a sweep computes the QR of a two-triangle Khatri-Rao product and the factor QRs. */
@@ -113,8 +118,8 @@ typedef struct {
   int64_t full_ttms;       /* TTMs that read all of X */
   double last_fit;         /* fit after the last sweep */
   double beta;             /* beta used by the last sweep */
-  int64_t proposals;       /* learned proposals evaluated */
-  int64_t accepted;        /* learned proposals accepted by the judge */
+  int64_t proposals;       /* learned proposals that differed from the rule's beta */
+  int64_t accepted;        /* ... of which ran (won the judge, or within an approval window) */
   int64_t launches;        /* kernels this context launched */
   double ms_bucket[CPQR_NBUCKETS];   /* device time per bucket (only while timing is on) */
   int64_t n_bucket[CPQR_NBUCKETS];   /* launches per bucket (only while timing is on) */
@@ -123,6 +128,8 @@ typedef struct {
   int64_t krp_split;       /* Khatri-Rao QRs (order >= 4, Gram route) that took the split route:
                               the QR of the other triangles formed one update ahead, only the level
                               with the last-updated triangle after that update */
+  int64_t judged;          /* learned proposals judged against the rule's sweep (two sweeps each) */
+  int64_t preapproved;     /* learned proposals run within an approval window */
 } cpqr_stats;
 
 /* Turn per-launch CUDA-event timing on (1) or off (0); resets the bucket times. */
@@ -258,6 +265,11 @@ cpqr_status cpqr_krp_qr(const double* Rs_dev, int32_t m, int32_t R, double* Q0_d
 #define CPQR_MLP_HIDDEN 128
 #define CPQR_MLP_CLASSES 8
 #define CPQR_MLP_NPARAMS (32 * 128 + 128 + 2 * (128 * 128 + 128) + 128 * 8 + 8)
+
+/* The device proposer state of a CPQR_EXTRAP_LEARNED context after its last sweep: the features
+ * (CPQR_MLP_FEATURES floats, as cpqr_mlp_features defines them), the logits (CPQR_MLP_CLASSES)
+ * and the proposed class (any pointer may be NULL).  CPQR_EUNSUPPORTED without a learned model. */
+cpqr_status cp_als_qr_mlp_state(cpqr_ctx* ctx, float* features_host, float* logits_host, int32_t* cls);
 
 /* beta of class c (0 <= c < CPQR_MLP_CLASSES); class 0 is beta = 0; NaN otherwise. */
 double cp_als_qr_mlp_beta(int32_t c);

@@ -46,7 +46,7 @@ class Stats(C.Structure):
                 ("last_fit", C.c_double), ("beta", C.c_double), ("proposals", C.c_int64),
                 ("accepted", C.c_int64), ("launches", C.c_int64), ("ms_bucket", C.c_double * NBUCKETS),
                 ("n_bucket", C.c_int64 * NBUCKETS), ("qr_fallbacks", C.c_int64),
-                ("krp_split", C.c_int64)]
+                ("krp_split", C.c_int64), ("judged", C.c_int64), ("preapproved", C.c_int64)]
 
 
 _lib = None
@@ -92,6 +92,7 @@ def lib() -> C.CDLL:
     L.cp_als_qr_commit.argtypes = [vp]
     L.cp_als_qr_sweep_beta.argtypes = [vp, dbl, P(dbl)]
     L.cp_als_qr_test_wait_timeout.argtypes = [vp, C.c_uint64]
+    L.cp_als_qr_mlp_state.argtypes = [vp, P(C.c_float), P(C.c_float), P(i32)]
     L.cp_als_qr_history.argtypes = [vp, P(dbl), P(dbl), i32, P(i32), P(dbl), P(i32)]
     L.cpqr_house_qr.argtypes = [vp, i64, i32, vp, vp, vp]
     L.cpqr_krp_qr.argtypes = [vp, i32, i32, vp, vp, vp]
@@ -99,7 +100,7 @@ def lib() -> C.CDLL:
     for name in ("cp_als_qr_init", "cp_als_qr_sweep", "cp_als_qr_fit", "cp_als_qr_get", "cp_als_qr_stats",
                  "cp_als_qr_fit_exact", "cp_als_qr_set_timing", "cp_als_qr_schedule", "cp_als_qr_run_host",
                  "cpqr_mlp_features", "cpqr_mlp_forward", "cpqr_mlp_grad", "cpqr_mlp_adam", "cp_als_qr_checkpoint",
-                 "cp_als_qr_rollback", "cp_als_qr_commit", "cp_als_qr_sweep_beta", "cp_als_qr_test_wait_timeout", "cp_als_qr_history", "cpqr_ttm", "cpqr_house_qr", "cpqr_krp_qr", "cpqr_house_qr_noalloc"):
+                 "cp_als_qr_rollback", "cp_als_qr_commit", "cp_als_qr_sweep_beta", "cp_als_qr_test_wait_timeout", "cp_als_qr_mlp_state", "cp_als_qr_history", "cpqr_ttm", "cpqr_house_qr", "cpqr_krp_qr", "cpqr_house_qr_noalloc"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -277,6 +278,16 @@ def cp_als_qr_sweep_beta(ctx, beta: float) -> float:
     f = C.c_double()
     _check(lib().cp_als_qr_sweep_beta(ctx, float(beta), C.byref(f)), "cp_als_qr_sweep_beta")
     return f.value
+
+
+def cp_als_qr_mlp_state(ctx):
+    """(features, logits, proposed class) of a learned context's device proposer."""
+    f = np.zeros(MLP_FEATURES, dtype=np.float32)
+    lg = np.zeros(MLP_CLASSES, dtype=np.float32)
+    c = C.c_int32()
+    _check(lib().cp_als_qr_mlp_state(ctx, f.ctypes.data_as(C.POINTER(C.c_float)),
+                                     lg.ctypes.data_as(C.POINTER(C.c_float)), C.byref(c)), "cp_als_qr_mlp_state")
+    return f, lg, c.value
 
 
 def cp_als_qr_test_wait_timeout(ctx, limit_ns: int) -> None:

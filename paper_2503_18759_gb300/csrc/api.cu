@@ -96,6 +96,7 @@ struct Checkpoint {
   double* Q0 = nullptr;
   float* Q0fprev[CPQR_MAXN] = {};
   float* Q0f = nullptr;
+  int next_class = -1;
 };
 
 struct cpqr_ctx {
@@ -127,13 +128,18 @@ struct cpqr_ctx {
   std::vector<void*> owned;  // cudaMalloc'd, freed at destroy
   void* arena = nullptr;     // every per-mode state array (factors, QRs, Q0 history, staging)
   size_t arena_bytes = 0;
-  Checkpoint ckpt[2];        // 0: caller's slot, 1: learned-proposal speculation
+  Checkpoint ckpt[3];        // 0: caller's slot, 1 and 2: the two branches of a judged proposal
   std::map<int, NodeBuf> orphans;  // nodes freed while a checkpoint still references them
-  // learned proposer
+  // learned proposer: FP32 parameters, their bf16 transposed copy, and the device state (fit /
+  // beta history, rule state, proposal) in the state arena
   float* mlp_params = nullptr;
-  void* mlp_work = nullptr;
-  float* mlp_io = nullptr;     // device: features (F) then logits (C)
-  float* h_mlp = nullptr;      // pinned host: features + logits
+  __nv_bfloat16* mlp_wt = nullptr;
+  MlpState* mlp_state = nullptr;
+  int next_class = -1;        // proposal for the next sweep, read with the last sweep's fit
+  // judging: a proposal that beat the rule's sweep from the same checkpoint stays approved for
+  // approve_left more sweeps while the fit does not drop; each win doubles the window (<= 32)
+  int approved_class = -1, approve_window = 1, approve_left = 0;
+  int64_t judged = 0, preapproved = 0;
   double* A[CPQR_MAXN] = {};
   double* Q[CPQR_MAXN] = {};
   double* Rf[CPQR_MAXN] = {};
@@ -232,7 +238,6 @@ struct cpqr_ctx {
     pool.release();
     for (void* p : owned) cudaFree(p);
     if (h_pinned) cudaFreeHost(h_pinned);
-    if (h_mlp) cudaFreeHost(h_mlp);
   }
 
   template <typename T>
@@ -489,6 +494,7 @@ cpqr_status checkpoint_save(cpqr_ctx* ctx, int slot) {
   }
   c.Q0 = ctx->Q0;
   c.Q0f = ctx->Q0f;
+  c.next_class = ctx->next_class;
   c.valid = true;
   return CPQR_OK;
 }
@@ -518,6 +524,7 @@ cpqr_status checkpoint_restore(cpqr_ctx* ctx, int slot) {
   }
   ctx->Q0 = c.Q0;
   ctx->Q0f = c.Q0f;
+  ctx->next_class = c.next_class;
   ctx->z_pending = false;
   ctx->zchol_mode = -1;
   ctx->wpf_mode = -1;
@@ -823,7 +830,7 @@ cpqr_status flush_lag(cpqr_ctx* ctx) {
 // Split path: the reduced form cancels ||X||^2 against terms that carry the split operands'
 // ~2^-16 relative error, which can exceed a 1e-6 change in fit, so the fit comes from an
 // explicit residual pass over X with the current factors instead (one read of X).
-cpqr_status read_fit(cpqr_ctx* ctx, double* fit) {
+cpqr_status read_fit(cpqr_ctx* ctx, double* fit, double beta) {
   const bool explicit_fit = (ctx->prec == CPQR_PREC_SPLIT_BF16);
   if (explicit_fit) {
     Timed tm(ctx, CPQR_BUCKET_FIT, 1);
@@ -832,14 +839,29 @@ cpqr_status read_fit(cpqr_ctx* ctx, double* fit) {
     CK(launch_residual2<float>((const float*)ctx->X, ctx->N, ctx->dims.data(), A, ctx->lambda, ctx->R,
                                ctx->d_scalar, ctx->res_work, ctx->dstatus, ctx->st));
   }
+  const bool propose = ctx->mlp_state != nullptr;
+  if (propose) {
+    // the learned proposer's next proposal, from this sweep's fit, on the device
+    Timed tm(ctx, CPQR_BUCKET_OTHER, 1);
+    MlpFitSource src{explicit_fit ? ctx->d_scalar : nullptr, ctx->fit_terms, ctx->normX2};
+    CK(mlp_propose(ctx->mlp_wt, ctx->mlp_params, ctx->mlp_state, src, beta, ctx->st));
+  }
   {
     Timed tm(ctx, CPQR_BUCKET_OTHER, 0);
     if (explicit_fit)
       CK(cudaMemcpyAsync(ctx->h_pinned + 3, ctx->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaMemcpyAsync(ctx->h_pinned, ctx->fit_terms, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaMemcpyAsync(ctx->h_pinned + 2, ctx->dstatus, sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->st));
+    if (propose)
+      CK(cudaMemcpyAsync(ctx->h_pinned + 5, &ctx->mlp_state->cls, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                         ctx->st));
   }
   CK(cudaStreamSynchronize(ctx->st));
+  if (propose) {
+    int32_t c;
+    std::memcpy(&c, ctx->h_pinned + 5, sizeof(c));
+    ctx->next_class = (c >= 0 && c < CPQR_MLP_CLASSES) ? c : -1;
+  }
   if (ctx->timing) {
     CK(cudaStreamSynchronize(ctx->st2));  // the next sweep's W may still be running there
     collect_timing(ctx);
@@ -950,7 +972,7 @@ cpqr_status one_sweep(cpqr_ctx* ctx, double* fit_out, const double* forced_beta 
     return CPQR_OK;
   }
   double fit = 0.0;
-  cpqr_status s = read_fit(ctx, &fit);
+  cpqr_status s = read_fit(ctx, &fit, beta);
   if (s != CPQR_OK) return s;
   ctx->last_beta = beta;
   ++ctx->sweeps;
@@ -984,51 +1006,63 @@ void mlp_features(const double* fits, const double* betas, int n, double rule_be
   f[26] = activated ? 1.f : 0.f;
 }
 
-// CPQR_EXTRAP_LEARNED: the network proposes beta; a sweep with beta > 0 runs speculatively and
-// is kept only if its fit does not fall below the previous sweep's, else it is rolled back and
-// redone with the Section 4.2 rule's beta.
+// CPQR_EXTRAP_LEARNED.  After every sweep the device proposes the next sweep's beta (features and
+// network in one kernel, read back with the fit).  A proposal equal to the Section 4.2 rule's beta
+// runs as is.  Any other proposal, beta = 0 included, is judged: from one checkpoint the proposal's
+// sweep and the rule's sweep both run, and the proposal is kept only if its fit is higher, else the
+// rule's sweep stands (the rule is the fallback).  A proposal that won stays approved for the next
+// approve_window sweeps (1, 2, 4, ... 32 after consecutive wins) as long as the fit does not drop;
+// a drop or a loss ends the approval, and the next differing proposal is judged again.
 cpqr_status learned_sweep(cpqr_ctx* ctx, double* fit_out) {
   const double rule = rule_beta_next(ctx);
-  if (!ctx->mlp_params || ctx->fits.size() < 2) return one_sweep(ctx, fit_out, &rule);
-  float* hf = ctx->h_mlp;
-  mlp_features(ctx->fits.data(), ctx->betas.data(), (int)ctx->fits.size(), rule, ctx->activated ? 1 : 0, hf);
-  CK(cudaMemcpyAsync(ctx->mlp_io, hf, CPQR_MLP_FEATURES * sizeof(float), cudaMemcpyHostToDevice, ctx->st));
-  {
-    Timed tm(ctx, CPQR_BUCKET_OTHER, 7);
-    CK(mlp_forward(ctx->mlp_params, ctx->mlp_io, 1, ctx->mlp_io + CPQR_MLP_FEATURES, ctx->mlp_work, ctx->st));
-  }
-  CK(cudaMemcpyAsync(hf + CPQR_MLP_FEATURES, ctx->mlp_io + CPQR_MLP_FEATURES, CPQR_MLP_CLASSES * sizeof(float),
-                     cudaMemcpyDeviceToHost, ctx->st));
-  CK(cudaStreamSynchronize(ctx->st));
-  int best = 0;
-  for (int c = 1; c < CPQR_MLP_CLASSES; ++c)
-    if (hf[CPQR_MLP_FEATURES + c] > hf[CPQR_MLP_FEATURES + best]) best = c;
-  const double prop = kMlpBetas[best];
+  const int cls = ctx->next_class;
+  if (!ctx->mlp_state || ctx->fits.size() < 2 || cls < 0) return one_sweep(ctx, fit_out, &rule);
+  const double prop = kMlpBetas[cls];
   if (prop == rule) return one_sweep(ctx, fit_out, &rule);
-  if (prop == 0.0) {
-    // without extrapolation every mode update is an exact least-squares step, so the fit
-    // cannot drop: nothing to judge
-    ++ctx->proposals;
-    ++ctx->accepted;
-    return one_sweep(ctx, fit_out, &prop);
-  }
-  const double prev = ctx->fits.back();
-  cpqr_status s = checkpoint_save(ctx, 1);
-  if (s != CPQR_OK) return s;
-  double f = 0.0;
-  s = one_sweep(ctx, &f, &prop);
-  if (s != CPQR_OK) return s;
   ++ctx->proposals;
-  if (f >= prev) {
+  double f = 0.0;
+  if (cls == ctx->approved_class && ctx->approve_left > 0) {
+    --ctx->approve_left;
+    const double prev = ctx->fits.back();
+    cpqr_status s = one_sweep(ctx, &f, &prop);
+    if (s != CPQR_OK) return s;
     ++ctx->accepted;
-    checkpoint_drop(ctx, 1);
+    ++ctx->preapproved;
+    if (!(f >= prev)) {
+      ctx->approved_class = -1;
+      ctx->approve_window = 1;
+      ctx->approve_left = 0;
+    }
     if (fit_out) *fit_out = f;
     return CPQR_OK;
   }
-  s = checkpoint_restore(ctx, 1);
+  ++ctx->judged;
+  cpqr_status s = checkpoint_save(ctx, 1);
   if (s != CPQR_OK) return s;
+  double fp = 0.0, fr = 0.0;
+  s = one_sweep(ctx, &fp, &prop);
+  if (s == CPQR_OK) s = checkpoint_save(ctx, 2);  // the proposal's branch
+  if (s == CPQR_OK) s = checkpoint_restore(ctx, 1);
+  if (s == CPQR_OK) s = one_sweep(ctx, &fr, &rule);
+  if (s != CPQR_OK) return s;
+  if (fp > fr) {
+    s = checkpoint_restore(ctx, 2);
+    if (s != CPQR_OK) return s;
+    ++ctx->accepted;
+    ctx->approved_class = cls;
+    ctx->approve_window = std::min(2 * ctx->approve_window, 32);
+    ctx->approve_left = ctx->approve_window;
+    f = fp;
+  } else {
+    ctx->approved_class = -1;
+    ctx->approve_window = 1;
+    ctx->approve_left = 0;
+    f = fr;
+  }
   checkpoint_drop(ctx, 1);
-  return one_sweep(ctx, fit_out, &rule);
+  checkpoint_drop(ctx, 2);
+  if (fit_out) *fit_out = f;
+  return CPQR_OK;
 }
 
 cpqr_status next_sweep(cpqr_ctx* ctx, double* fit_out) {
@@ -1142,6 +1176,8 @@ cpqr_status cp_als_qr_init(cpqr_ctx** out, int32_t N, const int64_t* dims, int32
       oC[n] = take((size_t)CPQR_MAXR * 8);
     }
     size_t oQ0 = take(M0 * R * 8), oL = take(R * 8), oQ0f = split ? take(M0 * R * 4) : 0;
+    const bool learned = opt.extrap == CPQR_EXTRAP_LEARNED && opt.mlp_weights;
+    size_t oM = learned ? take(sizeof(MlpState)) : 0;
     ctx->arena_bytes = off;
     CK(cudaMalloc(&ctx->arena, off));
     ctx->owned.push_back(ctx->arena);
@@ -1161,6 +1197,7 @@ cpqr_status cp_als_qr_init(cpqr_ctx** out, int32_t N, const int64_t* dims, int32
     ctx->Q0 = (double*)(a + oQ0);
     if (split) ctx->Q0f = (float*)(a + oQ0f);
     ctx->lambda = (double*)(a + oL);
+    if (learned) ctx->mlp_state = (MlpState*)(a + oM);  // zeroed with the arena
   }
   CK(ctx->alloc(&ctx->R0, (size_t)R * R));
   CK(ctx->alloc(&ctx->V, Imax * 2 * R));
@@ -1264,8 +1301,12 @@ cpqr_status cp_als_qr_init(cpqr_ctx** out, int32_t N, const int64_t* dims, int32
     CK(launch_split_x((const float*)X_dev, ctx->Xhi, ctx->Xlo, nX, st));
   }
   // ||X||^2 (precomputed once, Section 4.1).
-  if (ctx->x64) CK(launch_norm2<double>((const double*)X_dev, nX, ctx->d_scalar, nullptr, st));
-  else CK(launch_norm2<float>((const float*)X_dev, nX, ctx->d_scalar, nullptr, st));
+  {
+    double* nwork = nullptr;
+    CK(ctx->alloc(&nwork, norm2_work_doubles()));
+    if (ctx->x64) CK(launch_norm2<double>((const double*)X_dev, nX, ctx->d_scalar, nwork, st));
+    else CK(launch_norm2<float>((const float*)X_dev, nX, ctx->d_scalar, nwork, st));
+  }
   CK(cudaMemcpyAsync(ctx->h_pinned, ctx->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(ctx->h_pinned + 2, ctx->dstatus, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -1282,9 +1323,8 @@ cpqr_status cp_als_qr_init(cpqr_ctx** out, int32_t N, const int64_t* dims, int32
     CK(ctx->alloc(&ctx->mlp_params, CPQR_MLP_NPARAMS));
     CK(cudaMemcpyAsync(ctx->mlp_params, opt.mlp_weights, CPQR_MLP_NPARAMS * sizeof(float), cudaMemcpyHostToDevice,
                        st));
-    CK(ctx->alloc((char**)&ctx->mlp_work, (size_t)mlp_work_bytes(1)));
-    CK(ctx->alloc(&ctx->mlp_io, CPQR_MLP_FEATURES + CPQR_MLP_CLASSES));
-    CK(cudaMallocHost(&ctx->h_mlp, (CPQR_MLP_FEATURES + CPQR_MLP_CLASSES) * sizeof(float)));
+    CK(ctx->alloc(&ctx->mlp_wt, CPQR_MLP_NPARAMS));
+    CK(mlp_prepare_weights(ctx->mlp_params, ctx->mlp_wt, st));
     CK(cudaStreamSynchronize(st));
   }
   try {
@@ -1372,6 +1412,8 @@ cpqr_status cp_als_qr_stats(cpqr_ctx* ctx, cpqr_stats* out) {
   out->beta = ctx->last_beta;
   out->proposals = ctx->proposals;
   out->accepted = ctx->accepted;
+  out->judged = ctx->judged;
+  out->preapproved = ctx->preapproved;
   out->launches = ctx->launches;
   out->krp_split = ctx->n_split;
   for (int b = 0; b < CPQR_NBUCKETS; ++b) {
@@ -1472,6 +1514,19 @@ cpqr_status cp_als_qr_history(cpqr_ctx* ctx, double* fits_host, double* betas_ho
   if (rule_beta) *rule_beta = rule_beta_next(ctx);
   if (activated) *activated = ctx->activated ? 1 : 0;
   return ctx->err;
+}
+
+cpqr_status cp_als_qr_mlp_state(cpqr_ctx* ctx, float* features_host, float* logits_host, int32_t* cls) {
+  if (!ctx) return CPQR_EINVAL;
+  if (ctx->err != CPQR_OK) return ctx->err;
+  if (!ctx->mlp_state) return CPQR_EUNSUPPORTED;
+  MlpState h;
+  CK(cudaMemcpyAsync(&h, ctx->mlp_state, sizeof(h), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  if (features_host) std::memcpy(features_host, h.feat, sizeof(h.feat));
+  if (logits_host) std::memcpy(logits_host, h.logits, sizeof(h.logits));
+  if (cls) *cls = h.cls;
+  return CPQR_OK;
 }
 
 double cp_als_qr_mlp_beta(int32_t c) {

@@ -233,9 +233,13 @@ cudaError_t launch_tri_gram(const double* T, int R, float2* Gf, double* s, cudaS
 // Runs of the Householder fallback recorded in a Gram-route workspace (device int counter).
 int* gram_fallback_counter(double* gram_work);
 
-// ||X||^2 in FP64 (partials into work, final into out[0]).
+// ||X||^2 in FP64: block partials into work (norm2_work_doubles()), summed in a fixed order into
+// out[0], so every context on the same tensor gets the same bits.
 template <typename TX>
 cudaError_t launch_norm2(const TX* X, int64_t n, double* out, double* work, cudaStream_t st);
+size_t norm2_work_doubles();
+// out[0] = sum of part[0..np-1] in a fixed order (one block).
+cudaError_t launch_sum_parts(const double* part, int np, double* out, cudaStream_t st);
 
 // ||X - [[lambda; A]]||^2 (FP32 model entries, FP64 total); X dims d[0..N-1]; A: host array of N
 // device pointers; work: device scratch of residual2_work_bytes(N, d, R).  FP32 tensors whose
@@ -255,12 +259,37 @@ cudaError_t launch_residual2(const TX* X, int N, const int64_t* d, const double*
 // Af: host array of N device pointers to the FP32 factors (lambda folded into Af[0], Af[N-1]
 // stored transposed, R x I_last); accumulates ||X - K||^2 into *out (not cleared).
 bool residual_tc_supported(int N, const int64_t* d, int R, const void* X);
-cudaError_t launch_residual_tc(const float* X, int N, const int64_t* d, const float* const* Af, int R, double* out,
-                               unsigned int* dev_status, cudaStream_t st, int reserve_sms = 0);
+cudaError_t launch_residual_tc(const float* X, int N, const int64_t* d, const float* const* Af, int R, double* part,
+                               int max_parts, int* nparts, unsigned int* dev_status, cudaStream_t st,
+                               int reserve_sms = 0);
 
 cudaError_t launch_to_f32(const double* a, float* b, int64_t n, cudaStream_t st);
 
 // ----- learned proposer (mlp.cu) -----
+// Device state of the learned proposer (kept in the solver's state arena, so a checkpoint saves it):
+// the fits of the last MLP_RING + 1 sweeps and the betas of the last MLP_RING (most recent last),
+// the Section 4.2 rule's state, and the last features, logits and proposed class.
+constexpr int MLP_RING = 8;
+struct MlpState {
+  double fit[MLP_RING + 1];
+  double beta[MLP_RING];
+  double rule_beta;
+  int32_t n, activated, cls, pad;
+  float feat[CPQR_MLP_FEATURES];
+  float logits[CPQR_MLP_CLASSES];
+};
+// Where a sweep's fit comes from: the explicit residual r2 (split path), else the fit terms
+// <V0, V^>, ||V^||^2 of the last update (FP64 path).
+struct MlpFitSource {
+  const double* r2;
+  const double* terms;
+  double normX2;
+};
+// bf16 transposed weights (CPQR_MLP_NPARAMS slots) from the FP32 parameters.
+cudaError_t mlp_prepare_weights(const float* params, __nv_bfloat16* wt, cudaStream_t st);
+// After a sweep that used beta_used: update the state and propose the next sweep's class.
+cudaError_t mlp_propose(const __nv_bfloat16* wt, const float* params, MlpState* state, MlpFitSource src,
+                        double beta_used, cudaStream_t st);
 size_t mlp_work_bytes(int B);
 cudaError_t mlp_forward(const float* params, const float* X, int B, float* logits, void* work, cudaStream_t st);
 cudaError_t mlp_grad(const float* params, const float* X, const int32_t* y, int B, float* grad, float* loss,

@@ -119,7 +119,110 @@ __global__ void adam_kernel(float* __restrict__ w, float* __restrict__ m, float*
   }
 }
 
+// bf16 copy of the weights, each layer transposed to (in x out) so that the threads of a layer
+// (one output each) read consecutive addresses.
+__global__ void prepare_weights_kernel(const float* __restrict__ params, __nv_bfloat16* __restrict__ wt) {
+  for (int l = 0; l < NL; ++l) {
+    const int in = layer_in(l), out = layer_out(l);
+    const float* W = params + layer_off(l);
+    __nv_bfloat16* T = wt + layer_off(l);  // same offsets; the bias slots stay unused
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < in * out; e += gridDim.x * blockDim.x) {
+      const int o = e / in, i = e - o * in;
+      T[i * out + o] = __float2bfloat16_rn(W[e]);
+    }
+  }
+}
+
+__device__ double beta_band_dev(double fit) {
+  if (fit > 0.95) return 1.0 / 20000.0;
+  if (fit > 0.90) return 1.0 / 2000.0;
+  if (fit > 0.70) return 1.0 / 500.0;
+  return 1.0 / 250.0;
+}
+
+// One block of H threads after a sweep: the sweep's fit from its raw terms, the fit / beta history,
+// the Section 4.2 rule's state, the features (same definition as cpqr_mlp_features), the network
+// (bf16 weights and activations, FP32 accumulation in the order of fwd_layer_kernel) and the
+// proposal for the next sweep (arg max of the logits, first maximum).
+__global__ void __launch_bounds__(H) mlp_propose_kernel(const __nv_bfloat16* __restrict__ wt,
+                                                         const float* __restrict__ params, MlpState* __restrict__ st,
+                                                         MlpFitSource src, double beta_used) {
+  __shared__ float x0[H], x1[H];
+  const int o = threadIdx.x;
+  if (o == 0) {
+    const double r2 = src.r2 ? src.r2[0] : src.normX2 - 2.0 * src.terms[0] + src.terms[1];
+    const double fit = 1.0 - sqrt(fmax(r2, 0.0)) / sqrt(src.normX2);
+    for (int j = 0; j < MLP_RING; ++j) st->fit[j] = st->fit[j + 1];
+    st->fit[MLP_RING] = fit;
+    for (int j = 0; j + 1 < MLP_RING; ++j) st->beta[j] = st->beta[j + 1];
+    st->beta[MLP_RING - 1] = beta_used;
+    const int n = ++st->n;
+    if (!st->activated && n >= 2 && fabs(st->fit[MLP_RING] - st->fit[MLP_RING - 1]) < 0.03) {
+      st->rule_beta = beta_band_dev(fit);
+      st->activated = 1;
+    }
+    float f[F];
+    for (int i = 0; i < F; ++i) f[i] = 0.f;
+    for (int j = 0; j < 8 && n - 1 - j >= 0; ++j) {
+      const int k = n - 1 - j;  // sweep index (0-based) j sweeps back
+      const double fk = st->fit[MLP_RING - j];
+      f[3 * j] = (float)(log10(fmax(1.0 - fk, 1e-12)) / 12.0);
+      if (k >= 1) {
+        const double d = fk - st->fit[MLP_RING - j - 1];
+        const double m = (log10(fmax(fabs(d), 1e-14)) + 14.0) / 14.0;
+        f[3 * j + 1] = (float)(d >= 0 ? m : -m);
+      }
+      f[3 * j + 2] = (float)(log10(st->beta[MLP_RING - 1 - j] + 1e-8) / 8.0);
+    }
+    f[24] = (float)(log10((double)n + 1.0) / 3.0);
+    f[25] = (float)(log10(st->rule_beta + 1e-8) / 8.0);
+    f[26] = st->activated ? 1.f : 0.f;
+    for (int i = 0; i < F; ++i) {
+      st->feat[i] = f[i];
+      x0[i] = __bfloat162float(__float2bfloat16_rn(f[i]));
+    }
+  }
+  __syncthreads();
+  float* in_act = x0;
+  float* out_act = x1;
+  for (int l = 0; l < NL; ++l) {
+    const int in = layer_in(l), out = layer_out(l);
+    const __nv_bfloat16* T = wt + layer_off(l);
+    if (o < out) {
+      float acc = params[layer_off(l) + in * out + o];
+      for (int i = 0; i < in; ++i) acc += in_act[i] * __bfloat162float(T[i * out + o]);
+      if (l < NL - 1) {
+        acc = acc > 0.f ? acc : 0.f;
+        out_act[o] = __bfloat162float(__float2bfloat16_rn(acc));
+      } else {
+        st->logits[o] = acc;
+      }
+    }
+    __syncthreads();
+    float* t = in_act;
+    in_act = out_act;
+    out_act = t;
+  }
+  if (o == 0) {
+    int best = 0;
+    for (int c = 1; c < NC; ++c)
+      if (st->logits[c] > st->logits[best]) best = c;
+    st->cls = best;
+  }
+}
+
 }  // namespace
+
+cudaError_t mlp_prepare_weights(const float* params, __nv_bfloat16* wt, cudaStream_t st) {
+  prepare_weights_kernel<<<64, 256, 0, st>>>(params, wt);
+  return cudaGetLastError();
+}
+
+cudaError_t mlp_propose(const __nv_bfloat16* wt, const float* params, MlpState* state, MlpFitSource src,
+                        double beta_used, cudaStream_t st) {
+  mlp_propose_kernel<<<1, H, 0, st>>>(wt, params, state, src, beta_used);
+  return cudaGetLastError();
+}
 
 // Workspace (device, floats): bf16 weight copy + activations + gradients of activations.
 struct MlpWork {

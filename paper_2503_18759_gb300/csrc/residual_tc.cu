@@ -46,7 +46,7 @@ struct RtParams {
   int cpg;                    // CTAs per column group
   int gw;                     // columns per group (multiple of 4); the last group may be narrower
   int ncp;                    // MMA N = gw rounded up to 32
-  double* out;
+  double* part;  // one partial sum per CTA, added in a fixed order afterwards
   unsigned int* status;
 };
 
@@ -329,7 +329,7 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
       }
     }
   }
-  if (threadIdx.x == 0 && ntl > 0) atomicAdd(p.out, tail->red[0] + tail->red[1] + tail->red[2] + tail->red[3]);
+  if (threadIdx.x == 0) p.part[blockIdx.x] = (ntl > 0) ? tail->red[0] + tail->red[1] + tail->red[2] + tail->red[3] : 0.0;
   __syncthreads();
   if (warp == 1) {
     fence_after();
@@ -357,8 +357,9 @@ size_t residual_tc_smem_bytes(int ncp) {
   return 1024 + (size_t)2 * ncp * 128 + (size_t)4 * RT_WBYTES + (size_t)RT_NXS * RT_XBOX + sizeof(RtTail);
 }
 
-cudaError_t launch_residual_tc(const float* X, int N, const int64_t* d, const float* const* Af, int R, double* out,
-                               unsigned int* dev_status, cudaStream_t st, int reserve_sms) {
+cudaError_t launch_residual_tc(const float* X, int N, const int64_t* d, const float* const* Af, int R, double* part,
+                               int max_parts, int* nparts, unsigned int* dev_status, cudaStream_t st,
+                               int reserve_sms) {
   if (!residual_tc_supported(N, d, R, X)) return cudaErrorNotSupported;
   tc::EncodeTiledFn enc = tc::encode_tiled_fn();
   if (!enc) return cudaErrorNotSupported;
@@ -379,7 +380,7 @@ cudaError_t launch_residual_tc(const float* X, int N, const int64_t* d, const fl
   p.ncp = (p.gw + 31) & ~31;
   if (p.ncp > RT_MAXW) return cudaErrorNotSupported;
   p.cpg = std::max(1, std::min(p.rtiles, tc::num_sms() / ncg));
-  p.out = out;
+  p.part = part;
   p.status = dev_status;
   CUtensorMap tm;
   {
@@ -424,12 +425,16 @@ cudaError_t launch_residual_tc(const float* X, int N, const int64_t* d, const fl
       const int ctas = (nclusters - 1) * cl;
       p.cpg = std::max(1, std::min(p.rtiles, ctas / ncg));
       cfg.gridDim = dim3((unsigned)ctas, 1, 1);
+      if (ctas > max_parts) return cudaErrorInvalidValue;
+      *nparts = ctas;
       e = cudaLaunchKernelEx(&cfg, residual_tc_kernel, tm, p);
       if (e == cudaSuccess) return cudaSuccess;
     }
     cudaGetLastError();
     p.cpg = std::max(1, std::min(p.rtiles, (tc::num_sms() - reserve_sms) / ncg));
   }
+  if (ncg * p.cpg > max_parts) return cudaErrorInvalidValue;
+  *nparts = ncg * p.cpg;
   residual_tc_kernel<<<(unsigned)(ncg * p.cpg), RT_THREADS, smem, st>>>(tm, p);
   return cudaGetLastError();
 }

@@ -351,7 +351,7 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 }
 
 template <typename TX>
-__global__ void norm2_kernel(const TX* __restrict__ X, int64_t n, double* __restrict__ out) {
+__global__ void norm2_kernel(const TX* __restrict__ X, int64_t n, double* __restrict__ part) {
   __shared__ double sh[32];
   double acc = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -359,7 +359,16 @@ __global__ void norm2_kernel(const TX* __restrict__ X, int64_t n, double* __rest
     acc += v * v;
   }
   double t = block_sum(acc, sh);
-  if (threadIdx.x == 0) atomicAdd(out, t);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+// Sum of the block partials in a fixed order (the same ||X||^2 in every context).
+__global__ void sum_parts_kernel(const double* __restrict__ part, int np, double* __restrict__ out) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) acc += part[i];
+  double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) out[0] = t;
 }
 
 // Explicit residual ||X - [[lambda; A]]||^2.  X is viewed as rows (modes 0..N-2) x I_last.
@@ -544,7 +553,7 @@ __global__ void __launch_bounds__(RNT, 2) residual2_kernel(const TX* __restrict_
     if (q == 0) ++rt;
   }
   double t = block_sum(acc, sh);
-  if (threadIdx.x == 0) atomicAdd(out, t);
+  if (threadIdx.x == 0) out[blockIdx.x] = t;  // per-block partial, summed in a fixed order afterwards
 }
 
 __global__ void to_f32_kernel(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
@@ -633,19 +642,29 @@ template cudaError_t launch_leaf_v<float, float>(const float*, int64_t, int64_t,
                                                  int, int, float*, int*, cudaStream_t);
 
 template <typename TX>
-cudaError_t launch_norm2(const TX* X, int64_t n, double* out, double* /*work*/, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), st);
-  if (e != cudaSuccess) return e;
-  norm2_kernel<TX><<<grid_for(n, 256 * 16), 256, 0, st>>>(X, n, out);
+cudaError_t launch_norm2(const TX* X, int64_t n, double* out, double* work, cudaStream_t st) {
+  if (!work) return cudaErrorInvalidValue;
+  const int g = grid_for(n, 256 * 16);  // <= norm2_work_doubles()
+  norm2_kernel<TX><<<g, 256, 0, st>>>(X, n, work);
+  sum_parts_kernel<<<1, 256, 0, st>>>(work, g, out);
   return cudaGetLastError();
 }
+
+size_t norm2_work_doubles() { return 152 * 8; }
+
+cudaError_t launch_sum_parts(const double* part, int np, double* out, cudaStream_t st) {
+  sum_parts_kernel<<<1, 256, 0, st>>>(part, np, out);
+  return cudaGetLastError();
+}
+
+constexpr int kResidualParts = 1024;  // partial-sum slots of the residual passes (grids <= 2 x 152 CTAs)
 template cudaError_t launch_norm2<float>(const float*, int64_t, double*, double*, cudaStream_t);
 template cudaError_t launch_norm2<double>(const double*, int64_t, double*, double*, cudaStream_t);
 
 size_t residual2_work_bytes(int N, const int64_t* d, int R) {
   int64_t total = 0;
   for (int n = 0; n < N; ++n) total += d[n] * R;
-  return (size_t)((total + 3) / 4) * 16 + CPQR_MAXN * sizeof(double*) + 64;
+  return (size_t)((total + 3) / 4) * 16 + CPQR_MAXN * sizeof(double*) + 64 + kResidualParts * sizeof(double);
 }
 
 template <typename TX>
@@ -666,6 +685,8 @@ cudaError_t launch_residual2(const TX* X, int N, const int64_t* d, const double*
   if (rows > 0x7fffffff || total > 0x7fffffff) return cudaErrorInvalidValue;
   float* f32 = reinterpret_cast<float*>(work);
   const double** ptrs = reinterpret_cast<const double**>(f32 + ((total + 3) / 4) * 4);
+  // per-CTA partial sums after the pointers (8-byte aligned: the float block is a multiple of 16 bytes)
+  double* part = reinterpret_cast<double*>(ptrs + CPQR_MAXN) + 8;
   int64_t off = 0;
   for (int n = 0; n < N; ++n) {
     rp.A[n] = f32 + off;
@@ -681,17 +702,20 @@ cudaError_t launch_residual2(const TX* X, int N, const int64_t* d, const double*
     if (e != cudaSuccess) return e;
   }
   if (!(parts & RESIDUAL_EVALUATE)) return cudaSuccess;
-  e = cudaMemsetAsync(out, 0, sizeof(double), st);
-  if (e != cudaSuccess) return e;
   if (std::is_same<TX, float>::value && residual_tc_supported(N, d, R, X)) {
-    e = launch_residual_tc(reinterpret_cast<const float*>(X), N, d, rp.A, R, out, dev_status, st, reserve_sms);
+    int np = 0;
+    e = launch_residual_tc(reinterpret_cast<const float*>(X), N, d, rp.A, R, part, kResidualParts, &np, dev_status,
+                           st, reserve_sms);
+    if (e == cudaSuccess) return launch_sum_parts(part, np, out, st);
     if (e != cudaErrorNotSupported) return e;
   }
   // contiguous ranges of (row tile, column chunk) items, two CTAs per SM
   const int64_t items = ((rows + RM - 1) / RM) * ((d[N - 1] + RC - 1) / RC);
   const int grid = (int)std::min<int64_t>(items, 152 * 2);
-  residual2_kernel<TX><<<grid, RNT, 0, st>>>(X, rp, (int)rows, out);
-  return cudaGetLastError();
+  residual2_kernel<TX><<<grid, RNT, 0, st>>>(X, rp, (int)rows, part);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_sum_parts(part, grid, out, st);
 }
 template cudaError_t launch_residual2<float>(const float*, int, const int64_t*, const double* const*, const double*,
                                              int, double*, double*, unsigned int*, cudaStream_t, int, int);

@@ -1,7 +1,7 @@
 """Training and evaluation of the learned extrapolation proposer.
 
-The solver itself generates the data: along a trajectory, at every sweep after the
-second, the state is checkpointed and each candidate beta (cp_als_qr_mlp_beta) is run
+The solver itself generates the data: along a trajectory, every `stride` sweeps from the
+second on, the state is checkpointed and each candidate beta (cp_als_qr_mlp_beta) is run
 for `horizon` sweeps; the candidate with the highest fit (ties: the smaller beta) is the
 label of the features of that state, and the trajectory continues with it.  The network
 (3 hidden layers of 128, bf16) is trained with the library's own forward / backward /
@@ -9,7 +9,7 @@ Adam kernels.  Evaluation compares, on held-out tensors, sweeps and time to the 
 tolerance with the learned proposer (judged against the Section 4.2 rule), with the rule
 alone and without extrapolation.
 
-  python -m paper_2503_18759_gb300.learn train --problems 2000 --out weights.npy
+  python -m paper_2503_18759_gb300.learn train --problems 2000 --out weights.npy --eval-problems 200 --record r.json
   python -m paper_2503_18759_gb300.learn eval --weights weights.npy --problems 200
 """
 from __future__ import annotations
@@ -56,14 +56,22 @@ def problem_set(start: int, count: int, order: int = 3, base_seed: int = 0):
                                          eta=eta)
 
 
-def trajectories(problems, sweeps: int = 12, horizon: int = 2, start: int = 2, prec: int = b.PREC_SPLIT_BF16):
+def trajectories(problems, sweeps: int = 60, horizon: int = 2, start: int = 2, stride: int = 5,
+                 prec: int = b.PREC_SPLIT_BF16):
+    """Labelled states every `stride` sweeps from `start` to `sweeps`: features of the history and
+    the candidate with the highest fit after `horizon` sweeps from that state (ties: the smaller
+    beta).  The trajectory advances with the label between labelled states."""
     cand = candidates()
     feats, labels = [], []
     for prob in problems:
         opts = b.make_options(tree=b.TREE_RESTRUCTURED, prec=prec, extrap=b.EXTRAP_PAPER)
         with b.Decomposition(prob.dims, prob.R, prob.X.data_ptr(), False, prob.A0, opts) as d:
             d.sweep(start)
-            for _ in range(start, sweeps):
+            best = 0
+            for k in range(start, sweeps):
+                if (k - start) % stride:
+                    d.sweep_beta(cand[best])
+                    continue
                 fits, betas, rule, act = d.history()
                 f = b.cpqr_mlp_features(fits, betas, rule, act)
                 d.checkpoint()
@@ -147,11 +155,12 @@ def accuracy(params: np.ndarray, feats: np.ndarray, labels: np.ndarray) -> float
     return float(np.mean(pred == labels))
 
 
-def evaluate(params, problems, max_sweeps: int = 120, prec: int = b.PREC_FP64, gap: float = 1e-6):
+def evaluate(params, problems, max_sweeps: int = 120, prec: int = b.PREC_SPLIT_BF16, gap: float = 1e-6):
     """Per problem: every mode (no extrapolation, the Section 4.2 rule, the learned proposer)
     runs max_sweeps sweeps; f* is the best fit any of them reaches; reported are the sweeps and
     the seconds each mode needs to reach f* - gap (max_sweeps / its full time if never), the
-    final fit and the proposal counters.  Per-sweep fits are exact enough on the FP64 path."""
+    final fit and the proposal counters.  The split path's per-sweep fits come from the explicit
+    residual (~1e-7 of the fit), fine enough for the 1e-6 target."""
     import torch
 
     out = []
@@ -168,15 +177,15 @@ def evaluate(params, problems, max_sweeps: int = 120, prec: int = b.PREC_FP64, g
                     fits.append(float(d.sweep(1)[0]))
                     stamps.append(time.perf_counter() - t0)
                 st = d.stats()
-                traces[name] = (np.array(fits), np.array(stamps), st.proposals, st.accepted)
+                traces[name] = (np.array(fits), np.array(stamps), st.proposals, st.accepted, st.judged)
         fstar = max(float(t[0].max()) for t in traces.values())
         row = {"name": prob.name, "dims": prob.dims, "R": prob.R, "fstar": fstar}
-        for name, (f, t, props, acc) in traces.items():
+        for name, (f, t, props, acc, jd) in traces.items():
             hit = np.nonzero(f >= fstar - gap)[0]
             k = int(hit[0]) if len(hit) else max_sweeps - 1
             row[name] = {"sweeps_to_target": k + 1, "seconds_to_target": float(t[k]), "reached": bool(len(hit)),
                          "final_fit": float(f[-1]), "s_per_sweep": float(t[-1] / len(t)), "proposals": int(props),
-                         "accepted": int(acc)}
+                         "accepted": int(acc), "judged": int(jd)}
         out.append(row)
     return out
 
@@ -191,6 +200,14 @@ def summarize(rows):
                    "mean_s_per_sweep": float(np.mean([r[name]["s_per_sweep"] for r in rows]))}
     s["learned"]["accept_rate"] = float(sum(r["learned"]["accepted"] for r in rows) /
                                         max(1, sum(r["learned"]["proposals"] for r in rows)))
+    s["learned"]["judged_per_sweep"] = float(sum(r["learned"]["judged"] for r in rows) /
+                                             max(1, sum(r["learned"]["sweeps_to_target"] for r in rows)))
+    # head-to-head: problems where the learned proposer reaches the target in fewer / more
+    # seconds than each other mode
+    for other in ("none", "paper"):
+        faster = sum(1 for r in rows if r["learned"]["seconds_to_target"] < r[other]["seconds_to_target"])
+        s["learned"][f"faster_than_{other}"] = faster
+        s["learned"][f"slower_than_{other}"] = len(rows) - faster
     return s
 
 
@@ -198,7 +215,11 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("cmd", choices=["train", "eval"])
     ap.add_argument("--problems", type=int, default=200)
-    ap.add_argument("--sweeps", type=int, default=12)
+    ap.add_argument("--sweeps", type=int, default=60)
+    ap.add_argument("--stride", type=int, default=5)
+    ap.add_argument("--record", default=None, help="write the training / evaluation record (JSON) here")
+    ap.add_argument("--eval-problems", type=int, default=0, help="after training: evaluate on this many held-out "
+                    "problems, half order 3 and half order 4")
     ap.add_argument("--epochs", type=int, default=60)
     ap.add_argument("--out", default="beta_mlp.npy")
     ap.add_argument("--weights", default="beta_mlp.npy")
@@ -210,12 +231,31 @@ def main():
     b.lib()
     if args.cmd == "train":
         t0 = time.time()
-        F, y = trajectories(problem_set(args.start, args.problems), sweeps=args.sweeps, horizon=args.horizon)
+        F, y = trajectories(problem_set(args.start, args.problems), sweeps=args.sweeps, horizon=args.horizon,
+                            stride=args.stride)
         t1 = time.time()
         w = train(F, y, epochs=args.epochs)
         np.save(args.out, w)
-        print(json.dumps({"states": len(y), "label_counts": np.bincount(y, minlength=b.MLP_CLASSES).tolist(),
-                          "generate_s": t1 - t0, "train_s": time.time() - t1, "train_acc": accuracy(w, F, y)}))
+        rec = {"command": "python -m paper_2503_18759_gb300.learn " + " ".join(__import__("sys").argv[1:]),
+               "data": f"{args.problems} seeded order-3 training problems (sides U{{64..256}}, rank U{{8..32}}, "
+                       f"congruence U[0,0.95], noise log-uniform [1e-4,1e-2]); a labelled state every "
+                       f"{args.stride} sweeps from sweep 2 to {args.sweeps}; label = candidate beta with the highest "
+                       f"fit after {args.horizon} sweeps (ties: the smaller beta); split-precision solver",
+               "states": int(len(y)), "label_counts": np.bincount(y, minlength=b.MLP_CLASSES).tolist(),
+               "generate_s": t1 - t0, "train_s": time.time() - t1, "train_accuracy": accuracy(w, F, y)}
+        if args.eval_problems:
+            half = args.eval_problems // 2
+            rows = evaluate(w, problem_set(10000, half, order=3), max_sweeps=args.max_sweeps)
+            rows += evaluate(w, problem_set(10000, args.eval_problems - half, order=4), max_sweeps=args.max_sweeps)
+            rec["heldout"] = {"problems": f"{half} order-3 and {args.eval_problems - half} order-4 held-out problems "
+                                          f"(seeds apart from training; order-4 sides U{{24..64}}), split path, "
+                                          f"{args.max_sweeps} sweeps each, target f* - 1e-6 with f* the best fit "
+                                          f"of the three modes",
+                              "summary": summarize(rows)}
+        print(json.dumps(rec))
+        if args.record:
+            with open(args.record, "w") as fh:
+                json.dump(rec, fh, indent=1)
     else:
         w = np.load(args.weights).astype(np.float32)
         rows = evaluate(w, problem_set(10000 + args.start, args.problems, order=args.order),

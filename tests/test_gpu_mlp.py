@@ -128,6 +128,93 @@ def test_checkpoint_rollback_reproduces_branches(prec, N):
     assert not np.allclose(a[:2], c)
 
 
+def test_device_proposer_features_and_logits_follow_their_definitions():
+    """The features the device computes after each sweep equal cpqr_mlp_features of the fit / beta
+    history, and its logits equal cpqr_mlp_forward on those features (same bf16 rounding, same
+    accumulation order); the proposal is their first arg max."""
+    prob = _problem(3)
+    X = _t(prob.X)
+    w = mo.init_params(7).astype(np.float32)
+    for prec in (b.PREC_FP64, b.PREC_SPLIT_BF16):
+        opts = b.make_options(tree=b.TREE_RESTRUCTURED, prec=prec, extrap=b.EXTRAP_LEARNED, mlp_weights=w)
+        with b.Decomposition(prob.dims, prob.R, X.data_ptr(), False, prob.A0, opts) as d:
+            for k in range(11):
+                d.sweep(1)
+                fits, betas, rule, act = d.history()
+                f_dev, lg_dev, cls = b.cp_als_qr_mlp_state(d.ctx)
+                f_host = b.cpqr_mlp_features(fits, betas, rule, act)
+                assert np.allclose(f_dev, f_host, rtol=1e-6, atol=1e-7), (k, f_dev, f_host)
+                pd, xd = _t(w), _t(f_dev[None, :].copy())
+                lg = torch.empty((1, b.MLP_CLASSES), dtype=torch.float32, device=DEV)
+                work = torch.empty(b.cpqr_mlp_work_bytes(1), dtype=torch.uint8, device=DEV)
+                b.cpqr_mlp_forward(pd.data_ptr(), xd.data_ptr(), 1, lg.data_ptr(), work.data_ptr())
+                torch.cuda.synchronize()
+                assert np.allclose(lg_dev, lg.cpu().numpy()[0], rtol=1e-5, atol=1e-5)
+                assert cls == int(np.argmax(lg_dev))
+
+
+def _constant_network(c):
+    """A network whose logits are its last-layer biases: it always proposes class c."""
+    p = np.zeros(mo.NPARAMS, dtype=np.float32)
+    p[-mo.C:] = -1.0
+    p[-mo.C + c] = 1.0
+    return p
+
+
+@pytest.mark.parametrize("c", [0, 6])
+def test_judge_protocol_replayed_through_the_public_api(c):
+    """A network that always proposes class c (beta = 0, or beta = 1e-2) on the split path.  The
+    same run replayed by hand through checkpoint / sweep_beta / rollback: a proposal equal to the
+    rule's beta runs as is; otherwise, inside an approval window it runs as is, else both branches
+    run from one checkpoint and the proposal is kept only if its fit is higher; wins double the
+    window (<= 32), losses and fit drops reset it.  Fits and betas agree bit for bit."""
+    prob = _problem(3)
+    X = _t(prob.X)
+    w = _constant_network(c)
+    beta_c = b.cp_als_qr_mlp_beta(c)
+    sweeps = 24
+    opts = b.make_options(tree=b.TREE_RESTRUCTURED, prec=b.PREC_SPLIT_BF16, extrap=b.EXTRAP_LEARNED, mlp_weights=w)
+    with b.Decomposition(prob.dims, prob.R, X.data_ptr(), False, prob.A0, opts) as d:
+        for _ in range(sweeps):
+            d.sweep(1)
+        fits_l, betas_l, _, _ = d.history()
+        st = d.stats()
+    opts = b.make_options(tree=b.TREE_RESTRUCTURED, prec=b.PREC_SPLIT_BF16, extrap=b.EXTRAP_PAPER)
+    judged = wins = 0
+    with b.Decomposition(prob.dims, prob.R, X.data_ptr(), False, prob.A0, opts) as d:
+        approved, window, left = -1, 1, 0
+        for k in range(sweeps):
+            fits, betas, rule, act = d.history()
+            if len(fits) < 2 or beta_c == rule:
+                d.sweep_beta(rule)
+                continue
+            if approved == c and left > 0:
+                left -= 1
+                f = d.sweep_beta(beta_c)
+                if not f >= fits[-1]:
+                    approved, window, left = -1, 1, 0
+                continue
+            judged += 1
+            d.checkpoint()
+            fp = d.sweep_beta(beta_c)
+            d.rollback()
+            fr = d.sweep_beta(rule)
+            if fp > fr:
+                d.rollback()
+                d.sweep_beta(beta_c)
+                wins += 1
+                approved, window = c, min(2 * window, 32)
+                left = window
+            else:
+                approved, window, left = -1, 1, 0
+            d.commit()
+        fits_m, betas_m, _, _ = d.history()
+    assert np.array_equal(betas_l, betas_m), (betas_l, betas_m)
+    assert np.array_equal(fits_l, fits_m)
+    assert st.judged == judged and judged >= 1
+    assert st.accepted == wins + st.preapproved
+
+
 def test_learned_sweep_with_a_random_network_is_judged():
     """An untrained network still runs: every accepted proposal keeps the fit from dropping, a
     rejected one is replaced by the Section 4.2 rule's sweep."""
