@@ -19,7 +19,7 @@
  *    same context returns the same status.  cp_als_qr_strerror() names them.
  *  - The library owns all of its workspaces; the caller owns X and every
  *    buffer it passes.  X is borrowed read-only and must outlive the context.
- *  - Limits: 3 <= N <= 5, 1 <= R <= 32, R <= I_n for every n (compact QR of
+ *  - Limits: 3 <= N <= 6, 1 <= R <= 32, R <= I_n for every n (compact QR of
  *    each factor), prod(I_n) < 2^40.
  */
 #ifndef CPQR_H

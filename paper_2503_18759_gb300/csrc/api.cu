@@ -220,6 +220,7 @@ struct cpqr_ctx {
   // tile loads and its pipeline waits give up after test_wait_ns
   bool test_skip_next_ttm = false;
   unsigned long long test_wait_ns = 0;
+  TcSplitWork tc_split{};  // stream-K workspace of the tensor-core TTMs (all on st)
 
   ~cpqr_ctx() {
     if (st) cudaStreamSynchronize(st);
@@ -417,8 +418,8 @@ cpqr_status run_ttm(cpqr_ctx* ctx, const Op& op) {
       const int reserve = (ctx->z_pending && !ctx->gram) ? qr_cluster_sms() : 0;
       const bool skip = ctx->test_skip_next_ttm;
       ctx->test_skip_next_ttm = false;
-      CK(launch_ttm_tc(shi, slo, ctx->Qt[k], ctx->Rp, ctx->Kp[k], of, P, K, S, R, ctx->dstatus, st, reserve, ohi,
-                       olo, skip ? ctx->test_wait_ns : 0, skip ? 1 : 0));
+      CK(launch_ttm_tc(shi, slo, ctx->Qt[k], ctx->Rp, ctx->Kp[k], of, P, K, S, R, ctx->dstatus, st, ctx->tc_split,
+                       reserve, ohi, olo, skip ? ctx->test_wait_ns : 0, skip ? 1 : 0));
     } else {
       if (!sb.has_f32) return fail(ctx, CPQR_EINVAL);  // not produced for a CUDA-core consumer
       float* o32 = of;
@@ -1247,9 +1248,11 @@ cpqr_status cp_als_qr_init(cpqr_ctx** out, int32_t N, const int64_t* dims, int32
   CK(cudaMemsetAsync(ctx->fit_terms, 0, 2 * sizeof(double), st));
   CK(cudaMemsetAsync(ctx->lambda, 0, R * sizeof(double), st));
 
-  // Khatri-Rao row plan (identical for every mode: N-1 triangles of size R).
+  // Khatri-Rao row plans: of the N-1 triangles (identical for every mode; only an order-3 tensor's
+  // two-triangle product uses it directly, higher orders go through two-triangle levels) and of a
+  // two-triangle product.
   {
-    std::vector<int32_t> perm = krp_perm(N - 1, R);
+    std::vector<int32_t> perm = krp_perm(N == 3 ? N - 1 : 1, R);
     CK(ctx->alloc(&ctx->d_perm, perm.size()));
     CK(cudaMemcpyAsync(ctx->d_perm, perm.data(), perm.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     ctx->zplan.m = N - 1;
@@ -1298,6 +1301,13 @@ cpqr_status cp_als_qr_init(cpqr_ctx** out, int32_t N, const int64_t* dims, int32
     }
     CK(ctx->alloc(&ctx->Xhi, nX));
     CK(ctx->alloc(&ctx->Xlo, nX));
+    int nsm = 0, dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    ctx->tc_split.ctas = std::max(nsm, 1);
+    CK(ctx->alloc(&ctx->tc_split.part, ttm_tc_split_floats(ctx->tc_split.ctas)));
+    CK(ctx->alloc(&ctx->tc_split.cnt, (size_t)ctx->tc_split.ctas));
+    CK(cudaMemsetAsync(ctx->tc_split.cnt, 0, ctx->tc_split.ctas * sizeof(int), st));
     CK(launch_split_x((const float*)X_dev, ctx->Xhi, ctx->Xlo, nX, st));
   }
   // ||X||^2 (precomputed once, Section 4.1).
@@ -1646,19 +1656,27 @@ cpqr_status cpqr_ttm(const void* T_dev, int32_t nd, const int64_t* tdims, int32_
       const int64_t n = P * K * S;
       __nv_bfloat16 *xh = nullptr, *xl = nullptr, *qt = nullptr;
       unsigned int* ds = nullptr;
+      int nsm = 0, dev = 0;
+      if (cudaGetDevice(&dev) != cudaSuccess ||
+          cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return CPQR_ECUDA;
+      TcSplitWork sk{nullptr, nullptr, std::max(nsm, 1)};
       if (cudaMalloc(&xh, n * 2) != cudaSuccess || cudaMalloc(&xl, n * 2) != cudaSuccess ||
-          cudaMalloc(&qt, (size_t)2 * Rp * Kp * 2) != cudaSuccess || cudaMalloc(&ds, 4) != cudaSuccess) {
-        cudaFree(xh); cudaFree(xl); cudaFree(qt); cudaFree(ds);
+          cudaMalloc(&qt, (size_t)2 * Rp * Kp * 2) != cudaSuccess || cudaMalloc(&ds, 4) != cudaSuccess ||
+          cudaMalloc(&sk.part, ttm_tc_split_floats(sk.ctas) * 4) != cudaSuccess ||
+          cudaMalloc(&sk.cnt, (size_t)sk.ctas * 4) != cudaSuccess) {
+        cudaFree(xh); cudaFree(xl); cudaFree(qt); cudaFree(ds); cudaFree(sk.part); cudaFree(sk.cnt);
         return CPQR_ENOMEM;
       }
       e = cudaMemsetAsync(ds, 0, 4, st);
+      if (e == cudaSuccess) e = cudaMemsetAsync(sk.cnt, 0, (size_t)sk.ctas * 4, st);
       if (e == cudaSuccess) e = launch_split_x((const float*)T_dev, xh, xl, n, st);
       if (e == cudaSuccess) e = launch_split_q((const double*)Q_dev, K, R, qt, Rp, Kp, st);
-      if (e == cudaSuccess) e = launch_ttm_tc(xh, xl, qt, Rp, Kp, (float*)out_dev, P, K, S, R, ds, st);
+      if (e == cudaSuccess) e = launch_ttm_tc(xh, xl, qt, Rp, Kp, (float*)out_dev, P, K, S, R, ds, st, sk);
       unsigned int hs = 0;
       if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, ds, 4, cudaMemcpyDeviceToHost, st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-      cudaFree(xh); cudaFree(xl); cudaFree(qt); cudaFree(ds);
+      cudaFree(xh); cudaFree(xl); cudaFree(qt); cudaFree(ds); cudaFree(sk.part); cudaFree(sk.cnt);
       if (e == cudaSuccess && hs) return status_of_device_word(hs);
       break;
     }

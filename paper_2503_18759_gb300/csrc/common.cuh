@@ -7,7 +7,7 @@
 #include "cpqr.h"
 
 #define CPQR_MAXR 32
-#define CPQR_MAXN 5
+#define CPQR_MAXN 6
 
 // Device-side error flags (bitwise OR into ctx status word).
 #define CPQR_DEV_SINGULAR 1u
@@ -76,9 +76,18 @@ cudaError_t launch_split_x(const float* X, __nv_bfloat16* Xhi, __nv_bfloat16* Xl
 // S % 8 == 0 (MN-major) or S == 1 with K % 8 == 0 (K-major); K <= 512.  Returns
 // cudaErrorNotSupported if the shape is outside the kernel's range.
 // reserve_sms: SMs the persistent grid leaves free for concurrent work (a cluster QR).
+// Workspace of the tensor-core TTM's stream-K split: ttm_tc_split_floats(ctas) floats of partial
+// tiles and ctas zeroed counters (the kernel leaves them zero); launches that share one must run
+// in stream order.
+struct TcSplitWork {
+  float* part;
+  int* cnt;
+  int ctas;
+};
+size_t ttm_tc_split_floats(int ctas);
 cudaError_t launch_ttm_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo, const __nv_bfloat16* Qt,
                           int Rp, int64_t Kp, float* out, int64_t P, int64_t K, int64_t S, int R,
-                          unsigned int* dev_status, cudaStream_t st, int reserve_sms = 0,
+                          unsigned int* dev_status, cudaStream_t st, const TcSplitWork& sk, int reserve_sms = 0,
                           __nv_bfloat16* out_hi = nullptr, __nv_bfloat16* out_lo = nullptr,
                           unsigned long long wait_ns = 0, int skip_x_loads = 0);
 bool ttm_tc_supported(int64_t P, int64_t K, int64_t S, int R);

@@ -136,6 +136,8 @@ CASES = [
     ("order3_r32", dict(dims=[40, 36, 33], R=32, c=0.5, eta=1e-3, dtype=np.float64), b.TREE_RESTRUCTURED, b.EXTRAP_FIXED, 0.001, 5),
     ("order3_r1", dict(dims=[9, 7, 8], R=1, c=None, eta=1e-3, dtype=np.float64), b.TREE_RESTRUCTURED, b.EXTRAP_NONE, 0.0, 4),
     ("order3_r2_square", dict(dims=[2, 5, 3], R=2, c=0.4, eta=1e-3, dtype=np.float64), b.TREE_STANDARD, b.EXTRAP_FIXED, 0.01, 4),
+    ("order6_rest", dict(dims=[5, 6, 4, 5, 4, 5], R=3, c=None, eta=1e-3, dtype=np.float64), b.TREE_RESTRUCTURED, b.EXTRAP_FIXED, 0.01, 6),
+    ("order6_std", dict(dims=[6, 5, 5, 4, 6, 4], R=4, c=0.3, eta=1e-3, dtype=np.float32), b.TREE_STANDARD, b.EXTRAP_NONE, 0.0, 4),
 ]
 
 
@@ -251,6 +253,7 @@ MIXED = [
     ("mixed_order3", dict(dims=[40, 36, 33], R=8, c=0.5, eta=1e-2), b.TREE_RESTRUCTURED, b.EXTRAP_FIXED, 0.01, 8),
     ("mixed_order4", dict(dims=[14, 12, 13, 11], R=5, c=0.3, eta=1e-2), b.TREE_RESTRUCTURED, b.EXTRAP_NONE, 0.0, 6),
     ("mixed_order5", dict(dims=[8, 7, 9, 8, 7], R=4, c=None, eta=1e-2), b.TREE_STANDARD, b.EXTRAP_FIXED, 0.01, 5),
+    ("mixed_order6", dict(dims=[8, 6, 8, 5, 6, 8], R=4, c=None, eta=1e-2), b.TREE_RESTRUCTURED, b.EXTRAP_NONE, 0.0, 5),
 ]
 
 

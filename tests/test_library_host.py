@@ -51,7 +51,8 @@ def _oracle_ops(dims, R, tree, sweeps):
 
 @pytest.mark.parametrize("tree", [0, 1, 2])
 @pytest.mark.parametrize("dims,R", [((400, 400, 400), 32), ((5, 7, 11), 3), ((128,) * 4, 24), ((5, 7, 11, 13), 3),
-                                    ((48,) * 5, 16), ((9, 4, 7, 5, 6), 3), ((60, 60, 60), 5), ((10, 30, 20), 4)])
+                                    ((48,) * 5, 16), ((9, 4, 7, 5, 6), 3), ((60, 60, 60), 5), ((10, 30, 20), 4),
+                                    ((25,) * 6, 8), ((5, 4, 6, 3, 5, 4), 2)])
 def test_schedule_identical_to_oracle(L, tree, dims, R):
     sweeps = 9
     ops, flops = b.cp_als_qr_schedule(dims, R, tree, sweeps)

@@ -35,10 +35,7 @@ def test_standard_tree_per_sweep_tables_1_and_4():
                   ((2, 3, 4), 2): 1, ((3, 4), 3): 1}
 
 
-@pytest.mark.parametrize("tree", ["none", "standard", "restructured"])
-def test_corollary1_order5(tree):
-    cor = GOLD["corollary1"]
-    N = cor["N"]
+def _corollary1_terms(N, tree):
     counts = o.schedule_monomial_counts([9] * N, 3, TREES[tree], 3)
     got = {"IN_R": 0, "IN1_R2": 0, "I2_RN1": 0}
     for (F, p), c in counts.items():
@@ -48,12 +45,30 @@ def test_corollary1_order5(tree):
             got["IN1_R2"] += 2 * c
         elif len(F) == 2:
             got["I2_RN1"] += 2 * c
-    assert got == cor[tree]
+    return got
+
+
+@pytest.mark.parametrize("tree", ["none", "standard", "restructured"])
+def test_corollary1_order5(tree):
+    cor = GOLD["corollary1"]
+    assert _corollary1_terms(cor["N"], tree) == cor[tree]
+
+
+@pytest.mark.parametrize("tree", ["none", "standard", "restructured"])
+def test_corollary1_order6(tree):
+    """Corollary 1 holds for every order N > 4: over the first three sweeps the coefficients of
+    I^N R, I^(N-1) R^2 and I^2 R^(N-1) are 6N, 6N, 6N (no tree), 12, 18, 6N (dimension tree) and
+    8, 14, 6N (restructured tree).  At N = 6: 36, 36, 36 / 12, 18, 36 / 8, 14, 36."""
+    N = 6
+    want = {"none": {"IN_R": 6 * N, "IN1_R2": 6 * N, "I2_RN1": 6 * N},
+            "standard": {"IN_R": 12, "IN1_R2": 18, "I2_RN1": 6 * N},
+            "restructured": {"IN_R": 8, "IN1_R2": 14, "I2_RN1": 6 * N}}
+    assert _corollary1_terms(N, tree) == want[tree]
 
 
 def test_restructured_cut_is_one_third_over_three_sweeps_and_half_asymptotically():
     """33% fewer dominant-term flops over three sweeps (Cor. 1); 2(K+1) vs 4K full TTMs over K sweeps."""
-    for N in (3, 4, 5):
+    for N in (3, 4, 5, 6):
         dims = [8] * N
         full = {}
         for tree in (o.TREE_STANDARD, o.TREE_RESTRUCTURED):
@@ -69,12 +84,12 @@ def test_restructured_cut_is_one_third_over_three_sweeps_and_half_asymptotically
         assert all(v == 2 for v in full[o.TREE_STANDARD])
 
 
-@pytest.mark.parametrize("N,tree", [(N, t) for N in (3, 4, 5) for t in (0, 1, 2)])
+@pytest.mark.parametrize("N,tree", [(N, t) for N in (3, 4, 5, 6) for t in (0, 1, 2)])
 def test_every_scheduled_leaf_equals_direct_multi_ttm(N, tree):
     """Every update's leaf equals X x_{k != n} Q_k^T with the latest Q_k (brute force),
     over enough sweeps to leave the explicit order-4 sweeps and reach the periodic regime."""
     g = np.random.default_rng(N * 7 + tree)
-    dims = [4, 5, 3, 4, 3][:N]
+    dims = [4, 5, 3, 4, 3, 3][:N]
     R = 2
     X = g.standard_normal(dims)
     A0 = [g.standard_normal((d, R)) for d in dims]
@@ -82,7 +97,7 @@ def test_every_scheduled_leaf_equals_direct_multi_ttm(N, tree):
 
 
 def test_schedule_frees_every_node_it_creates_and_keeps_memory_bounded():
-    for N in (3, 4, 5):
+    for N in (3, 4, 5, 6):
         for tree in (0, 1, 2):
             s = o.Schedule([6] * N, 2, tree)
             live_max = 0
@@ -120,7 +135,7 @@ def test_mode_orders_order3_follow_section_3_1():
     assert sources[1:4] == [(1, 3), (2, 3), (1, 3)]
 
 
-@pytest.mark.parametrize("N", [3, 4, 5])
+@pytest.mark.parametrize("N", [3, 4, 5, 6])
 @pytest.mark.parametrize("tree", [o.TREE_NONE, o.TREE_STANDARD, o.TREE_RESTRUCTURED])
 def test_every_sweep_updates_each_mode_once_and_no_update_is_a_no_op(N, tree):
     """Alternating updates (Section 3.1): each sweep updates every mode exactly once, and no update
