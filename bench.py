@@ -391,7 +391,46 @@ def extras(args, prob, X, dev, b):
                             "qr_fallbacks": int(d.stats().qr_fallbacks)}
     res["qr_routes"] = routes
     res["other_workloads"] = other_workloads(b, dev)
+    res["e1_shapes"] = e1_shapes(b, dev)
     return res
+
+
+E1_SHAPES = [[700] * 3, [150] * 4, [50] * 5, [25] * 6]
+
+
+def e1_shapes(b, dev, ranks=(8, 16, 32), sweeps=10):
+    """The paper's per-iteration breakdown over orders 3 to 6 (700^3, 150^4, 50^5, 25^6) and rank:
+    split-precision ALS-QR-BRE, ms per sweep (CUDA events, after 3 warm-up sweeps) and the device
+    time per bucket (per-launch events, a second run of the same sweeps).  Seeded synthetic tensors:
+    N(0,1) rank-R factors, 1e-3 noise."""
+    import torch
+    from paper_2503_18759_gb300 import inputs
+    out = {}
+    for dims in E1_SHAPES:
+        for R in ranks:
+            if R > dims[0]:
+                continue
+            name = "x".join(str(d) for d in dims) + f"_r{R}"
+            prob = inputs.make_problem_device(name, dims, R, seed=5, c=None, eta=1e-3, device=str(dev))
+            o = b.make_options(tree=b.TREE_RESTRUCTURED, prec=b.PREC_SPLIT_BF16, extrap=b.EXTRAP_PAPER)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with b.Decomposition(prob.dims, prob.R, prob.X.data_ptr(), False, prob.A0, o) as d:
+                d.sweep(3)
+                torch.cuda.synchronize()
+                e0.record()
+                d.sweep(sweeps)
+                e1.record()
+                torch.cuda.synchronize()
+                d.set_timing(True)
+                d.sweep(sweeps)
+                st = d.stats()
+                d.set_timing(False)
+            out[name] = {"ms_per_sweep": e0.elapsed_time(e1) / sweeps,
+                         "buckets_ms_per_sweep": {nm: st.ms_bucket[i] / sweeps for i, nm in enumerate(b.BUCKETS)},
+                         "qr_fallbacks": int(st.qr_fallbacks)}
+            del prob
+            torch.cuda.empty_cache()
+    return out
 
 
 def other_workloads(b, dev):

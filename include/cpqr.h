@@ -76,8 +76,10 @@ typedef enum {
                              rule's beta (beta = 0 included) is judged: from one checkpoint both
                              the proposal's and the rule's sweep run and the proposal is kept only
                              if its fit is higher; the rule is the fallback.  A winning proposal
-                             stays approved for 1, 2, 4, ... 32 further sweeps (doubling on
-                             consecutive wins) while the fit does not drop */
+                             stays approved for 2, 4, ... 32 further sweeps (doubling on
+                             consecutive wins) while the fit does not drop; after a losing one the
+                             rule runs unjudged for 1, 2, ... 32 sweeps (doubling on consecutive
+                             losses) */
 } cpqr_extrap;
 
 /* How a sweep computes the QR of a two-triangle Khatri-Rao product and the factor QRs. */
@@ -130,6 +132,7 @@ typedef struct {
                               with the last-updated triangle after that update */
   int64_t judged;          /* learned proposals judged against the rule's sweep (two sweeps each) */
   int64_t preapproved;     /* learned proposals run within an approval window */
+  int64_t deferred;        /* learned proposals set aside (the rule ran) within a hold after a loss */
 } cpqr_stats;
 
 /* Turn per-launch CUDA-event timing on (1) or off (0); resets the bucket times. */

@@ -46,7 +46,8 @@ class Stats(C.Structure):
                 ("last_fit", C.c_double), ("beta", C.c_double), ("proposals", C.c_int64),
                 ("accepted", C.c_int64), ("launches", C.c_int64), ("ms_bucket", C.c_double * NBUCKETS),
                 ("n_bucket", C.c_int64 * NBUCKETS), ("qr_fallbacks", C.c_int64),
-                ("krp_split", C.c_int64), ("judged", C.c_int64), ("preapproved", C.c_int64)]
+                ("krp_split", C.c_int64), ("judged", C.c_int64), ("preapproved", C.c_int64),
+                ("deferred", C.c_int64)]
 
 
 _lib = None

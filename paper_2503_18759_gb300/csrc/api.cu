@@ -139,7 +139,9 @@ struct cpqr_ctx {
   // judging: a proposal that beat the rule's sweep from the same checkpoint stays approved for
   // approve_left more sweeps while the fit does not drop; each win doubles the window (<= 32)
   int approved_class = -1, approve_window = 1, approve_left = 0;
-  int64_t judged = 0, preapproved = 0;
+  // after a loss the rule runs unjudged for hold_left sweeps; consecutive losses double the hold
+  int hold_window = 1, hold_left = 0;
+  int64_t judged = 0, preapproved = 0, deferred = 0;
   double* A[CPQR_MAXN] = {};
   double* Q[CPQR_MAXN] = {};
   double* Rf[CPQR_MAXN] = {};
@@ -1012,8 +1014,11 @@ void mlp_features(const double* fits, const double* betas, int n, double rule_be
 // runs as is.  Any other proposal, beta = 0 included, is judged: from one checkpoint the proposal's
 // sweep and the rule's sweep both run, and the proposal is kept only if its fit is higher, else the
 // rule's sweep stands (the rule is the fallback).  A proposal that won stays approved for the next
-// approve_window sweeps (1, 2, 4, ... 32 after consecutive wins) as long as the fit does not drop;
-// a drop or a loss ends the approval, and the next differing proposal is judged again.
+// approve_window sweeps (2, 4, ... 32 after consecutive wins) as long as the fit does not drop; a
+// drop ends the approval.  After a loss the rule runs for hold_window sweeps (1, 2, ... 32 after
+// consecutive losses) with the proposals deferred unjudged; then the next differing proposal is
+// judged again.  Judging costs two sweeps, so the windows keep it to a few per cent of the sweeps
+// once either side keeps winning.
 cpqr_status learned_sweep(cpqr_ctx* ctx, double* fit_out) {
   const double rule = rule_beta_next(ctx);
   const int cls = ctx->next_class;
@@ -1021,6 +1026,11 @@ cpqr_status learned_sweep(cpqr_ctx* ctx, double* fit_out) {
   const double prop = kMlpBetas[cls];
   if (prop == rule) return one_sweep(ctx, fit_out, &rule);
   ++ctx->proposals;
+  if (ctx->hold_left > 0) {  // a recent loss: the rule runs, the proposal is deferred unjudged
+    --ctx->hold_left;
+    ++ctx->deferred;
+    return one_sweep(ctx, fit_out, &rule);
+  }
   double f = 0.0;
   if (cls == ctx->approved_class && ctx->approve_left > 0) {
     --ctx->approve_left;
@@ -1053,11 +1063,14 @@ cpqr_status learned_sweep(cpqr_ctx* ctx, double* fit_out) {
     ctx->approved_class = cls;
     ctx->approve_window = std::min(2 * ctx->approve_window, 32);
     ctx->approve_left = ctx->approve_window;
+    ctx->hold_window = 1;
     f = fp;
   } else {
     ctx->approved_class = -1;
     ctx->approve_window = 1;
     ctx->approve_left = 0;
+    ctx->hold_left = ctx->hold_window;
+    ctx->hold_window = std::min(2 * ctx->hold_window, 32);
     f = fr;
   }
   checkpoint_drop(ctx, 1);
@@ -1424,6 +1437,7 @@ cpqr_status cp_als_qr_stats(cpqr_ctx* ctx, cpqr_stats* out) {
   out->accepted = ctx->accepted;
   out->judged = ctx->judged;
   out->preapproved = ctx->preapproved;
+  out->deferred = ctx->deferred;
   out->launches = ctx->launches;
   out->krp_split = ctx->n_split;
   for (int b = 0; b < CPQR_NBUCKETS; ++b) {

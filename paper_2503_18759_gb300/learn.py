@@ -223,7 +223,7 @@ def main():
     ap.add_argument("--epochs", type=int, default=60)
     ap.add_argument("--out", default="beta_mlp.npy")
     ap.add_argument("--weights", default="beta_mlp.npy")
-    ap.add_argument("--order", type=int, default=3)
+    ap.add_argument("--order", type=int, default=3, help="eval: 3 or 4, or 0 for half of each")
     ap.add_argument("--start", type=int, default=0)
     ap.add_argument("--horizon", type=int, default=3)
     ap.add_argument("--max-sweeps", type=int, default=120)
@@ -258,9 +258,28 @@ def main():
                 json.dump(rec, fh, indent=1)
     else:
         w = np.load(args.weights).astype(np.float32)
-        rows = evaluate(w, problem_set(10000 + args.start, args.problems, order=args.order),
-                        max_sweeps=args.max_sweeps)
-        print(json.dumps(summarize(rows)))
+        if args.order == 0:  # half order 3, half order 4 (the held-out set of the training record)
+            half = args.problems // 2
+            rows = evaluate(w, problem_set(10000 + args.start, half, order=3), max_sweeps=args.max_sweeps)
+            rows += evaluate(w, problem_set(10000 + args.start, args.problems - half, order=4),
+                             max_sweeps=args.max_sweeps)
+        else:
+            rows = evaluate(w, problem_set(10000 + args.start, args.problems, order=args.order),
+                            max_sweeps=args.max_sweeps)
+        summary = summarize(rows)
+        print(json.dumps(summary))
+        if args.record:  # update the held-out part of an existing training record
+            with open(args.record) as fh:
+                rec = json.load(fh)
+            rec["heldout"] = {"problems": f"{args.problems} held-out problems (order " +
+                                          ("3 and 4, half each" if args.order == 0 else str(args.order)) +
+                                          f"; order-4 sides U{{24..64}}), split path, {args.max_sweeps} sweeps each, "
+                                          "target f* - 1e-6 with f* the best fit of the three modes",
+                              "command": "python -m paper_2503_18759_gb300.learn " +
+                                         " ".join(__import__("sys").argv[1:]),
+                              "summary": summary}
+            with open(args.record, "w") as fh:
+                json.dump(rec, fh, indent=1)
 
 
 if __name__ == "__main__":

@@ -165,9 +165,11 @@ def _constant_network(c):
 def test_judge_protocol_replayed_through_the_public_api(c):
     """A network that always proposes class c (beta = 0, or beta = 1e-2) on the split path.  The
     same run replayed by hand through checkpoint / sweep_beta / rollback: a proposal equal to the
-    rule's beta runs as is; otherwise, inside an approval window it runs as is, else both branches
-    run from one checkpoint and the proposal is kept only if its fit is higher; wins double the
-    window (<= 32), losses and fit drops reset it.  Fits and betas agree bit for bit."""
+    rule's beta runs as is; within a hold after a loss the rule runs; inside an approval window the
+    proposal runs as is; else both branches run from one checkpoint and the proposal is kept only
+    if its fit is higher.  Wins double the approval window (<= 32) and reset the hold; losses
+    reset the approval and start a hold that doubles on consecutive losses (<= 32); a fit drop ends
+    an approval.  Fits and betas agree bit for bit."""
     prob = _problem(3)
     X = _t(prob.X)
     w = _constant_network(c)
@@ -183,9 +185,14 @@ def test_judge_protocol_replayed_through_the_public_api(c):
     judged = wins = 0
     with b.Decomposition(prob.dims, prob.R, X.data_ptr(), False, prob.A0, opts) as d:
         approved, window, left = -1, 1, 0
+        hold_window, hold_left = 1, 0
         for k in range(sweeps):
             fits, betas, rule, act = d.history()
             if len(fits) < 2 or beta_c == rule:
+                d.sweep_beta(rule)
+                continue
+            if hold_left > 0:
+                hold_left -= 1
                 d.sweep_beta(rule)
                 continue
             if approved == c and left > 0:
@@ -205,8 +212,11 @@ def test_judge_protocol_replayed_through_the_public_api(c):
                 wins += 1
                 approved, window = c, min(2 * window, 32)
                 left = window
+                hold_window = 1
             else:
                 approved, window, left = -1, 1, 0
+                hold_left = hold_window
+                hold_window = min(2 * hold_window, 32)
             d.commit()
         fits_m, betas_m, _, _ = d.history()
     assert np.array_equal(betas_l, betas_m), (betas_l, betas_m)
