@@ -19,8 +19,11 @@
  *    same context returns the same status.  cp_als_qr_strerror() names them.
  *  - The library owns all of its workspaces; the caller owns X and every
  *    buffer it passes.  X is borrowed read-only and must outlive the context.
- *  - Limits: 3 <= N <= 6, 1 <= R <= 32, R <= I_n for every n (compact QR of
- *    each factor), prod(I_n) < 2^40.
+ *  - Limits: 3 <= N <= 6, 1 <= R <= 192, R <= I_n for every n (compact QR of
+ *    each factor), prod(I_n) < 2^40.  Ranks up to 32 run the warp-per-factor kernels;
+ *    ranks 33..192 (the high-rank regime) run the wide-rank path: Cholesky QRs
+ *    (float-float Cholesky of the Gram, FP64 substitution, a second pass when the first
+ *    leaves |Q^T Q - I| > 1e-8, a first-order correction) and column-tiled kernels.
  */
 #ifndef CPQR_H
 #define CPQR_H
@@ -77,7 +80,8 @@ typedef enum {
                              the proposal's and the rule's sweep run and the proposal is kept only
                              if its fit is higher; the rule is the fallback.  A winning proposal
                              stays approved for 2, 4, ... 32 further sweeps (doubling on
-                             consecutive wins) while the fit does not drop; after a losing one the
+                             consecutive wins) while the fit does not drop by more than 1e-7;
+                             after a losing one the
                              rule runs unjudged for 1, 2, ... 32 sweeps (doubling on consecutive
                              losses) */
 } cpqr_extrap;
@@ -223,7 +227,8 @@ cpqr_status cpqr_ttm(const void* T_dev, int32_t nd, const int64_t* tdims, int32_
                      const void* Q_dev, int32_t R, void* out_dev, int32_t dtype, void* stream);
 
 /* Compact QR of an M x R FP64 matrix (row-major, device) by Householder reflections with
- * diag(R) > 0 (Alg. 2 line 10): Q_dev (M x R) and R_dev (R x R) receive the factors.  Returns
+ * diag(R) > 0 (Alg. 2 line 10): Q_dev (M x R) and R_dev (R x R) receive the factors.  For
+ * 32 < R <= 192 the wide-rank path's Cholesky QR gives the same factors (to rounding).  Returns
  * CPQR_ESINGULAR for a zero column (exactly zero Householder norm) and CPQR_ETIMEOUT if a bounded
  * wait of the cluster kernel gave up; Q and R then hold partial results.  Synchronises the
  * stream. */
@@ -254,7 +259,8 @@ cpqr_status cpqr_house_qr_noalloc(const double* A_dev, int64_t M, int32_t R, dou
  * matrices (Alg. 2 lines 3-4), rows (r_1, ..., r_m) with r_m fastest: Rs_dev holds the m
  * triangles back to back (device, FP64).  Q0_dev (R^m x R) and R0_dev (R x R) receive the
  * factors, diag(R0) > 0, by the guarded Gram route (see cpqr_prec) for m >= 2, whose fallback is
- * the Householder staircase QR (nested for m >= 3).  CPQR_ESINGULAR / CPQR_ETIMEOUT as for
+ * the Householder staircase QR (nested for m >= 3); for 32 < R <= 192 by the wide-rank Cholesky
+ * QR (the Gram is the Hadamard product of the triangles' Grams).  CPQR_ESINGULAR / CPQR_ETIMEOUT as for
  * cpqr_house_qr.  Synchronises the stream. */
 cpqr_status cpqr_krp_qr(const double* Rs_dev, int32_t m, int32_t R, double* Q0_dev,
                         double* R0_dev, void* stream);

@@ -104,6 +104,12 @@ struct cpqr_ctx {
   std::vector<int64_t> dims;
   int tree = 2, prec = 0, extrap = 1;
   bool gram = true;  // Gram QR route (cpqr_qr_route)
+  // wide-rank path (32 < R <= 192): Cholesky QRs, CUDA-core TTMs and V / finish kernels that tile the
+  // columns; workspaces of the factor QR (main stream) and of the Khatri-Rao QR (side stream)
+  bool wide = false;
+  double* wq_main = nullptr;
+  double* wq_side = nullptr;
+  double* wrows = nullptr;  // I x (R + 2): rows of A^ and per-row fit terms
   double alpha = kAlphaDefault, beta_fixed = 0.0;
   cudaStream_t st = nullptr;
   cudaStream_t st2 = nullptr;      // side stream: Khatri-Rao QR overlapped with the TTM chain
@@ -222,7 +228,6 @@ struct cpqr_ctx {
   // tile loads and its pipeline waits give up after test_wait_ns
   bool test_skip_next_ttm = false;
   unsigned long long test_wait_ns = 0;
-  TcSplitWork tc_split{};  // stream-K workspace of the tensor-core TTMs (all on st)
 
   ~cpqr_ctx() {
     if (st) cudaStreamSynchronize(st);
@@ -387,19 +392,31 @@ cpqr_status run_ttm(cpqr_ctx* ctx, const Op& op) {
       for (int q = j + 1; q < ctx->N; ++q) Sj *= od[q];
       if (!ttm_tc_supported(Pj, od[j], Sj, R)) cuda_core_consumer = true;
     }
-    need_split = nfree >= 2;
-    need_f32 = nfree < 2 || cuda_core_consumer;
+    need_split = nfree >= 2 && !ctx->wide;
+    need_f32 = nfree < 2 || cuda_core_consumer || ctx->wide;
   }
   const size_t bytes = split ? split_node_bytes(n_out, need_f32, need_split) : (size_t)n_out * es;
   void* out = nullptr;
   CK(ctx->pool.get(bytes, &out));
   cudaStream_t st = ctx->st;
   Timed tm(ctx, sb.is_x ? CPQR_BUCKET_TTM_FULL : CPQR_BUCKET_TTM_DEEP, 1);
-  if (!split) {
+  if (!split && ctx->wide) {
+    if (sb.is_x && !ctx->x64)
+      CK((launch_ttm_wide<float, double, double, double>((const float*)sb.p, ctx->Q[k], (double*)out, P, K, S, R,
+                                                         st)));
+    else
+      CK((launch_ttm_wide<double, double, double, double>((const double*)sb.p, ctx->Q[k], (double*)out, P, K, S, R,
+                                                          st)));
+  } else if (!split) {
     if (sb.is_x && !ctx->x64)
       CK(launch_ttm<float, double, double>((const float*)sb.p, ctx->Q[k], (double*)out, P, K, S, R, st));
     else
       CK(launch_ttm<double, double, double>((const double*)sb.p, ctx->Q[k], (double*)out, P, K, S, R, st));
+  } else if (ctx->wide) {
+    // the CUDA-core FP32 TTM from FP32 nodes (every wide-path node keeps its FP32 copy)
+    if (!sb.has_f32) return fail(ctx, CPQR_EINVAL);
+    CK((launch_ttm_wide<float, float, float, float>((const float*)sb.p, ctx->Qf[k], static_cast<float*>(out), P, K,
+                                                     S, R, st)));
   } else {
     __nv_bfloat16 *ohi = nullptr, *olo = nullptr;
     if (need_split) split_views(out, n_out, need_f32, &ohi, &olo);
@@ -420,8 +437,8 @@ cpqr_status run_ttm(cpqr_ctx* ctx, const Op& op) {
       const int reserve = (ctx->z_pending && !ctx->gram) ? qr_cluster_sms() : 0;
       const bool skip = ctx->test_skip_next_ttm;
       ctx->test_skip_next_ttm = false;
-      CK(launch_ttm_tc(shi, slo, ctx->Qt[k], ctx->Rp, ctx->Kp[k], of, P, K, S, R, ctx->dstatus, st, ctx->tc_split,
-                       reserve, ohi, olo, skip ? ctx->test_wait_ns : 0, skip ? 1 : 0));
+      CK(launch_ttm_tc(shi, slo, ctx->Qt[k], ctx->Rp, ctx->Kp[k], of, P, K, S, R, ctx->dstatus, st, reserve, ohi,
+                       olo, skip ? ctx->test_wait_ns : 0, skip ? 1 : 0));
     } else {
       if (!sb.has_f32) return fail(ctx, CPQR_EINVAL);  // not produced for a CUDA-core consumer
       float* o32 = of;
@@ -635,7 +652,10 @@ cpqr_status launch_z(cpqr_ctx* ctx, int n, int after) {
   CK(cudaStreamWaitEvent(ctx->st2, ctx->ev_ready, 0));
   {
     Timed tm(ctx, CPQR_BUCKET_Q0, 1, ctx->st2);
-    if (split) {
+    if (ctx->wide) {
+      CK(launch_wide_qr(nullptr, ipow(ctx->R, m), ctx->R, tri.p, m, ctx->Q0, ctx->Q0f, ctx->R0, ctx->wq_side,
+                        ctx->dstatus, ctx->st2));
+    } else if (split) {
       if (!(ctx->zchol_mode == n && ctx->zchol_split)) {
         CK(launch_krp_chol(z_grams(ctx, n), m, ctx->R, ctx->zg_work, ctx->st2, 0, gram_flag(ctx->wg_work)));
         ctx->launches += 1;
@@ -704,6 +724,24 @@ cpqr_status run_update(cpqr_ctx* ctx, int n, int leaf, double beta, int next_mod
     else
       CK(launch_leaf_v<float, float>((const float*)lb.p, P, I, S, ctx->Q0f, ctx->Q0fprev[n], R, C,
                                      (float*)ctx->v_work, &nparts, st));
+  }
+  if (ctx->wide) {
+    // Lines 8-10 on the wide path: eq. 19, the R0^{-T} solve, lambda, then the factor's Cholesky QR
+    Timed tm(ctx, CPQR_BUCKET_QR, 12);
+    const double b = ext ? beta : 0.0;
+    if (fp64)
+      CK(launch_wide_finish<double>(ctx->v_work, nparts, I, C, R, ctx->R0, b, ctx->alpha, ctx->A[n], ctx->lambda,
+                                    ctx->fit_terms, ctx->wrows, ctx->dstatus, st));
+    else
+      CK(launch_wide_finish<float>((const float*)ctx->v_work, nparts, I, C, R, ctx->R0, b, ctx->alpha, ctx->A[n],
+                                   ctx->lambda, ctx->fit_terms, ctx->wrows, ctx->dstatus, st));
+    CK(launch_wide_qr(ctx->A[n], I, R, nullptr, 0, ctx->Q[n], ctx->Qf[n], ctx->Rf[n], ctx->wq_main, ctx->dstatus,
+                      st));
+    std::swap(ctx->Q0, ctx->Q0prev[n]);
+    std::swap(ctx->Q0f, ctx->Q0fprev[n]);
+    ctx->has_prev[n] = true;
+    ctx->last_updated = n;
+    return CPQR_OK;
   }
   // Lines 8-10: eq. 19 and the R0^{-T} solve over all SMs, then normalisation and the factor QR.
   FinishOut fo{ctx->A[n], ctx->lambda, ctx->Q[n], ctx->Rf[n], ctx->Qf[n], ctx->fit_terms};
@@ -1014,8 +1052,8 @@ void mlp_features(const double* fits, const double* betas, int n, double rule_be
 // runs as is.  Any other proposal, beta = 0 included, is judged: from one checkpoint the proposal's
 // sweep and the rule's sweep both run, and the proposal is kept only if its fit is higher, else the
 // rule's sweep stands (the rule is the fallback).  A proposal that won stays approved for the next
-// approve_window sweeps (2, 4, ... 32 after consecutive wins) as long as the fit does not drop; a
-// drop ends the approval.  After a loss the rule runs for hold_window sweeps (1, 2, ... 32 after
+// approve_window sweeps (2, 4, ... 32 after consecutive wins) as long as the fit does not drop by
+// more than 1e-7; such a drop ends the approval.  After a loss the rule runs for hold_window sweeps (1, 2, ... 32 after
 // consecutive losses) with the proposals deferred unjudged; then the next differing proposal is
 // judged again.  Judging costs two sweeps, so the windows keep it to a few per cent of the sweeps
 // once either side keeps winning.
@@ -1039,7 +1077,9 @@ cpqr_status learned_sweep(cpqr_ctx* ctx, double* fit_out) {
     if (s != CPQR_OK) return s;
     ++ctx->accepted;
     ++ctx->preapproved;
-    if (!(f >= prev)) {
+    // a drop beyond the per-sweep fit's rounding (a sweep's explicit residual moves by ~1e-12 between
+    // nearly equal models) ends the approval
+    if (!(f >= prev - 1e-7)) {
       ctx->approved_class = -1;
       ctx->approve_window = 1;
       ctx->approve_left = 0;
@@ -1123,7 +1163,7 @@ cpqr_status cp_als_qr_init(cpqr_ctx** out, int32_t N, const int64_t* dims, int32
                            void* stream) {
   if (!out) return CPQR_EINVAL;
   *out = nullptr;
-  if (N < 3 || N > CPQR_MAXN || !dims || R < 1 || R > CPQR_MAXR || !X_dev) return CPQR_EINVAL;
+  if (N < 3 || N > CPQR_MAXN || !dims || R < 1 || R > CPQR_MAXR_WIDE || !X_dev) return CPQR_EINVAL;
   cpqr_options opt;
   if (opt_in) opt = *opt_in;
   else cp_als_qr_default_options(&opt);
@@ -1153,6 +1193,8 @@ cpqr_status cp_als_qr_init(cpqr_ctx** out, int32_t N, const int64_t* dims, int32
   ctx->prec = opt.prec;
   ctx->extrap = opt.extrap;
   ctx->gram = opt.qr_route == CPQR_QR_GRAM;
+  ctx->wide = R > CPQR_MAXR;
+  if (ctx->wide) ctx->gram = false;  // the wide path has its own (Cholesky) QRs
   ctx->alpha = opt.alpha > 0 ? opt.alpha : kAlphaDefault;
   ctx->beta_fixed = opt.beta_fixed;
   ctx->st = (cudaStream_t)stream;
@@ -1219,6 +1261,11 @@ cpqr_status cp_als_qr_init(cpqr_ctx** out, int32_t N, const int64_t* dims, int32
   CK(ctx->alloc(&ctx->qr_work, std::max<int64_t>(M0, Imax) * R));
   CK(ctx->alloc(&ctx->zq_work, std::max<size_t>((size_t)(M0 * R), krp_nested_work_doubles(N - 1, R))));
   CK(ctx->alloc(&ctx->zg_work, krp_gram_work_doubles(R)));
+  if (ctx->wide) {
+    CK(ctx->alloc(&ctx->wq_main, wide_work_doubles(R)));
+    CK(ctx->alloc(&ctx->wq_side, wide_work_doubles(R)));
+    CK(ctx->alloc(&ctx->wrows, (size_t)Imax * (R + 2)));
+  }
   CK(ctx->alloc(&ctx->fg_work, factor_gram_work_doubles(Imax, R)));
   CK(ctx->alloc(&ctx->hpart, (size_t)finish_prep_blocks(Imax) * 17 * 32));
   CK(cudaMemsetAsync(ctx->zg_work, 0, krp_gram_work_doubles(R) * sizeof(double), st));
@@ -1301,9 +1348,14 @@ cpqr_status cp_als_qr_init(cpqr_ctx** out, int32_t N, const int64_t* dims, int32
       }
     }
     CK(cudaMemcpyAsync(ctx->A[n], host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, st));
-    CK(launch_house_qr(ctx->A[n], dims[n], R, ctx->Q[n], ctx->Rf[n], ctx->qr_work, ctx->dstatus, st));
-    CK(launch_to_f32(ctx->Q[n], ctx->Qf[n], dims[n] * R, st));
-    CK(launch_tri_gram(ctx->Rf[n], R, ctx->Gf[n], ctx->cn[n], st));
+    if (ctx->wide) {
+      CK(launch_wide_qr(ctx->A[n], dims[n], R, nullptr, 0, ctx->Q[n], ctx->Qf[n], ctx->Rf[n], ctx->wq_main,
+                        ctx->dstatus, st));
+    } else {
+      CK(launch_house_qr(ctx->A[n], dims[n], R, ctx->Q[n], ctx->Rf[n], ctx->qr_work, ctx->dstatus, st));
+      CK(launch_to_f32(ctx->Q[n], ctx->Qf[n], dims[n] * R, st));
+      CK(launch_tri_gram(ctx->Rf[n], R, ctx->Gf[n], ctx->cn[n], st));
+    }
     CK(cudaStreamSynchronize(st));
   }
   // Split-precision staging.
@@ -1314,13 +1366,6 @@ cpqr_status cp_als_qr_init(cpqr_ctx** out, int32_t N, const int64_t* dims, int32
     }
     CK(ctx->alloc(&ctx->Xhi, nX));
     CK(ctx->alloc(&ctx->Xlo, nX));
-    int nsm = 0, dev = 0;
-    CK(cudaGetDevice(&dev));
-    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    ctx->tc_split.ctas = std::max(nsm, 1);
-    CK(ctx->alloc(&ctx->tc_split.part, ttm_tc_split_floats(ctx->tc_split.ctas)));
-    CK(ctx->alloc(&ctx->tc_split.cnt, (size_t)ctx->tc_split.ctas));
-    CK(cudaMemsetAsync(ctx->tc_split.cnt, 0, ctx->tc_split.ctas * sizeof(int), st));
     CK(launch_split_x((const float*)X_dev, ctx->Xhi, ctx->Xlo, nX, st));
   }
   // ||X||^2 (precomputed once, Section 4.1).
@@ -1670,27 +1715,19 @@ cpqr_status cpqr_ttm(const void* T_dev, int32_t nd, const int64_t* tdims, int32_
       const int64_t n = P * K * S;
       __nv_bfloat16 *xh = nullptr, *xl = nullptr, *qt = nullptr;
       unsigned int* ds = nullptr;
-      int nsm = 0, dev = 0;
-      if (cudaGetDevice(&dev) != cudaSuccess ||
-          cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-        return CPQR_ECUDA;
-      TcSplitWork sk{nullptr, nullptr, std::max(nsm, 1)};
       if (cudaMalloc(&xh, n * 2) != cudaSuccess || cudaMalloc(&xl, n * 2) != cudaSuccess ||
-          cudaMalloc(&qt, (size_t)2 * Rp * Kp * 2) != cudaSuccess || cudaMalloc(&ds, 4) != cudaSuccess ||
-          cudaMalloc(&sk.part, ttm_tc_split_floats(sk.ctas) * 4) != cudaSuccess ||
-          cudaMalloc(&sk.cnt, (size_t)sk.ctas * 4) != cudaSuccess) {
-        cudaFree(xh); cudaFree(xl); cudaFree(qt); cudaFree(ds); cudaFree(sk.part); cudaFree(sk.cnt);
+          cudaMalloc(&qt, (size_t)2 * Rp * Kp * 2) != cudaSuccess || cudaMalloc(&ds, 4) != cudaSuccess) {
+        cudaFree(xh); cudaFree(xl); cudaFree(qt); cudaFree(ds);
         return CPQR_ENOMEM;
       }
       e = cudaMemsetAsync(ds, 0, 4, st);
-      if (e == cudaSuccess) e = cudaMemsetAsync(sk.cnt, 0, (size_t)sk.ctas * 4, st);
       if (e == cudaSuccess) e = launch_split_x((const float*)T_dev, xh, xl, n, st);
       if (e == cudaSuccess) e = launch_split_q((const double*)Q_dev, K, R, qt, Rp, Kp, st);
-      if (e == cudaSuccess) e = launch_ttm_tc(xh, xl, qt, Rp, Kp, (float*)out_dev, P, K, S, R, ds, st, sk);
+      if (e == cudaSuccess) e = launch_ttm_tc(xh, xl, qt, Rp, Kp, (float*)out_dev, P, K, S, R, ds, st);
       unsigned int hs = 0;
       if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, ds, 4, cudaMemcpyDeviceToHost, st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-      cudaFree(xh); cudaFree(xl); cudaFree(qt); cudaFree(ds); cudaFree(sk.part); cudaFree(sk.cnt);
+      cudaFree(xh); cudaFree(xl); cudaFree(qt); cudaFree(ds);
       if (e == cudaSuccess && hs) return status_of_device_word(hs);
       break;
     }
@@ -1699,8 +1736,28 @@ cpqr_status cpqr_ttm(const void* T_dev, int32_t nd, const int64_t* tdims, int32_
   return e == cudaSuccess ? CPQR_OK : CPQR_ECUDA;
 }
 
+// The wide-rank Cholesky QR behind cpqr_house_qr / cpqr_krp_qr for 32 < R <= CPQR_MAXR_WIDE.
+static cpqr_status wide_entry_qr(const double* Y, int64_t M, int R, const double* const* tri, int m, double* Q,
+                                 double* Rout, cudaStream_t st) {
+  double* work = nullptr;
+  unsigned int* ds = nullptr;
+  if (cudaMalloc(&work, wide_work_doubles(R) * sizeof(double)) != cudaSuccess || cudaMalloc(&ds, 4) != cudaSuccess) {
+    cudaFree(work); cudaFree(ds);
+    return CPQR_ENOMEM;
+  }
+  unsigned int hs = 0;
+  cudaError_t e = cudaMemsetAsync(ds, 0, 4, st);
+  if (e == cudaSuccess) e = launch_wide_qr(Y, M, R, tri, m, Q, nullptr, Rout, work, ds, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, ds, 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(work);
+  cudaFree(ds);
+  return e == cudaSuccess ? status_of_device_word(hs) : CPQR_ECUDA;
+}
+
 cpqr_status cpqr_house_qr(const double* A_dev, int64_t M, int32_t R, double* Q_dev, double* R_dev, void* stream) {
-  if (!A_dev || !Q_dev || !R_dev || R < 1 || R > CPQR_MAXR || M < R) return CPQR_EINVAL;
+  if (!A_dev || !Q_dev || !R_dev || R < 1 || R > CPQR_MAXR_WIDE || M < R) return CPQR_EINVAL;
+  if (R > CPQR_MAXR) return wide_entry_qr(A_dev, M, R, nullptr, 0, Q_dev, R_dev, (cudaStream_t)stream);
   cudaStream_t st = (cudaStream_t)stream;
   double* work = nullptr;
   unsigned int* ds = nullptr;
@@ -1719,9 +1776,14 @@ cpqr_status cpqr_house_qr(const double* A_dev, int64_t M, int32_t R, double* Q_d
 }
 
 cpqr_status cpqr_krp_qr(const double* Rs_dev, int32_t m, int32_t R, double* Q0_dev, double* R0_dev, void* stream) {
-  if (!Rs_dev || !Q0_dev || !R0_dev || m < 1 || m > CPQR_MAXN - 1 || R < 1 || R > CPQR_MAXR) return CPQR_EINVAL;
+  if (!Rs_dev || !Q0_dev || !R0_dev || m < 1 || m > CPQR_MAXN - 1 || R < 1 || R > CPQR_MAXR_WIDE) return CPQR_EINVAL;
   int64_t M = ipow(R, m);
-  if (M < R) return CPQR_EINVAL;
+  if (M < R || M > (int64_t(1) << 34)) return CPQR_EINVAL;
+  if (R > CPQR_MAXR) {
+    const double* tri[CPQR_MAXN];
+    for (int k = 0; k < m; ++k) tri[k] = Rs_dev + (size_t)k * R * R;
+    return wide_entry_qr(nullptr, M, R, tri, m, Q0_dev, R0_dev, (cudaStream_t)stream);
+  }
   cudaStream_t st = (cudaStream_t)stream;
   const int mp = (m >= 3) ? 2 : m;  // m >= 3 goes through the nested QR of two-triangle products
   std::vector<int32_t> perm = krp_perm(mp, R);

@@ -6,7 +6,8 @@
 
 #include "cpqr.h"
 
-#define CPQR_MAXR 32
+#define CPQR_MAXR 32        // largest rank of the warp-per-factor kernels
+#define CPQR_MAXR_WIDE 192  // largest rank of the wide-rank path (wide.cu)
 #define CPQR_MAXN 6
 
 // Device-side error flags (bitwise OR into ctx status word).
@@ -76,18 +77,9 @@ cudaError_t launch_split_x(const float* X, __nv_bfloat16* Xhi, __nv_bfloat16* Xl
 // S % 8 == 0 (MN-major) or S == 1 with K % 8 == 0 (K-major); K <= 512.  Returns
 // cudaErrorNotSupported if the shape is outside the kernel's range.
 // reserve_sms: SMs the persistent grid leaves free for concurrent work (a cluster QR).
-// Workspace of the tensor-core TTM's stream-K split: ttm_tc_split_floats(ctas) floats of partial
-// tiles and ctas zeroed counters (the kernel leaves them zero); launches that share one must run
-// in stream order.
-struct TcSplitWork {
-  float* part;
-  int* cnt;
-  int ctas;
-};
-size_t ttm_tc_split_floats(int ctas);
 cudaError_t launch_ttm_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo, const __nv_bfloat16* Qt,
                           int Rp, int64_t Kp, float* out, int64_t P, int64_t K, int64_t S, int R,
-                          unsigned int* dev_status, cudaStream_t st, const TcSplitWork& sk, int reserve_sms = 0,
+                          unsigned int* dev_status, cudaStream_t st, int reserve_sms = 0,
                           __nv_bfloat16* out_hi = nullptr, __nv_bfloat16* out_lo = nullptr,
                           unsigned long long wait_ns = 0, int skip_x_loads = 0);
 bool ttm_tc_supported(int64_t P, int64_t K, int64_t S, int R);
@@ -275,6 +267,23 @@ cudaError_t launch_residual_tc(const float* X, int N, const int64_t* d, const fl
 cudaError_t launch_to_f32(const double* a, float* b, int64_t n, cudaStream_t st);
 
 // ----- learned proposer (mlp.cu) -----
+// ---- wide-rank path (32 < R <= CPQR_MAXR_WIDE), wide.cu ----
+bool wide_supported(int R);
+size_t wide_work_doubles(int R);
+// Cholesky QR (see wide.cu) of Y (M x R rows) or, with tri / m > 0, of the Khatri-Rao product of the
+// m upper triangles tri[0..m-1] (rows (i_1, ..., i_m), i_m fastest).
+cudaError_t launch_wide_qr(const double* Y, int64_t M, int R, const double* const* tri, int m, double* Q, float* Qf,
+                           double* Rout, double* work, unsigned int* status, cudaStream_t st);
+// A^ = V^ R0^{-T} (eq. 19 on the V slices), fit terms, lambda and A = A^ / lambda.  work_rows: I (R + 2).
+template <typename TV>
+cudaError_t launch_wide_finish(const TV* vw, int nparts, int64_t I, int C, int R, const double* R0, double beta,
+                               double alpha, double* A, double* lambda, double* fit_terms, double* work_rows,
+                               unsigned int* status, cudaStream_t st);
+// TTM on the CUDA cores for any R (tiled GEMM, accumulation in TAcc).
+template <typename TT, typename TQ, typename TO, typename TAcc>
+cudaError_t launch_ttm_wide(const TT* T, const TQ* Q, TO* out, int64_t P, int64_t K, int64_t S, int R,
+                            cudaStream_t st);
+
 // Device state of the learned proposer (kept in the solver's state arena, so a checkpoint saves it):
 // the fits of the last MLP_RING + 1 sweeps and the betas of the last MLP_RING (most recent last),
 // the Section 4.2 rule's state, and the last features, logits and proposed class.

@@ -254,6 +254,7 @@ __global__ void __launch_bounds__(256) leaf_v_kernel(const TY* __restrict__ Y, i
   // warps whose columns all lie at or past C skip the multiply; wider C keeps two row groups per
   // warp (one shared-memory broadcast of the rows instead of one of the columns)
   const bool narrow = C <= 32;
+  const int cb = blockIdx.z * VC;  // column tile (C > 64 on the wide-rank path)
   const int tx = narrow ? tid >> 4 : tid & 15, ty = narrow ? tid & 15 : tid >> 4;
   const bool busy = !narrow || (tid >> 5) * 8 < C;
   const int i0 = blockIdx.x * VI;
@@ -285,7 +286,7 @@ __global__ void __launch_bounds__(256) leaf_v_kernel(const TY* __restrict__ Y, i
 #pragma unroll
     for (int q = 0; q < NLQ; ++q) {
       const int e = tid + 256 * q;
-      const int kk = e / VC, c = e % VC;
+      const int kk = e / VC, c = cb + e % VC;
       const int k = k0 + kk;
       qbuf[q] = TQ(0);
       if (k < kend && c < C) qbuf[q] = (c < R) ? Q0[(int64_t)k * R + c] : Q0p[(int64_t)k * R + (c - R)];
@@ -328,7 +329,7 @@ __global__ void __launch_bounds__(256) leaf_v_kernel(const TY* __restrict__ Y, i
     TQ* dst = part + ((size_t)blockIdx.y * I + i) * C;
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
-      const int c = tx * 4 + b;
+      const int c = cb + tx * 4 + b;
       if (c < C) dst[c] = (TQ)acc[a][b];
     }
   }
@@ -556,6 +557,85 @@ __global__ void __launch_bounds__(RNT, 2) residual2_kernel(const TX* __restrict_
   if (threadIdx.x == 0) out[blockIdx.x] = t;  // per-block partial, summed in a fixed order afterwards
 }
 
+// The residual for ranks above 32 (the wide-rank path): 64 x 64 tiles of X (rows = modes 0..N-2,
+// columns = the last mode), the model tile K = W A_last^T in FP32 over R in 16-deep chunks, the
+// Khatri-Rao weights W of each chunk formed in shared memory from the FP32 factors, and the
+// (x - k)^2 of the tile summed per thread in FP32 and per block in FP64 (one partial per block,
+// added in a fixed order afterwards).
+constexpr int WRT = 64, WRK = 16;
+
+template <typename TX>
+__global__ void __launch_bounds__(256) residual_wide_kernel(const TX* __restrict__ X, const __grid_constant__ ResParams rp,
+                                                           int64_t rows, double* __restrict__ part) {
+  __shared__ float sW[WRK][WRT + 1];
+  __shared__ float sA[WRK][WRT + 1];
+  __shared__ double sh[32];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int Il = rp.d[rp.N - 1], R = rp.R;
+  const int64_t rtiles = (rows + WRT - 1) / WRT, ctiles = (Il + WRT - 1) / WRT;
+  const float* AlT = rp.A[rp.N - 1];  // R x I_last
+  double acc_tot = 0.0;
+  for (int64_t t = blockIdx.x; t < rtiles * ctiles; t += gridDim.x) {
+    const int64_t r0 = (t / ctiles) * WRT, c0 = (t % ctiles) * WRT;
+    float k[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) k[i][j] = 0.f;
+    for (int q0 = 0; q0 < R; q0 += WRK) {
+      for (int e = tid; e < WRK * WRT; e += 256) {
+        const int rr = e / WRT, m = e % WRT;
+        const int r = q0 + rr;
+        const int64_t row = r0 + m;
+        float w = 0.f;
+        if (r < R && row < rows) {
+          w = 1.f;
+          int64_t x = row;
+          for (int n = rp.N - 2; n >= 0; --n) {
+            const int in = (int)(x % rp.d[n]);
+            x /= rp.d[n];
+            w *= rp.A[n][(int64_t)in * R + r];
+          }
+        }
+        sW[rr][m] = w;
+        const int64_t col = c0 + m;
+        sA[rr][m] = (r < R && col < Il) ? AlT[(int64_t)r * Il + col] : 0.f;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int rr = 0; rr < WRK; ++rr) {
+        float a[4], bb[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          a[i] = sW[rr][ty * 4 + i];
+          bb[i] = sA[rr][tx * 4 + i];
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) k[i][j] = fmaf(a[i], bb[j], k[i][j]);
+      }
+      __syncthreads();
+    }
+    float racc = 0.f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int64_t row = r0 + ty * 4 + i;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int64_t col = c0 + tx * 4 + j;
+        if (row < rows && col < Il) {
+          const float e = (float)X[row * Il + col] - k[i][j];
+          racc = fmaf(e, e, racc);
+        }
+      }
+    }
+    acc_tot += (double)racc;
+  }
+  double tsum = block_sum(acc_tot, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = tsum;
+}
+
 __global__ void to_f32_kernel(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     b[i] = (float)a[i];
@@ -622,14 +702,14 @@ cudaError_t launch_leaf_v(const TY* Y, int64_t P, int64_t I, int64_t S, const TQ
                           TQ* work, int* nparts, cudaStream_t st) {
   const int64_t K = P * S;
   if (K > 0x7fffffff || I > 0x7fffffff) return cudaErrorInvalidValue;
-  if (C < 1 || C > 2 * CPQR_MAXR || R < 1 || R > CPQR_MAXR) return cudaErrorInvalidValue;
+  if (C < 1 || C > 2 * 192 || R < 1 || R > 192) return cudaErrorInvalidValue;  // wide-rank path: R <= 192
   const int64_t itiles = (I + VI - 1) / VI;
   const int splits = leaf_v_splits(I, K);
   int64_t kchunk = (K + splits - 1) / splits;
   kchunk = ((kchunk + VK - 1) / VK) * VK;
   if (kchunk < VK) kchunk = VK;
   const int64_t ktiles = (K + kchunk - 1) / kchunk;  // <= splits: fits the work slices
-  dim3 grid((unsigned)itiles, (unsigned)ktiles);
+  dim3 grid((unsigned)itiles, (unsigned)ktiles, (unsigned)((C + VC - 1) / VC));
   using TA = typename std::conditional<std::is_same<TY, double>::value, double, float>::type;
   *nparts = (int)ktiles;
   return launch_pdl(leaf_v_kernel<TY, TA, TQ>, grid, dim3(256), 0, st, Y, (int)P, (int)I, (int)S, Q0, Q0prev, R, C,
@@ -708,6 +788,14 @@ cudaError_t launch_residual2(const TX* X, int N, const int64_t* d, const double*
                            st, reserve_sms);
     if (e == cudaSuccess) return launch_sum_parts(part, np, out, st);
     if (e != cudaErrorNotSupported) return e;
+  }
+  if (R > CPQR_MAXR) {  // the wide-rank path
+    const int64_t tiles = ((rows + WRT - 1) / WRT) * ((d[N - 1] + WRT - 1) / WRT);
+    const int grid = (int)std::min<int64_t>(tiles, 152 * 4);
+    residual_wide_kernel<TX><<<grid, 256, 0, st>>>(X, rp, rows, part);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_sum_parts(part, grid, out, st);
   }
   // contiguous ranges of (row tile, column chunk) items, two CTAs per SM
   const int64_t items = ((rows + RM - 1) / RM) * ((d[N - 1] + RC - 1) / RC);

@@ -135,20 +135,7 @@ struct TcParams {
   unsigned int* status;
   unsigned long long wait_ns;  // limit of the pipeline waits (drain waits keep kTimeoutNs)
   int skip_x_loads;            // failure-detection test: issue no tile loads, so the MMA wait runs out
-  float* part;                 // stream-K partial tiles: 2 slots of 32 x 128 floats per CTA
-  int* cnt;                    // stream-K arrival counters, one per CTA (zero between launches)
 };
-
-// Stream-K split of the T x nkb (tile, 64-deep K block) iterations: CTA b takes [start(b), start(b+1)).
-__device__ __forceinline__ int64_t sk_start(int64_t b, int64_t W, int64_t G) { return b * W / G; }
-__device__ __forceinline__ int64_t sk_cta_of(int64_t w, int64_t W, int64_t G) {
-  int64_t b = w * G / W;
-  while (b + 1 < G && sk_start(b + 1, W, G) <= w) ++b;
-  while (b > 0 && sk_start(b, W, G) > w) --b;
-  return b;
-}
-
-__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
 struct TcSmemTail {
   unsigned long long full[TC_NST];
@@ -161,7 +148,6 @@ struct TcSmemTail {
   int abort_flag;
   int issued[TC_NST];
   int consumed[TC_NST];
-  int epi_flag;  // epilogue broadcast: wait outcome / last arrival of a split tile
 };
 
 using namespace tc;
@@ -172,38 +158,6 @@ __device__ __forceinline__ void store_out(const TcParams& p, int64_t idx, float 
     const __nv_bfloat16 h = __float2bfloat16_rn(v);
     p.out_hi[idx] = h;
     p.out_lo[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
-  }
-}
-
-// The epilogue's rows of one finished tile: thread m (0..127) holds row m of the 128 x R result.
-template <bool KM>
-__device__ __forceinline__ void write_tile(const TcParams& p, int64_t tile, const float* v, int warp, int lane,
-                                           float* epi) {
-  const int m = warp * 32 + lane;
-  if (KM) {
-    float* stg = epi + warp * (32 * 33);
-#pragma unroll
-    for (int r = 0; r < 32; ++r) stg[lane * 33 + r] = v[r];
-    __syncwarp();
-    const int64_t p0 = tile * 128 + warp * 32;  // this warp's rows, contiguous in out
-    const int nrows = (int)(p.P - p0 < 32 ? p.P - p0 : 32);
-    for (int e = lane; e < nrows * p.R; e += 32) {
-      const int row = e / p.R, r = e - row * p.R;
-      store_out(p, p0 * p.R + e, stg[row * 33 + r]);
-    }
-    __syncwarp();
-  } else {
-    const int64_t h = 2 * tile + (m >> 6);
-    if (h < p.H) {
-      const int64_t pp = h / p.nsb, sb = h % p.nsb;
-      const int64_t sidx = sb * 64 + (m & 63);
-      if (sidx < p.S) {
-        const int64_t o = (pp * p.R) * p.S + sidx;
-#pragma unroll
-        for (int r = 0; r < 32; ++r)
-          if (r < p.R) store_out(p, o + (int64_t)r * p.S, v[r]);
-      }
-    }
   }
 }
 
@@ -252,12 +206,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   fence_after();
   const uint32_t tmem = tail->tmem_base;
 
-  // Stream-K: CTA b owns the iterations [w0, w1) of the T x nkb (tile, K block) sequence, a chain
-  // of segments (consecutive K blocks of one tile).  Only a CTA's first and last segments can be
-  // parts of a tile; they go to the CTA's two partial slots, and the last of a tile's CTAs to
-  // arrive adds the parts in K order and writes the tile (no CTA ever waits for another).
-  const int64_t W = p.T * (int64_t)p.nkb, G = gridDim.x;
-  const int64_t w0 = sk_start(blockIdx.x, W, G), w1 = sk_start((int64_t)blockIdx.x + 1, W, G);
+  const int64_t ntile_local = (p.T > (int64_t)blockIdx.x) ? (p.T - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
   if (warp == 4) {
     if (lane == 0) {
@@ -270,9 +219,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
       int stage = 0;
       uint32_t phase = 0;
-      for (int64_t w = w0; w < w1; ++w) {
-        const int64_t tile = w / p.nkb;
-        const int kb = (int)(w - tile * p.nkb);
+      bool ok = true;
+      for (int64_t lt = 0; lt < ntile_local && ok; ++lt) {
+        const int64_t tile = blockIdx.x + lt * gridDim.x;
         const int64_t h0 = 2 * tile, h1 = 2 * tile + 1;
         int p0 = 0, sb0 = 0, p1 = (int)p.P, sb1 = 0;  // past the last half tile: an all-out-of-bounds box
         if (!KM) {
@@ -283,9 +232,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             sb1 = (int)(h1 % p.nsb);
           }
         }
-        if (!mbar_wait(smem_u32(&tail->empty[stage]), phase ^ 1u, &tail->abort_flag, p.status, true, p.wait_ns))
-          break;
-        if (!p.skip_x_loads) {  // (test hook: nothing arrives on full[stage], the MMA issuer's wait runs out)
+        for (int kb = 0; kb < p.nkb; ++kb) {
+          if (!mbar_wait(smem_u32(&tail->empty[stage]), phase ^ 1u, &tail->abort_flag, p.status, true, p.wait_ns)) {
+            ok = false;
+            break;
+          }
+          if (p.skip_x_loads) {  // nothing arrives on full[stage]: the MMA issuer's wait runs out
+            if (++stage == TC_NST) {
+              stage = 0;
+              phase ^= 1u;
+            }
+            continue;
+          }
           const uint32_t fb = smem_u32(&tail->full[stage]);
           const uint32_t dst = sA + stage * TC_STAGE_BYTES;
           mbar_expect_tx(fb, TC_STAGE_BYTES);
@@ -300,10 +258,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             tma_load_3d(dst + 3 * TC_HALF_BYTES, &tmXlo, sb1 * 64, kb * 64, p1, fb);
           }
           tail->issued[stage] += 1;
-        }
-        if (++stage == TC_NST) {
-          stage = 0;
-          phase ^= 1u;
+          if (++stage == TC_NST) {
+            stage = 0;
+            phase ^= 1u;
+          }
         }
       }
     }
@@ -317,21 +275,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       fence_after();
       int stage = 0;
       uint32_t phase = 0;
-      int64_t seg = 0;
-      for (int64_t w = w0; w < w1 && ok; ++seg) {
-        const int64_t tile = w / p.nkb;
-        const int a = (int)(w - tile * p.nkb);
-        const int e = (int)(p.nkb < a + (w1 - w) ? p.nkb : a + (w1 - w));
-        const int acc = (int)(seg & 1);
-        const uint32_t use = (uint32_t)(seg >> 1);
+      for (int64_t lt = 0; lt < ntile_local && ok; ++lt) {
+        const int acc = (int)(lt & 1);
+        const uint32_t use = (uint32_t)(lt >> 1);
         if (!mbar_wait(smem_u32(&tail->tempty[acc]), (use & 1u) ^ 1u, &tail->abort_flag, p.status, true, p.wait_ns))
           break;
         fence_after();
         const uint32_t d0 = tmem + (uint32_t)(acc * TC_ACC_COLS);
         const uint32_t dc = d0 + 64;  // correction products
-        for (int kb = a; kb < e; ++kb) {
-          const int jb = kb - a;                                // K block within the segment
-          const uint32_t dm = d0 + (uint32_t)((jb & 1) * 32);  // hi * hi of even / odd blocks
+        for (int kb = 0; kb < p.nkb; ++kb) {
+          const uint32_t dm = d0 + (uint32_t)((kb & 1) * 32);  // hi * hi of even / odd K blocks
           if (!mbar_wait(smem_u32(&tail->full[stage]), phase, &tail->abort_flag, p.status, true, p.wait_ns)) {
             ok = false;
             break;
@@ -349,8 +302,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const uint64_t al = KM ? smem_desc(a_lo + ks * 32, 16, 1024) : smem_desc(a_lo + ks * 2048, TC_HALF_BYTES, 1024);
             const uint64_t bh = smem_desc(b_hi + ks * 32, 16, 1024);
             const uint64_t bl = smem_desc(b_lo + ks * 32, 16, 1024);
-            mma_bf16(dm, ah, bh, idesc, (jb >= 2 || ks != 0) ? 1u : 0u);
-            mma_bf16(dc, ah, bl, idesc, (jb | ks) != 0 ? 1u : 0u);
+            mma_bf16(dm, ah, bh, idesc, (kb >= 2 || ks != 0) ? 1u : 0u);
+            mma_bf16(dc, ah, bl, idesc, (kb | ks) != 0 ? 1u : 0u);
             mma_bf16(dc, al, bh, idesc, 1u);
             mma_bf16(dc, al, bl, idesc, 1u);
           }
@@ -362,7 +315,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         if (!ok) break;
         mma_commit(smem_u32(&tail->tfull[acc]));
-        w += e - a;
       }
       // every MMA issued above has completed once tdown flips
       mma_commit(smem_u32(&tail->tdown));
@@ -370,80 +322,58 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
   } else {
     // ---------------- epilogue: warps 0-3, tensor-memory lanes 32w .. 32w+31 ----------------
-    // Thread 0 waits for each accumulator and the outcome is broadcast over a named barrier, so
-    // the four warps always leave (or continue) together.
     const int m = warp * 32 + lane;
-    int64_t seg = 0;
-    for (int64_t w = w0; w < w1; ++seg) {
-      const int64_t tile = w / p.nkb;
-      const int a = (int)(w - tile * p.nkb);
-      const int e = (int)(p.nkb < a + (w1 - w) ? p.nkb : a + (w1 - w));
-      const int acc = (int)(seg & 1);
-      const uint32_t use = (uint32_t)(seg >> 1);
-      if (threadIdx.x == 0)
-        tail->epi_flag = mbar_wait(smem_u32(&tail->tfull[acc]), use & 1u, &tail->abort_flag, p.status, true,
-                                   p.wait_ns) ? 1 : 0;
-      epi_bar();
-      const bool ok = tail->epi_flag != 0;
-      epi_bar();  // every thread has read the flag before thread 0 may write it again
-      if (!ok) break;
+    for (int64_t lt = 0; lt < ntile_local; ++lt) {
+      const int acc = (int)(lt & 1);
+      const uint32_t use = (uint32_t)(lt >> 1);
+      if (!mbar_wait(smem_u32(&tail->tfull[acc]), use & 1u, &tail->abort_flag, p.status, true, p.wait_ns)) break;
       fence_after();
-      float v[32], u[32];
+      float v[32], w[32];
 #pragma unroll
-      for (int r = 0; r < 32; ++r) v[r] = u[r] = 0.f;  // columns past Rp = 16 stay zero
+      for (int r = 0; r < 32; ++r) v[r] = w[r] = 0.f;  // columns past Rp = 16 stay zero
       const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc * TC_ACC_COLS);
-      // (even + odd) + corrections, each add rounded to nearest; a one-block segment has no odd part
+      // (even + odd) + corrections, each add rounded to nearest; a K of one block has no odd part
       if (p.Rp == 32) tmem_ld32(taddr, v);
       else tmem_ld16(taddr, v);
-      if (e - a > 1) {
-        if (p.Rp == 32) tmem_ld32(taddr + 32, u);
-        else tmem_ld16(taddr + 32, u);
+      if (p.nkb > 1) {
+        if (p.Rp == 32) tmem_ld32(taddr + 32, w);
+        else tmem_ld16(taddr + 32, w);
 #pragma unroll
-        for (int r = 0; r < 32; ++r) v[r] += u[r];
+        for (int r = 0; r < 32; ++r) v[r] += w[r];
       }
-      if (p.Rp == 32) tmem_ld32(taddr + 64, u);
-      else tmem_ld16(taddr + 64, u);
+      if (p.Rp == 32) tmem_ld32(taddr + 64, w);
+      else tmem_ld16(taddr + 64, w);
 #pragma unroll
-      for (int r = 0; r < 32; ++r) v[r] += u[r];
+      for (int r = 0; r < 32; ++r) v[r] += w[r];
       fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&tail->tempty[acc]));
-      if (a == 0 && e == p.nkb) {
-        write_tile<KM>(p, tile, v, warp, lane, epi);
-      } else {
-        // a part of the tile: into this CTA's slot (first segment: 2b, last: 2b + 1), column-major
-        // so that the 128 rows of a column are contiguous
-        float* slot = p.part + ((size_t)2 * blockIdx.x + (w == w0 ? 0 : 1)) * (32 * 128);
+      const int64_t tile = blockIdx.x + lt * gridDim.x;
+      if (KM) {
+        float* stg = epi + warp * (32 * 33);
 #pragma unroll
-        for (int r = 0; r < 32; ++r) slot[r * 128 + m] = v[r];
-        __threadfence();
-        epi_bar();
-        const int64_t b0 = sk_cta_of(tile * p.nkb, W, G), b1 = sk_cta_of(tile * p.nkb + p.nkb - 1, W, G);
-        if (threadIdx.x == 0) {
-          const int old = atomicAdd(&p.cnt[b0], 1);
-          const int last = (old == (int)(b1 - b0)) ? 1 : 0;
-          if (last) p.cnt[b0] = 0;  // every part has arrived: ready for the next launch
-          tail->epi_flag = last;
+        for (int r = 0; r < 32; ++r) stg[lane * 33 + r] = v[r];
+        __syncwarp();
+        const int64_t p0 = tile * 128 + warp * 32;  // this warp's rows, contiguous in out
+        const int nrows = (int)std::min<int64_t>(32, p.P - p0);
+        for (int e = lane; e < nrows * p.R; e += 32) {
+          const int row = e / p.R, r = e - row * p.R;
+          store_out(p, p0 * p.R + e, stg[row * 33 + r]);
         }
-        epi_bar();
-        const bool last = tail->epi_flag != 0;
-        epi_bar();
-        if (last) {
-          __threadfence();
-          float t[32];
+        __syncwarp();
+      } else {
+        const int64_t h = 2 * tile + (m >> 6);
+        if (h < p.H) {
+          const int64_t pp = h / p.nsb, sb = h % p.nsb;
+          const int64_t sidx = sb * 64 + (m & 63);
+          if (sidx < p.S) {
+            const int64_t o = (pp * p.R) * p.S + sidx;
 #pragma unroll
-          for (int r = 0; r < 32; ++r) t[r] = 0.f;
-          for (int64_t bb = b0; bb <= b1; ++bb) {
-            // CTA bb's part of this tile is its first segment unless its range began before the tile
-            const int64_t sl = 2 * bb + (sk_start(bb, W, G) < tile * p.nkb ? 1 : 0);
-            const float* src = p.part + (size_t)sl * (32 * 128);
-#pragma unroll
-            for (int r = 0; r < 32; ++r) t[r] += __ldcg(src + r * 128 + m);
+            for (int r = 0; r < 32; ++r)
+              if (r < p.R) store_out(p, o + (int64_t)r * p.S, v[r]);
           }
-          write_tile<KM>(p, tile, t, warp, lane, epi);
         }
       }
-      w += e - a;
     }
   }
 
@@ -468,8 +398,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
 }  // namespace
 
-size_t ttm_tc_split_floats(int ctas) { return (size_t)2 * ctas * 32 * 128; }
-
 bool ttm_tc_supported(int64_t P, int64_t K, int64_t S, int R) {
   if (R < 1 || R > 32 || K < 1 || K > 64 * TC_MAX_KB || P < 1 || P > 0x7fffffff || S > 0x7fffffff) return false;
   if (S == 1) return (K % 8) == 0 && (P + 127) / 128 < (int64_t(1) << 31);  // K-major: 16-byte row stride
@@ -481,9 +409,8 @@ bool ttm_tc_supported(int64_t P, int64_t K, int64_t S, int R) {
 
 cudaError_t launch_ttm_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo, const __nv_bfloat16* Qt, int Rp,
                           int64_t Kp, float* out, int64_t P, int64_t K, int64_t S, int R, unsigned int* dev_status,
-                          cudaStream_t st, const TcSplitWork& sk, int reserve_sms, __nv_bfloat16* out_hi,
-                          __nv_bfloat16* out_lo, unsigned long long wait_ns, int skip_x_loads) {
-  if (!sk.part || !sk.cnt || sk.ctas < 1) return cudaErrorInvalidValue;
+                          cudaStream_t st, int reserve_sms, __nv_bfloat16* out_hi, __nv_bfloat16* out_lo,
+                          unsigned long long wait_ns, int skip_x_loads) {
   if (!ttm_tc_supported(P, K, S, R) || (Rp != 16 && Rp != 32) || Rp < R || Kp < K || (Kp % 64) != 0)
     return cudaErrorNotSupported;
   if (((uintptr_t)Xhi & 15) || ((uintptr_t)Xlo & 15) || ((uintptr_t)Qt & 15)) return cudaErrorMisalignedAddress;
@@ -545,9 +472,6 @@ cudaError_t launch_ttm_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo, co
   prm.status = dev_status;
   prm.wait_ns = wait_ns ? wait_ns : tc::kTimeoutNs;
   prm.skip_x_loads = skip_x_loads;
-  prm.part = sk.part;
-  prm.cnt = sk.cnt;
-  const int64_t iters = prm.T * (int64_t)prm.nkb;  // stream-K iterations: no more CTAs than these
   if (prm.nkb * 64 > Kp) return cudaErrorInvalidValue;
   const size_t smem = 1024 + (size_t)TC_NST * TC_STAGE_BYTES + (size_t)prm.nkb * 2 * Rp * 128 +
                       ((sizeof(TcSmemTail) + 15) / 16) * 16 + (km ? 4 * 32 * 33 * sizeof(float) : 0);
@@ -577,17 +501,15 @@ cudaError_t launch_ttm_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo, co
     cfg.gridDim = dim3((unsigned)cl, 1, 1);
     int nclusters = 0;
     if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) == cudaSuccess && nclusters >= 2) {
-      const int64_t ncl = std::min<int64_t>(std::min<int64_t>(iters / cl, nclusters - 1), sk.ctas / cl);
-      if (ncl >= 1) {
-        cfg.gridDim = dim3((unsigned)(ncl * cl), 1, 1);
-        e = cudaLaunchKernelEx(&cfg, kern, tmh, tml, tmq, prm);
-        if (e == cudaSuccess) return cudaSuccess;
-      }
+      const int64_t want = (prm.T + cl - 1) / cl;  // clusters with at least one tile each
+      const int64_t ncl = std::min<int64_t>(want, nclusters - 1);
+      cfg.gridDim = dim3((unsigned)(ncl * cl), 1, 1);
+      e = cudaLaunchKernelEx(&cfg, kern, tmh, tml, tmq, prm);
+      if (e == cudaSuccess) return cudaSuccess;
     }
     cudaGetLastError();  // fall back to a plain grid that leaves reserve_sms SMs idle
   }
-  const int64_t grid = std::min<int64_t>(std::min<int64_t>(iters, std::max(1, tc::num_sms() - std::max(0, reserve_sms))),
-                                         sk.ctas);
+  const int64_t grid = std::min<int64_t>(prm.T, std::max(1, tc::num_sms() - std::max(0, reserve_sms)));
   kern<<<(unsigned)grid, TC_THREADS, smem, st>>>(tmh, tml, tmq, prm);
   return cudaGetLastError();
 }

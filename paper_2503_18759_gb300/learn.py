@@ -185,7 +185,7 @@ def evaluate(params, problems, max_sweeps: int = 120, prec: int = b.PREC_SPLIT_B
             k = int(hit[0]) if len(hit) else max_sweeps - 1
             row[name] = {"sweeps_to_target": k + 1, "seconds_to_target": float(t[k]), "reached": bool(len(hit)),
                          "final_fit": float(f[-1]), "s_per_sweep": float(t[-1] / len(t)), "proposals": int(props),
-                         "accepted": int(acc), "judged": int(jd)}
+                         "accepted": int(acc), "judged": int(jd), "sweeps_run": int(len(f))}
         out.append(row)
     return out
 
@@ -201,7 +201,7 @@ def summarize(rows):
     s["learned"]["accept_rate"] = float(sum(r["learned"]["accepted"] for r in rows) /
                                         max(1, sum(r["learned"]["proposals"] for r in rows)))
     s["learned"]["judged_per_sweep"] = float(sum(r["learned"]["judged"] for r in rows) /
-                                             max(1, sum(r["learned"]["sweeps_to_target"] for r in rows)))
+                                             max(1, sum(r["learned"]["sweeps_run"] for r in rows)))
     # head-to-head: problems where the learned proposer reaches the target in fewer / more
     # seconds than each other mode
     for other in ("none", "paper"):
