@@ -392,7 +392,60 @@ def extras(args, prob, X, dev, b):
     res["qr_routes"] = routes
     res["other_workloads"] = other_workloads(b, dev)
     res["e1_shapes"] = e1_shapes(b, dev)
+    res["high_rank"] = high_rank(b, dev)
     return res
+
+
+def high_rank(b, dev, sweeps=5):
+    """The high-rank regime (Table 7: 500^3 at R = 75 and 150, 600^3 at R = 175) on the split path:
+    ms per sweep, and the first-level TTM's device time (per-launch CUDA events) with its
+    tensor-core rates.  useful = 2 I^N R flops per full TTM; issued = the four bf16 products the
+    MMAs execute, 8 Rp flops per element of the tile-padded tensor.  Fractions are of the measured
+    bf16 peak (the MMA pipe's ceiling for these operands)."""
+    import torch
+    from paper_2503_18759_gb300 import inputs
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak = float(json.load(f)["bf16_tflops"])
+        kind = "measured"
+    except Exception:
+        peak, kind = 1900.0, "fallback"
+    out = {}
+    for dims, R in (([500] * 3, 75), ([500] * 3, 150), ([600] * 3, 175)):
+        name = "x".join(str(d) for d in dims) + f"_r{R}"
+        prob = inputs.make_problem_device(name, dims, R, seed=9, c=0.5, eta=1e-3, device=str(dev))
+        o = b.make_options(tree=b.TREE_RESTRUCTURED, prec=b.PREC_SPLIT_BF16, extrap=b.EXTRAP_PAPER)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with b.Decomposition(prob.dims, prob.R, prob.X.data_ptr(), False, prob.A0, o) as d:
+            d.sweep(2)
+            torch.cuda.synchronize()
+            e0.record()
+            f = d.sweep(sweeps)
+            e1.record()
+            torch.cuda.synchronize()
+            d.set_timing(True)
+            d.sweep(sweeps)
+            st = d.stats()
+            d.set_timing(False)
+        n_full = st.n_bucket[0]
+        full_ms = st.ms_bucket[0] / max(n_full, 1)
+        I = dims[0]
+        Rp = (R + 15) // 16 * 16
+        useful = 2.0 * I ** 3 * R
+        padded = I * I * (-(-I // 64) * 64)  # the contiguous mode padded to whole 64-wide blocks (MN-major)
+        issued = 8.0 * Rp * padded
+        tf_u = useful / (full_ms * 1e-3) / 1e12 if n_full else None
+        tf_i = issued / (full_ms * 1e-3) / 1e12 if n_full else None
+        out[name] = {"ms_per_sweep": e0.elapsed_time(e1) / sweeps, "fit_last": float(f[-1]),
+                     "ttm_full_ms": full_ms, "ttm_full_launches": int(n_full),
+                     "useful_tflops": tf_u, "issued_tflops": tf_i,
+                     "useful_frac": tf_u / peak if tf_u else None, "issued_frac": tf_i / peak if tf_i else None,
+                     "hbm_gbs": (I ** 3 * 4 + I * I * R * 4) / (full_ms * 1e-3) / 1e9 if n_full else None,
+                     "buckets_ms_per_sweep": {nm: st.ms_bucket[i] / sweeps for i, nm in enumerate(b.BUCKETS)},
+                     "peak_tflops": peak, "peak_kind": f"{kind} bf16 dense (burst)"}
+        del prob
+        torch.cuda.empty_cache()
+    return out
 
 
 E1_SHAPES = [[700] * 3, [150] * 4, [50] * 5, [25] * 6]

@@ -390,10 +390,11 @@ cpqr_status run_ttm(cpqr_ctx* ctx, const Op& op) {
       int64_t Pj = 1, Sj = 1;
       for (int q = 0; q < j; ++q) Pj *= od[q];
       for (int q = j + 1; q < ctx->N; ++q) Sj *= od[q];
-      if (!ttm_tc_supported(Pj, od[j], Sj, R)) cuda_core_consumer = true;
+      if (!(ctx->wide ? ttm_tc_wide_supported(Pj, od[j], Sj, R) : ttm_tc_supported(Pj, od[j], Sj, R)))
+        cuda_core_consumer = true;
     }
-    need_split = nfree >= 2 && !ctx->wide;
-    need_f32 = nfree < 2 || cuda_core_consumer || ctx->wide;
+    need_split = nfree >= 2;
+    need_f32 = nfree < 2 || cuda_core_consumer;
   }
   const size_t bytes = split ? split_node_bytes(n_out, need_f32, need_split) : (size_t)n_out * es;
   void* out = nullptr;
@@ -413,10 +414,34 @@ cpqr_status run_ttm(cpqr_ctx* ctx, const Op& op) {
     else
       CK(launch_ttm<double, double, double>((const double*)sb.p, ctx->Q[k], (double*)out, P, K, S, R, st));
   } else if (ctx->wide) {
-    // the CUDA-core FP32 TTM from FP32 nodes (every wide-path node keeps its FP32 copy)
-    if (!sb.has_f32) return fail(ctx, CPQR_EINVAL);
-    CK((launch_ttm_wide<float, float, float, float>((const float*)sb.p, ctx->Qf[k], static_cast<float*>(out), P, K,
-                                                     S, R, st)));
+    __nv_bfloat16 *ohi = nullptr, *olo = nullptr;
+    if (need_split) split_views(out, n_out, need_f32, &ohi, &olo);
+    float* of = need_f32 ? static_cast<float*>(out) : nullptr;
+    if (ttm_tc_wide_supported(P, K, S, R) && (sb.is_x || sb.has_split)) {
+      const __nv_bfloat16 *shi = ctx->Xhi, *slo = ctx->Xlo;
+      if (!sb.is_x) {
+        __nv_bfloat16 *h, *l;
+        split_views(sb.p, P * K * S, sb.has_f32, &h, &l);
+        shi = h;
+        slo = l;
+      }
+      CK(launch_ttm_tc_wide(shi, slo, ctx->Qt[k], ctx->Rp, ctx->Kp[k], of, P, K, S, R, ctx->dstatus, st, ohi, olo));
+    } else {
+      // the CUDA-core FP32 TTM from the node's FP32 copy (kept for every CUDA-core consumer)
+      if (!sb.has_f32) return fail(ctx, CPQR_EINVAL);
+      float* o32 = of;
+      if (!o32) {
+        void* tmp = nullptr;
+        CK(ctx->pool.get((size_t)n_out * 4, &tmp));
+        o32 = static_cast<float*>(tmp);
+      }
+      CK((launch_ttm_wide<float, float, float, float>((const float*)sb.p, ctx->Qf[k], o32, P, K, S, R, st)));
+      if (need_split) {
+        CK(launch_split_x(o32, ohi, olo, n_out, st));
+        ctx->launches += 1;
+      }
+      if (!of) ctx->pool.put((size_t)n_out * 4, o32);
+    }
   } else {
     __nv_bfloat16 *ohi = nullptr, *olo = nullptr;
     if (need_split) split_views(out, n_out, need_f32, &ohi, &olo);
@@ -737,6 +762,10 @@ cpqr_status run_update(cpqr_ctx* ctx, int n, int leaf, double beta, int next_mod
                                    ctx->lambda, ctx->fit_terms, ctx->wrows, ctx->dstatus, st));
     CK(launch_wide_qr(ctx->A[n], I, R, nullptr, 0, ctx->Q[n], ctx->Qf[n], ctx->Rf[n], ctx->wq_main, ctx->dstatus,
                       st));
+    if (!fp64) {  // the tensor cores' operand: bf16 hi / lo of the new Q_n^T
+      cpqr_status sq = stage_q(ctx, n);
+      if (sq != CPQR_OK) return sq;
+    }
     std::swap(ctx->Q0, ctx->Q0prev[n]);
     std::swap(ctx->Q0f, ctx->Q0fprev[n]);
     ctx->has_prev[n] = true;
@@ -1692,7 +1721,7 @@ cpqr_status cp_als_qr_schedule(int32_t N, const int64_t* dims, int32_t R, int32_
 
 cpqr_status cpqr_ttm(const void* T_dev, int32_t nd, const int64_t* tdims, int32_t k, const void* Q_dev, int32_t R,
                      void* out_dev, int32_t dtype, void* stream) {
-  if (!T_dev || !Q_dev || !out_dev || !tdims || nd < 1 || nd > 8 || k < 0 || k >= nd || R < 1 || R > CPQR_MAXR)
+  if (!T_dev || !Q_dev || !out_dev || !tdims || nd < 1 || nd > 8 || k < 0 || k >= nd || R < 1 || R > CPQR_MAXR_WIDE)
     return CPQR_EINVAL;
   int64_t P = 1, S = 1;
   for (int j = 0; j < k; ++j) P *= tdims[j];
@@ -1709,7 +1738,8 @@ cpqr_status cpqr_ttm(const void* T_dev, int32_t nd, const int64_t* tdims, int32_
       break;
     case 2: e = launch_ttm<float, double, double>((const float*)T_dev, (const double*)Q_dev, (double*)out_dev, P, K, S, R, st); break;
     case 3: {
-      if (!ttm_tc_supported(P, K, S, R)) return CPQR_EUNSUPPORTED;
+      const bool wide_tc = R > CPQR_MAXR;
+      if (!(wide_tc ? ttm_tc_wide_supported(P, K, S, R) : ttm_tc_supported(P, K, S, R))) return CPQR_EUNSUPPORTED;
       const int Rp = ((R + 15) / 16) * 16;
       const int64_t Kp = ((K + 63) / 64) * 64;
       const int64_t n = P * K * S;
@@ -1723,7 +1753,9 @@ cpqr_status cpqr_ttm(const void* T_dev, int32_t nd, const int64_t* tdims, int32_
       e = cudaMemsetAsync(ds, 0, 4, st);
       if (e == cudaSuccess) e = launch_split_x((const float*)T_dev, xh, xl, n, st);
       if (e == cudaSuccess) e = launch_split_q((const double*)Q_dev, K, R, qt, Rp, Kp, st);
-      if (e == cudaSuccess) e = launch_ttm_tc(xh, xl, qt, Rp, Kp, (float*)out_dev, P, K, S, R, ds, st);
+      if (e == cudaSuccess)
+        e = wide_tc ? launch_ttm_tc_wide(xh, xl, qt, Rp, Kp, (float*)out_dev, P, K, S, R, ds, st)
+                    : launch_ttm_tc(xh, xl, qt, Rp, Kp, (float*)out_dev, P, K, S, R, ds, st);
       unsigned int hs = 0;
       if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, ds, 4, cudaMemcpyDeviceToHost, st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(st);

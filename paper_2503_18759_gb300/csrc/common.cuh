@@ -279,6 +279,13 @@ template <typename TV>
 cudaError_t launch_wide_finish(const TV* vw, int nparts, int64_t I, int C, int R, const double* R0, double beta,
                                double alpha, double* A, double* lambda, double* fit_terms, double* work_rows,
                                unsigned int* status, cudaStream_t st);
+// Tensor-core TTM for 32 < R <= 192 (ttm_tc_wide.cu): operands as for launch_ttm_tc, Rp = R rounded
+// up to 16, Qt = bf16 hi / lo of Q^T (2 x Rp x Kp).
+bool ttm_tc_wide_supported(int64_t P, int64_t K, int64_t S, int R);
+cudaError_t launch_ttm_tc_wide(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo, const __nv_bfloat16* Qt, int Rp,
+                               int64_t Kp, float* out, int64_t P, int64_t K, int64_t S, int R,
+                               unsigned int* dev_status, cudaStream_t st, __nv_bfloat16* out_hi = nullptr,
+                               __nv_bfloat16* out_lo = nullptr);
 // TTM on the CUDA cores for any R (tiled GEMM, accumulation in TAcc).
 template <typename TT, typename TQ, typename TO, typename TAcc>
 cudaError_t launch_ttm_wide(const TT* T, const TQ* Q, TO* out, int64_t P, int64_t K, int64_t S, int R,

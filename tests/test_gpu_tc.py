@@ -64,3 +64,23 @@ def test_split_ttm_has_no_systematic_bias(P, K, S):
     rel = (out.double() - ref) / ref
     assert abs(rel.mean().item()) < 1e-7, rel.mean().item()
     assert rel.pow(2).mean().sqrt().item() < 5e-7
+
+
+# wide ranks (the high-rank regime): MN-major and K-major, Rp = 48 .. 192, ragged tails, two
+# accumulator buffers (Rp <= 128) and one (Rp > 128)
+SHAPES_WIDE = [(1, 64, 200, 48), (3, 130, 72, 64), (2, 400, 136, 100), (1, 160, 1000, 150), (300, 200, 1, 150),
+               (77, 200, 1, 192), (2, 200, 64, 176), (1000, 400, 1, 64)]
+
+
+@pytest.mark.parametrize("P,K,S,R", SHAPES_WIDE)
+def test_wide_split_ttm_matches_oracle(P, K, S, R):
+    g = np.random.default_rng(P * 31 + K * 7 + S + R)
+    X = g.standard_normal((P, K, S)).astype(np.float32)
+    Q = np.linalg.qr(g.standard_normal((K, R)))[0]
+    ref = o.ttm_qt(X.astype(np.float64), Q, 1)
+    Xd, Qd = torch.from_numpy(X).to(DEV), torch.from_numpy(Q).to(DEV)
+    out = torch.empty((P, R, S), dtype=torch.float32, device=DEV)
+    b.cpqr_ttm(Xd.data_ptr(), [P, K, S], 1, Qd.data_ptr(), R, out.data_ptr(), b.TTM_SPLIT_BF16)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < 2e-4
