@@ -35,7 +35,7 @@ WORKLOAD = "cube400_r32_c09"
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture of the current kernels
 # on this workload (the same launch shapes through bench.py --kernel); None where a kernel changed
 # after its capture
-TTM_TC_TRAFFIC = 270.5e6    # ttm_tc_kernel<0>, 1 x 400 x 160000 -> R = 32 (256.1 MB read + 14.4 MB written)
+TTM_TC_TRAFFIC = 270.8e6    # ttm_tc_kernel<0>, 1 x 400 x 160000 -> R = 32 (256.1 MB read + 14.6 MB written)
 TTM_DEEP_TRAFFIC = 20.6e6   # ttm_tc_kernel<1>, 12800 x 400 x 1 -> R = 32 (20.6 MB read, output left in L2)
 # whole-GPU FP64 DFMA rate measured by a probe on the GB300s (TFLOP/s)
 FP64_PEAK_TFLOPS = 1.20
@@ -130,6 +130,13 @@ def run_reference(args, rank):
             "e2e": {"value": per, "unit": "s/sweep", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def _guard(st, args):
+    """How the Gram-route QRs of the run (warm-up, timed and timing sweeps) were finished when their
+    first Cholesky pass was not accurate enough: by a second Cholesky pass or by the Householder QR."""
+    return {"second_cholesky_pass": int(st.qr_second_pass), "householder": int(st.qr_fallbacks),
+            "sweeps": int(args.warmup + 2 * args.steps)}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2503_18759_gb300 import binding as b
@@ -196,6 +203,7 @@ def run_ours(args, rank, world, local_rank):
                    {name: st.n_bucket[i] / max(args.steps, 1) for i, name in enumerate(b.BUCKETS)},
                "ttm_flops_per_sweep": st.ttm_flops / (args.warmup + 2 * args.steps), "gpu_launches": int(launches),
                "fit_last": float(fits[-1]) if len(fits) else None,
+               "qr_guard": _guard(st, args),
                "note": "extra workload: not the bench line (no roofline, e2e or CPU baseline)"}
     elif rank == 0:
         hbm, peak_kind = _peaks()
@@ -263,7 +271,8 @@ def run_ours(args, rank, world, local_rank):
                "roofline_factor_qr": roof_qr,
                "buckets_ms_per_sweep": buckets,
                "gpu_launches": int(launches),
-               "fit_last": float(fits[-1]) if len(fits) else None}
+               "fit_last": float(fits[-1]) if len(fits) else None,
+               "qr_guard": _guard(st, args)}
     dec.close()
     if rank == 0 and not args.quick and wname == WORKLOAD:
         out.update(extras(args, prob, X, dev, b))

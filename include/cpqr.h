@@ -137,6 +137,9 @@ typedef struct {
   int64_t judged;          /* learned proposals judged against the rule's sweep (two sweeps each) */
   int64_t preapproved;     /* learned proposals run within an approval window */
   int64_t deferred;        /* learned proposals set aside (the rule ran) within a hold after a loss */
+  int64_t qr_second_pass;  /* Gram-route QRs (R <= 32) whose first Cholesky pass left 1e-8 < max |E| <=
+                              1e-3 and that a second Cholesky pass finished (CholeskyQR2) instead
+                              of the Householder QR; reading it synchronises the context's streams */
 } cpqr_stats;
 
 /* Turn per-launch CUDA-event timing on (1) or off (0); resets the bucket times. */

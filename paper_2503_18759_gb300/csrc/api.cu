@@ -1519,12 +1519,17 @@ cpqr_status cp_als_qr_stats(cpqr_ctx* ctx, cpqr_stats* out) {
     out->n_bucket[b] = ctx->n_bucket[b];
   }
   if (ctx->zg_work && ctx->fg_work) {
-    int cnt[2] = {0, 0};
+    int cnt[4] = {0, 0, 0, 0};
     if (cudaStreamSynchronize(ctx->st) != cudaSuccess || cudaStreamSynchronize(ctx->st2) != cudaSuccess ||
         cudaMemcpy(&cnt[0], gram_fallback_counter(ctx->zg_work), sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
-        cudaMemcpy(&cnt[1], gram_fallback_counter(ctx->fg_work), sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        cudaMemcpy(&cnt[1], gram_fallback_counter(ctx->fg_work), sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(&cnt[2], gram_second_pass_counter(ctx->zg_work), sizeof(int), cudaMemcpyDeviceToHost) !=
+            cudaSuccess ||
+        cudaMemcpy(&cnt[3], gram_second_pass_counter(ctx->fg_work), sizeof(int), cudaMemcpyDeviceToHost) !=
+            cudaSuccess)
       return fail(ctx, CPQR_ECUDA);
     out->qr_fallbacks = (int64_t)cnt[0] + cnt[1];
+    out->qr_second_pass = (int64_t)cnt[2] + cnt[3];
   }
   return ctx->err;
 }

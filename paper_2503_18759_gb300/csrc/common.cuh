@@ -105,9 +105,21 @@ size_t house_qr_work_doubles(int64_t M, int R);
 struct TriPtrs {
   const double* p[CPQR_MAXN];
 };
-// run_if (optional device pair): the QR runs only if run_if[0] != 0, and then adds 1 to run_if[1].
+// The first Cholesky pass of a guarded Gram-route QR of an M x R matrix Y (device, row stride
+// CPQR_MAXR for F and R1, R for Q1): F = striu(E) + diag(E) / 2 with E = Q1^T Q1 - I, Q1 (M x R)
+// and R1 with Q1 R1 = Y.  Given to the fallback QR, a flag of exactly 1 (the first pass's E too
+// large for its first-order correction, every pivot positive) makes it finish by a second
+// Cholesky pass instead of the Householder QR: R2 = chol(I + E), Q = Q1 R2^{-1}, R = R2 R1.
+struct CholQr2Src {
+  const double* F;
+  const double* Q1;
+  const double* R1;
+};
+// run_if (optional device triple): the QR runs only if run_if[0] != 0; a Householder QR that runs
+// adds 1 to run_if[1], a second Cholesky pass (c2 given, run_if[0] == 1) adds 1 to run_if[2].
 cudaError_t launch_krp_qr(const ZPlan& plan, TriPtrs Rs, double* Q0, double* R0, double* work,
-                          unsigned int* dev_status, cudaStream_t st, float* Q0f = nullptr, int* run_if = nullptr);
+                          unsigned int* dev_status, cudaStream_t st, float* Q0f = nullptr, int* run_if = nullptr,
+                          const CholQr2Src* c2 = nullptr);
 size_t krp_qr_work_doubles(const ZPlan& plan);
 // QR of a product of m >= 2 triangles as m - 1 staircase QRs of two-triangle products (plan2:
 // the plan for m = 2) and m - 2 FP64 assemblies; work: krp_nested_work_doubles(m, R) doubles.
@@ -210,7 +222,8 @@ struct FinishOut {
   int64_t Kp = 0;
 };
 cudaError_t launch_mode_finish(const double* Ahat, const double* fitpart, int nfit, int64_t I, int R, FinishOut out,
-                               double* work, unsigned int* dev_status, cudaStream_t st, int* run_if = nullptr);
+                               double* work, unsigned int* dev_status, cudaStream_t st, int* run_if = nullptr,
+                               const CholQr2Src* c2 = nullptr);
 // The same finish by the guarded Gram route (krp_gram.cu): Gram of A^ from the hpart block
 // partials of launch_finish_prep, lambda, Cholesky of the equilibrated Gram (..._chol, which can
 // also store the new factor's equilibrated Gram, float-float 32 x 32 upper, and its unit column
@@ -233,6 +246,8 @@ cudaError_t launch_finish_gram(const double* Ahat, const double* hpart, const do
 cudaError_t launch_tri_gram(const double* T, int R, float2* Gf, double* s, cudaStream_t st);
 // Runs of the Householder fallback recorded in a Gram-route workspace (device int counter).
 int* gram_fallback_counter(double* gram_work);
+// Runs of the second Cholesky pass recorded in a Gram-route workspace (device int counter).
+int* gram_second_pass_counter(double* gram_work);
 
 // ||X||^2 in FP64: block partials into work (norm2_work_doubles()), summed in a fixed order into
 // out[0], so every context on the same tensor gets the same bits.

@@ -13,8 +13,11 @@
 // order.  Q0 R0 = Q1 (I - F^2) R1 = Z - O(|E|^2), Q0^T Q0 = I + O(|E|^2), and R0 has a positive
 // diagonal, so (Q0, R0) is the unique QR of Z whenever |E| is small; |E| grows like
 // kappa(Z)^2 * 2^-53.  If a pivot of the Cholesky is not positive or max |E| > kEMax, a device flag
-// makes the Householder staircase QR (smallqr.cu), launched after these kernels, recompute Q0 and
-// R0; otherwise it returns at once.  The Householder QR's stability is thus kept for every Z,
+// makes the QR kernel launched after these (smallqr.cu) recompute Q0 and R0; otherwise it returns at
+// once.  The flag has two levels: max |E| in (kEMax, kE2Max] with every pivot positive (bit 0
+// alone) sends it to a second Cholesky pass on Q1 (CholeskyQR2: R2 = chol(I + E), Q = Q1 R2^{-1},
+// R = R2 R1), which leaves Q^T Q - I at rounding level because Q1 is already within 1e-3 of
+// orthonormal; a failed pivot, a larger or non-finite E (bit 1) send it to the Householder QR.  The Householder QR's stability is thus kept for every Z,
 // while the common well-conditioned case costs one 32-step Cholesky plus three row-parallel FP64
 // passes over all SMs instead of 32 cluster-wide Householder steps.  For Z, the Gram is the
 // Hadamard product of the two factors' stored Grams (kg_chol_kernel); for A, it comes from the
@@ -41,6 +44,8 @@ constexpr int KG_MAXR = CPQR_MAXR;
 constexpr int KG_LD = KG_MAXR + 1;
 // max |E| accepted: the neglected O(E^2) terms stay below 1e-16
 constexpr double kEMax = 1e-8;
+// max |E| handed to the second Cholesky pass instead of the Householder QR
+constexpr double kE2Max = 1e-3;
 
 // Workspace layout (doubles, every section 128-byte aligned): the int pair {fallback flag,
 // fallback count} (at a fixed offset, so the count survives calls with different row counts),
@@ -264,7 +269,8 @@ __device__ __forceinline__ void chol_outputs(float2 (*U)[KG_LD], float2 (*V)[KG_
     w.R1[i * KG_MAXR + j] = r;
     w.S[i * KG_MAXR + j] = sv;
   }
-  if (tid == 0) *w.flag = acc ? (*w.flag | *bad) : *bad;  // acc: a later level of one nested QR
+  // bit 1 of the flag: a pivot failed (acc: a later level of one nested QR)
+  if (tid == 0) *w.flag = acc ? (*w.flag | (*bad ? 2 : 0)) : (*bad ? 2 : 0);
 }
 
 // Equilibrated Gram of an upper triangle T (one CTA of 256 threads per triangle, FP64):
@@ -554,7 +560,7 @@ __global__ void __launch_bounds__(128) kg_e_kernel(int M, int R, KgWork w) {
     const double f = (c == d) ? 0.5 * e : e;
     w.F[c * KG_MAXR + d] = f;
     w.Ff[c * KG_MAXR + d] = ff_st(ff_from_bits(f));
-    if (!(fabs(e) <= kEMax)) atomicOr(w.flag, 1);  // also catches NaN
+    if (!(fabs(e) <= kEMax)) atomicOr(w.flag, (fabs(e) <= kE2Max) ? 1 : 3);  // NaN: 3
   }
 }
 
@@ -619,7 +625,7 @@ __global__ void __launch_bounds__(128) kg_ered_kernel(int nblk, int R, KgWork w)
       const double f = (i == j) ? 0.5 * e : e;
       w.F[i * KG_MAXR + j] = f;
       w.Ff[i * KG_MAXR + j] = ff_st(ff_from_bits(f));
-      if (!(fabs(e) <= kEMax)) atomicOr(w.flag, 1);  // also catches NaN
+      if (!(fabs(e) <= kEMax)) atomicOr(w.flag, (fabs(e) <= kE2Max) ? 1 : 3);  // NaN: 3
     }
   }
 }
@@ -707,6 +713,7 @@ cudaError_t kg_cluster_attributes() {
 
 size_t factor_gram_work_doubles(int64_t Imax, int R) { return kg_work_doubles(Imax, R); }
 int* gram_fallback_counter(double* gram_work) { return reinterpret_cast<int*>(gram_work) + 1; }
+int* gram_second_pass_counter(double* gram_work) { return reinterpret_cast<int*>(gram_work) + 2; }
 
 cudaError_t launch_tri_gram(const double* T, int R, float2* Gf, double* s, cudaStream_t st) {
   if (R < 1 || R > KG_MAXR) return cudaErrorInvalidValue;
@@ -761,8 +768,10 @@ cudaError_t launch_krp_rows(const ZPlan& plan2, TriPtrs tri, int m, const GramPt
       if (nlaunch) *nlaunch = launches;
       return cudaSuccess;
     }
-    // the Householder staircase QR, which returns at once unless the flag was raised
-    e = launch_krp_qr(plan2, tri, Q0, R0, qr_work, dev_status, st, Q0f, w.flag);
+    // the second Cholesky pass or the Householder staircase QR, which return at once unless the
+    // flag was raised
+    const CholQr2Src c2{w.F, w.Q1, w.R1};
+    e = launch_krp_qr(plan2, tri, Q0, R0, qr_work, dev_status, st, Q0f, w.flag, &c2);
     if (nlaunch) *nlaunch = launches + 1;
     return e;
   }
@@ -877,8 +886,10 @@ cudaError_t launch_finish_gram_rows(const double* Ahat, const double* fitpart, i
   e = launch_pdl(kg_q0_kernel, dim3((M + 3) / 4), dim3(128), 0, st, M, R, w, out.Q, out.Qf, out.Rn, out.Qt, out.Rp,
                  out.Kp);
   if (e != cudaSuccess) return e;
-  // the Householder finish, which returns at once unless the flag was raised
-  return launch_mode_finish(Ahat, fitpart, nblk, I, R, out, qr_work, dev_status, st, w.flag);
+  // the second Cholesky pass or the Householder finish, which return at once unless the flag was
+  // raised
+  const CholQr2Src c2{w.F, w.Q1, w.R1};
+  return launch_mode_finish(Ahat, fitpart, nblk, I, R, out, qr_work, dev_status, st, w.flag, &c2);
 }
 
 cudaError_t launch_finish_gram(const double* Ahat, const double* hpart, const double* fitpart, int nblk, int64_t I,

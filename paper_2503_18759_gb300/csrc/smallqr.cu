@@ -83,6 +83,11 @@ struct QrParams {
   unsigned int* status;
   int* run_if;  // when set: the QR runs only if run_if[0] != 0 (a guarded fallback) and counts
                 // its runs in run_if[1]
+  // the guarded QR's first Cholesky pass (optional): with run_if[0] == 1 a second pass finishes
+  // the QR (counted in run_if[2]) and the Householder QR runs only if its Cholesky fails
+  const double* c2F;   // F = striu(E) + diag(E) / 2, E = Q1^T Q1 - I (row stride CPQR_MAXR)
+  const double* c2Q1;  // M x R, row stride R
+  const double* c2R1;  // R x R upper, row stride CPQR_MAXR
 };
 
 struct SmemLayout {
@@ -165,6 +170,160 @@ __device__ __forceinline__ void house_scalars(double s, double xj, double& alpha
   }
 }
 
+// Second Cholesky pass of a guarded Gram-route QR (CholeskyQR2), on the whole cluster; returns
+// false (every CTA alike) when it does not converge, and the caller then runs the Householder QR.
+// With E = Q1^T Q1 - I (max |E| <= 1e-3) and F = striu(E) + diag(E) / 2, the second Cholesky
+// factor is chol(I + E) = I + D with D upper triangular and D + D^T + D^T D = E, i.e. the fixed
+// point of D = F - up(D^T D), up(S) = striu(S) + diag(S) / 2 (a contraction by ~2 ||D||).  Its
+// inverse is I + X with X = -D - D X (a contraction by ~||D||).  Both iterations run on small
+// quantities only, in float-float on CTA 0 (~2^-48 relative of entries below 5e-4), until no
+// entry moves by more than 1e-17; then R = (I + D) R1 = R1 + D R1 and every row of
+// Q = Q1 (I + X) = Q1 + Q1 X take one FP64 addition each (as the first pass's correction does):
+// GB300's FP64 pipe is ~64 times slower than FP32, so an FP64 Cholesky and substitution here would
+// cost tens of microseconds.  Q R = Q1 R1 = the input, and Q^T Q = (I + D)^{-T} (I + E) (I + D)^{-1}
+// = I, both to the rounding of the final additions.  Every CTA copies X out of CTA 0's shared
+// memory and forms its rows t = rank + CL u, written where the Householder QR would write them
+// (with the FP32 copy and the tensor cores' hi / lo staging).  scr: 4 x 32 x 33 float2 + a flag of
+// this CTA's shared memory (the rows region, unused until the Householder prologue, which follows
+// a cluster barrier).
+template <int CL>
+__device__ bool second_pass(const QrParams& p, cg::cluster_group& cluster, int rank, double* scr) {
+  using namespace ffa;
+  constexpr int LD = CPQR_MAXR + 1;
+  constexpr int RR32 = CPQR_MAXR * CPQR_MAXR;
+  constexpr int EPT = RR32 / NT;  // entries per thread
+  constexpr float kMove = 1e-17f;
+  constexpr int kIters = 16;
+  float2 (*Dm)[LD] = reinterpret_cast<float2 (*)[LD]>(scr);
+  float2 (*Fm)[LD] = Dm + CPQR_MAXR;
+  float2 (*Xm)[LD] = Fm + CPQR_MAXR;
+  float2 (*Tm)[LD] = Xm + CPQR_MAXR;  // R1 in float-float
+  int* okp = reinterpret_cast<int*>(Tm + CPQR_MAXR);
+  const int tid = threadIdx.x, lane = tid & 31, R = p.R;
+  const ffn zero = ff_make(0.0f, 0.0f);
+  if (rank == 0) {
+    for (int e = tid; e < RR32; e += NT) {
+      const int i = e / CPQR_MAXR, j = e % CPQR_MAXR;
+      const bool up = (i <= j && j < R);
+      const float2 f = up ? ff_st(ff_from_bits(p.c2F[i * CPQR_MAXR + j])) : make_float2(0.0f, 0.0f);
+      Fm[i][j] = f;
+      Dm[i][j] = f;
+      Tm[i][j] = up ? ff_st(ff_from_bits(p.c2R1[i * CPQR_MAXR + j])) : make_float2(0.0f, 0.0f);
+    }
+    __syncthreads();
+    // D = F - up(D^T D), (D^T D)[i][j] = sum_{k <= i} D[k][i] D[k][j]
+    bool conv = false;
+    for (int it = 0; it < kIters && !conv; ++it) {
+      ffn nv[EPT];
+      int moved = 0;
+#pragma unroll
+      for (int q = 0; q < EPT; ++q) {
+        const int e = tid + q * NT, i = e / CPQR_MAXR, j = e % CPQR_MAXR;
+        nv[q] = zero;
+        if (i <= j && j < R) {
+          ffn s = zero;
+          for (int k = 0; k <= i; ++k) s = ff_fms(s, ff_neg(ff_ld(Dm[k][i])), ff_ld(Dm[k][j]));
+          if (i == j) s = ff_make(0.5f * s.hi, 0.5f * s.lo);
+          nv[q] = ff_add(ff_ld(Fm[i][j]), ff_neg(s));
+          if (!(fabsf(ff_add(nv[q], ff_neg(ff_ld(Dm[i][j]))).hi) <= kMove)) moved = 1;  // NaN moves
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < EPT; ++q) {
+        const int e = tid + q * NT, i = e / CPQR_MAXR, j = e % CPQR_MAXR;
+        if (i <= j && j < R) Dm[i][j] = ff_st(nv[q]);
+      }
+      conv = (__syncthreads_or(moved) == 0);
+    }
+    // X = -D - D X, (D X)[i][j] = sum_{i <= k <= j} D[i][k] X[k][j]; X_0 = -D
+    bool convx = false;
+    if (conv) {
+      for (int e = tid; e < RR32; e += NT) {
+        const int i = e / CPQR_MAXR, j = e % CPQR_MAXR;
+        Xm[i][j] = (i <= j && j < R) ? ff_st(ff_neg(ff_ld(Dm[i][j]))) : make_float2(0.0f, 0.0f);
+      }
+      __syncthreads();
+      for (int it = 0; it < kIters && !convx; ++it) {
+        ffn nv[EPT];
+        int moved = 0;
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) {
+          const int e = tid + q * NT, i = e / CPQR_MAXR, j = e % CPQR_MAXR;
+          nv[q] = zero;
+          if (i <= j && j < R) {
+            ffn s = ff_ld(Dm[i][j]);
+            for (int k = i; k <= j; ++k) s = ff_fms(s, ff_neg(ff_ld(Dm[i][k])), ff_ld(Xm[k][j]));
+            nv[q] = ff_neg(s);
+            if (!(fabsf(ff_add(nv[q], ff_neg(ff_ld(Xm[i][j]))).hi) <= kMove)) moved = 1;
+          }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) {
+          const int e = tid + q * NT, i = e / CPQR_MAXR, j = e % CPQR_MAXR;
+          if (i <= j && j < R) Xm[i][j] = ff_st(nv[q]);
+        }
+        convx = (__syncthreads_or(moved) == 0);
+      }
+    }
+    if (convx) {
+      // R = R1 + D R1, (D R1)[i][j] = sum_{i <= k <= j} D[i][k] R1[k][j]
+      for (int e = tid; e < RR32; e += NT) {
+        const int i = e / CPQR_MAXR, j = e % CPQR_MAXR;
+        if (i < R && j < R) {
+          double r = 0.0;
+          if (i <= j) {
+            ffn s = zero;
+            for (int k = i; k <= j; ++k) s = ff_fms(s, ff_neg(ff_ld(Dm[i][k])), ff_ld(Tm[k][j]));
+            r = p.c2R1[i * CPQR_MAXR + j] + ff_val(s);
+          }
+          p.Rout[i * R + j] = r;
+        }
+      }
+      if (tid == 0) atomicAdd(p.run_if + 2, 1);
+    }
+    if (tid == 0) *okp = convx ? 1 : 0;
+  }
+  cluster.sync();
+  float2 (*X0)[LD] = cluster.map_shared_rank(Xm, 0);
+  // not converged: every CTA goes on to the Householder QR, whose prologue writes this shared
+  // memory only after its first cluster barrier
+  if (*cluster.map_shared_rank(okp, 0) == 0) return false;
+  if (rank != 0) {
+    for (int e = tid; e < CPQR_MAXR * LD; e += NT) Xm[e / LD][e % LD] = X0[e / LD][e % LD];
+    __syncthreads();
+  }
+  cluster.sync();  // no CTA reads CTA 0's copy any more
+  const int M = p.M;
+  const int L = (M > rank) ? (M - rank + CL - 1) / CL : 0;
+  ffn xcol[CPQR_MAXR];  // X[k][lane], k <= lane
+#pragma unroll
+  for (int k = 0; k < CPQR_MAXR; ++k) xcol[k] = (k <= lane && lane < R) ? ff_ld(Xm[k][lane]) : zero;
+  for (int u = (int)(threadIdx.x >> 5); u < L; u += NW) {
+    const int t = rank + CL * u;
+    const double q1 = (lane < R) ? p.c2Q1[(size_t)t * R + lane] : 0.0;
+    const ffn qf = ff_from_bits(q1);
+    ffn acc[4] = {zero, zero, zero, zero};
+#pragma unroll
+    for (int k = 0; k < CPQR_MAXR; ++k)
+      if (k < R) acc[k & 3] = ff_fms(acc[k & 3], ff_neg(ff_shfl(qf, k)), xcol[k]);
+    const double q = q1 + ff_val(ff_add(ff_add(acc[0], acc[1]), ff_add(acc[2], acc[3])));
+    if (lane < R) {
+      p.Q[(size_t)t * R + lane] = q;
+      if (p.Qf) p.Qf[(size_t)t * R + lane] = (float)q;
+      if (p.mode == MODE_FINISH && p.fin.Qt) {
+        const float q32 = (float)q;
+        const __nv_bfloat16 h = __float2bfloat16_rn(q32);
+        const size_t e = (size_t)lane * p.fin.Kp + t;
+        p.fin.Qt[e] = h;
+        p.fin.Qt[(size_t)p.fin.Rp * p.fin.Kp + e] = __float2bfloat16_rn(q32 - __bfloat162float(h));
+      }
+    }
+  }
+  return true;
+}
+
 // Named barrier for warps 0..3 (128 threads).
 __device__ __forceinline__ void sync_warps0to3() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
@@ -198,7 +357,9 @@ __global__ void __launch_bounds__(NT, 1) qr_cluster_kernel(QrParams p) {
   double (*VT)[CPQR_MAXR] = reinterpret_cast<double (*)[CPQR_MAXR]>(&sm.big[RR]);
 
   if (p.run_if) {
-    if (*(volatile const int*)p.run_if == 0) return;  // every CTA reads the same flag
+    const int flag = *(volatile const int*)p.run_if;  // every CTA reads the same flag
+    if (flag == 0) return;
+    if (flag == 1 && p.c2F && second_pass<CL>(p, cluster, rank, rows_smem)) return;
     if (rank == 0 && tid == 0) atomicAdd(p.run_if + 1, 1);
   }
   // mbarriers of the st.async exchanges, armed for their first phase before any peer can send
@@ -707,7 +868,7 @@ cudaError_t launch_house_qr(const double* A, int64_t M, int R, double* Q, double
 }
 
 cudaError_t launch_krp_qr(const ZPlan& plan, TriPtrs Rs, double* Q0, double* R0, double* work,
-                          unsigned int* dev_status, cudaStream_t st, float* Q0f, int* run_if) {
+                          unsigned int* dev_status, cudaStream_t st, float* Q0f, int* run_if, const CholQr2Src* c2) {
   QrParams p{};
   p.mode = MODE_KRP;
   if (plan.M > (int64_t(1) << 30)) return cudaErrorInvalidValue;
@@ -723,6 +884,11 @@ cudaError_t launch_krp_qr(const ZPlan& plan, TriPtrs Rs, double* Q0, double* R0,
   p.Rout = R0;
   p.status = dev_status;
   p.run_if = run_if;
+  if (c2 && run_if) {
+    p.c2F = c2->F;
+    p.c2Q1 = c2->Q1;
+    p.c2R1 = c2->R1;
+  }
   return run(p, st);
 }
 
@@ -928,7 +1094,8 @@ template cudaError_t launch_finish_prep<float>(const float*, int, int64_t, int, 
                                                double*, double*, double*, unsigned int*, cudaStream_t);
 
 cudaError_t launch_mode_finish(const double* Ahat, const double* fitpart, int nfit, int64_t I, int R, FinishOut out,
-                               double* work, unsigned int* dev_status, cudaStream_t st, int* run_if) {
+                               double* work, unsigned int* dev_status, cudaStream_t st, int* run_if,
+                               const CholQr2Src* c2) {
   QrParams p{};
   p.mode = MODE_FINISH;
   if (I > (int64_t(1) << 30)) return cudaErrorInvalidValue;
@@ -945,6 +1112,11 @@ cudaError_t launch_mode_finish(const double* Ahat, const double* fitpart, int nf
   p.Rout = out.Rn;
   p.status = dev_status;
   p.run_if = run_if;
+  if (c2 && run_if) {
+    p.c2F = c2->F;
+    p.c2Q1 = c2->Q1;
+    p.c2R1 = c2->R1;
+  }
   return run(p, st);
 }
 

@@ -207,6 +207,38 @@ def test_factor_qr_guard_hands_collinear_factor_to_householder(route):
         assert st.qr_fallbacks == 0
 
 
+@pytest.mark.parametrize("route", [b.QR_GRAM, b.QR_HOUSEHOLDER], ids=["gram", "householder"])
+def test_factor_qr_second_cholesky_pass_on_moderately_collinear_factor(route):
+    """Mode 0's true factor has two columns 0.03 apart.  From sweep 2 on, ALS drives the mode-0
+    iterate to kappa ~ 1e4 .. 1e5 (measured on the oracle), so the first Cholesky pass of its
+    Gram-route QR leaves max |E| ~ kappa^2 2^-48 ~ 1e-6 .. 3e-5: above the first-order correction's
+    1e-8, below 1e-3.  A second Cholesky pass (CholeskyQR2) must finish those QRs, without the
+    Householder QR, and the result must still be the unique QR: fits and factors as the oracle's,
+    Q orthonormal and Q R = A to rounding."""
+    dims, R, seed = [30, 28, 26], 5, 11
+    B = inputs.gaussian_factors(dims, R, seed)
+    g = np.random.default_rng(seed)
+    B[0][:, 1] = B[0][:, 0] + 0.03 * g.standard_normal(dims[0])
+    X = inputs.add_noise(inputs.cp_dense(B), 1e-6, seed)
+    prob = inputs.Problem("moderately_collinear_mode0", dims, R, np.ascontiguousarray(X),
+                          inputs.init_factors(dims, R, seed), B, 1e-6, seed)
+    sweeps = 5
+    fits, A, lam, Q, Rn, st = _run_gpu(prob, b.TREE_RESTRUCTURED, b.EXTRAP_NONE, 0.0, sweeps, route=route)
+    ref = _run_oracle(prob, b.TREE_RESTRUCTURED, b.EXTRAP_NONE, 0.0, sweeps)
+    assert np.linalg.cond(A[0]) > 3e3
+    assert np.max(np.abs(fits - np.array(ref.fits))) <= 1e-10, (fits, ref.fits)
+    for n in range(3):
+        assert np.allclose(A[n], ref.A[n], atol=1e-8), (n, np.abs(A[n] - ref.A[n]).max())
+        assert np.abs(Q[n].T @ Q[n] - np.eye(R)).max() < 1e-13
+        assert np.allclose(Q[n] @ Rn[n], A[n], atol=1e-13)
+        assert np.all(np.diag(Rn[n]) > 0)
+    if route == b.QR_GRAM:
+        assert st.qr_second_pass >= 3, (st.qr_second_pass, st.qr_fallbacks)
+        assert st.qr_fallbacks == 0, (st.qr_second_pass, st.qr_fallbacks)
+    else:
+        assert st.qr_second_pass == 0 and st.qr_fallbacks == 0
+
+
 @pytest.mark.parametrize("order", [4, 5])
 def test_split_krp_qr_carries_the_guard_of_its_prefetched_half(order):
     """The starting factors of modes 2 .. N-1 have columns 0 and 1 1e-7 apart, so the Khatri-Rao
@@ -329,13 +361,15 @@ def test_lagged_fit_equals_sweep_by_sweep_fit(extrap, beta):
     assert np.array_equal(lam1, lam2)
 
 
-@pytest.mark.parametrize("delta", [1e-10, 0.0])
+@pytest.mark.parametrize("delta", [1e-2, 1e-4, 1e-10, 0.0])
 def test_krp_qr_gram_route_falls_back_on_ill_conditioned_products(delta):
     """The Khatri-Rao QR of two triangles goes through the Gram matrix (Cholesky of the Hadamard
-    product of the triangles' Grams, one orthogonality correction) and falls back to the
-    Householder QR when the correction is not small.  Columns 0 and 1 of both source matrices
-    nearly coincide here (kappa(Z) ~ 1e5, or a singular Gram at delta = 0): the result must still
-    be the Householder one, orthonormal and reproducing Z to rounding."""
+    product of the triangles' Grams, one orthogonality correction); when the correction is not
+    small it is finished by a second Cholesky pass or, for a failed pivot or a larger E, by the
+    Householder QR.  Columns 0 and 1 of both source matrices are delta apart (a singular Gram at
+    delta = 0): whichever finishes it, the result must be the unique QR, orthonormal and
+    reproducing Z to rounding, with R as the oracle's up to the QR's perturbation bound
+    (kappa(Z) times the rounding unit)."""
     R = 12
     g = np.random.default_rng(77)
     tri = []
@@ -356,7 +390,8 @@ def test_krp_qr_gram_route_falls_back_on_ill_conditioned_products(delta):
     assert np.all(np.diag(Rg)[np.abs(np.diag(Rg)) > 1e-12] > 0)
     if delta > 0:
         Q0r, R0r = o.householder_qr(Z)
-        assert np.allclose(Rg, R0r, atol=1e-12 * np.abs(R0r).max())
+        tol = max(1e-12, 1e-15 * np.linalg.cond(Z))
+        assert np.allclose(Rg, R0r, atol=tol * np.abs(R0r).max()), (np.abs(Rg - R0r).max(), np.linalg.cond(Z))
 
 
 CONVERGED_MIXED = [
