@@ -205,6 +205,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __syncthreads();
   fence_after();
   const uint32_t tmem = tail->tmem_base;
+  // launched as a programmatic dependent: the set-up above overlapped the previous kernel's tail;
+  // nothing in global memory is read or written before that kernel has finished
+  pdl_wait();
 
   const int64_t ntile_local = (p.T > (int64_t)blockIdx.x) ? (p.T - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
@@ -510,8 +513,7 @@ cudaError_t launch_ttm_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo, co
     cudaGetLastError();  // fall back to a plain grid that leaves reserve_sms SMs idle
   }
   const int64_t grid = std::min<int64_t>(prm.T, std::max(1, tc::num_sms() - std::max(0, reserve_sms)));
-  kern<<<(unsigned)grid, TC_THREADS, smem, st>>>(tmh, tml, tmq, prm);
-  return cudaGetLastError();
+  return launch_pdl(kern, dim3((unsigned)grid), dim3(TC_THREADS), smem, st, tmh, tml, tmq, prm);
 }
 
 namespace tc {
