@@ -373,7 +373,9 @@ def extras(args, prob, X, dev, b):
         to_fstar[name] = {"reached": k is not None, "sweeps": k, "seconds": sec, "sweeps_run": len(fits),
                           "s_per_sweep": wall / max(len(fits), 1), "best_fit": float(np.max(fits)),
                           "final_fit_exact": fx, "gap_to_fstar": fstar - float(np.max(fits)),
-                          "proposals": int(st.proposals), "accepted": int(st.accepted)}
+                          "proposals": int(st.proposals), "accepted": int(st.accepted), "judged": int(st.judged),
+                          "lagged_fits": int(st.lagged_fits), "second_cholesky_pass": int(st.qr_second_pass),
+                          "householder_qr": int(st.qr_fallbacks)}
         if name in ("fp64_plain_cpalsqr", "fp64_bre_rule", "split_bre_rule", "split_bre_learned", "split_br_none"):
             with b.Decomposition(prob.dims, prob.R, X.data_ptr(), False, prob.A0, o) as d:
                 torch.cuda.synchronize()

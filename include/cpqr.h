@@ -140,6 +140,8 @@ typedef struct {
   int64_t qr_second_pass;  /* Gram-route QRs (R <= 32) whose first Cholesky pass left 1e-8 < max |E| <=
                               1e-3 and that a second Cholesky pass finished (CholeskyQR2) instead
                               of the Householder QR; reading it synchronises the context's streams */
+  int64_t lagged_fits;     /* sweeps whose fit was read one sweep late (split path, inside one
+                              multi-sweep call, once beta no longer depends on that fit) */
 } cpqr_stats;
 
 /* Turn per-launch CUDA-event timing on (1) or off (0); resets the bucket times. */

@@ -47,7 +47,7 @@ class Stats(C.Structure):
                 ("accepted", C.c_int64), ("launches", C.c_int64), ("ms_bucket", C.c_double * NBUCKETS),
                 ("n_bucket", C.c_int64 * NBUCKETS), ("qr_fallbacks", C.c_int64),
                 ("krp_split", C.c_int64), ("judged", C.c_int64), ("preapproved", C.c_int64),
-                ("deferred", C.c_int64), ("qr_second_pass", C.c_int64)]
+                ("deferred", C.c_int64), ("qr_second_pass", C.c_int64), ("lagged_fits", C.c_int64)]
 
 
 _lib = None

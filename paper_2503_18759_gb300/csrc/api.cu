@@ -124,6 +124,12 @@ struct cpqr_ctx {
   bool lag_ok = false;             // set by the sweep loops that need no fit before the next sweep
   bool resid_pending = false;      // snapshot of the factors taken, residual not launched yet
   bool resid_inflight = false;     // residual launched, fit not read yet
+  // the sweep behind the pending / in-flight residual: its beta (the learned proposer's history)
+  // and whether it ran inside an approval window (its fit drop is checked when the fit arrives)
+  double pending_beta = 0.0, inflight_beta = 0.0;
+  bool pending_check = false, inflight_check = false;
+  bool sweep_check = false;        // the sweep being run is inside an approval window
+  int64_t lagged_fits = 0;
   bool z_pending = false;
   int z_mode = -1;
   const void* X = nullptr;
@@ -837,8 +843,8 @@ double fit_from_r2(const cpqr_ctx* ctx, double r2) {
 bool can_lag(const cpqr_ctx* ctx) {
   if (!ctx->lag_ok || ctx->prec != CPQR_PREC_SPLIT_BF16 || ctx->x64) return false;
   if (!residual_tc_supported(ctx->N, ctx->dims.data(), ctx->R, ctx->X)) return false;
-  if (ctx->extrap == CPQR_EXTRAP_LEARNED) return false;
-  if (ctx->extrap == CPQR_EXTRAP_PAPER && !ctx->activated) return false;
+  // the rule's beta depends on the fit until it has activated (the learned proposer's fallback)
+  if ((ctx->extrap == CPQR_EXTRAP_PAPER || ctx->extrap == CPQR_EXTRAP_LEARNED) && !ctx->activated) return false;
   return true;
 }
 
@@ -855,10 +861,20 @@ cpqr_status launch_lagged_residual(cpqr_ctx* ctx) {
                                ctx->d_scalar + 1, ctx->res_work, ctx->dstatus, ctx->st3, RESIDUAL_EVALUATE,
                                qr_cluster_sms()));
   }
+  if (ctx->mlp_state) {
+    // the learned proposer's next proposal from this fit, beside the sweep that follows it
+    Timed tm(ctx, CPQR_BUCKET_OTHER, 1, ctx->st3);
+    MlpFitSource src{ctx->d_scalar + 1, ctx->fit_terms, ctx->normX2};
+    CK(mlp_propose(ctx->mlp_wt, ctx->mlp_params, ctx->mlp_state, src, ctx->pending_beta, ctx->st3));
+    CK(cudaMemcpyAsync(ctx->h_pinned + 5, &ctx->mlp_state->cls, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                       ctx->st3));
+  }
   CK(cudaMemcpyAsync(ctx->h_pinned + 4, ctx->d_scalar + 1, sizeof(double), cudaMemcpyDeviceToHost, ctx->st3));
   CK(cudaEventRecord(ctx->ev_fit, ctx->st3));
   ctx->resid_pending = false;
   ctx->resid_inflight = true;
+  ctx->inflight_beta = ctx->pending_beta;
+  ctx->inflight_check = ctx->pending_check;
   return CPQR_OK;
 }
 
@@ -871,7 +887,20 @@ cpqr_status collect_lagged_fit(cpqr_ctx* ctx) {
   ctx->resid_inflight = false;
   const double f = fit_from_r2(ctx, ctx->h_pinned[4]);
   if (!std::isfinite(f)) return fail(ctx, CPQR_ENONFINITE);
+  const double prev = ctx->fits.empty() ? NAN : ctx->fits.back();
   observe_fit(ctx, f);
+  if (ctx->mlp_state) {
+    int32_t c;
+    std::memcpy(&c, ctx->h_pinned + 5, sizeof(c));
+    ctx->next_class = (c >= 0 && c < CPQR_MLP_CLASSES) ? c : -1;
+  }
+  // a sweep run inside an approval window: a drop beyond the fit's rounding ends the approval
+  if (ctx->inflight_check && !(f >= prev - 1e-7)) {
+    ctx->approved_class = -1;
+    ctx->approve_window = 1;
+    ctx->approve_left = 0;
+  }
+  ctx->inflight_check = false;
   return CPQR_OK;
 }
 
@@ -966,9 +995,11 @@ void observe_fit(cpqr_ctx* ctx, double fit) {
   }
 }
 
-cpqr_status one_sweep(cpqr_ctx* ctx, double* fit_out, const double* forced_beta = nullptr) {
+// allow_lag: a forced beta that may still have its fit read one sweep late (the learned
+// proposer's unjudged sweeps)
+cpqr_status one_sweep(cpqr_ctx* ctx, double* fit_out, const double* forced_beta = nullptr, bool allow_lag = false) {
   const double beta = forced_beta ? *forced_beta : beta_for_sweep(ctx);
-  const bool lag = !forced_beta && can_lag(ctx);
+  const bool lag = (!forced_beta || allow_lag) && can_lag(ctx);
   if (!lag) {
     cpqr_status s = flush_lag(ctx);
     if (s != CPQR_OK) return s;
@@ -1038,6 +1069,9 @@ cpqr_status one_sweep(cpqr_ctx* ctx, double* fit_out, const double* forced_beta 
     cpqr_status s = collect_lagged_fit(ctx);  // the previous sweep's
     if (s != CPQR_OK) return s;
     ctx->resid_pending = true;
+    ++ctx->lagged_fits;
+    ctx->pending_beta = beta;
+    ctx->pending_check = ctx->sweep_check;
     if (fit_out) *fit_out = NAN;
     return CPQR_OK;
   }
@@ -1089,26 +1123,31 @@ void mlp_features(const double* fits, const double* betas, int n, double rule_be
 cpqr_status learned_sweep(cpqr_ctx* ctx, double* fit_out) {
   const double rule = rule_beta_next(ctx);
   const int cls = ctx->next_class;
-  if (!ctx->mlp_state || ctx->fits.size() < 2 || cls < 0) return one_sweep(ctx, fit_out, &rule);
+  // Sweeps that are not judged may read their fit one sweep late (inside a multi-sweep call, once
+  // the rule has activated): the proposal then comes from the fits up to the sweep before, and an
+  // approved sweep's fit drop is checked when its fit arrives.
+  if (!ctx->mlp_state || ctx->fits.size() < 2 || cls < 0) return one_sweep(ctx, fit_out, &rule, true);
   const double prop = kMlpBetas[cls];
-  if (prop == rule) return one_sweep(ctx, fit_out, &rule);
+  if (prop == rule) return one_sweep(ctx, fit_out, &rule, true);
   ++ctx->proposals;
   if (ctx->hold_left > 0) {  // a recent loss: the rule runs, the proposal is deferred unjudged
     --ctx->hold_left;
     ++ctx->deferred;
-    return one_sweep(ctx, fit_out, &rule);
+    return one_sweep(ctx, fit_out, &rule, true);
   }
   double f = 0.0;
   if (cls == ctx->approved_class && ctx->approve_left > 0) {
     --ctx->approve_left;
     const double prev = ctx->fits.back();
-    cpqr_status s = one_sweep(ctx, &f, &prop);
+    ctx->sweep_check = true;
+    cpqr_status s = one_sweep(ctx, &f, &prop, true);
+    ctx->sweep_check = false;
     if (s != CPQR_OK) return s;
     ++ctx->accepted;
     ++ctx->preapproved;
     // a drop beyond the per-sweep fit's rounding (a sweep's explicit residual moves by ~1e-12 between
-    // nearly equal models) ends the approval
-    if (!(f >= prev - 1e-7)) {
+    // nearly equal models) ends the approval; a lagged fit (NaN here) is checked when it arrives
+    if (!std::isnan(f) && !(f >= prev - 1e-7)) {
       ctx->approved_class = -1;
       ctx->approve_window = 1;
       ctx->approve_left = 0;
@@ -1117,7 +1156,10 @@ cpqr_status learned_sweep(cpqr_ctx* ctx, double* fit_out) {
     return CPQR_OK;
   }
   ++ctx->judged;
-  cpqr_status s = checkpoint_save(ctx, 1);
+  // both branches start from one checkpoint with every fit read
+  cpqr_status s = flush_lag(ctx);
+  if (s != CPQR_OK) return s;
+  s = checkpoint_save(ctx, 1);
   if (s != CPQR_OK) return s;
   double fp = 0.0, fr = 0.0;
   s = one_sweep(ctx, &fp, &prop);
@@ -1514,6 +1556,7 @@ cpqr_status cp_als_qr_stats(cpqr_ctx* ctx, cpqr_stats* out) {
   out->deferred = ctx->deferred;
   out->launches = ctx->launches;
   out->krp_split = ctx->n_split;
+  out->lagged_fits = ctx->lagged_fits;
   for (int b = 0; b < CPQR_NBUCKETS; ++b) {
     out->ms_bucket[b] = ctx->ms_bucket[b];
     out->n_bucket[b] = ctx->n_bucket[b];

@@ -105,7 +105,10 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
   const int Il = p.d[p.N - 1];
   const int cg = blockIdx.x / p.cpg, kq = blockIdx.x % p.cpg;
   const int c0 = cg * p.gw;
-  if (c0 >= Il) return;  // padding CTA of a clustered launch: no column group
+  if (c0 >= Il) {  // padding CTA of a clustered launch: no column group, a zero partial
+    if (threadIdx.x == 0) p.part[blockIdx.x] = 0.0;
+    return;
+  }
   const int width = min(p.gw, Il - c0);
   const int t0 = (int)((int64_t)p.rtiles * kq / p.cpg), t1 = (int)((int64_t)p.rtiles * (kq + 1) / p.cpg);
   const int ntl = t1 - t0;
@@ -426,7 +429,7 @@ cudaError_t launch_residual_tc(const float* X, int N, const int64_t* d, const fl
       p.cpg = std::max(1, std::min(p.rtiles, ctas / ncg));
       cfg.gridDim = dim3((unsigned)ctas, 1, 1);
       if (ctas > max_parts) return cudaErrorInvalidValue;
-      *nparts = ctas;
+      *nparts = ncg * p.cpg;  // the CTAs with work; the padding CTAs after them only write zeros
       e = cudaLaunchKernelEx(&cfg, residual_tc_kernel, tm, p);
       if (e == cudaSuccess) return cudaSuccess;
     }

@@ -225,6 +225,35 @@ def test_judge_protocol_replayed_through_the_public_api(c):
     assert st.accepted == wins + st.preapproved
 
 
+@pytest.mark.parametrize("c", [0, 6])
+def test_lagged_learned_sweeps_replay_through_the_public_api(c):
+    """Inside one multi-sweep call on the split path the learned proposer's unjudged sweeps read
+    their fit one sweep late (once the rule has activated), with the proposal computed on the
+    device beside the next sweep, while judged sweeps first complete every pending fit and run both
+    branches from one checkpoint.  Whatever was decided, the kept history must be the trajectory of
+    its own betas: replaying them one sweep at a time from the same start reproduces every fit bit
+    for bit, and the run judged at least once."""
+    # last side a multiple of 4: the tensor-core residual (and so the lag) serves this tensor
+    prob = inputs.make_problem("lagged", [30, 28, 24], 6, seed=9, c=0.6, eta=1e-2, dtype=np.float32)
+    X = _t(prob.X)
+    w = _constant_network(c)
+    sweeps = 30
+    opts = b.make_options(tree=b.TREE_RESTRUCTURED, prec=b.PREC_SPLIT_BF16, extrap=b.EXTRAP_LEARNED, mlp_weights=w)
+    with b.Decomposition(prob.dims, prob.R, X.data_ptr(), False, prob.A0, opts) as d:
+        fits_call = d.sweep(sweeps)
+        fits_l, betas_l, _, act = d.history()
+        st = d.stats()
+    assert act, "the rule never activated: no sweep could lag"
+    assert np.array_equal(fits_call, fits_l)
+    assert st.judged >= 1 and st.proposals >= st.judged
+    assert st.lagged_fits >= 1, (st.lagged_fits, st.judged)
+    opts = b.make_options(tree=b.TREE_RESTRUCTURED, prec=b.PREC_SPLIT_BF16, extrap=b.EXTRAP_PAPER)
+    with b.Decomposition(prob.dims, prob.R, X.data_ptr(), False, prob.A0, opts) as d:
+        fits_r = [d.sweep_beta(float(beta)) for beta in betas_l]
+    assert np.array_equal(np.array(fits_r), fits_l), (np.array(fits_r) - fits_l, betas_l, st.judged, st.preapproved,
+                                                      st.lagged_fits)
+
+
 def test_learned_sweep_with_a_random_network_is_judged():
     """An untrained network still runs: every accepted proposal keeps the fit from dropping, a
     rejected one is replaced by the Section 4.2 rule's sweep."""

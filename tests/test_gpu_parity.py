@@ -361,6 +361,29 @@ def test_lagged_fit_equals_sweep_by_sweep_fit(extrap, beta):
     assert np.array_equal(lam1, lam2)
 
 
+def test_lagged_fit_of_a_small_tensor_after_a_large_one():
+    """The lagged residual runs as clusters over all but one GPC; a tensor with fewer row tiles than
+    those CTAs leaves most of them without work.  Their partial-sum slots must not enter the fit:
+    a large tensor's lagged sweeps first fill every slot of a workspace that the small tensor's
+    context may then reuse, and the small tensor's lagged fits must still equal its
+    sweep-by-sweep fits."""
+    big = inputs.make_problem("lag_big", [160, 150, 144], 8, seed=3, c=0.5, eta=1e-3, dtype=np.float32)
+    small = inputs.make_problem("lag_small", [30, 28, 24], 6, seed=9, c=0.6, eta=1e-2, dtype=np.float32)
+    opts = b.make_options(tree=b.TREE_RESTRUCTURED, prec=b.PREC_SPLIT_BF16, extrap=b.EXTRAP_FIXED, beta_fixed=0.01)
+    Xb = _dev(big.X)
+    with b.Decomposition(big.dims, big.R, Xb.data_ptr(), False, big.A0, opts) as d:
+        d.sweep(6)
+    del Xb
+    Xs = _dev(small.X)
+    with b.Decomposition(small.dims, small.R, Xs.data_ptr(), False, small.A0, opts) as d:
+        f_many = d.sweep(12)
+        lagged = d.stats().lagged_fits
+    with b.Decomposition(small.dims, small.R, Xs.data_ptr(), False, small.A0, opts) as d:
+        f_one = np.array([d.sweep(1)[0] for _ in range(12)])
+    assert lagged >= 1
+    assert np.allclose(f_many, f_one, rtol=0, atol=1e-12), (f_many - f_one)
+
+
 @pytest.mark.parametrize("delta", [1e-2, 1e-4, 1e-10, 0.0])
 def test_krp_qr_gram_route_falls_back_on_ill_conditioned_products(delta):
     """The Khatri-Rao QR of two triangles goes through the Gram matrix (Cholesky of the Hadamard
