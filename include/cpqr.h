@@ -79,10 +79,10 @@ typedef enum {
                              rule's beta (beta = 0 included) is judged: from one checkpoint both
                              the proposal's and the rule's sweep run and the proposal is kept only
                              if its fit is higher; the rule is the fallback.  A winning proposal
-                             stays approved for 2, 4, ... 32 further sweeps (doubling on
+                             stays approved for 2, 4, ... 128 further sweeps (doubling on
                              consecutive wins) while the fit does not drop by more than 1e-7;
                              after a losing one the
-                             rule runs unjudged for 1, 2, ... 32 sweeps (doubling on consecutive
+                             rule runs unjudged for 1, 2, ... 128 sweeps (doubling on consecutive
                              losses) */
 } cpqr_extrap;
 

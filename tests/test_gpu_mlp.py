@@ -167,8 +167,8 @@ def test_judge_protocol_replayed_through_the_public_api(c):
     same run replayed by hand through checkpoint / sweep_beta / rollback: a proposal equal to the
     rule's beta runs as is; within a hold after a loss the rule runs; inside an approval window the
     proposal runs as is; else both branches run from one checkpoint and the proposal is kept only
-    if its fit is higher.  Wins double the approval window (<= 32) and reset the hold; losses
-    reset the approval and start a hold that doubles on consecutive losses (<= 32); a fit drop of
+    if its fit is higher.  Wins double the approval window (<= 128) and reset the hold; losses
+    reset the approval and start a hold that doubles on consecutive losses (<= 128); a fit drop of
     more than 1e-7 ends an approval.  Fits and betas agree bit for bit."""
     prob = _problem(3)
     X = _t(prob.X)
@@ -210,13 +210,13 @@ def test_judge_protocol_replayed_through_the_public_api(c):
                 d.rollback()
                 d.sweep_beta(beta_c)
                 wins += 1
-                approved, window = c, min(2 * window, 32)
+                approved, window = c, min(2 * window, 128)
                 left = window
                 hold_window = 1
             else:
                 approved, window, left = -1, 1, 0
                 hold_left = hold_window
-                hold_window = min(2 * hold_window, 32)
+                hold_window = min(2 * hold_window, 128)
             d.commit()
         fits_m, betas_m, _, _ = d.history()
     assert np.array_equal(betas_l, betas_m), (betas_l, betas_m)
