@@ -434,45 +434,52 @@ __global__ void wide_trmm_kernel(const double* __restrict__ A, const double* __r
   }
 }
 
-// In place, row by row: q <- q (I - F) (F upper, R x R row-major), and the FP32 copy.
+// In place, row by row: q <- q (I - F) (F upper, R x R row-major), and the FP32 copy.  The
+// correction q F is summed in float-float on the FP32 pipe (F in shared memory as float-float,
+// q_l split once per row): its ~2^-48 relative error is of the correction, not of q, and one FP64
+// subtraction per entry remains, so the result equals the FP64 form to FP64 rounding at a fraction
+// of the FP64 pipe's time.
 __global__ void __launch_bounds__(256) wide_rowmul_kernel(double* __restrict__ Q, int64_t M, int R,
                                                          const double* __restrict__ F, float* __restrict__ Qf) {
-  extern __shared__ double sF[];  // packed upper rows of F
+  using namespace ffa;
+  extern __shared__ float2 sFf[];  // packed upper rows of F, float-float
   for (int64_t e = threadIdx.x; e < (int64_t)R * R; e += blockDim.x) {
     const int i = (int)(e / R), c = (int)(e - (int64_t)i * R);
-    if (c >= i) sF[tri_off(i, R) + c - i] = F[e];
+    if (c >= i) sFf[tri_off(i, R) + c - i] = ff_st(ff_from_bits(F[e]));
   }
   __syncthreads();
   const int lane = threadIdx.x & 31;
+  const ffn zero = ff_make(0.0f, 0.0f);
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < M; row += warps) {
-    double q[WR_MAX / 32], o[WR_MAX / 32];
+    ffn qf[WR_MAX / 32], acc[WR_MAX / 32];
 #pragma unroll
     for (int qq = 0; qq < WR_MAX / 32; ++qq) {
       const int c = lane + 32 * qq;
-      q[qq] = (c < R) ? Q[row * R + c] : 0.0;
-      o[qq] = q[qq];
+      qf[qq] = ff_from_bits((c < R) ? Q[row * R + c] : 0.0);
+      acc[qq] = zero;
     }
-    // o_c = q_c - sum_{l <= c} q_l F_lc, l in order
+    // acc_c = sum_{l <= c} q_l F_lc, l in order
     for (int l = 0; l < R; ++l) {
-      double ql = 0.0;
+      ffn ql = zero;
 #pragma unroll
       for (int qq = 0; qq < WR_MAX / 32; ++qq)
-        if (qq == (l >> 5)) ql = q[qq];
-      ql = __shfl_sync(0xffffffffu, ql, l & 31);
+        if (qq == (l >> 5)) ql = qf[qq];
+      ql = ff_shfl(ql, l & 31);
       const int64_t ol = tri_off(l, R);
 #pragma unroll
       for (int qq = 0; qq < WR_MAX / 32; ++qq) {
         const int c = lane + 32 * qq;
-        if (c >= l && c < R) o[qq] -= ql * sF[ol + c - l];
+        if (c >= l && c < R) acc[qq] = ff_fms(acc[qq], ff_neg(ql), ff_ld(sFf[ol + c - l]));
       }
     }
 #pragma unroll
     for (int qq = 0; qq < WR_MAX / 32; ++qq) {
       const int c = lane + 32 * qq;
       if (c < R) {
-        Q[row * R + c] = o[qq];
-        if (Qf) Qf[row * R + c] = (float)o[qq];
+        const double o = Q[row * R + c] - ff_val(acc[qq]);  // q read again (L2): fewer registers
+        Q[row * R + c] = o;
+        if (Qf) Qf[row * R + c] = (float)o;
       }
     }
   }
