@@ -527,12 +527,14 @@ static cudaError_t gemm(const TA* A, const TB* B, TC* C, GemmView v, int batches
   return cudaGetLastError();
 }
 
-// K splits so that the grid covers the GPU about twice (at least 256 K per split, at most 64).
+// Split-K count: at most two CTAs per SM in all (the FP64 pipe is the limit and two CTAs fit an SM;
+// one more CTA than that makes its SM run a third K-range after the others have finished), and
+// K-ranges of at least 32.
 static int ksplits(int64_t M, int64_t N, int64_t K, bool upper) {
   int64_t tm = (M + GT - 1) / GT, tiles = tm * ((N + GT - 1) / GT);
   if (upper) tiles = (tiles + tm) / 2;
-  int64_t want = (2 * 152 + tiles - 1) / tiles;
-  want = std::min<int64_t>(want, std::max<int64_t>(1, K / 256));
+  int64_t want = std::max<int64_t>(1, (2 * 152) / tiles);
+  want = std::min<int64_t>(want, std::max<int64_t>(1, K / 32));
   return (int)std::max<int64_t>(1, std::min<int64_t>(want, 64));
 }
 
@@ -651,12 +653,12 @@ cudaError_t launch_wide_qr(const double* Y, int64_t M, int R, const double* cons
   // pass 1: R1 = chol(G), Q = Y R1^{-1}
   if (kr.m > 0) {
     for (int i = 0; i < kr.m && e == cudaSuccess; ++i) {
-      GemmView v{};  // T_i^T T_i
+      GemmView v{};  // T_i^T T_i (both triangles: the Hadamard product reads all of it)
       v.M = R; v.N = R; v.K = R;
       v.sAm = 1; v.sAk = R; v.sBk = R; v.sBn = 1; v.sCm = R; v.sCn = 1;
-      v.ksplit = 1;
-      e = gemm<double, double, double, double>(tri[i], tri[i], k.Gk + (size_t)i * R * R, v, 1, nullptr, 0, nullptr,
-                                               0, nullptr, st);
+      v.ksplit = ksplits(R, R, R, false);
+      e = gemm<double, double, double, double>(tri[i], tri[i], k.Gk + (size_t)i * R * R, v, 1, k.part,
+                                               (size_t)64 * R * R, nullptr, 0, nullptr, st);
     }
     if (e != cudaSuccess) return e;
     wide_hadamard_kernel<<<(R * R + 255) / 256, 256, 0, st>>>(k.Gk, kr.m, R, k.G);
