@@ -438,11 +438,15 @@ __global__ void wide_trmm_kernel(const double* __restrict__ A, const double* __r
 // correction q F is summed in float-float on the FP32 pipe (F in shared memory as float-float,
 // q_l split once per row): its ~2^-48 relative error is of the correction, not of q, and one FP64
 // subtraction per entry remains, so the result equals the FP64 form to FP64 rounding at a fraction
-// of the FP64 pipe's time.
+// of the FP64 pipe's time.  Each warp takes two rows at a time (two independent chains per
+// column) and reads q_l from its own rows staged in shared memory (a broadcast load per l).
+constexpr int RM_ROWS = 2;
 __global__ void __launch_bounds__(256) wide_rowmul_kernel(double* __restrict__ Q, int64_t M, int R,
                                                          const double* __restrict__ F, float* __restrict__ Qf) {
   using namespace ffa;
-  extern __shared__ float2 sFf[];  // packed upper rows of F, float-float
+  extern __shared__ float2 sFf[];  // packed upper rows of F (float-float), then the staged rows
+  const int64_t nF = tri_off(R, R);
+  float2* sQ = sFf + nF + (threadIdx.x >> 5) * RM_ROWS * WR_MAX;  // this warp's rows
   for (int64_t e = threadIdx.x; e < (int64_t)R * R; e += blockDim.x) {
     const int i = (int)(e / R), c = (int)(e - (int64_t)i * R);
     if (c >= i) sFf[tri_off(i, R) + c - i] = ff_st(ff_from_bits(F[e]));
@@ -451,37 +455,50 @@ __global__ void __launch_bounds__(256) wide_rowmul_kernel(double* __restrict__ Q
   const int lane = threadIdx.x & 31;
   const ffn zero = ff_make(0.0f, 0.0f);
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < M; row += warps) {
-    ffn qf[WR_MAX / 32], acc[WR_MAX / 32];
+  for (int64_t row0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * RM_ROWS; row0 < M;
+       row0 += warps * RM_ROWS) {
+    ffn acc[RM_ROWS][WR_MAX / 32];
 #pragma unroll
-    for (int qq = 0; qq < WR_MAX / 32; ++qq) {
-      const int c = lane + 32 * qq;
-      qf[qq] = ff_from_bits((c < R) ? Q[row * R + c] : 0.0);
-      acc[qq] = zero;
-    }
-    // acc_c = sum_{l <= c} q_l F_lc, l in order
-    for (int l = 0; l < R; ++l) {
-      ffn ql = zero;
-#pragma unroll
-      for (int qq = 0; qq < WR_MAX / 32; ++qq)
-        if (qq == (l >> 5)) ql = qf[qq];
-      ql = ff_shfl(ql, l & 31);
-      const int64_t ol = tri_off(l, R);
+    for (int r = 0; r < RM_ROWS; ++r)
 #pragma unroll
       for (int qq = 0; qq < WR_MAX / 32; ++qq) {
         const int c = lane + 32 * qq;
-        if (c >= l && c < R) acc[qq] = ff_fms(acc[qq], ff_neg(ql), ff_ld(sFf[ol + c - l]));
+        const int64_t row = row0 + r;
+        if (c < R) sQ[r * WR_MAX + c] = ff_st(ff_from_bits(row < M ? Q[row * R + c] : 0.0));
+        acc[r][qq] = zero;
+      }
+    __syncwarp();
+    // acc_c = sum_{l <= c} q_l F_lc, l in order
+    for (int l = 0; l < R; ++l) {
+      const int64_t ol = tri_off(l, R);
+      ffn ql[RM_ROWS];
+#pragma unroll
+      for (int r = 0; r < RM_ROWS; ++r) ql[r] = ff_ld(sQ[r * WR_MAX + l]);
+#pragma unroll
+      for (int qq = 0; qq < WR_MAX / 32; ++qq) {
+        const int c = lane + 32 * qq;
+        if (c >= l && c < R) {
+          const ffn f = ff_ld(sFf[ol + c - l]);
+#pragma unroll
+          for (int r = 0; r < RM_ROWS; ++r) acc[r][qq] = ff_fms(acc[r][qq], ff_neg(ql[r]), f);
+        }
       }
     }
 #pragma unroll
-    for (int qq = 0; qq < WR_MAX / 32; ++qq) {
-      const int c = lane + 32 * qq;
-      if (c < R) {
-        const double o = Q[row * R + c] - ff_val(acc[qq]);  // q read again (L2): fewer registers
-        Q[row * R + c] = o;
-        if (Qf) Qf[row * R + c] = (float)o;
+    for (int r = 0; r < RM_ROWS; ++r) {
+      const int64_t row = row0 + r;
+      if (row >= M) break;
+#pragma unroll
+      for (int qq = 0; qq < WR_MAX / 32; ++qq) {
+        const int c = lane + 32 * qq;
+        if (c < R) {
+          const double o = Q[row * R + c] - ff_val(acc[r][qq]);  // q read again (L2): fewer registers
+          Q[row * R + c] = o;
+          if (Qf) Qf[row * R + c] = (float)o;
+        }
       }
     }
+    __syncwarp();
   }
 }
 
@@ -580,6 +597,7 @@ static cudaError_t gram(const double* Y, int64_t M, int R, double* G, double* pa
 
 static size_t chol_smem(int R) { return (size_t)tri_off(R, R) * sizeof(float2); }
 static size_t tri_smem(int R) { return ((size_t)tri_off(R, R) + R) * sizeof(double); }
+static size_t rowmul_smem(int R) { return ((size_t)tri_off(R, R) + 8 * RM_ROWS * WR_MAX) * sizeof(float2); }
 
 static cudaError_t set_smem_attrs() {
   static bool done = false;
@@ -590,7 +608,8 @@ static cudaError_t set_smem_attrs() {
     e = cudaFuncSetAttribute(wide_trsm_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)tri_smem(WR_MAX));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(wide_rowmul_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tri_smem(WR_MAX));
+    e = cudaFuncSetAttribute(wide_rowmul_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)rowmul_smem(WR_MAX));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(wide_finish_prep_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)tri_smem(WR_MAX));
@@ -681,7 +700,7 @@ cudaError_t launch_wide_qr(const double* Y, int64_t M, int R, const double* cons
   if (e != cudaSuccess) return e;
   // first-order correction from the last E: Q <- Q (I - F), R = (I + F) T
   wide_e_kernel<<<1, 256, 0, st>>>(k.G, R, nullptr, k.F, k.IF, nullptr);
-  wide_rowmul_kernel<<<rows_grid(M), 256, tri_smem(R), st>>>(Q, M, R, k.F, Qf);
+  wide_rowmul_kernel<<<rows_grid((M + RM_ROWS - 1) / RM_ROWS), 256, rowmul_smem(R), st>>>(Q, M, R, k.F, Qf);
   wide_trmm_kernel<<<R, 128, 0, st>>>(k.IF, k.T, R, Rout, nullptr);
   return cudaGetLastError();
 }
