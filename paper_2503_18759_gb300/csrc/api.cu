@@ -164,6 +164,7 @@ struct cpqr_ctx {
   int Rp = 0;
   int64_t Kp[CPQR_MAXN] = {};
   __nv_bfloat16 *Xhi = nullptr, *Xlo = nullptr;
+  SplitLayout xlay;  // the split X's rows padded to a multiple of 8 when the last side is not
   double* lambda = nullptr;
   double* Q0 = nullptr;
   float* Q0f = nullptr;                // split path: FP32 copy of Q0 for V = Y_(n) Q0
@@ -423,7 +424,8 @@ cpqr_status run_ttm(cpqr_ctx* ctx, const Op& op) {
     __nv_bfloat16 *ohi = nullptr, *olo = nullptr;
     if (need_split) split_views(out, n_out, need_f32, &ohi, &olo);
     float* of = need_f32 ? static_cast<float*>(out) : nullptr;
-    if (ttm_tc_wide_supported(P, K, S, R) && (sb.is_x || sb.has_split)) {
+    const SplitLayout lay = sb.is_x ? ctx->xlay : SplitLayout{};
+    if (ttm_tc_wide_supported(P, K, S, R, lay) && (sb.is_x || sb.has_split)) {
       const __nv_bfloat16 *shi = ctx->Xhi, *slo = ctx->Xlo;
       if (!sb.is_x) {
         __nv_bfloat16 *h, *l;
@@ -431,7 +433,8 @@ cpqr_status run_ttm(cpqr_ctx* ctx, const Op& op) {
         shi = h;
         slo = l;
       }
-      CK(launch_ttm_tc_wide(shi, slo, ctx->Qt[k], ctx->Rp, ctx->Kp[k], of, P, K, S, R, ctx->dstatus, st, ohi, olo));
+      CK(launch_ttm_tc_wide(shi, slo, ctx->Qt[k], ctx->Rp, ctx->Kp[k], of, P, K, S, R, ctx->dstatus, st, ohi, olo,
+                            lay));
     } else {
       // the CUDA-core FP32 TTM from the node's FP32 copy (kept for every CUDA-core consumer)
       if (!sb.has_f32) return fail(ctx, CPQR_EINVAL);
@@ -452,7 +455,8 @@ cpqr_status run_ttm(cpqr_ctx* ctx, const Op& op) {
     __nv_bfloat16 *ohi = nullptr, *olo = nullptr;
     if (need_split) split_views(out, n_out, need_f32, &ohi, &olo);
     float* of = need_f32 ? static_cast<float*>(out) : nullptr;
-    if (ttm_tc_supported(P, K, S, R) && (sb.is_x || sb.has_split)) {
+    const SplitLayout lay = sb.is_x ? ctx->xlay : SplitLayout{};
+    if (ttm_tc_supported(P, K, S, R, lay) && (sb.is_x || sb.has_split)) {
       const __nv_bfloat16 *shi = ctx->Xhi, *slo = ctx->Xlo;
       if (!sb.is_x) {
         __nv_bfloat16 *h, *l;
@@ -469,7 +473,7 @@ cpqr_status run_ttm(cpqr_ctx* ctx, const Op& op) {
       const bool skip = ctx->test_skip_next_ttm;
       ctx->test_skip_next_ttm = false;
       CK(launch_ttm_tc(shi, slo, ctx->Qt[k], ctx->Rp, ctx->Kp[k], of, P, K, S, R, ctx->dstatus, st, reserve, ohi,
-                       olo, skip ? ctx->test_wait_ns : 0, skip ? 1 : 0));
+                       olo, skip ? ctx->test_wait_ns : 0, skip ? 1 : 0, lay));
     } else {
       if (!sb.has_f32) return fail(ctx, CPQR_EINVAL);  // not produced for a CUDA-core consumer
       float* o32 = of;
@@ -1437,9 +1441,21 @@ cpqr_status cp_als_qr_init(cpqr_ctx** out, int32_t N, const int64_t* dims, int32
       cpqr_status s = stage_q(ctx, n);
       if (s != CPQR_OK) return s;
     }
-    CK(ctx->alloc(&ctx->Xhi, nX));
-    CK(ctx->alloc(&ctx->Xlo, nX));
-    CK(launch_split_x((const float*)X_dev, ctx->Xhi, ctx->Xlo, nX, st));
+    const int64_t last = dims[N - 1];
+    if (last % 8 == 0) {
+      CK(ctx->alloc(&ctx->Xhi, nX));
+      CK(ctx->alloc(&ctx->Xlo, nX));
+      CK(launch_split_x((const float*)X_dev, ctx->Xhi, ctx->Xlo, nX, st));
+    } else {
+      // TMA rows must be multiples of 16 bytes: pad the last dimension of the split copy so that
+      // every TTM over X can take the tensor cores
+      const int64_t ld = (last + 7) / 8 * 8, rows = nX / last;
+      CK(ctx->alloc(&ctx->Xhi, rows * ld));
+      CK(ctx->alloc(&ctx->Xlo, rows * ld));
+      CK(launch_split_x_padded((const float*)X_dev, ctx->Xhi, ctx->Xlo, rows, last, ld, st));
+      ctx->xlay.last = last;
+      ctx->xlay.ld = ld;
+    }
   }
   // ||X||^2 (precomputed once, Section 4.1).
   {

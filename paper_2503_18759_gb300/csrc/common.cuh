@@ -70,19 +70,39 @@ cudaError_t launch_ttm_f32_tiled(const float* T, const float* Q, float* out, int
 cudaError_t launch_split_q(const double* Q, int64_t K, int R, __nv_bfloat16* Qt, int Rp, int64_t Kp,
                            cudaStream_t st);
 // X (n elements FP32) -> Xhi, Xlo bf16 with X = hi + lo + O(2^-16 |X|).
+// X (rows x last, dense FP32) into bf16 hi / lo with rows of ld >= last elements, the padding zero.
+cudaError_t launch_split_x_padded(const float* X, __nv_bfloat16* Xhi, __nv_bfloat16* Xlo, int64_t rows, int64_t last,
+                                  int64_t ld, cudaStream_t st);
 cudaError_t launch_split_x(const float* X, __nv_bfloat16* Xhi, __nv_bfloat16* Xlo, int64_t n,
                            cudaStream_t st);
+// Storage of a bf16 split source: dense (ld = 0), or its last dimension (extent last) padded to a
+// row stride of ld elements (ld a multiple of 8 >= last, the padding zero), so that TMA's 16-byte
+// row strides hold for any last side.
+struct SplitLayout {
+  int64_t last = 0, ld = 0;
+};
+// How a TTM of (P, K, S) sees a source with layout lay: the iteration extent of S (Sit), the
+// stride between consecutive K (rowS, elements), the dense output extent So, and the remap of an
+// iteration index s onto the output, (s / s_pad) s_last + s % s_pad with s % s_pad < s_last, when
+// S spans rows of the padded last dimension (s_pad = 0: none).  ok = false: the layout cannot
+// serve this TTM.
+struct TtmView {
+  bool ok;
+  int64_t Sit, rowS, So, s_last, s_pad, ldK;
+};
+TtmView ttm_view(int64_t K, int64_t S, SplitLayout lay);
 // out[p, r, s] = sum_i X[p, i, s] Q[i, r] from split operands; out FP32 and, if out_hi /
 // out_lo are given, its bf16 split (the operand format of a following tensor-core TTM).
-// S % 8 == 0 (MN-major) or S == 1 with K % 8 == 0 (K-major); K <= 512.  Returns
-// cudaErrorNotSupported if the shape is outside the kernel's range.
+// Dense sources: S % 8 == 0 (MN-major) or S == 1 with K % 8 == 0 (K-major); a padded source
+// (lay): any S that ttm_view serves.  K <= 512.  Returns cudaErrorNotSupported if the shape is
+// outside the kernel's range.
 // reserve_sms: SMs the persistent grid leaves free for concurrent work (a cluster QR).
 cudaError_t launch_ttm_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo, const __nv_bfloat16* Qt,
                           int Rp, int64_t Kp, float* out, int64_t P, int64_t K, int64_t S, int R,
                           unsigned int* dev_status, cudaStream_t st, int reserve_sms = 0,
                           __nv_bfloat16* out_hi = nullptr, __nv_bfloat16* out_lo = nullptr,
-                          unsigned long long wait_ns = 0, int skip_x_loads = 0);
-bool ttm_tc_supported(int64_t P, int64_t K, int64_t S, int R);
+                          unsigned long long wait_ns = 0, int skip_x_loads = 0, SplitLayout lay = {});
+bool ttm_tc_supported(int64_t P, int64_t K, int64_t S, int R, SplitLayout lay = {});
 
 // ----- small FP64 kernels (smallqr.cu) -----
 struct ZPlan {          // row order of the Khatri-Rao product used by the staircase QR
@@ -296,11 +316,11 @@ cudaError_t launch_wide_finish(const TV* vw, int nparts, int64_t I, int C, int R
                                unsigned int* status, cudaStream_t st);
 // Tensor-core TTM for 32 < R <= 192 (ttm_tc_wide.cu): operands as for launch_ttm_tc, Rp = R rounded
 // up to 16, Qt = bf16 hi / lo of Q^T (2 x Rp x Kp).
-bool ttm_tc_wide_supported(int64_t P, int64_t K, int64_t S, int R);
+bool ttm_tc_wide_supported(int64_t P, int64_t K, int64_t S, int R, SplitLayout lay = {});
 cudaError_t launch_ttm_tc_wide(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo, const __nv_bfloat16* Qt, int Rp,
                                int64_t Kp, float* out, int64_t P, int64_t K, int64_t S, int R,
                                unsigned int* dev_status, cudaStream_t st, __nv_bfloat16* out_hi = nullptr,
-                               __nv_bfloat16* out_lo = nullptr);
+                               __nv_bfloat16* out_lo = nullptr, SplitLayout lay = {});
 // TTM on the CUDA cores for any R (tiled GEMM, accumulation in TAcc).
 template <typename TT, typename TQ, typename TO, typename TAcc>
 cudaError_t launch_ttm_wide(const TT* T, const TQ* Q, TO* out, int64_t P, int64_t K, int64_t S, int R,

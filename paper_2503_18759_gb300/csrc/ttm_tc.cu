@@ -43,6 +43,19 @@ __global__ void split_x_kernel(const float* __restrict__ X, __nv_bfloat16* __res
   }
 }
 
+// Rows of ld elements: hi / lo of X's row (last elements), zero in the padding.
+__global__ void split_x_padded_kernel(const float* __restrict__ X, __nv_bfloat16* __restrict__ hi,
+                                      __nv_bfloat16* __restrict__ lo, int64_t rows, int64_t last, int64_t ld) {
+  const int64_t total = rows * ld;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / ld, c = e - r * ld;
+    const float v = (c < last) ? X[r * last + c] : 0.0f;
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    hi[e] = h;
+    lo[e] = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
+}
+
 // Qt[0][r][i] = hi(Q[i][r]), Qt[1][r][i] = lo(Q[i][r]); zero outside R x K.
 __global__ void split_q_kernel(const double* __restrict__ Q, int64_t K, int R, __nv_bfloat16* __restrict__ Qt,
                                int Rp, int64_t Kp) {
@@ -67,6 +80,52 @@ cudaError_t launch_split_x(const float* X, __nv_bfloat16* Xhi, __nv_bfloat16* Xl
   }
   split_x_kernel<<<152 * 8, 256, 0, st>>>(X, Xhi, Xlo, n);
   return cudaGetLastError();
+}
+
+cudaError_t launch_split_x_padded(const float* X, __nv_bfloat16* Xhi, __nv_bfloat16* Xlo, int64_t rows, int64_t last,
+                                  int64_t ld, cudaStream_t st) {
+  if (last < 1 || ld < last || (ld % 8) != 0 || rows < 1) return cudaErrorInvalidValue;
+  split_x_padded_kernel<<<152 * 8, 256, 0, st>>>(X, Xhi, Xlo, rows, last, ld);
+  return cudaGetLastError();
+}
+
+TtmView ttm_view(int64_t K, int64_t S, SplitLayout lay) {
+  TtmView v{};
+  v.ok = true;
+  if (lay.ld == 0) {  // dense
+    v.Sit = S;
+    v.So = S;
+    v.rowS = S;
+    v.ldK = K;
+    return v;
+  }
+  if (lay.last < 1 || lay.ld < lay.last || (lay.ld % 8) != 0) {
+    v.ok = false;
+    return v;
+  }
+  if (S == 1) {  // the contracted mode is the padded last one
+    v.ok = (K == lay.last);
+    v.Sit = v.So = v.rowS = 1;
+    v.ldK = lay.ld;
+    return v;
+  }
+  if (S % lay.last != 0) {
+    v.ok = false;
+    return v;
+  }
+  const int64_t q = S / lay.last;
+  v.So = S;
+  v.ldK = K;
+  if (q == 1) {  // S is the padded last dimension itself: its extent with the padded stride
+    v.Sit = S;
+    v.rowS = lay.ld;
+  } else {  // S spans rows of it: iterate over the padded rows, skip the padding in the epilogue
+    v.Sit = q * lay.ld;
+    v.rowS = v.Sit;
+    v.s_last = lay.last;
+    v.s_pad = lay.ld;
+  }
+  return v;
 }
 
 cudaError_t launch_split_q(const double* Q, int64_t K, int R, __nv_bfloat16* Qt, int Rp, int64_t Kp,
@@ -124,7 +183,8 @@ constexpr int TC_ACC_COLS = TC_NACC * 32;   // per tile buffer
 constexpr int TC_TMEM_COLS = 256;           // two tile buffers (192 columns), rounded to a power of 2
 
 struct TcParams {
-  int64_t P, K, S;
+  int64_t P, K, S;  // S: iteration extent of the S dimension (see ttm_view)
+  int64_t So, s_last, s_pad;  // dense output extent; remap of padded S rows (s_pad = 0: none)
   int R, Rp, nkb;
   int64_t nsb;  // 64-wide s blocks per p (MN-major)
   int64_t H;    // half tiles = P * nsb (MN-major)
@@ -369,11 +429,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (h < p.H) {
           const int64_t pp = h / p.nsb, sb = h % p.nsb;
           const int64_t sidx = sb * 64 + (m & 63);
-          if (sidx < p.S) {
-            const int64_t o = (pp * p.R) * p.S + sidx;
+          bool live = sidx < p.S;
+          int64_t so = sidx;
+          if (p.s_pad) {  // a padded source: skip the padding of its last dimension
+            const int64_t qd = sidx / p.s_pad, i2 = sidx - qd * p.s_pad;
+            live = live && i2 < p.s_last;
+            so = qd * p.s_last + i2;
+          }
+          if (live) {
+            const int64_t o = (pp * p.R) * p.So + so;
 #pragma unroll
             for (int r = 0; r < 32; ++r)
-              if (r < p.R) store_out(p, o + (int64_t)r * p.S, v[r]);
+              if (r < p.R) store_out(p, o + (int64_t)r * p.So, v[r]);
           }
         }
       }
@@ -401,11 +468,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
 }  // namespace
 
-bool ttm_tc_supported(int64_t P, int64_t K, int64_t S, int R) {
+bool ttm_tc_supported(int64_t P, int64_t K, int64_t S, int R, SplitLayout lay) {
   if (R < 1 || R > 32 || K < 1 || K > 64 * TC_MAX_KB || P < 1 || P > 0x7fffffff || S > 0x7fffffff) return false;
-  if (S == 1) return (K % 8) == 0 && (P + 127) / 128 < (int64_t(1) << 31);  // K-major: 16-byte row stride
-  if (S < 8 || (S % 8) != 0) return false;
-  const int64_t nsb = (S + 63) / 64;
+  const TtmView v = ttm_view(K, S, lay);
+  if (!v.ok || v.Sit > 0x7fffffff) return false;
+  if (S == 1) return (v.ldK % 8) == 0 && (P + 127) / 128 < (int64_t(1) << 31);  // K-major: 16-byte row stride
+  if (v.rowS < 8 || (v.rowS % 8) != 0) return false;                          // MN-major: 16-byte row stride
+  const int64_t nsb = (v.Sit + 63) / 64;
   if (P * nsb > (int64_t(1) << 40)) return false;
   return true;
 }
@@ -413,9 +482,10 @@ bool ttm_tc_supported(int64_t P, int64_t K, int64_t S, int R) {
 cudaError_t launch_ttm_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo, const __nv_bfloat16* Qt, int Rp,
                           int64_t Kp, float* out, int64_t P, int64_t K, int64_t S, int R, unsigned int* dev_status,
                           cudaStream_t st, int reserve_sms, __nv_bfloat16* out_hi, __nv_bfloat16* out_lo,
-                          unsigned long long wait_ns, int skip_x_loads) {
-  if (!ttm_tc_supported(P, K, S, R) || (Rp != 16 && Rp != 32) || Rp < R || Kp < K || (Kp % 64) != 0)
+                          unsigned long long wait_ns, int skip_x_loads, SplitLayout lay) {
+  if (!ttm_tc_supported(P, K, S, R, lay) || (Rp != 16 && Rp != 32) || Rp < R || Kp < K || (Kp % 64) != 0)
     return cudaErrorNotSupported;
+  const TtmView view = ttm_view(K, S, lay);
   if (((uintptr_t)Xhi & 15) || ((uintptr_t)Xlo & 15) || ((uintptr_t)Qt & 15)) return cudaErrorMisalignedAddress;
   if ((out_hi == nullptr) != (out_lo == nullptr)) return cudaErrorInvalidValue;
   const bool km = (S == 1);
@@ -424,7 +494,7 @@ cudaError_t launch_ttm_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo, co
   CUtensorMap tmh, tml, tmq;
   if (km) {
     cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)P};
-    cuuint64_t strides[1] = {(cuuint64_t)K * 2};
+    cuuint64_t strides[1] = {(cuuint64_t)view.ldK * 2};
     cuuint32_t box[2] = {64, 128};
     cuuint32_t es[2] = {1, 1};
     if (enc(&tmh, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)Xhi, dims, strides, box, es,
@@ -436,8 +506,8 @@ cudaError_t launch_ttm_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo, co
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return cudaErrorInvalidValue;
   } else {
-    cuuint64_t dims[3] = {(cuuint64_t)S, (cuuint64_t)K, (cuuint64_t)P};
-    cuuint64_t strides[2] = {(cuuint64_t)S * 2, (cuuint64_t)S * K * 2};
+    cuuint64_t dims[3] = {(cuuint64_t)view.Sit, (cuuint64_t)K, (cuuint64_t)P};
+    cuuint64_t strides[2] = {(cuuint64_t)view.rowS * 2, (cuuint64_t)view.rowS * K * 2};
     cuuint32_t box[3] = {64, 64, 1};
     cuuint32_t es[3] = {1, 1, 1};
     if (enc(&tmh, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)Xhi, dims, strides, box, es,
@@ -462,11 +532,14 @@ cudaError_t launch_ttm_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo, co
   TcParams prm;
   prm.P = P;
   prm.K = K;
-  prm.S = S;
   prm.R = R;
   prm.Rp = Rp;
   prm.nkb = (int)((K + 63) / 64);
-  prm.nsb = km ? 1 : (S + 63) / 64;
+  prm.S = view.Sit;
+  prm.So = view.So;
+  prm.s_last = view.s_last;
+  prm.s_pad = view.s_pad;
+  prm.nsb = km ? 1 : (view.Sit + 63) / 64;
   prm.H = P * prm.nsb;
   prm.T = km ? (P + 127) / 128 : (prm.H + 1) / 2;
   prm.out = out;

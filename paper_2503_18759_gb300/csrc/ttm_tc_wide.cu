@@ -28,7 +28,8 @@ constexpr int TW_MAXST = 3;
 constexpr int TW_SMEM_LIMIT = 227 * 1024;
 
 struct TwParams {
-  int64_t P, K, S;
+  int64_t P, K, S;  // S: iteration extent of the S dimension (see ttm_view)
+  int64_t So, s_last, s_pad;  // dense output extent; remap of padded S rows (s_pad = 0: none)
   int R, Rp, nkb, nst, nbuf;
   uint32_t stage_bytes, tmem_cols;
   int64_t nsb, H, T;
@@ -233,11 +234,18 @@ __global__ void __launch_bounds__(TW_THREADS, 1)
           if (h < p.H) {
             const int64_t pp = h / p.nsb, sb = h % p.nsb;
             const int64_t sidx = sb * 64 + (m & 63);
-            if (sidx < p.S) {
-              const int64_t o = (pp * p.R) * p.S + sidx;
+            bool live = sidx < p.S;
+            int64_t so = sidx;
+            if (p.s_pad) {  // a padded source: skip the padding of its last dimension
+              const int64_t qd = sidx / p.s_pad, i2 = sidx - qd * p.s_pad;
+              live = live && i2 < p.s_last;
+              so = qd * p.s_last + i2;
+            }
+            if (live) {
+              const int64_t o = (pp * p.R) * p.So + so;
 #pragma unroll
               for (int r = 0; r < 32; ++r)
-                if (r < w && c0 + r < p.R) store_w(p, o + (int64_t)(c0 + r) * p.S, v[r]);
+                if (r < w && c0 + r < p.R) store_w(p, o + (int64_t)(c0 + r) * p.So, v[r]);
             }
           }
         }
@@ -270,21 +278,24 @@ size_t tw_tail_bytes(bool km) { return ((sizeof(TwTail) + 15) / 16) * 16 + (km ?
 
 }  // namespace
 
-bool ttm_tc_wide_supported(int64_t P, int64_t K, int64_t S, int R) {
+bool ttm_tc_wide_supported(int64_t P, int64_t K, int64_t S, int R, SplitLayout lay) {
   if (R <= 32 || R > 192 || K < 1 || P < 1 || P > 0x7fffffff || S > 0x7fffffff) return false;
   if (K > 0x3fffffff) return false;
-  if (S == 1) return (K % 8) == 0 && (P + 127) / 128 < (int64_t(1) << 31);
-  if (S < 8 || (S % 8) != 0) return false;
-  const int64_t nsb = (S + 63) / 64;
+  const TtmView v = ttm_view(K, S, lay);
+  if (!v.ok || v.Sit > 0x7fffffff) return false;
+  if (S == 1) return (v.ldK % 8) == 0 && (P + 127) / 128 < (int64_t(1) << 31);
+  if (v.rowS < 8 || (v.rowS % 8) != 0) return false;
+  const int64_t nsb = (v.Sit + 63) / 64;
   return P * nsb <= (int64_t(1) << 40);
 }
 
 cudaError_t launch_ttm_tc_wide(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo, const __nv_bfloat16* Qt, int Rp,
                                int64_t Kp, float* out, int64_t P, int64_t K, int64_t S, int R,
                                unsigned int* dev_status, cudaStream_t st, __nv_bfloat16* out_hi,
-                               __nv_bfloat16* out_lo) {
-  if (!ttm_tc_wide_supported(P, K, S, R) || Rp % 16 || Rp < R || Rp > 192 || Kp < K || (Kp % 64) != 0)
+                               __nv_bfloat16* out_lo, SplitLayout lay) {
+  if (!ttm_tc_wide_supported(P, K, S, R, lay) || Rp % 16 || Rp < R || Rp > 192 || Kp < K || (Kp % 64) != 0)
     return cudaErrorNotSupported;
+  const TtmView view = ttm_view(K, S, lay);
   if (((uintptr_t)Xhi & 15) || ((uintptr_t)Xlo & 15) || ((uintptr_t)Qt & 15)) return cudaErrorMisalignedAddress;
   if ((out_hi == nullptr) != (out_lo == nullptr)) return cudaErrorInvalidValue;
   const bool km = (S == 1);
@@ -293,7 +304,7 @@ cudaError_t launch_ttm_tc_wide(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xl
   CUtensorMap tmh, tml, tmq;
   if (km) {
     cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)P};
-    cuuint64_t strides[1] = {(cuuint64_t)K * 2};
+    cuuint64_t strides[1] = {(cuuint64_t)view.ldK * 2};
     cuuint32_t box[2] = {64, 128};
     cuuint32_t es[2] = {1, 1};
     if (enc(&tmh, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)Xhi, dims, strides, box, es,
@@ -304,8 +315,8 @@ cudaError_t launch_ttm_tc_wide(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xl
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return cudaErrorInvalidValue;
   } else {
-    cuuint64_t dims[3] = {(cuuint64_t)S, (cuuint64_t)K, (cuuint64_t)P};
-    cuuint64_t strides[2] = {(cuuint64_t)S * 2, (cuuint64_t)S * K * 2};
+    cuuint64_t dims[3] = {(cuuint64_t)view.Sit, (cuuint64_t)K, (cuuint64_t)P};
+    cuuint64_t strides[2] = {(cuuint64_t)view.rowS * 2, (cuuint64_t)view.rowS * K * 2};
     cuuint32_t box[3] = {64, 64, 1};
     cuuint32_t es[3] = {1, 1, 1};
     if (enc(&tmh, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)Xhi, dims, strides, box, es,
@@ -329,11 +340,14 @@ cudaError_t launch_ttm_tc_wide(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xl
   TwParams prm{};
   prm.P = P;
   prm.K = K;
-  prm.S = S;
+  prm.S = view.Sit;
+  prm.So = view.So;
+  prm.s_last = view.s_last;
+  prm.s_pad = view.s_pad;
   prm.R = R;
   prm.Rp = Rp;
   prm.nkb = (int)((K + 63) / 64);
-  prm.nsb = km ? 1 : (S + 63) / 64;
+  prm.nsb = km ? 1 : (view.Sit + 63) / 64;
   prm.H = P * prm.nsb;
   prm.T = km ? (P + 127) / 128 : (prm.H + 1) / 2;
   prm.out = out;

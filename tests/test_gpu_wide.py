@@ -110,8 +110,9 @@ def _sensitivity(prob, sweeps, **kw):
 
 
 def test_wide_split_precision_solver_tracks_oracle():
-    """The split path at R = 64 (FP32 tensor; sides not multiples of 8, so the contracted modes of
-    the tensor itself go to the CUDA cores; FP64 QRs, explicit residual fit): per-sweep fits within
+    """The split path at R = 64 (FP32 tensor; its last side, 68, is not a multiple of 8, so the
+    TTMs over the tensor take the tensor cores through the padded split copy, the deeper ones the
+    CUDA cores; FP64 QRs, explicit residual fit): per-sweep fits within
     1e-4 of the oracle, factor subspaces within 10x the oracle's own change under a 2^-16 relative
     perturbation of X (R = 64 of 68 columns makes the factors' subspaces sensitive)."""
     prob = inputs.make_problem("wide_split", [72, 70, 68], 64, seed=7, c=0.3, eta=1e-2, dtype=np.float32)
