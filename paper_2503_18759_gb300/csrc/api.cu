@@ -776,6 +776,11 @@ cpqr_status run_update(cpqr_ctx* ctx, int n, int leaf, double beta, int next_mod
       cpqr_status sq = stage_q(ctx, n);
       if (sq != CPQR_OK) return sq;
     }
+    if (ctx->resid_pending) {  // the previous sweep's residual, beside the rest of this sweep
+      CK(cudaEventRecord(ctx->ev_prep, st));
+      cpqr_status sr = launch_lagged_residual(ctx);
+      if (sr != CPQR_OK) return sr;
+    }
     std::swap(ctx->Q0, ctx->Q0prev[n]);
     std::swap(ctx->Q0f, ctx->Q0fprev[n]);
     ctx->has_prev[n] = true;
@@ -843,10 +848,14 @@ double fit_from_r2(const cpqr_ctx* ctx, double r2) {
 }
 
 // Whether the fit of the current sweep may be read one sweep late: split path with the tensor-
-// core residual, and a beta for the following sweeps that no longer depends on the fit.
+// core residual or on the wide path, and a beta for the following sweeps that no longer depends on
+// the fit.
 bool can_lag(const cpqr_ctx* ctx) {
   if (!ctx->lag_ok || ctx->prec != CPQR_PREC_SPLIT_BF16 || ctx->x64) return false;
-  if (!residual_tc_supported(ctx->N, ctx->dims.data(), ctx->R, ctx->X)) return false;
+  // the tensor-core residual (R <= 32), which leaves a GPC free for the chain's cluster kernels, or
+  // the wide path's CUDA-core residual, beside QRs that launch no clusters (its FP32 work shares
+  // the SMs with their FP64 work)
+  if (!ctx->wide && !residual_tc_supported(ctx->N, ctx->dims.data(), ctx->R, ctx->X)) return false;
   // the rule's beta depends on the fit until it has activated (the learned proposer's fallback)
   if ((ctx->extrap == CPQR_EXTRAP_PAPER || ctx->extrap == CPQR_EXTRAP_LEARNED) && !ctx->activated) return false;
   return true;
@@ -1058,7 +1067,13 @@ cpqr_status one_sweep(cpqr_ctx* ctx, double* fit_out, const double* forced_beta 
   }
   if (lag) {
     // snapshot of this sweep's factors for its residual (launched during the next sweep); the
-    // previous residual reads the same buffer, so the snapshot waits for it
+    // previous residual reads the same buffer, so the snapshot waits for it (and a residual still
+    // pending, had no update launched it, goes first)
+    if (ctx->resid_pending) {
+      CK(cudaEventRecord(ctx->ev_prep, ctx->st));
+      cpqr_status sp = launch_lagged_residual(ctx);
+      if (sp != CPQR_OK) return sp;
+    }
     if (ctx->resid_inflight) CK(cudaStreamWaitEvent(ctx->st, ctx->ev_fit, 0));
     {
       Timed tm(ctx, CPQR_BUCKET_OTHER, 1);
@@ -1506,6 +1521,7 @@ cpqr_status cp_als_qr_sweep(cpqr_ctx* ctx, int32_t nsweeps, double* fits_host) {
   if (s != CPQR_OK) return s;
   s = flush_lag(ctx);
   if (s != CPQR_OK) return s;
+  if ((int64_t)ctx->fits.size() < nsweeps) return fail(ctx, CPQR_EINVAL);  // every fit is read by now
   if (fits_host)
     for (int i = 0; i < nsweeps; ++i) fits_host[i] = ctx->fits[ctx->fits.size() - nsweeps + i];
   return CPQR_OK;

@@ -156,3 +156,24 @@ def test_wide_split_solver_on_the_tensor_cores_tracks_oracle():
     assert np.max(np.abs(fits - np.array(ref.fits))) <= 1e-4, (fits, ref.fits)
     for n in range(3):
         assert o.subspace_sine(A[n], ref.A[n]) <= 10 * max(sens[n], 1e-6), (n, sens[n])
+
+
+def test_wide_lagged_fit_equals_sweep_by_sweep_fit():
+    """On the wide path the split solver's explicit residual (CUDA cores) is read one sweep late
+    inside a multi-sweep call too, beside the next sweep; the fits, betas and factors equal those of
+    sweep-by-sweep reads, up to the order of the residual's block partials."""
+    prob = inputs.make_problem("wide_lag", [64, 56, 72], 48, seed=8, c=0.3, eta=1e-2, dtype=np.float32)
+    X = _dev(prob.X)
+    opts = b.make_options(tree=b.TREE_RESTRUCTURED, prec=b.PREC_SPLIT_BF16, extrap=b.EXTRAP_FIXED, beta_fixed=0.01)
+    with b.Decomposition(prob.dims, prob.R, X.data_ptr(), False, prob.A0, opts) as d:
+        f_many = d.sweep(10)
+        A1, lam1, _, _ = d.factors()
+        lagged = d.stats().lagged_fits
+    with b.Decomposition(prob.dims, prob.R, X.data_ptr(), False, prob.A0, opts) as d:
+        f_one = np.array([d.sweep(1)[0] for _ in range(10)])
+        A2, lam2, _, _ = d.factors()
+    assert lagged >= 1
+    assert np.allclose(f_many, f_one, rtol=0, atol=1e-12), (f_many - f_one)
+    for a1, a2 in zip(A1, A2):
+        assert np.array_equal(a1, a2)
+    assert np.array_equal(lam1, lam2)
