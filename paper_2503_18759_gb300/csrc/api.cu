@@ -70,6 +70,7 @@ struct NodeBuf {
   // split path: which copies the node holds, back to back in p: FP32, then bf16 hi, lo
   bool has_f32 = true;
   bool has_split = false;
+  SplitLayout lay;  // the split copy's rows (last dimension padded to a multiple of 8, or dense)
 };
 
 uint64_t splitmix64(uint64_t& s) {
@@ -361,13 +362,24 @@ size_t align16(size_t b) { return (b + 15) / 16 * 16; }
 // Split-path tree nodes hold what their consumers read: the bf16 hi / lo split (the operand
 // of the tensor-core TTMs) for a node with two or more uncontracted modes, the FP32 tensor for
 // a leaf (V = Y_(n) Q0) and for a node that a CUDA-core TTM will read.
-size_t split_node_bytes(int64_t n, bool f32, bool split) {
-  return (f32 ? align16((size_t)n * 4) : 0) + (split ? 2 * align16((size_t)n * 2) : 0);
+// The split copy of a node whose last dimension is `last`: rows padded to a multiple of 8 (so that
+// every TTM over it can take the tensor cores) unless already one.
+SplitLayout node_split_layout(int64_t last) {
+  SplitLayout l;
+  if (last % 8 != 0) {
+    l.last = last;
+    l.ld = (last + 7) / 8 * 8;
+  }
+  return l;
 }
-void split_views(void* base, int64_t n, bool f32, __nv_bfloat16** hi, __nv_bfloat16** lo) {
+int64_t split_elems(int64_t n, SplitLayout lay) { return lay.ld ? n / lay.last * lay.ld : n; }
+size_t split_node_bytes(int64_t n, bool f32, bool split, SplitLayout lay) {
+  return (f32 ? align16((size_t)n * 4) : 0) + (split ? 2 * align16((size_t)split_elems(n, lay) * 2) : 0);
+}
+void split_views(void* base, int64_t n, bool f32, SplitLayout lay, __nv_bfloat16** hi, __nv_bfloat16** lo) {
   char* b = static_cast<char*>(base) + (f32 ? align16((size_t)n * 4) : 0);
   *hi = reinterpret_cast<__nv_bfloat16*>(b);
-  *lo = reinterpret_cast<__nv_bfloat16*>(b + align16((size_t)n * 2));
+  *lo = reinterpret_cast<__nv_bfloat16*>(b + align16((size_t)split_elems(n, lay) * 2));
 }
 
 cpqr_status run_ttm(cpqr_ctx* ctx, const Op& op) {
@@ -387,8 +399,10 @@ cpqr_status run_ttm(cpqr_ctx* ctx, const Op& op) {
   const uint32_t out_mask = sb.free_mask & ~(1u << k);
   // split path: which copies the output needs (see split_node_bytes)
   bool need_f32 = true, need_split = false;
+  SplitLayout olay;
   if (split) {
     const std::vector<int64_t> od = node_dims(ctx, out_mask);
+    olay = node_split_layout(od[ctx->N - 1]);
     int nfree = 0;
     bool cuda_core_consumer = false;
     for (int j = 0; j < ctx->N; ++j) {
@@ -397,13 +411,14 @@ cpqr_status run_ttm(cpqr_ctx* ctx, const Op& op) {
       int64_t Pj = 1, Sj = 1;
       for (int q = 0; q < j; ++q) Pj *= od[q];
       for (int q = j + 1; q < ctx->N; ++q) Sj *= od[q];
-      if (!(ctx->wide ? ttm_tc_wide_supported(Pj, od[j], Sj, R) : ttm_tc_supported(Pj, od[j], Sj, R)))
+      if (!(ctx->wide ? ttm_tc_wide_supported(Pj, od[j], Sj, R, olay) : ttm_tc_supported(Pj, od[j], Sj, R, olay)))
         cuda_core_consumer = true;
     }
     need_split = nfree >= 2;
     need_f32 = nfree < 2 || cuda_core_consumer;
+    if (!need_split) olay = SplitLayout{};
   }
-  const size_t bytes = split ? split_node_bytes(n_out, need_f32, need_split) : (size_t)n_out * es;
+  const size_t bytes = split ? split_node_bytes(n_out, need_f32, need_split, olay) : (size_t)n_out * es;
   void* out = nullptr;
   CK(ctx->pool.get(bytes, &out));
   cudaStream_t st = ctx->st;
@@ -422,19 +437,19 @@ cpqr_status run_ttm(cpqr_ctx* ctx, const Op& op) {
       CK(launch_ttm<double, double, double>((const double*)sb.p, ctx->Q[k], (double*)out, P, K, S, R, st));
   } else if (ctx->wide) {
     __nv_bfloat16 *ohi = nullptr, *olo = nullptr;
-    if (need_split) split_views(out, n_out, need_f32, &ohi, &olo);
+    if (need_split) split_views(out, n_out, need_f32, olay, &ohi, &olo);
     float* of = need_f32 ? static_cast<float*>(out) : nullptr;
-    const SplitLayout lay = sb.is_x ? ctx->xlay : SplitLayout{};
+    const SplitLayout lay = sb.is_x ? ctx->xlay : sb.lay;
     if (ttm_tc_wide_supported(P, K, S, R, lay) && (sb.is_x || sb.has_split)) {
       const __nv_bfloat16 *shi = ctx->Xhi, *slo = ctx->Xlo;
       if (!sb.is_x) {
         __nv_bfloat16 *h, *l;
-        split_views(sb.p, P * K * S, sb.has_f32, &h, &l);
+        split_views(sb.p, P * K * S, sb.has_f32, sb.lay, &h, &l);
         shi = h;
         slo = l;
       }
       CK(launch_ttm_tc_wide(shi, slo, ctx->Qt[k], ctx->Rp, ctx->Kp[k], of, P, K, S, R, ctx->dstatus, st, ohi, olo,
-                            lay));
+                            lay, olay));
     } else {
       // the CUDA-core FP32 TTM from the node's FP32 copy (kept for every CUDA-core consumer)
       if (!sb.has_f32) return fail(ctx, CPQR_EINVAL);
@@ -446,21 +461,24 @@ cpqr_status run_ttm(cpqr_ctx* ctx, const Op& op) {
       }
       CK((launch_ttm_wide<float, float, float, float>((const float*)sb.p, ctx->Qf[k], o32, P, K, S, R, st)));
       if (need_split) {
-        CK(launch_split_x(o32, ohi, olo, n_out, st));
+        if (olay.ld)
+          CK(launch_split_x_padded(o32, ohi, olo, n_out / olay.last, olay.last, olay.ld, st));
+        else
+          CK(launch_split_x(o32, ohi, olo, n_out, st));
         ctx->launches += 1;
       }
       if (!of) ctx->pool.put((size_t)n_out * 4, o32);
     }
   } else {
     __nv_bfloat16 *ohi = nullptr, *olo = nullptr;
-    if (need_split) split_views(out, n_out, need_f32, &ohi, &olo);
+    if (need_split) split_views(out, n_out, need_f32, olay, &ohi, &olo);
     float* of = need_f32 ? static_cast<float*>(out) : nullptr;
-    const SplitLayout lay = sb.is_x ? ctx->xlay : SplitLayout{};
+    const SplitLayout lay = sb.is_x ? ctx->xlay : sb.lay;
     if (ttm_tc_supported(P, K, S, R, lay) && (sb.is_x || sb.has_split)) {
       const __nv_bfloat16 *shi = ctx->Xhi, *slo = ctx->Xlo;
       if (!sb.is_x) {
         __nv_bfloat16 *h, *l;
-        split_views(sb.p, P * K * S, sb.has_f32, &h, &l);
+        split_views(sb.p, P * K * S, sb.has_f32, sb.lay, &h, &l);
         shi = h;
         slo = l;
       }
@@ -473,7 +491,7 @@ cpqr_status run_ttm(cpqr_ctx* ctx, const Op& op) {
       const bool skip = ctx->test_skip_next_ttm;
       ctx->test_skip_next_ttm = false;
       CK(launch_ttm_tc(shi, slo, ctx->Qt[k], ctx->Rp, ctx->Kp[k], of, P, K, S, R, ctx->dstatus, st, reserve, ohi,
-                       olo, skip ? ctx->test_wait_ns : 0, skip ? 1 : 0, lay));
+                       olo, skip ? ctx->test_wait_ns : 0, skip ? 1 : 0, lay, olay));
     } else {
       if (!sb.has_f32) return fail(ctx, CPQR_EINVAL);  // not produced for a CUDA-core consumer
       float* o32 = of;
@@ -487,7 +505,10 @@ cpqr_status run_ttm(cpqr_ctx* ctx, const Op& op) {
                                                                            S, R, st);
       CK(e);
       if (need_split) {
-        CK(launch_split_x(o32, ohi, olo, n_out, st));
+        if (olay.ld)
+          CK(launch_split_x_padded(o32, ohi, olo, n_out / olay.last, olay.last, olay.ld, st));
+        else
+          CK(launch_split_x(o32, ohi, olo, n_out, st));
         ctx->launches += 1;
       }
       if (!of) ctx->pool.put((size_t)n_out * 4, o32);  // stream order protects it until the split ran
@@ -496,6 +517,7 @@ cpqr_status run_ttm(cpqr_ctx* ctx, const Op& op) {
   NodeBuf nb{out, bytes, out_mask, false};
   nb.has_f32 = need_f32;
   nb.has_split = need_split;
+  nb.lay = olay;
   ctx->nodes[dst] = nb;
   return CPQR_OK;
 }

@@ -94,14 +94,16 @@ TtmView ttm_view(int64_t K, int64_t S, SplitLayout lay);
 // out[p, r, s] = sum_i X[p, i, s] Q[i, r] from split operands; out FP32 and, if out_hi /
 // out_lo are given, its bf16 split (the operand format of a following tensor-core TTM).
 // Dense sources: S % 8 == 0 (MN-major) or S == 1 with K % 8 == 0 (K-major); a padded source
-// (lay): any S that ttm_view serves.  K <= 512.  Returns cudaErrorNotSupported if the shape is
+// (lay): any S that ttm_view serves; out_lay: the layout of the split copy of out (padded rows of
+// its last dimension, as a padded source).  K <= 512.  Returns cudaErrorNotSupported if the shape is
 // outside the kernel's range.
 // reserve_sms: SMs the persistent grid leaves free for concurrent work (a cluster QR).
 cudaError_t launch_ttm_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo, const __nv_bfloat16* Qt,
                           int Rp, int64_t Kp, float* out, int64_t P, int64_t K, int64_t S, int R,
                           unsigned int* dev_status, cudaStream_t st, int reserve_sms = 0,
                           __nv_bfloat16* out_hi = nullptr, __nv_bfloat16* out_lo = nullptr,
-                          unsigned long long wait_ns = 0, int skip_x_loads = 0, SplitLayout lay = {});
+                          unsigned long long wait_ns = 0, int skip_x_loads = 0, SplitLayout lay = {},
+                          SplitLayout out_lay = {});
 bool ttm_tc_supported(int64_t P, int64_t K, int64_t S, int R, SplitLayout lay = {});
 
 // ----- small FP64 kernels (smallqr.cu) -----
@@ -320,7 +322,7 @@ bool ttm_tc_wide_supported(int64_t P, int64_t K, int64_t S, int R, SplitLayout l
 cudaError_t launch_ttm_tc_wide(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo, const __nv_bfloat16* Qt, int Rp,
                                int64_t Kp, float* out, int64_t P, int64_t K, int64_t S, int R,
                                unsigned int* dev_status, cudaStream_t st, __nv_bfloat16* out_hi = nullptr,
-                               __nv_bfloat16* out_lo = nullptr, SplitLayout lay = {});
+                               __nv_bfloat16* out_lo = nullptr, SplitLayout lay = {}, SplitLayout out_lay = {});
 // TTM on the CUDA cores for any R (tiled GEMM, accumulation in TAcc).
 template <typename TT, typename TQ, typename TO, typename TAcc>
 cudaError_t launch_ttm_wide(const TT* T, const TQ* Q, TO* out, int64_t P, int64_t K, int64_t S, int R,

@@ -192,6 +192,7 @@ struct TcParams {
   float* out;             // FP32 result (may be null when only the split is wanted)
   __nv_bfloat16* out_hi;  // optional split copy of out (hi + lo = out to ~2^-16)
   __nv_bfloat16* out_lo;
+  int64_t oh_last, oh_ld;  // the split copy's rows: last dimension padded to oh_ld (0: dense)
   unsigned int* status;
   unsigned long long wait_ns;  // limit of the pipeline waits (drain waits keep kTimeoutNs)
   int skip_x_loads;            // failure-detection test: issue no tile loads, so the MMA wait runs out
@@ -212,16 +213,18 @@ struct TcSmemTail {
 
 using namespace tc;
 
-__device__ __forceinline__ void store_out(const TcParams& p, int64_t idx, float v) {
+// out[idx] and, if asked, the split copy at si (idx, or its place in the padded rows)
+__device__ __forceinline__ void store_out(const TcParams& p, int64_t idx, int64_t si, float v) {
   if (p.out) p.out[idx] = v;
   if (p.out_hi) {
     const __nv_bfloat16 h = __float2bfloat16_rn(v);
-    p.out_hi[idx] = h;
-    p.out_lo[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
+    p.out_hi[si] = h;
+    p.out_lo[si] = __float2bfloat16_rn(v - __bfloat162float(h));
   }
 }
 
-template <bool KM>
+// PO: the split copy of the output goes to padded rows (a dense output compiles without it)
+template <bool KM, bool PO>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     ttm_tc_kernel(const __grid_constant__ CUtensorMap tmXhi, const __grid_constant__ CUtensorMap tmXlo,
                   const __grid_constant__ CUtensorMap tmQ, TcParams p) {
@@ -421,7 +424,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int nrows = (int)std::min<int64_t>(32, p.P - p0);
         for (int e = lane; e < nrows * p.R; e += 32) {
           const int row = e / p.R, r = e - row * p.R;
-          store_out(p, p0 * p.R + e, stg[row * 33 + r]);
+          // K-major output: rows of R (the split copy's rows padded to oh_ld when R is not a multiple of 8)
+          const int64_t idx = p0 * p.R + e;
+          store_out(p, idx, (PO && p.oh_ld) ? (p0 + row) * p.oh_ld + r : idx, stg[row * 33 + r]);
         }
         __syncwarp();
       } else {
@@ -438,9 +443,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           }
           if (live) {
             const int64_t o = (pp * p.R) * p.So + so;
+            // the split copy in padded rows of the output's last dimension: one division here,
+            // element (pp, r, so) then at row (pp R + r) q + so / last, column so % last
+            int64_t q = 0, srow = 0, scol = 0;
+            if (PO && p.oh_ld) {
+              q = p.So / p.oh_last;
+              const int64_t sq = so / p.oh_last;
+              srow = pp * p.R * q + sq;
+              scol = so - sq * p.oh_last;
+            }
 #pragma unroll
             for (int r = 0; r < 32; ++r)
-              if (r < p.R) store_out(p, o + (int64_t)r * p.So, v[r]);
+              if (r < p.R) {
+                const int64_t idx = o + (int64_t)r * p.So;
+                store_out(p, idx, (PO && p.oh_ld) ? (srow + (int64_t)r * q) * p.oh_ld + scol : idx, v[r]);
+              }
           }
         }
       }
@@ -482,7 +499,7 @@ bool ttm_tc_supported(int64_t P, int64_t K, int64_t S, int R, SplitLayout lay) {
 cudaError_t launch_ttm_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo, const __nv_bfloat16* Qt, int Rp,
                           int64_t Kp, float* out, int64_t P, int64_t K, int64_t S, int R, unsigned int* dev_status,
                           cudaStream_t st, int reserve_sms, __nv_bfloat16* out_hi, __nv_bfloat16* out_lo,
-                          unsigned long long wait_ns, int skip_x_loads, SplitLayout lay) {
+                          unsigned long long wait_ns, int skip_x_loads, SplitLayout lay, SplitLayout out_lay) {
   if (!ttm_tc_supported(P, K, S, R, lay) || (Rp != 16 && Rp != 32) || Rp < R || Kp < K || (Kp % 64) != 0)
     return cudaErrorNotSupported;
   const TtmView view = ttm_view(K, S, lay);
@@ -545,13 +562,17 @@ cudaError_t launch_ttm_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo, co
   prm.out = out;
   prm.out_hi = out_hi;
   prm.out_lo = out_lo;
+  prm.oh_last = out_lay.ld ? out_lay.last : 0;
+  prm.oh_ld = out_lay.ld;
   prm.status = dev_status;
   prm.wait_ns = wait_ns ? wait_ns : tc::kTimeoutNs;
   prm.skip_x_loads = skip_x_loads;
   if (prm.nkb * 64 > Kp) return cudaErrorInvalidValue;
   const size_t smem = 1024 + (size_t)TC_NST * TC_STAGE_BYTES + (size_t)prm.nkb * 2 * Rp * 128 +
                       ((sizeof(TcSmemTail) + 15) / 16) * 16 + (km ? 4 * 32 * 33 * sizeof(float) : 0);
-  auto kern = km ? ttm_tc_kernel<true> : ttm_tc_kernel<false>;
+  const bool po = out_hi && out_lay.ld;
+  auto kern = km ? (po ? ttm_tc_kernel<true, true> : ttm_tc_kernel<true, false>)
+                  : (po ? ttm_tc_kernel<false, true> : ttm_tc_kernel<false, false>);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (reserve_sms > 0) {

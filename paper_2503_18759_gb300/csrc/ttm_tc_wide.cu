@@ -36,6 +36,7 @@ struct TwParams {
   float* out;
   __nv_bfloat16* out_hi;
   __nv_bfloat16* out_lo;
+  int64_t oh_last, oh_ld;  // the split copy's rows: last dimension padded to oh_ld (0: dense)
   unsigned int* status;
 };
 
@@ -51,16 +52,18 @@ struct TwTail {
   int consumed[TW_MAXST];
 };
 
-__device__ __forceinline__ void store_w(const TwParams& p, int64_t idx, float v) {
+// out[idx] and, if asked, the split copy at si (idx, or its place in the padded rows)
+__device__ __forceinline__ void store_w(const TwParams& p, int64_t idx, int64_t si, float v) {
   if (p.out) p.out[idx] = v;
   if (p.out_hi) {
     const __nv_bfloat16 h = __float2bfloat16_rn(v);
-    p.out_hi[idx] = h;
-    p.out_lo[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
+    p.out_hi[si] = h;
+    p.out_lo[si] = __float2bfloat16_rn(v - __bfloat162float(h));
   }
 }
 
-template <bool KM>
+// PO: the split copy of the output goes to padded rows (a dense output compiles without it)
+template <bool KM, bool PO>
 __global__ void __launch_bounds__(TW_THREADS, 1)
     ttm_tc_wide_kernel(const __grid_constant__ CUtensorMap tmXhi, const __grid_constant__ CUtensorMap tmXlo,
                        const __grid_constant__ CUtensorMap tmQ, TwParams p) {
@@ -226,7 +229,8 @@ __global__ void __launch_bounds__(TW_THREADS, 1)
           const int wc = std::min(w, p.R - c0);    // valid columns of the chunk
           for (int e = lane; e < nrows * wc; e += 32) {
             const int row = e / wc, rr = e - row * wc;
-            store_w(p, (r0 + row) * p.R + c0 + rr, stg[row * 33 + rr]);
+            const int64_t idx = (r0 + row) * p.R + c0 + rr;
+            store_w(p, idx, (PO && p.oh_ld) ? (r0 + row) * p.oh_ld + c0 + rr : idx, stg[row * 33 + rr]);
           }
           __syncwarp();
         } else {
@@ -243,9 +247,20 @@ __global__ void __launch_bounds__(TW_THREADS, 1)
             }
             if (live) {
               const int64_t o = (pp * p.R) * p.So + so;
+              // the split copy in padded rows of the output's last dimension (see ttm_tc.cu)
+              int64_t q = 0, srow = 0, scol = 0;
+              if (PO && p.oh_ld) {
+                q = p.So / p.oh_last;
+                const int64_t sq = so / p.oh_last;
+                srow = pp * p.R * q + sq;
+                scol = so - sq * p.oh_last;
+              }
 #pragma unroll
               for (int r = 0; r < 32; ++r)
-                if (r < w && c0 + r < p.R) store_w(p, o + (int64_t)(c0 + r) * p.So, v[r]);
+                if (r < w && c0 + r < p.R) {
+                  const int64_t idx = o + (int64_t)(c0 + r) * p.So;
+                  store_w(p, idx, (PO && p.oh_ld) ? (srow + (int64_t)(c0 + r) * q) * p.oh_ld + scol : idx, v[r]);
+                }
             }
           }
         }
@@ -292,7 +307,7 @@ bool ttm_tc_wide_supported(int64_t P, int64_t K, int64_t S, int R, SplitLayout l
 cudaError_t launch_ttm_tc_wide(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo, const __nv_bfloat16* Qt, int Rp,
                                int64_t Kp, float* out, int64_t P, int64_t K, int64_t S, int R,
                                unsigned int* dev_status, cudaStream_t st, __nv_bfloat16* out_hi,
-                               __nv_bfloat16* out_lo, SplitLayout lay) {
+                               __nv_bfloat16* out_lo, SplitLayout lay, SplitLayout out_lay) {
   if (!ttm_tc_wide_supported(P, K, S, R, lay) || Rp % 16 || Rp < R || Rp > 192 || Kp < K || (Kp % 64) != 0)
     return cudaErrorNotSupported;
   const TtmView view = ttm_view(K, S, lay);
@@ -353,6 +368,8 @@ cudaError_t launch_ttm_tc_wide(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xl
   prm.out = out;
   prm.out_hi = out_hi;
   prm.out_lo = out_lo;
+  prm.oh_last = out_lay.ld ? out_lay.last : 0;
+  prm.oh_ld = out_lay.ld;
   prm.status = dev_status;
   if ((int64_t)prm.nkb * 64 > Kp) return cudaErrorInvalidValue;
   prm.stage_bytes = (uint32_t)(TW_A_BYTES + 2 * Rp * 128);
@@ -368,7 +385,9 @@ cudaError_t launch_ttm_tc_wide(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xl
   if (fixed + (size_t)nst * prm.stage_bytes > (size_t)TW_SMEM_LIMIT) return cudaErrorNotSupported;
   prm.nst = nst;
   const size_t smem = fixed + (size_t)nst * prm.stage_bytes;
-  auto kern = km ? ttm_tc_wide_kernel<true> : ttm_tc_wide_kernel<false>;
+  const bool po = out_hi && out_lay.ld;
+  auto kern = km ? (po ? ttm_tc_wide_kernel<true, true> : ttm_tc_wide_kernel<true, false>)
+                  : (po ? ttm_tc_wide_kernel<false, true> : ttm_tc_wide_kernel<false, false>);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int64_t grid = std::min<int64_t>(prm.T, tc::num_sms());
