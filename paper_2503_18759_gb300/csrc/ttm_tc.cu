@@ -223,8 +223,47 @@ __device__ __forceinline__ void store_out(const TcParams& p, int64_t idx, int64_
   }
 }
 
-// PO: the split copy of the output goes to padded rows (a dense output compiles without it)
-template <bool KM, bool PO>
+// The MN-major epilogue's stores of one row s: out[o + r So] for r < R, FP32 and / or the split
+// copy (hi and lo of a pair of columns converted together; each is rounded on its own, so the
+// pair conversion equals two single ones).  Base pointers advance by So per column, so a column
+// costs its conversion and stores only.
+template <int RPT>
+__device__ __forceinline__ void store_row_mn(const TcParams& p, int64_t o, const float* v) {
+  const int64_t So = p.So;
+  const int R = p.R;
+  if (p.out_hi) {
+    __nv_bfloat16* dh = p.out_hi + o;
+    __nv_bfloat16* dl = p.out_lo + o;
+#pragma unroll
+    for (int r = 0; r < RPT; r += 2) {
+      const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[r], v[r + 1]);
+      const float2 hf = __bfloat1622float2(h2);
+      const __nv_bfloat162 l2 = __floats2bfloat162_rn(v[r] - hf.x, v[r + 1] - hf.y);
+      if (r < R) {
+        dh[0] = h2.x;
+        dl[0] = l2.x;
+      }
+      if (r + 1 < R) {
+        dh[So] = h2.y;
+        dl[So] = l2.y;
+      }
+      dh += 2 * So;
+      dl += 2 * So;
+    }
+  }
+  if (p.out) {
+    float* df = p.out + o;
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      if (r < R) *df = v[r];
+      df += So;
+    }
+  }
+}
+
+// PO: the split copy of the output goes to padded rows (a dense output compiles without it);
+// RPT: accumulator columns read back per part (Rp, 16 or 32)
+template <bool KM, bool PO, int RPT>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     ttm_tc_kernel(const __grid_constant__ CUtensorMap tmXhi, const __grid_constant__ CUtensorMap tmXlo,
                   const __grid_constant__ CUtensorMap tmQ, TcParams p) {
@@ -389,28 +428,31 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   } else {
     // ---------------- epilogue: warps 0-3, tensor-memory lanes 32w .. 32w+31 ----------------
     const int m = warp * 32 + lane;
+    // K-major: element e = lane + 32 j of the warp's rows x R block is (row, r); both advance by
+    // 32 / R rows and 32 % R columns per step
+    const int km_dq = 32 / p.R, km_dr = 32 - km_dq * p.R;
     for (int64_t lt = 0; lt < ntile_local; ++lt) {
       const int acc = (int)(lt & 1);
       const uint32_t use = (uint32_t)(lt >> 1);
       if (!mbar_wait(smem_u32(&tail->tfull[acc]), use & 1u, &tail->abort_flag, p.status, true, p.wait_ns)) break;
       fence_after();
-      float v[32], w[32];
-#pragma unroll
-      for (int r = 0; r < 32; ++r) v[r] = w[r] = 0.f;  // columns past Rp = 16 stay zero
+      // (even + odd) + corrections, each add rounded to nearest; a K of one block has no odd part.
+      // The parts are loaded together, with one wait.
       const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc * TC_ACC_COLS);
-      // (even + odd) + corrections, each add rounded to nearest; a K of one block has no odd part
-      if (p.Rp == 32) tmem_ld32(taddr, v);
-      else tmem_ld16(taddr, v);
+      float v[RPT];
+      uint32_t raw[3 * RPT];
       if (p.nkb > 1) {
-        if (p.Rp == 32) tmem_ld32(taddr + 32, w);
-        else tmem_ld16(taddr + 32, w);
+        if (RPT == 32) tmem_ld32x3(taddr, taddr + 32, taddr + 64, raw);
+        else tmem_ld16x3(taddr, taddr + 32, taddr + 64, raw);
 #pragma unroll
-        for (int r = 0; r < 32; ++r) v[r] += w[r];
+        for (int r = 0; r < RPT; ++r)
+          v[r] = (__uint_as_float(raw[r]) + __uint_as_float(raw[RPT + r])) + __uint_as_float(raw[2 * RPT + r]);
+      } else {
+        if (RPT == 32) tmem_ld32x2(taddr, taddr + 64, raw);
+        else tmem_ld16x2(taddr, taddr + 64, raw);
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) v[r] = __uint_as_float(raw[r]) + __uint_as_float(raw[RPT + r]);
       }
-      if (p.Rp == 32) tmem_ld32(taddr + 64, w);
-      else tmem_ld16(taddr + 64, w);
-#pragma unroll
-      for (int r = 0; r < 32; ++r) v[r] += w[r];
       fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&tail->tempty[acc]));
@@ -418,21 +460,35 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (KM) {
         float* stg = epi + warp * (32 * 33);
 #pragma unroll
-        for (int r = 0; r < 32; ++r) stg[lane * 33 + r] = v[r];
+        for (int r = 0; r < RPT; ++r) stg[lane * 33 + r] = v[r];
         __syncwarp();
         const int64_t p0 = tile * 128 + warp * 32;  // this warp's rows, contiguous in out
         const int nrows = (int)std::min<int64_t>(32, p.P - p0);
+        int row = lane / p.R, r = lane - row * p.R;
         for (int e = lane; e < nrows * p.R; e += 32) {
-          const int row = e / p.R, r = e - row * p.R;
           // K-major output: rows of R (the split copy's rows padded to oh_ld when R is not a multiple of 8)
           const int64_t idx = p0 * p.R + e;
           store_out(p, idx, (PO && p.oh_ld) ? (p0 + row) * p.oh_ld + r : idx, stg[row * 33 + r]);
+          row += km_dq;
+          r += km_dr;
+          if (r >= p.R) {
+            r -= p.R;
+            ++row;
+          }
         }
         __syncwarp();
       } else {
         const int64_t h = 2 * tile + (m >> 6);
         if (h < p.H) {
-          const int64_t pp = h / p.nsb, sb = h % p.nsb;
+          int64_t pp, sb;
+          if (p.H <= 0x7fffffffLL) {  // the common case: a 32-bit division
+            const uint32_t q = (uint32_t)h / (uint32_t)p.nsb;
+            pp = q;
+            sb = (int64_t)((uint32_t)h - q * (uint32_t)p.nsb);
+          } else {
+            pp = h / p.nsb;
+            sb = h - pp * p.nsb;
+          }
           const int64_t sidx = sb * 64 + (m & 63);
           bool live = sidx < p.S;
           int64_t so = sidx;
@@ -443,21 +499,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           }
           if (live) {
             const int64_t o = (pp * p.R) * p.So + so;
-            // the split copy in padded rows of the output's last dimension: one division here,
-            // element (pp, r, so) then at row (pp R + r) q + so / last, column so % last
-            int64_t q = 0, srow = 0, scol = 0;
             if (PO && p.oh_ld) {
-              q = p.So / p.oh_last;
+              // the split copy in padded rows of the output's last dimension: one division here,
+              // element (pp, r, so) then at row (pp R + r) q + so / last, column so % last
+              const int64_t q = p.So / p.oh_last;
               const int64_t sq = so / p.oh_last;
-              srow = pp * p.R * q + sq;
-              scol = so - sq * p.oh_last;
-            }
+              const int64_t srow = pp * p.R * q + sq;
+              const int64_t scol = so - sq * p.oh_last;
 #pragma unroll
-            for (int r = 0; r < 32; ++r)
-              if (r < p.R) {
-                const int64_t idx = o + (int64_t)r * p.So;
-                store_out(p, idx, (PO && p.oh_ld) ? (srow + (int64_t)r * q) * p.oh_ld + scol : idx, v[r]);
-              }
+              for (int r = 0; r < RPT; ++r)
+                if (r < p.R) {
+                  const int64_t idx = o + (int64_t)r * p.So;
+                  store_out(p, idx, (srow + (int64_t)r * q) * p.oh_ld + scol, v[r]);
+                }
+            } else {
+              store_row_mn<RPT>(p, o, v);
+            }
           }
         }
       }
@@ -571,8 +628,11 @@ cudaError_t launch_ttm_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo, co
   const size_t smem = 1024 + (size_t)TC_NST * TC_STAGE_BYTES + (size_t)prm.nkb * 2 * Rp * 128 +
                       ((sizeof(TcSmemTail) + 15) / 16) * 16 + (km ? 4 * 32 * 33 * sizeof(float) : 0);
   const bool po = out_hi && out_lay.ld;
-  auto kern = km ? (po ? ttm_tc_kernel<true, true> : ttm_tc_kernel<true, false>)
-                  : (po ? ttm_tc_kernel<false, true> : ttm_tc_kernel<false, false>);
+  auto kern = (Rp == 16)
+                  ? (km ? (po ? ttm_tc_kernel<true, true, 16> : ttm_tc_kernel<true, false, 16>)
+                        : (po ? ttm_tc_kernel<false, true, 16> : ttm_tc_kernel<false, false, 16>))
+                  : (km ? (po ? ttm_tc_kernel<true, true, 32> : ttm_tc_kernel<true, false, 32>)
+                        : (po ? ttm_tc_kernel<false, true, 32> : ttm_tc_kernel<false, false, 32>));
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (reserve_sms > 0) {
