@@ -464,6 +464,31 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         __syncwarp();
         const int64_t p0 = tile * 128 + warp * 32;  // this warp's rows, contiguous in out
         const int nrows = (int)std::min<int64_t>(32, p.P - p0);
+        if (!(PO && p.oh_ld) && (p.R & 1) == 0) {
+          // dense rows of even R: a lane stores a pair of adjacent columns (float2, bf16x2)
+          const int half = p.R >> 1;
+          const int dq = 32 / half, dc = 32 - dq * half;
+          int row = lane / half, c = lane - row * half;
+          for (int e = lane; e < nrows * half; e += 32) {
+            const float a = stg[row * 33 + 2 * c], b = stg[row * 33 + 2 * c + 1];
+            const int64_t idx = p0 * p.R + 2 * e;  // = (p0 + row) R + 2 c
+            if (p.out) *reinterpret_cast<float2*>(p.out + idx) = make_float2(a, b);
+            if (p.out_hi) {
+              const __nv_bfloat162 h2 = __floats2bfloat162_rn(a, b);
+              const float2 hf = __bfloat1622float2(h2);
+              *reinterpret_cast<__nv_bfloat162*>(p.out_hi + idx) = h2;
+              *reinterpret_cast<__nv_bfloat162*>(p.out_lo + idx) = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+            }
+            row += dq;
+            c += dc;
+            if (c >= half) {
+              c -= half;
+              ++row;
+            }
+          }
+          __syncwarp();
+          continue;
+        }
         int row = lane / p.R, r = lane - row * p.R;
         for (int e = lane; e < nrows * p.R; e += 32) {
           // K-major output: rows of R (the split copy's rows padded to oh_ld when R is not a multiple of 8)

@@ -62,6 +62,41 @@ __device__ __forceinline__ void store_w(const TwParams& p, int64_t idx, int64_t 
   }
 }
 
+// The MN-major stores of one row s for the nc columns of a chunk: out[o + r So], r < nc (o at
+// the chunk's first column), FP32 and / or the split copy (pair conversion as in ttm_tc.cu);
+// base pointers advance by So per column.
+__device__ __forceinline__ void store_chunk_mn(const TwParams& p, int64_t o, const float* v, int nc) {
+  const int64_t So = p.So;
+  if (p.out_hi) {
+    __nv_bfloat16* dh = p.out_hi + o;
+    __nv_bfloat16* dl = p.out_lo + o;
+#pragma unroll
+    for (int r = 0; r < 32; r += 2) {
+      const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[r], v[r + 1]);
+      const float2 hf = __bfloat1622float2(h2);
+      const __nv_bfloat162 l2 = __floats2bfloat162_rn(v[r] - hf.x, v[r + 1] - hf.y);
+      if (r < nc) {
+        dh[0] = h2.x;
+        dl[0] = l2.x;
+      }
+      if (r + 1 < nc) {
+        dh[So] = h2.y;
+        dl[So] = l2.y;
+      }
+      dh += 2 * So;
+      dl += 2 * So;
+    }
+  }
+  if (p.out) {
+    float* df = p.out + o;
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+      if (r < nc) *df = v[r];
+      df += So;
+    }
+  }
+}
+
 // PO: the split copy of the output goes to padded rows (a dense output compiles without it)
 template <bool KM, bool PO>
 __global__ void __launch_bounds__(TW_THREADS, 1)
@@ -205,20 +240,56 @@ __global__ void __launch_bounds__(TW_THREADS, 1)
       fence_after();
       const int64_t tile = blockIdx.x + lt * gridDim.x;
       const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)acc * acc_cols;
+      // MN-major: this thread's row s of the tile (a 32-bit division in the common case)
+      int64_t o_row = -1, po_q = 0, po_srow = 0, po_scol = 0;
+      if (!KM) {
+        const int64_t h = 2 * tile + (m >> 6);
+        if (h < p.H) {
+          int64_t pp, sb;
+          if (p.H <= 0x7fffffffLL) {
+            const uint32_t q = (uint32_t)h / (uint32_t)p.nsb;
+            pp = q;
+            sb = (int64_t)((uint32_t)h - q * (uint32_t)p.nsb);
+          } else {
+            pp = h / p.nsb;
+            sb = h - pp * p.nsb;
+          }
+          const int64_t sidx = sb * 64 + (m & 63);
+          bool live = sidx < p.S;
+          int64_t so = sidx;
+          if (p.s_pad) {  // a padded source: skip the padding of its last dimension
+            const int64_t qd = sidx / p.s_pad, i2 = sidx - qd * p.s_pad;
+            live = live && i2 < p.s_last;
+            so = qd * p.s_last + i2;
+          }
+          if (live) {
+            o_row = (pp * p.R) * p.So + so;
+            if (PO && p.oh_ld) {
+              // the split copy in padded rows of the output's last dimension (see ttm_tc.cu)
+              po_q = p.So / p.oh_last;
+              const int64_t sq = so / p.oh_last;
+              po_srow = pp * p.R * po_q + sq;
+              po_scol = so - sq * p.oh_last;
+            }
+          }
+        }
+      }
       for (int c0 = 0; c0 < p.Rp; c0 += 32) {
         const int w = (p.Rp - c0 >= 32) ? 32 : 16;
-        float v[32], u[32];
-#pragma unroll
-        for (int r = 0; r < 32; ++r) v[r] = u[r] = 0.f;
+        // hi*hi and the corrections of the chunk, loaded with one wait
+        float v[32];
+        uint32_t raw[64];
         if (w == 32) {
-          tmem_ld32(tbase + (uint32_t)c0, v);
-          tmem_ld32(tbase + rpa + (uint32_t)c0, u);
-        } else {
-          tmem_ld16(tbase + (uint32_t)c0, v);
-          tmem_ld16(tbase + rpa + (uint32_t)c0, u);
-        }
+          tmem_ld32x2(tbase + (uint32_t)c0, tbase + rpa + (uint32_t)c0, raw);
 #pragma unroll
-        for (int r = 0; r < 32; ++r) v[r] += u[r];
+          for (int r = 0; r < 32; ++r) v[r] = __uint_as_float(raw[r]) + __uint_as_float(raw[32 + r]);
+        } else {
+          tmem_ld16x2(tbase + (uint32_t)c0, tbase + rpa + (uint32_t)c0, raw);
+#pragma unroll
+          for (int r = 0; r < 16; ++r) v[r] = __uint_as_float(raw[r]) + __uint_as_float(raw[16 + r]);
+#pragma unroll
+          for (int r = 16; r < 32; ++r) v[r] = 0.f;
+        }
         if (KM) {
           float* stg = epi + warp * (32 * 33);
 #pragma unroll
@@ -227,41 +298,30 @@ __global__ void __launch_bounds__(TW_THREADS, 1)
           const int64_t r0 = tile * 128 + warp * 32;  // this warp's rows
           const int nrows = (int)std::min<int64_t>(32, p.P - r0);
           const int wc = std::min(w, p.R - c0);    // valid columns of the chunk
+          const int dq = 32 / wc, dr = 32 - dq * wc;
+          int row = lane / wc, rr = lane - row * wc;
           for (int e = lane; e < nrows * wc; e += 32) {
-            const int row = e / wc, rr = e - row * wc;
             const int64_t idx = (r0 + row) * p.R + c0 + rr;
             store_w(p, idx, (PO && p.oh_ld) ? (r0 + row) * p.oh_ld + c0 + rr : idx, stg[row * 33 + rr]);
+            row += dq;
+            rr += dr;
+            if (rr >= wc) {
+              rr -= wc;
+              ++row;
+            }
           }
           __syncwarp();
-        } else {
-          const int64_t h = 2 * tile + (m >> 6);
-          if (h < p.H) {
-            const int64_t pp = h / p.nsb, sb = h % p.nsb;
-            const int64_t sidx = sb * 64 + (m & 63);
-            bool live = sidx < p.S;
-            int64_t so = sidx;
-            if (p.s_pad) {  // a padded source: skip the padding of its last dimension
-              const int64_t qd = sidx / p.s_pad, i2 = sidx - qd * p.s_pad;
-              live = live && i2 < p.s_last;
-              so = qd * p.s_last + i2;
-            }
-            if (live) {
-              const int64_t o = (pp * p.R) * p.So + so;
-              // the split copy in padded rows of the output's last dimension (see ttm_tc.cu)
-              int64_t q = 0, srow = 0, scol = 0;
-              if (PO && p.oh_ld) {
-                q = p.So / p.oh_last;
-                const int64_t sq = so / p.oh_last;
-                srow = pp * p.R * q + sq;
-                scol = so - sq * p.oh_last;
-              }
+        } else if (o_row >= 0) {
+          const int nc = std::min(w, p.R - c0);
+          if (PO && p.oh_ld) {
 #pragma unroll
-              for (int r = 0; r < 32; ++r)
-                if (r < w && c0 + r < p.R) {
-                  const int64_t idx = o + (int64_t)(c0 + r) * p.So;
-                  store_w(p, idx, (PO && p.oh_ld) ? (srow + (int64_t)(c0 + r) * q) * p.oh_ld + scol : idx, v[r]);
-                }
-            }
+            for (int r = 0; r < 32; ++r)
+              if (r < nc) {
+                const int64_t idx = o_row + (int64_t)(c0 + r) * p.So;
+                store_w(p, idx, (po_srow + (int64_t)(c0 + r) * po_q) * p.oh_ld + po_scol, v[r]);
+              }
+          } else {
+            store_chunk_mn(p, o_row + (int64_t)c0 * p.So, v, nc);
           }
         }
       }
