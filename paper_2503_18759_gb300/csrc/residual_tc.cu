@@ -1,9 +1,12 @@
 // Explicit residual ||X - [[lambda; A]]||^2 (Section 4.1's fit without the cancellation of the
 // reduced form) on the tensor cores.
 //
-// X (FP32, C order) is viewed as rows x I_last, rows = prod_{n<N-1} I_n.  The model block of a
-// tile of 128 rows is K = W A_last^T with the Khatri-Rao weights W[row, r] =
-// prod_{n<N-1} A_n[i_n, r] (lambda folded into A_0), a 128 x R by R x I_last product.  It runs
+// X (FP32, C order) is viewed as rows x columns: the columns run over the trailing nt modes, the
+// rows over the others (nt = 1 unless the last side is below 128: then trailing modes are folded
+// into the columns until they reach 128, so that the weights of a tile serve enough columns).  The
+// model block of a tile of 128 rows is K = W B^T with the Khatri-Rao weights W[row, r] =
+// prod_{row modes n} A_n[i_n, r] (lambda folded into A_0) and B[c, r] = prod_{column modes n}
+// A_n[i_n, r], a 128 x R by R x columns product.  It runs
 // as tcgen05 kind::tf32 MMAs with FP32 accumulation in tensor memory, each operand split into a
 // TF32 high part and a TF32 remainder, both rounded to nearest: W A^T ~ Wh Ah^T + Wh Al^T +
 // Wl Ah^T, relative error ~2^-21 per product, of either sign, against ~1e-3 residuals.  The residual (x - k)^2 is summed in FP32 per 32 columns
@@ -36,12 +39,15 @@ constexpr int RT_XBOX = RT_M * 128;      // 128 rows x 32 FP32 columns
 constexpr int RT_WBYTES = RT_M * 128;    // 128 rows x 32 FP32 weights, one of hi / lo
 constexpr int RT_MAXW = 256;             // columns per CTA: one accumulator
 constexpr int RT_TMEM_COLS = 2 * RT_MAXW;
+constexpr int RT_FOLD = 128;             // a last side below this takes the modes before it into the columns
 
 struct RtParams {
   int N, R;
   int d[CPQR_MAXN];
   const float* A[CPQR_MAXN];  // FP32 factors, lambda folded into A[0]; A[N-1] stored transposed (R x I_last)
-  int rows;                   // prod_{n<N-1} d[n] (< 2^31)
+  int nt;                     // trailing modes folded into the columns (1 .. N - 1)
+  int Ic;                     // columns: prod_{n >= N - nt} d[n]
+  int rows;                   // prod_{n < N - nt} d[n] (< 2^31)
   int rtiles;                 // ceil(rows / 128)
   int cpg;                    // CTAs per column group
   int gw;                     // columns per group (multiple of 4); the last group may be narrower
@@ -102,7 +108,7 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
   const uint32_t sB = smem_u32(gB), sW = smem_u32(gW), sX = smem_u32(gX);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int Il = p.d[p.N - 1];
+  const int Il = p.Ic;
   const int cg = blockIdx.x / p.cpg, kq = blockIdx.x % p.cpg;
   const int c0 = cg * p.gw;
   if (c0 >= Il) {  // padding CTA of a clustered launch: no column group, a zero partial
@@ -133,18 +139,32 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
   }
   if (warp == 1) tmem_alloc(smem_u32(&tail->tmem_base), RT_TMEM_COLS);
 
-  // B operand: row c of the group = A_last[c0 + c, 0..31] (zero past the group or past R)
+  // B operand: row c of the group = prod over the column modes of A_n[i_n, 0..31] for column
+  // c0 + c (zero past the group or past R; A_last is stored transposed)
   {
+    const int Ilast = p.d[p.N - 1];
     const float* AlT = p.A[p.N - 1];
     for (int e = threadIdx.x; e < p.ncp * 8; e += RT_THREADS) {
       const int c = e >> 3, q = e & 7;
+      float v4[4] = {0.f, 0.f, 0.f, 0.f};
+      if (c < width) {
+        const int col = c0 + c;
+        int x = col / Ilast;
+        const int il = col - x * Ilast;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v4[j] = (4 * q + j < p.R) ? AlT[(int64_t)(4 * q + j) * Ilast + il] : 0.f;
+        for (int n = p.N - 2; n >= p.N - p.nt; --n) {
+          const int qd = x / p.d[n];
+          const float* an = p.A[n] + (int64_t)(x - qd * p.d[n]) * p.R;
+          x = qd;
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (4 * q + j < p.R) v4[j] *= an[4 * q + j];
+        }
+      }
       float h[4], l[4];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int r = 4 * q + j;
-        const float v = (c < width && r < p.R) ? AlT[(int64_t)r * Il + c0 + c] : 0.f;
-        split_tf32(v, h[j], l[j]);
-      }
+      for (int j = 0; j < 4; ++j) split_tf32(v4[j], h[j], l[j]);
       *reinterpret_cast<float4*>(gB + sw128(c, q)) = make_float4(h[0], h[1], h[2], h[3]);
       *reinterpret_cast<float4*>(gB + bbytes + sw128(c, q)) = make_float4(l[0], l[1], l[2], l[3]);
     }
@@ -231,7 +251,7 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
       for (int r = 0; r < 32; ++r) w[r] = (row < p.rows && r < p.R) ? 1.f : 0.f;
       if (row < p.rows) {
         int x = row;
-        for (int n = p.N - 2; n >= 0; --n) {
+        for (int n = p.N - 1 - p.nt; n >= 0; --n) {
           int in = x;
           if (n > 0) {
             const int qd = x / p.d[n];
@@ -369,13 +389,22 @@ cudaError_t launch_residual_tc(const float* X, int N, const int64_t* d, const fl
   RtParams p{};
   p.N = N;
   p.R = R;
-  int64_t rows = 1;
   for (int n = 0; n < N; ++n) {
     p.d[n] = (int)d[n];
     p.A[n] = Af[n];
-    if (n < N - 1) rows *= d[n];
   }
-  const int Il = (int)d[N - 1];
+  // columns: the last mode, with the modes before it folded in while the columns are fewer than
+  // RT_FOLD (a short last side leaves the weights and the hand-offs of a tile serving few bytes of
+  // X; 128 columns, 64 KB a tile, already keep a CTA's share of the bandwidth busy, and folding
+  // them would leave fewer row tiles than CTAs per column group)
+  int nt = 1;
+  int64_t Ic = d[N - 1];
+  while (Ic < RT_FOLD && nt < N - 1 && Ic * d[N - 1 - nt] <= (int64_t(1) << 30)) Ic *= d[N - 1 - nt++];
+  int64_t rows = 1;
+  for (int n = 0; n < N - nt; ++n) rows *= d[n];
+  const int Il = (int)Ic;
+  p.nt = nt;
+  p.Ic = Il;
   p.rows = (int)rows;
   p.rtiles = (int)((rows + RT_M - 1) / RT_M);
   const int ncg = (Il + RT_MAXW - 1) / RT_MAXW;

@@ -330,11 +330,15 @@ def test_fit_exact_matches_dense_residual(dtype):
     assert abs(fits[-1] - ref) <= 1e-8
 
 
-@pytest.mark.parametrize("dims,R", [([37, 29, 36], 6), ([20, 30, 260], 8), ([36, 33, 40, 64], 32)])
+@pytest.mark.parametrize("dims,R", [([37, 29, 36], 6), ([20, 30, 260], 8), ([36, 33, 40, 64], 32),
+                                    ([6, 5, 7, 4, 8], 4), ([3, 4, 8], 3), ([150, 130, 128], 16)])
 def test_fit_exact_tensor_core_residual(dims, R):
-    """FP32 tensors whose last dimension is a multiple of 4 take the tensor-core residual (3xTF32):
-    ragged row tiles (37 * 29 = 1073 rows), a masked column tail (36 of 64 MMA columns), two
-    column groups (I_last = 260), order 4 with R = 32.  Fit against the oracle's dense residual."""
+    """FP32 tensors whose last dimension is a multiple of 4 take the tensor-core residual (3xTF32).
+    A last side below 128 takes the modes before it into the columns: 29 x 36 = 1044 columns in
+    five ragged groups over one ragged row tile, 40 x 64 at order 4 with R = 32, three modes
+    folded (7 x 4 x 8) at order 5, every mode but the first folded (4 x 8, three rows); unfolded:
+    two column groups (I_last = 260), and 128 columns over 150 x 130 rows.  Fit against the
+    oracle's dense residual."""
     prob = inputs.make_problem("fxtc", dims, R, seed=13, c=0.5, eta=2e-3, dtype=np.float32)
     X = _dev(prob.X)
     opts = b.make_options(tree=b.TREE_RESTRUCTURED, prec=b.PREC_FP64, extrap=b.EXTRAP_NONE)
