@@ -35,8 +35,8 @@ WORKLOAD = "cube400_r32_c09"
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture of the current kernels
 # on this workload (the same launch shapes through bench.py --kernel); None where a kernel changed
 # after its capture
-TTM_TC_TRAFFIC = 270.8e6    # ttm_tc_kernel<0>, 1 x 400 x 160000 -> R = 32 (256.1 MB read + 14.6 MB written)
-TTM_DEEP_TRAFFIC = 20.6e6   # ttm_tc_kernel<1>, 12800 x 400 x 1 -> R = 32 (20.6 MB read, output left in L2)
+TTM_TC_TRAFFIC = 270.4e6    # ttm_tc_kernel<0, 0, 32>, 1 x 400 x 160000 -> R = 32 (256.1 MB read + 14.3 MB written)
+TTM_DEEP_TRAFFIC = 20.6e6   # ttm_tc_kernel<1, 0, 32>, 12800 x 400 x 1 -> R = 32 (20.6 MB read, output left in L2)
 # whole-GPU FP64 DFMA rate measured by a probe on the GB300s (TFLOP/s)
 FP64_PEAK_TFLOPS = 1.20
 
@@ -172,9 +172,14 @@ def run_ours(args, rank, world, local_rank):
 
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if args.profile_range:
+        torch.cuda.profiler.start()
     e0.record()
     fits = dec.sweep(args.steps)
     e1.record()
+    if args.profile_range:
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
     barrier()
     ms = e0.elapsed_time(e1) / max(args.steps, 1)
     launches = dec.stats().launches - launches0
@@ -661,6 +666,8 @@ def main():
                     help="dimension tree of the extra workloads (the bench line is always restructured)")
     ap.add_argument("--kernel", default=None, help="time one library kernel instead (see run_kernel)")
     ap.add_argument("--shape", nargs="*", default=[], help="sizes of the --kernel case")
+    ap.add_argument("--profile-range", action="store_true",
+                    help="bracket the timed sweeps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     args = ap.parse_args()
     if args.kernel:
         print(json.dumps(run_kernel(args)))
