@@ -203,8 +203,18 @@ cpqr_status cp_als_qr_run_host(int32_t N, const int64_t* dims, int32_t R, const 
                                double* const* A_out_host, double* lambda_out_host,
                                double* final_fit, int32_t* sweeps_done, void* stream);
 
-/* Release every device allocation of ctx (NULL is ignored). */
+/* Release every device allocation of ctx (NULL is ignored).  The blocks go to a process-wide
+ * cache, keyed by device and size, from which the next context of the same shape takes them
+ * without cudaMalloc; at most a quarter of a device's memory stays cached (see
+ * cpqr_release_cached_memory). */
 void cp_als_qr_destroy(cpqr_ctx* ctx);
+
+/* Not from the paper: runtime memory management.  Frees every device and pinned host block that
+ * destroyed contexts left in the library's cache (cp_als_qr_destroy, cp_als_qr_run_host).  Call
+ * it when the memory is wanted elsewhere, and before cudaDeviceReset (blocks that a reset made
+ * invalid are otherwise detected and dropped when next requested).  Thread-safe; no context may
+ * be in use on another thread while it runs.  Returns CPQR_ECUDA if a free failed. */
+cpqr_status cpqr_release_cached_memory(void);
 
 /* Static string for a status code. */
 const char* cp_als_qr_strerror(int32_t status);

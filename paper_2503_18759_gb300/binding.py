@@ -74,6 +74,7 @@ def lib() -> C.CDLL:
     L.cp_als_qr_set_timing.argtypes = [vp, i32]
     L.cp_als_qr_destroy.argtypes = [vp]
     L.cp_als_qr_destroy.restype = None
+    L.cpqr_release_cached_memory.argtypes = []
     L.cp_als_qr_strerror.argtypes = [i32]
     L.cp_als_qr_strerror.restype = C.c_char_p
     L.cp_als_qr_schedule.argtypes = [i32, P(i64), i32, i32, i32, P(i32), i64, P(i64), P(i64)]
@@ -123,6 +124,11 @@ def _dptr(a: np.ndarray):
 
 def cp_als_qr_strerror(status: int) -> str:
     return lib().cp_als_qr_strerror(int(status)).decode()
+
+
+def cpqr_release_cached_memory() -> None:
+    """Free the device and pinned blocks that destroyed contexts left in the library's cache."""
+    _check(lib().cpqr_release_cached_memory(), "cpqr_release_cached_memory")
 
 
 def cp_als_qr_default_options() -> Options:

@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcpqr.so")
 
 SOURCES = ["api.cu", "ttm.cu", "ttm_tc.cu", "ttm_tc_wide.cu", "residual_tc.cu", "smallqr.cu", "krp_gram.cu", "mlp.cu", "noalloc.cu",
-           "wide.cu", "schedule.cpp"]
+           "wide.cu", "schedule.cpp", "memcache.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-I", os.path.join(ROOT, "include"), "-I", CSRC]

@@ -35,7 +35,8 @@ struct DeviceBuf {
   size_t bytes = 0;
 };
 
-// Caching pool for tree nodes: blocks are kept by size and reused.
+// Caching pool for tree nodes: blocks are kept by size and reused; at release they go back to
+// the process-wide cache.
 class Pool {
  public:
   ~Pool() { release(); }
@@ -46,20 +47,20 @@ class Pool {
       free_.erase(it);
       return cudaSuccess;
     }
-    cudaError_t e = cudaMalloc(out, bytes);
-    if (e == cudaSuccess) all_.push_back(*out);
+    cudaError_t e = cache_malloc(out, bytes);
+    if (e == cudaSuccess) all_.emplace_back(*out, bytes);
     return e;
   }
   void put(size_t bytes, void* p) { free_.emplace(bytes, p); }
   void release() {
-    for (void* p : all_) cudaFree(p);
+    for (auto& b : all_) cache_free(b.first, b.second);
     all_.clear();
     free_.clear();
   }
 
  private:
   std::multimap<size_t, void*> free_;
-  std::vector<void*> all_;
+  std::vector<std::pair<void*, size_t>> all_;
 };
 
 struct NodeBuf {
@@ -138,7 +139,7 @@ struct cpqr_ctx {
   int64_t nX = 0;
   cpqr_status err = CPQR_OK;
 
-  std::vector<void*> owned;  // cudaMalloc'd, freed at destroy
+  std::vector<std::pair<void*, size_t>> owned;  // from the block cache, returned at destroy
   void* arena = nullptr;     // every per-mode state array (factors, QRs, Q0 history, staging)
   size_t arena_bytes = 0;
   Checkpoint ckpt[3];        // 0: caller's slot, 1 and 2: the two branches of a judged proposal
@@ -246,22 +247,23 @@ struct cpqr_ctx {
     if (ev_fit) cudaEventDestroy(ev_fit);
     if (st3) cudaStreamDestroy(st3);
     for (Checkpoint& c : ckpt)
-      if (c.arena) cudaFree(c.arena);
+      if (c.arena) cache_free(c.arena, arena_bytes);
     if (ev_ready) cudaEventDestroy(ev_ready);
     if (ev_z) cudaEventDestroy(ev_z);
     if (ev_gram) cudaEventDestroy(ev_gram);
     if (st2) cudaStreamDestroy(st2);
     pool.release();
-    for (void* p : owned) cudaFree(p);
-    if (h_pinned) cudaFreeHost(h_pinned);
+    for (auto& b : owned) cache_free(b.first, b.second);
+    if (h_pinned) cache_free_host(h_pinned, 8 * sizeof(double));
   }
 
   template <typename T>
   cudaError_t alloc(T** p, size_t count) {
     void* q = nullptr;
-    cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+    const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    cudaError_t e = cache_malloc(&q, bytes);
     if (e == cudaSuccess) {
-      owned.push_back(q);
+      owned.emplace_back(q, bytes);
       *p = static_cast<T*>(q);
     }
     return e;
@@ -550,7 +552,7 @@ void sweep_orphans(cpqr_ctx* ctx) {
 
 cpqr_status checkpoint_save(cpqr_ctx* ctx, int slot) {
   Checkpoint& c = ctx->ckpt[slot];
-  if (!c.arena) CK(cudaMalloc(&c.arena, ctx->arena_bytes));
+  if (!c.arena) CK(cache_malloc(&c.arena, ctx->arena_bytes));
   CK(cudaMemcpyAsync(c.arena, ctx->arena, ctx->arena_bytes, cudaMemcpyDeviceToDevice, ctx->st));
   if (c.valid) {  // re-saving: previously pinned nodes may become free
     c.valid = false;
@@ -1320,7 +1322,7 @@ cpqr_status cp_als_qr_init(cpqr_ctx** out, int32_t N, const int64_t* dims, int32
   const int64_t M0 = ipow(R, N - 1);
   int64_t Imax = 0;
   for (int n = 0; n < N; ++n) Imax = std::max(Imax, dims[n]);
-  CK(cudaMallocHost(&ctx->h_pinned, 8 * sizeof(double)));
+  CK(cache_malloc_host((void**)&ctx->h_pinned, 8 * sizeof(double)));
   // Per-mode state lives in one arena so that a checkpoint is a single copy.
   const bool split = opt.prec == CPQR_PREC_SPLIT_BF16;
   ctx->Rp = ((R + 15) / 16) * 16;
@@ -1349,8 +1351,8 @@ cpqr_status cp_als_qr_init(cpqr_ctx** out, int32_t N, const int64_t* dims, int32
     const bool learned = opt.extrap == CPQR_EXTRAP_LEARNED && opt.mlp_weights;
     size_t oM = learned ? take(sizeof(MlpState)) : 0;
     ctx->arena_bytes = off;
-    CK(cudaMalloc(&ctx->arena, off));
-    ctx->owned.push_back(ctx->arena);
+    CK(cache_malloc(&ctx->arena, off));
+    ctx->owned.emplace_back(ctx->arena, off);
     CK(cudaMemsetAsync(ctx->arena, 0, off, st));
     char* a = static_cast<char*>(ctx->arena);
     for (int n = 0; n < N; ++n) {
@@ -1445,10 +1447,12 @@ cpqr_status cp_als_qr_init(cpqr_ctx** out, int32_t N, const int64_t* dims, int32
     CK(cudaStreamSynchronize(st));  // the perm vectors go out of scope
   }
 
-  // Starting factors (Alg. 2 "Initialize") and their QRs.
-  std::vector<double> host;
+  // Starting factors (Alg. 2 "Initialize") and their QRs, issued back to back (one host copy of
+  // each factor, alive until the synchronisation after the loop).
+  std::vector<std::vector<double>> hosts(N);
   uint64_t seed = opt.seed;
   for (int n = 0; n < N; ++n) {
+    std::vector<double>& host = hosts[n];
     host.resize(dims[n] * R);
     if (A0_host && A0_host[n]) {
       std::memcpy(host.data(), A0_host[n], host.size() * sizeof(double));
@@ -1461,6 +1465,9 @@ cpqr_status cp_als_qr_init(cpqr_ctx** out, int32_t N, const int64_t* dims, int32
         host[i] = std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
       }
     }
+  }
+  for (int n = 0; n < N; ++n) {
+    const std::vector<double>& host = hosts[n];
     CK(cudaMemcpyAsync(ctx->A[n], host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, st));
     if (ctx->wide) {
       CK(launch_wide_qr(ctx->A[n], dims[n], R, nullptr, 0, ctx->Q[n], ctx->Qf[n], ctx->Rf[n], ctx->wq_main,
@@ -1470,8 +1477,8 @@ cpqr_status cp_als_qr_init(cpqr_ctx** out, int32_t N, const int64_t* dims, int32
       CK(launch_to_f32(ctx->Q[n], ctx->Qf[n], dims[n] * R, st));
       CK(launch_tri_gram(ctx->Rf[n], R, ctx->Gf[n], ctx->cn[n], st));
     }
-    CK(cudaStreamSynchronize(st));
   }
+  CK(cudaStreamSynchronize(st));
   // Split-precision staging.
   if (ctx->prec == CPQR_PREC_SPLIT_BF16) {
     for (int n = 0; n < N; ++n) {
@@ -1781,7 +1788,7 @@ cpqr_status cp_als_qr_run_host(int32_t N, const int64_t* dims, int32_t R, const 
   const size_t bytes = (size_t)n * (x_is_fp64 ? 8 : 4);
   cudaStream_t st = (cudaStream_t)stream;
   void* X = nullptr;
-  if (cudaMalloc(&X, bytes) != cudaSuccess) return CPQR_ENOMEM;
+  if (cache_malloc(&X, bytes) != cudaSuccess) return CPQR_ENOMEM;
   cpqr_status s = CPQR_OK;
   if (cudaMemcpyAsync(X, X_host, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) s = CPQR_ECUDA;
   cpqr_ctx* ctx = nullptr;
@@ -1794,7 +1801,8 @@ cpqr_status cp_als_qr_run_host(int32_t N, const int64_t* dims, int32_t R, const 
     if (s == CPQR_OK) s = fs;
   }
   cp_als_qr_destroy(ctx);
-  cudaFree(X);
+  cudaStreamSynchronize(st);  // a failed set-up may leave the copy running
+  cache_free(X, bytes);
   return s;
 }
 

@@ -17,6 +17,13 @@
 
 namespace cpqr {
 
+// Device and pinned host blocks from the process-wide cache (memcache.cpp): a freed block is kept
+// for the next request of the same size on the same device.
+cudaError_t cache_malloc(void** p, size_t bytes);
+void cache_free(void* p, size_t bytes);
+cudaError_t cache_malloc_host(void** p, size_t bytes);
+void cache_free_host(void* p, size_t bytes);
+
 // Library status of a device status word: a timed-out wait first (its results are partial), then
 // a zero pivot or norm, then a non-finite value.
 inline cpqr_status status_of_device_word(unsigned int w) {

@@ -363,6 +363,39 @@ __global__ void norm2_kernel(const TX* __restrict__ X, int64_t n, double* __rest
   if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
+// ||X||^2 of an FP32 tensor off the FP64 pipe (GB300 runs FP64 at 1/64 of FP32; one DFMA per
+// element held the FP64 version at ~1 TB/s).  Each square is kept exactly as a float pair
+// (p = x * x rounded, e = fma(x, x, -p) its error), and the pairs of a thread are summed in
+// float-float (two-sum for the high part, the errors added into the low part) over runs of 16
+// elements, whose sum then goes into an FP64 accumulator: the float-float error of a run is at
+// most ~16 * 2^-48 of it.  Round-to-nearest intrinsics keep the compiler from contracting the
+// error-free steps.
+__global__ void norm2_f32_kernel(const float* __restrict__ X, int64_t n, double* __restrict__ part) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  float hi = 0.f, lo = 0.f;
+  int run = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const float x = X[i];
+    const float p = __fmul_rn(x, x);
+    const float e = fmaf(x, x, -p);
+    const float s = __fadd_rn(hi, p);
+    const float bb = __fsub_rn(s, hi);
+    const float t = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(t, e));
+    if (++run == 16) {
+      acc += (double)hi + (double)lo;
+      hi = lo = 0.f;
+      run = 0;
+    }
+  }
+  acc += (double)hi + (double)lo;
+  double tt = block_sum(acc, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = tt;
+}
+
 // Sum of the block partials in a fixed order (the same ||X||^2 in every context).
 __global__ void sum_parts_kernel(const double* __restrict__ part, int np, double* __restrict__ out) {
   __shared__ double sh[32];
@@ -725,7 +758,8 @@ template <typename TX>
 cudaError_t launch_norm2(const TX* X, int64_t n, double* out, double* work, cudaStream_t st) {
   if (!work) return cudaErrorInvalidValue;
   const int g = grid_for(n, 256 * 16);  // <= norm2_work_doubles()
-  norm2_kernel<TX><<<g, 256, 0, st>>>(X, n, work);
+  if constexpr (std::is_same<TX, float>::value) norm2_f32_kernel<<<g, 256, 0, st>>>(X, n, work);
+  else norm2_kernel<TX><<<g, 256, 0, st>>>(X, n, work);
   sum_parts_kernel<<<1, 256, 0, st>>>(work, g, out);
   return cudaGetLastError();
 }
