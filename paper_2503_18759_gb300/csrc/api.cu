@@ -1466,18 +1466,33 @@ cpqr_status cp_als_qr_init(cpqr_ctx** out, int32_t N, const int64_t* dims, int32
       }
     }
   }
+  // The narrow path's QRs are independent 16-CTA cluster kernels: the modes go round-robin over
+  // the three streams, each stream with Householder scratch of its own.
+  cudaStream_t qs[3] = {st, ctx->st2, ctx->st3};
+  double* qw[3] = {ctx->qr_work, nullptr, nullptr};
+  if (!ctx->wide) {
+    for (int k = 1; k < 3 && k < N; ++k) CK(ctx->alloc(&qw[k], (size_t)std::max<int64_t>(M0, Imax) * R));
+    // after everything already queued on st (the arena's and the status word's clearing)
+    CK(cudaEventRecord(ctx->ev_ready, st));
+    CK(cudaStreamWaitEvent(ctx->st2, ctx->ev_ready, 0));
+    CK(cudaStreamWaitEvent(ctx->st3, ctx->ev_ready, 0));
+  }
   for (int n = 0; n < N; ++n) {
     const std::vector<double>& host = hosts[n];
-    CK(cudaMemcpyAsync(ctx->A[n], host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, st));
     if (ctx->wide) {
+      CK(cudaMemcpyAsync(ctx->A[n], host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, st));
       CK(launch_wide_qr(ctx->A[n], dims[n], R, nullptr, 0, ctx->Q[n], ctx->Qf[n], ctx->Rf[n], ctx->wq_main,
                         ctx->dstatus, st));
     } else {
-      CK(launch_house_qr(ctx->A[n], dims[n], R, ctx->Q[n], ctx->Rf[n], ctx->qr_work, ctx->dstatus, st));
-      CK(launch_to_f32(ctx->Q[n], ctx->Qf[n], dims[n] * R, st));
-      CK(launch_tri_gram(ctx->Rf[n], R, ctx->Gf[n], ctx->cn[n], st));
+      cudaStream_t s = qs[n % 3];
+      CK(cudaMemcpyAsync(ctx->A[n], host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+      CK(launch_house_qr(ctx->A[n], dims[n], R, ctx->Q[n], ctx->Rf[n], qw[n % 3], ctx->dstatus, s));
+      CK(launch_to_f32(ctx->Q[n], ctx->Qf[n], dims[n] * R, s));
+      CK(launch_tri_gram(ctx->Rf[n], R, ctx->Gf[n], ctx->cn[n], s));
     }
   }
+  CK(cudaStreamSynchronize(ctx->st2));
+  CK(cudaStreamSynchronize(ctx->st3));
   CK(cudaStreamSynchronize(st));
   // Split-precision staging.
   if (ctx->prec == CPQR_PREC_SPLIT_BF16) {
