@@ -12,11 +12,23 @@
 #include <stdexcept>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/cpqr.h"
 #include "common.cuh"
 #include "schedule.h"
 
 using namespace cpqr;
+
+// NVTX ranges on the host timeline of a sweep (cpqr:sweep, cpqr:ttm, cpqr:krp_qr, cpqr:update,
+// cpqr:residual): a profiler selects the kernels launched inside one, e.g. ncu --nvtx
+// --nvtx-include "cpqr:sweep/".  Without a tool attached they cost a call into a no-op.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 namespace {
 
@@ -385,6 +397,7 @@ void split_views(void* base, int64_t n, bool f32, SplitLayout lay, __nv_bfloat16
 }
 
 cpqr_status run_ttm(cpqr_ctx* ctx, const Op& op) {
+  NvtxRange nvtx_range("cpqr:ttm");
   const int dst = op.a, src = op.b, k = op.c;
   auto it = ctx->nodes.find(src);
   if (it == ctx->nodes.end()) return fail(ctx, CPQR_EINVAL);
@@ -699,6 +712,7 @@ bool split_ready(const cpqr_ctx* ctx, int n) {
 // formed for n, only the level with the last update's triangle is left (split route), and the W
 // of the update after n (`after`, -1 if none in this sweep) is started.
 cpqr_status launch_z(cpqr_ctx* ctx, int n, int after) {
+  NvtxRange nvtx_range("cpqr:krp_qr");
   TriPtrs tri{};
   int m = 0, s = -1;
   for (int k = 0; k < ctx->N; ++k)
@@ -757,6 +771,7 @@ cpqr_status launch_z(cpqr_ctx* ctx, int n, int after) {
 cpqr_status launch_lagged_residual(cpqr_ctx* ctx);
 
 cpqr_status run_update(cpqr_ctx* ctx, int n, int leaf, double beta, int next_mode) {
+  NvtxRange nvtx_range("cpqr:update");
   auto it = ctx->nodes.find(leaf);
   if (it == ctx->nodes.end()) return fail(ctx, CPQR_EINVAL);
   const NodeBuf lb = it->second;
@@ -889,6 +904,7 @@ bool can_lag(const cpqr_ctx* ctx) {
 // snapshot), leaving one GPC free for the cluster kernels of the chain; its value goes to
 // h_pinned[4].
 cpqr_status launch_lagged_residual(cpqr_ctx* ctx) {
+  NvtxRange nvtx_range("cpqr:residual");
   CK(cudaStreamWaitEvent(ctx->st3, ctx->ev_prep, 0));
   {
     Timed tm(ctx, CPQR_BUCKET_FIT, 1, ctx->st3);
@@ -1035,6 +1051,7 @@ void observe_fit(cpqr_ctx* ctx, double fit) {
 // allow_lag: a forced beta that may still have its fit read one sweep late (the learned
 // proposer's unjudged sweeps)
 cpqr_status one_sweep(cpqr_ctx* ctx, double* fit_out, const double* forced_beta = nullptr, bool allow_lag = false) {
+  NvtxRange nvtx_range("cpqr:sweep");
   const double beta = forced_beta ? *forced_beta : beta_for_sweep(ctx);
   const bool lag = (!forced_beta || allow_lag) && can_lag(ctx);
   if (!lag) {
