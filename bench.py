@@ -278,6 +278,8 @@ def run_ours(args, rank, world, local_rank):
                "gpu_launches": int(launches),
                "fit_last": float(fits[-1]) if len(fits) else None,
                "qr_guard": _guard(st, args)}
+    if args.metrics_jsonl and rank == 0:
+        dec.write_history_jsonl(args.metrics_jsonl, workload=wname, ms_per_sweep_timed_avg=ms)
     dec.close()
     if rank == 0 and not args.quick and wname == WORKLOAD:
         out.update(extras(args, prob, X, dev, b))
@@ -672,6 +674,8 @@ def main():
                     help="dimension tree of the extra workloads (the bench line is always restructured)")
     ap.add_argument("--kernel", default=None, help="time one library kernel instead (see run_kernel)")
     ap.add_argument("--shape", nargs="*", default=[], help="sizes of the --kernel case")
+    ap.add_argument("--metrics-jsonl", default=None,
+                    help="append one JSON line per sweep of the bench context (fit, beta) to this file")
     ap.add_argument("--profile-range", action="store_true",
                     help="bracket the timed sweeps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     args = ap.parse_args()

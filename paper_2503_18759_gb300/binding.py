@@ -313,6 +313,17 @@ def cp_als_qr_history(ctx, cap: int = 100000):
     return fits[:m], betas[:m], rb.value, bool(act.value)
 
 
+def history_jsonl_lines(fits, betas, **extra) -> List[str]:
+    """Per-sweep metrics as JSON lines: {"sweep": k (1-based), "fit": ..., "beta": ..., **extra}."""
+    import json
+    out = []
+    for k, (f, bt) in enumerate(zip(fits, betas)):
+        rec = {"sweep": k + 1, "fit": float(f), "beta": float(bt)}
+        rec.update(extra)
+        out.append(json.dumps(rec))
+    return out
+
+
 def cp_als_qr_destroy(ctx) -> None:
     if ctx:
         lib().cp_als_qr_destroy(ctx)
@@ -398,6 +409,16 @@ class Decomposition:
 
     def history(self):
         return cp_als_qr_history(self.ctx)
+
+    def write_history_jsonl(self, path: str, **extra) -> int:
+        """Append one JSON line per sweep done (fit, beta, and the extra keys) to path; returns
+        the number of lines."""
+        fits, betas, _, _ = self.history()
+        lines = history_jsonl_lines(fits, betas, **extra)
+        with open(path, "a") as fh:
+            for ln in lines:
+                fh.write(ln + "\n")
+        return len(lines)
 
     def close(self):
         if self.ctx:

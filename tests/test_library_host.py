@@ -63,3 +63,25 @@ def test_schedule_identical_to_oracle(L, tree, dims, R):
     for _ in range(sweeps):
         s.next_sweep()
     assert flops == s.flops
+
+
+def test_history_jsonl_lines_round_trip():
+    """Per-sweep metrics lines: one JSON object per sweep, 1-based sweep index, the extra keys on
+    every line, values that read back exactly."""
+    import json
+    fits = np.array([0.5, 0.75, 0.875])
+    betas = np.array([0.0, 0.004, 0.004])
+    lines = b.history_jsonl_lines(fits, betas, workload="w", ms_per_sweep_timed_avg=0.25)
+    assert len(lines) == 3
+    recs = [json.loads(ln) for ln in lines]
+    assert [r["sweep"] for r in recs] == [1, 2, 3]
+    assert [r["fit"] for r in recs] == list(fits)
+    assert [r["beta"] for r in recs] == list(betas)
+    assert all(r["workload"] == "w" and r["ms_per_sweep_timed_avg"] == 0.25 for r in recs)
+    assert b.history_jsonl_lines([], []) == []
+
+
+def test_release_cached_memory_without_a_gpu(L):
+    """Releasing the block cache succeeds; with nothing cached (as on a machine without a GPU) it
+    frees nothing."""
+    assert L.cpqr_release_cached_memory() == b.OK
