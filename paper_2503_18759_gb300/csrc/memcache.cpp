@@ -42,13 +42,14 @@ Cache& cache() {
 
 constexpr size_t kHostCacheMax = 64;  // pinned blocks kept (each a few bytes)
 
-bool still_device_memory(void* p) {
+// p is still a live device allocation of device d
+bool still_device_memory(void* p, int d) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice;
+  return a.type == cudaMemoryTypeDevice && a.device == d;
 }
 
 }  // namespace
@@ -66,7 +67,7 @@ cudaError_t cache_malloc(void** p, size_t bytes) {
       void* q = it->second;
       c.dev.erase(it);
       c.dev_bytes[d] -= bytes;
-      if (still_device_memory(q)) {
+      if (still_device_memory(q, d)) {
         *p = q;
         return cudaSuccess;
       }
@@ -84,20 +85,23 @@ cudaError_t cache_malloc(void** p, size_t bytes) {
 
 void cache_free(void* p, size_t bytes) {
   if (!p) return;
-  int d = 0;
-  if (cudaGetDevice(&d) != cudaSuccess) {
+  // the block's own device (the current one may have changed since it was allocated)
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess || a.type != cudaMemoryTypeDevice) {
+    cudaGetLastError();
     cudaFree(p);
     return;
   }
+  const int d = a.device;
   Cache& c = cache();
   std::lock_guard<std::mutex> g(c.mu);
   auto cap = c.dev_cap.find(d);
   if (cap == c.dev_cap.end()) {
-    size_t fr = 0, tot = 0;
-    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
-      cudaGetLastError();
-      tot = 0;
-    }
+    // total memory of device d, read without making it current
+    size_t tot = 0;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, d) == cudaSuccess) tot = prop.totalGlobalMem;
+    else cudaGetLastError();
     cap = c.dev_cap.emplace(d, tot / 4).first;
   }
   if (c.dev_bytes[d] + bytes > cap->second) {
