@@ -193,6 +193,7 @@ struct TcParams {
   __nv_bfloat16* out_hi;  // optional split copy of out (hi + lo = out to ~2^-16)
   __nv_bfloat16* out_lo;
   int64_t oh_last, oh_ld;  // the split copy's rows: last dimension padded to oh_ld (0: dense)
+  int pair_ok;             // out 8-byte and out_hi / out_lo 4-byte aligned: column pairs stored together
   unsigned int* status;
   unsigned long long wait_ns;  // limit of the pipeline waits (drain waits keep kTimeoutNs)
   int skip_x_loads;            // failure-detection test: issue no tile loads, so the MMA wait runs out
@@ -464,7 +465,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         __syncwarp();
         const int64_t p0 = tile * 128 + warp * 32;  // this warp's rows, contiguous in out
         const int nrows = (int)std::min<int64_t>(32, p.P - p0);
-        if (!(PO && p.oh_ld) && (p.R & 1) == 0) {
+        if (!(PO && p.oh_ld) && (p.R & 1) == 0 && p.pair_ok) {
           // dense rows of even R: a lane stores a pair of adjacent columns (float2, bf16x2)
           const int half = p.R >> 1;
           const int dq = 32 / half, dc = 32 - dq * half;
@@ -646,6 +647,7 @@ cudaError_t launch_ttm_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo, co
   prm.out_lo = out_lo;
   prm.oh_last = out_lay.ld ? out_lay.last : 0;
   prm.oh_ld = out_lay.ld;
+  prm.pair_ok = ((uintptr_t)out & 7) == 0 && ((uintptr_t)out_hi & 3) == 0 && ((uintptr_t)out_lo & 3) == 0;
   prm.status = dev_status;
   prm.wait_ns = wait_ns ? wait_ns : tc::kTimeoutNs;
   prm.skip_x_loads = skip_x_loads;

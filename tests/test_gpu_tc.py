@@ -47,6 +47,25 @@ def test_ttm_split_bf16_tensor_cores(P, K, S, R):
     assert err < 2e-4, err
 
 
+@pytest.mark.parametrize("P,K,S,R", [(300, 64, 1, 32), (130, 48, 1, 16), (5, 72, 40, 24)])
+def test_ttm_output_at_an_odd_word_offset(P, K, S, R):
+    """An output pointer that is 4 but not 8-byte aligned (a view into a larger buffer): the
+    K-major epilogue then stores single columns instead of column pairs; results as the oracle."""
+    g = np.random.default_rng(P + K + S + R)
+    X = g.standard_normal((P, K, S)).astype(np.float32)
+    Q, _ = np.linalg.qr(g.standard_normal((K, R)))
+    ref = o.ttm_qt(X.astype(np.float64), Q, 1)
+    Xd = torch.from_numpy(X).to(DEV)
+    Qd = torch.from_numpy(np.ascontiguousarray(Q)).to(DEV)
+    buf = torch.full((ref.size + 1,), float("nan"), dtype=torch.float32, device=DEV)
+    assert buf.data_ptr() % 8 == 0
+    b.cpqr_ttm(Xd.data_ptr(), [P, K, S], 1, Qd.data_ptr(), R, buf.data_ptr() + 4, b.TTM_SPLIT_BF16)
+    torch.cuda.synchronize()
+    got = buf[1:].cpu().numpy().astype(np.float64).reshape(ref.shape)
+    assert np.isfinite(got).all() and np.isnan(buf[0].item())
+    assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < 2e-4
+
+
 @pytest.mark.parametrize("P,K,S", [(4096, 400, 1), (1, 400, 4096), (2048, 512, 1)])
 def test_split_ttm_has_no_systematic_bias(P, K, S):
     """Positive X and Q (entries in [0.5, 1.5]), so every output is a sum of K positive terms: the
