@@ -369,7 +369,9 @@ __global__ void norm2_kernel(const TX* __restrict__ X, int64_t n, double* __rest
 // float-float (two-sum for the high part, the errors added into the low part) over runs of 16
 // elements, whose sum then goes into an FP64 accumulator: the float-float error of a run is at
 // most ~16 * 2^-48 of it.  Round-to-nearest intrinsics keep the compiler from contracting the
-// error-free steps.
+// error-free steps.  Values whose square (or a run of 16 squares) would leave FP32's normal range
+// (|x| >= 1e18, or 0 < |x| < 1e-15, where the product's error term would be subnormal), NaN and
+// Inf, are squared in FP64 instead.
 __global__ void norm2_f32_kernel(const float* __restrict__ X, int64_t n, double* __restrict__ part) {
   __shared__ double sh[32];
   double acc = 0.0;
@@ -378,6 +380,11 @@ __global__ void norm2_f32_kernel(const float* __restrict__ X, int64_t n, double*
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const float x = X[i];
+    const float ax = fabsf(x);
+    if (!(ax < 1e18f && (ax >= 1e-15f || x == 0.f))) {
+      acc += (double)x * (double)x;
+      continue;
+    }
     const float p = __fmul_rn(x, x);
     const float e = fmaf(x, x, -p);
     const float s = __fadd_rn(hi, p);
